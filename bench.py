@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Throughput of the batched anonymized-network-sensing path on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic
+windows: pack + sort + run-length reduction to per-window DCSR matrices, the
+nine quantities of every window, and the time sum of all windows of the batch
+(its DCSR and quantities).  The default workload is the 64-window batch
+(64 x 2^17 packets, src Zipf(1.1)/2^20, dst Zipf(1.3)/2^22, 5% bursts).
+
+Prints ONE JSON line (rank 0).  Fields beyond the base contract:
+  per_window   the same work as 64 separate ans_build_window calls + one
+               ans_sum_windows (the plain one-window-per-launch method)
+  roofline     dominant kernel: algorithmic bytes per launch / mean launch
+               time (CUDA events on the launching stream, inside the timed
+               region) against the measured HBM copy bandwidth
+  path_roofline  the whole step's algorithmic bytes / step time
+  cpu_baseline the CPU oracle timed on this host on a bounded sample
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): independent replicas, one batch of distinct windows per
+rank, barrier + max-over-ranks timing, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "packets/s (batched hot path: per-window DCSR + 9 quantities + time sum)"
+UNIT = "packets/s"
+FLUSH_BYTES = 512 << 20  # > 129 MB L2
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    2: "64 windows x 2^17 packets (8.4M pairs); src Zipf(1.1)/2^20, dst Zipf(1.3)/2^22, 5% bursts of 2..100; "
+       "per-window DCSR + 9 quantities + 64-window time sum",
+    3: "1024 windows, P loguniform [2^10, 2^20]; heavy hitter 10%, scanners, rest Zipf(1.1)/2^24; "
+       "per-window DCSR + 9 quantities + time sum",
+    4: "2^13 windows x 2^17 (2^30 pairs); src, dst Zipf(1.05) over 2^32; per-window DCSR + quantities + time sum",
+}
+DEFAULT_NWIN = {2: 64, 3: 1024, 4: 8192}
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_onesweep launch on
+# the 64-window batch (profiles/onesweep_cfg2.md); None until captured for the
+# current kernel.
+ONESWEEP_NCU_TRAFFIC = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS))
+    ap.add_argument("--nwin", type=int, default=None, help="override the number of windows per step")
+    ap.add_argument("--impl", default="ans", choices=["ans", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-window", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(sizes, quants, sum_q):
+    """Sec. 8(d) bytes of one step: read pairs, write DCSR + quantities per
+    window, write the time-summed DCSR + quantities."""
+    b = 0
+    for p, q in zip(sizes, quants):
+        b += 8 * int(p) + 12 * q["unique_links"] + 12 * q["unique_sources"] + 8 + 72
+    if sum_q is not None:
+        b += 12 * sum_q["unique_links"] + 12 * sum_q["unique_sources"] + 8 + 72
+    return b
+
+
+def oracle_step(w):
+    import oracle
+    oracle.batch(w.src, w.dst, w.offsets, want_sum=True)
+
+
+def time_oracle(w, budget_s=12.0):
+    """Run the oracle over windows of `w` until ~budget_s has elapsed (at
+    least one window); return (packets/s, windows used)."""
+    import oracle
+    t0 = time.perf_counter()
+    mats, pk, n = [], 0, 0
+    for i in range(w.nwin):
+        s, d = w.window(i)
+        m = oracle.traffic_matrix(s, d)
+        oracle.network_quantities(m)
+        mats.append(m)
+        pk += len(s)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    oracle.network_quantities(oracle.sum_matrices(mats))
+    dt = time.perf_counter() - t0
+    return pk / dt, n, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2510_14050_gb300 import synth
+    nwin = args.nwin or DEFAULT_NWIN[args.config]
+    sample = max(1, min(nwin, 8))
+    w = synth.generate(args.config, nwin=sample)
+    for _ in range(args.warmup):
+        oracle_step(w.subset(0, 1))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(w)
+    dt = time.perf_counter() - t0
+    value = w.total * args.steps / dt
+    sample_desc = f"first {sample} of {nwin} windows ({w.total} packets) + their time sum, per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_2510_14050_gb300 import ans, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cfg = args.config
+    nwin = args.nwin or DEFAULT_NWIN[cfg]
+    w = synth.generate(cfg, nwin=nwin, first_window=rank * nwin)
+    total = w.total
+    sizes = np.diff(w.offsets)
+
+    ctx = ans.Context(local)
+    stream = torch.cuda.current_stream()
+    src_h = torch.from_numpy(w.src.view(np.int32)).pin_memory()
+    dst_h = torch.from_numpy(w.dst.view(np.int32)).pin_memory()
+    src_d = src_h.cuda()
+    dst_d = dst_h.cuda()
+    q_dev = torch.zeros((nwin, 9), dtype=torch.int64, device="cuda")
+    q_host = torch.zeros((nwin, 9), dtype=torch.int64).pin_memory()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flags = ans.BATCH_MATRICES | ans.BATCH_SUM
+
+    def step(s, d):
+        mats, summ, _ = ctx.batch_submit(s, d, w.offsets, flags, out=q_dev, want_ticket=False)
+        return mats, summ
+
+    def release(res):
+        mats, summ = res
+        for m in mats:
+            m.free()
+        summ.free()
+
+    for _ in range(max(args.warmup, 0)):
+        res = step(src_d, dst_d)
+        torch.cuda.synchronize()
+        release(res)
+    quants = ans.quantities_from_tensor(q_dev)
+    res = step(src_d, dst_d)
+    torch.cuda.synchronize()
+    sum_q = res[1].quantities()
+    release(res)
+    alg_bytes = algorithmic_bytes(sizes, quants, sum_q)
+
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ctx.profile(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    keep = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        keep.append(step(src_d, dst_d))
+        evs[i][1].record(stream)
+    barrier()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    for r in keep:
+        release(r)
+    keep = []
+    t_ms = max_over_ranks(sum(step_ms))
+    value = total * args.steps * world / (t_ms / 1e3)
+
+    # ---- dominant kernel and roofline
+    peak, peak_kind = hbm_peak()
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    launches = sum(n for n, _ in prof.values())
+    roof = None
+    if dom is not None:
+        name, (n_l, ms_l) = dom
+        mean_ms = ms_l / n_l
+        if name == "onesweep":
+            per_launch = 16 * total        # read + write every key of the batch once
+            unit_desc = "16 B per packet per digit pass"
+        else:
+            per_launch = alg_bytes
+            unit_desc = "whole-step algorithmic bytes"
+        ach = per_launch / (mean_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": ONESWEEP_NCU_TRAFFIC if name == "onesweep" else None,
+                "kernel": name, "mean_launch_ms": round(mean_ms, 5), "bytes_per_launch": per_launch,
+                "bytes_rule": unit_desc, "peak_kind": f"of {peak_kind}"}
+    path_gbs = alg_bytes * args.steps / (t_ms / 1e3) / 1e9
+    kernel_share = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4) for k, v in prof.items()}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        src_e = torch.empty_like(src_d)
+        dst_e = torch.empty_like(dst_d)
+        for _ in range(2):
+            src_e.copy_(src_h, non_blocking=True)
+            dst_e.copy_(dst_h, non_blocking=True)
+            r = step(src_e, dst_e)
+            q_host.copy_(q_dev, non_blocking=True)
+            torch.cuda.synchronize()
+            release(r)
+        barrier()
+        evs2 = []
+        keep = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            src_e.copy_(src_h, non_blocking=True)
+            dst_e.copy_(dst_h, non_blocking=True)
+            keep.append(step(src_e, dst_e))
+            q_host.copy_(q_dev, non_blocking=True)
+            b.record(stream)
+            evs2.append((a, b))
+        barrier()
+        e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs2))
+        for r in keep:
+            release(r)
+        e2e = {"value": total * args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 72 * nwin}
+
+    # ---- the plain per-window method on the same GPU
+    per_window = None
+    if not args.no_per_window:
+        k2 = max(1, min(args.steps, 3))
+
+        def pw_step():
+            mats = []
+            for i in range(nwin):
+                a, b = int(w.offsets[i]), int(w.offsets[i + 1])
+                mats.append(ctx.build_window(src_d[a:], dst_d[a:], b - a))
+            return mats, ctx.sum_windows(mats)
+
+        release(pw_step())
+        torch.cuda.synchronize()
+        barrier()
+        evs3, keep = [], []
+        for i in range(k2):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            keep.append(pw_step())
+            b.record(stream)
+            evs3.append((a, b))
+        barrier()
+        pw_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs3))
+        for r in keep:
+            release(r)
+        per_window = {"value": total * k2 * world / (pw_ms / 1e3), "unit": UNIT, "steps": k2,
+                      "ms_per_step": pw_ms / k2, "launches": f"{nwin} x ans_build_window + ans_sum_windows"}
+
+    # ---- CPU oracle baseline (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n_used, dt = time_oracle(w)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n_used} of {nwin} windows + their time sum ({dt:.1f} s, numpy, 1 thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[cfg], "windows": nwin, "packets_per_step": total,
+                       "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "path_roofline": {"achieved": round(path_gbs, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(path_gbs / peak, 4), "bytes_per_step": alg_bytes},
+            "per_window": per_window,
+            "batched_over_per_window": (value / per_window["value"]) if per_window else None,
+            "kernel_time_share": kernel_share, "clocks": clk, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

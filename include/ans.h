@@ -1,0 +1,180 @@
+/*
+ * ans.h -- C ABI of the GB300 anonymized-network-sensing library (libans.so).
+ *
+ * The library turns windows of anonymized (src, dst) uint32 packet pairs into
+ * hypersparse 2^32 x 2^32 traffic matrices stored as DCSR, sums windows over
+ * time, and reduces matrices to the Graph Challenge network quantities.  Every
+ * result is an exact integer.
+ *
+ * Definitions (paper: Table I, Sec. IV-B, Sec. IV-C):
+ *   A(i, j)  = number of packets from source i to destination j in a window
+ *              (Table I caption; rows are sources, columns destinations).
+ *   DCSR     = nonempty rows ascending (row_ids), row_ptr = exclusive prefix of
+ *              per-row nonzero counts (the paper's "degrees", Sec. IV-B), column
+ *              ids ascending within a row ("edges"), uint64 values ("weights").
+ *   time sum = (sum_t A_t)(i, j) = sum_t A_t(i, j)  (Table I: A_t at time t).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: ANS_OK (0) or a negative ANS_ERR_* code.  ans_last_error()
+ *     gives a human-readable detail for the calling thread.
+ *   - Pointers prefixed d_ are device pointers on the context's device;
+ *     h_ are host pointers.  Inputs are borrowed: they must stay valid and
+ *     unmodified until the work of the call has completed on its stream.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are stream-ordered and asynchronous unless a comment says otherwise.
+ *     Calls that share one context must be ordered (one stream, or the caller
+ *     orders them): the context's scratch memory is reused from call to call.
+ *   - Matrices are owned by the caller once returned and released with
+ *     ans_matrix_free().  A matrix keeps its memory alive independently of
+ *     the context's scratch.
+ *   - Every packet is valid (the paper does not say what makes a packet
+ *     invalid), so a window's valid-packet count is its length.  Addresses 0
+ *     and 0xFFFFFFFF are ordinary.  Self-links (src == dst) are ordinary
+ *     diagonal entries.  Quantities of an empty matrix are all 0.
+ *   - Limits: a window holds at most 2^31 - 1 packets; a time sum combines at
+ *     most 2^31 - 1 stored links per call.
+ */
+#ifndef ANS_H
+#define ANS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define ANS_OK               0
+#define ANS_ERR_INVALID_ARG (-1)  /* bad pointer, size or flag */
+#define ANS_ERR_BUDGET      (-2)  /* the call would exceed the context's memory budget */
+#define ANS_ERR_OOM         (-3)  /* the allocator failed */
+#define ANS_ERR_CUDA        (-4)  /* a CUDA runtime call failed */
+#define ANS_ERR_TIMEOUT     (-5)  /* ans_wait ran out of time, or a bounded device wait gave up */
+#define ANS_ERR_INTERNAL    (-6)  /* a device-side consistency check failed */
+
+/* Flags of ans_batch_submit. */
+#define ANS_BATCH_MATRICES   0x1u /* return one DCSR matrix per window in per_window[] */
+#define ANS_BATCH_SUM        0x2u /* return the time sum of all windows in *sum */
+#define ANS_BATCH_SYNC       0x4u /* block until the batch has completed */
+
+typedef struct ans_ctx ans_ctx;       /* opaque: device, allocator, budget, scratch */
+typedef struct ans_matrix ans_matrix; /* opaque: one DCSR matrix in device memory */
+typedef uint64_t ans_ticket;          /* completion handle of an asynchronous batch */
+
+/* The nine network quantities of one matrix, in this order (Table I rows and
+ * the maxima of Sec. IV-C).  Fan-out/fan-in are the largest per-row/per-column
+ * nonzero counts (Table I's C++ column: max of the per-row degrees). */
+typedef struct {
+    uint64_t valid_packets;           /* sum_ij A(i,j) */
+    uint64_t unique_links;            /* #{(i,j) : A(i,j) > 0} */
+    uint64_t max_link_packets;        /* max_ij A(i,j) */
+    uint64_t unique_sources;          /* #{i : row i nonempty} */
+    uint64_t max_source_packets;      /* max_i sum_j A(i,j) */
+    uint64_t max_source_fanout;       /* max_i #{j : A(i,j) > 0} */
+    uint64_t unique_destinations;     /* #{j : column j nonempty} */
+    uint64_t max_destination_packets; /* max_j sum_i A(i,j) */
+    uint64_t max_destination_fanin;   /* max_j #{i : A(i,j) > 0} */
+} ans_quantities;
+
+/* Device allocator hooks.  alloc returns NULL on failure; both receive the
+ * stream the memory is used on and the `user` pointer given at creation. */
+typedef void* (*ans_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*ans_free_fn)(void* ptr, void* stream, void* user);
+
+/* Create a context on CUDA device `device`.
+ * mem_budget_bytes: ceiling on the device memory the context holds at once
+ *   (scratch plus live matrices); 0 = no ceiling.  A call that would exceed it
+ *   fails with ANS_ERR_BUDGET and leaves no work queued.
+ * alloc/free: both NULL selects cudaMallocAsync/cudaFreeAsync; otherwise both
+ *   must be given.  Errors: ANS_ERR_INVALID_ARG, ANS_ERR_CUDA. */
+int ans_ctx_create(ans_ctx** out, int device, size_t mem_budget_bytes,
+                   ans_alloc_fn alloc, ans_free_fn free_fn, void* user);
+
+/* Wait for the context's outstanding work and release its scratch.  Matrices
+ * created from it must be freed before the context is destroyed. */
+int ans_ctx_destroy(ans_ctx* ctx);
+
+/* Traffic matrix of one window (Table I caption): A(i,j) = #{k : d_src[k] == i,
+ * d_dst[k] == j} for k < n, as DCSR with uint64 counts.  d_src/d_dst: device
+ * arrays of n uint32 (any alignment).  n == 0 gives an empty matrix.  The
+ * matrix's quantities are computed in the same pass and are returned by
+ * ans_matrix_quantities() without further device work.
+ * Errors: ANS_ERR_INVALID_ARG (NULL pointers with n > 0, n >= 2^31),
+ * ANS_ERR_BUDGET, ANS_ERR_OOM, ANS_ERR_CUDA. */
+int ans_build_window(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
+                     ans_matrix** out, void* stream);
+
+/* Time sum of k matrices (Table I: A_t indexed by t): (sum_t A_t)(i,j) =
+ * sum_t A_t(i,j), as a new DCSR matrix.  The inputs are only read; they may
+ * come from different calls on the same device.  k == 0 gives an empty matrix.
+ * Errors: ANS_ERR_INVALID_ARG, ANS_ERR_BUDGET, ANS_ERR_OOM, ANS_ERR_CUDA. */
+int ans_sum_windows(ans_ctx* ctx, const ans_matrix* const* mats, size_t k, ans_matrix** out,
+                    void* stream);
+
+/* The nine quantities of a matrix (Table I, Sec. IV-C), recomputed on the
+ * device from its DCSR arrays: row statistics by segmented reductions over
+ * rows, column statistics by a transpose-free hash pass over the stored links.
+ * out: host or device pointer to one ans_quantities.  With a device pointer
+ * (or pinned host memory) the call is asynchronous; with pageable host memory
+ * it returns once the result has been written. */
+int ans_network_quantities(ans_ctx* ctx, const ans_matrix* m, ans_quantities* out, void* stream);
+
+/* Batched analysis of nwin windows stored back to back (Sec. III-C batching,
+ * taken to its limit: every window of the batch in one fixed launch sequence).
+ *   d_src, d_dst : device arrays holding h_offsets[nwin] packets.
+ *   h_offsets    : HOST array of nwin + 1 nondecreasing offsets, h_offsets[0]
+ *                  may be nonzero; window w is [h_offsets[w], h_offsets[w+1]).
+ *   flags        : ANS_BATCH_* bits.
+ *   out          : nwin ans_quantities (host or device memory; pageable host
+ *                  memory makes the call blocking).  May be NULL.
+ *   per_window   : with ANS_BATCH_MATRICES, receives nwin matrices.
+ *   sum          : with ANS_BATCH_SUM, receives the time sum of all windows.
+ *   ticket       : optional; ans_wait(ctx, *ticket, ...) waits for the batch.
+ * Results equal those of one ans_build_window per window followed by
+ * ans_sum_windows.  Errors: ANS_ERR_INVALID_ARG, ANS_ERR_BUDGET, ANS_ERR_OOM,
+ * ANS_ERR_CUDA. */
+int ans_batch_submit(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst,
+                     const uint64_t* h_offsets, size_t nwin, uint32_t flags, ans_quantities* out,
+                     ans_matrix** per_window, ans_matrix** sum, ans_ticket* ticket, void* stream);
+
+/* Wait (bounded) for a batch.  timeout_ns == 0 polls once.  Returns ANS_OK,
+ * ANS_ERR_TIMEOUT (still running), ANS_ERR_INTERNAL (a bounded device wait or
+ * a hash probe gave up inside the batch: its results are not valid) or
+ * ANS_ERR_INVALID_ARG (unknown ticket). */
+int ans_wait(ans_ctx* ctx, ans_ticket ticket, uint64_t timeout_ns);
+
+/* Host-side view of a matrix: counts and device pointers to its arrays
+ * (row_ids[nrows], row_ptr[nrows + 1], col_ids[nnz], vals[nnz]).  Blocks
+ * until the matrix has been computed.  Any output pointer may be NULL. */
+int ans_matrix_view(const ans_matrix* m, uint64_t* nrows, uint64_t* nnz, const uint32_t** row_ids,
+                    const uint64_t** row_ptr, const uint32_t** col_ids, const uint64_t** vals);
+
+/* Quantities computed while the matrix was built (host copy; blocks until
+ * the matrix is complete). */
+int ans_matrix_quantities(const ans_matrix* m, ans_quantities* out);
+
+/* Release a matrix (waits for the work that produces it).  NULL is a no-op. */
+int ans_matrix_free(ans_matrix* m);
+
+/* Diagnostics: per-kernel timing.  While enabled, every kernel launch of the
+ * context is bracketed by CUDA events on its launching stream (the paper
+ * reports wall-clock analysis time, Sec. V-A; this splits it by kernel).
+ * ans_profile_enable clears the accumulated data.  ans_profile_read waits for
+ * the recorded launches, then writes one line per kernel name,
+ * "<name> <launches> <total milliseconds>\n", NUL-terminated and truncated to
+ * buflen; *needed (optional) receives the full length including the NUL. */
+int ans_profile_enable(ans_ctx* ctx, int enable);
+int ans_profile_read(ans_ctx* ctx, char* buf, size_t buflen, size_t* needed);
+
+/* Static description of a status code. */
+const char* ans_status_string(int status);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char* ans_last_error(ans_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANS_H */

@@ -1,0 +1,312 @@
+"""ctypes binding of ``include/ans.h`` (libans.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  PyTorch supplies device memory (tensors) and
+streams.  If libans.so cannot be loaded the import of this module fails; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Sequence
+
+import numpy as np
+
+from . import buildlib
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_BUDGET = -2
+ERR_OOM = -3
+ERR_CUDA = -4
+ERR_TIMEOUT = -5
+ERR_INTERNAL = -6
+
+BATCH_MATRICES = 0x1
+BATCH_SUM = 0x2
+BATCH_SYNC = 0x4
+
+QUANTITY_NAMES = (
+    "valid_packets",
+    "unique_links",
+    "max_link_packets",
+    "unique_sources",
+    "max_source_packets",
+    "max_source_fanout",
+    "unique_destinations",
+    "max_destination_packets",
+    "max_destination_fanin",
+)
+
+# Every symbol the header declares.
+EXPORTS = (
+    "ans_ctx_create", "ans_ctx_destroy", "ans_build_window", "ans_sum_windows", "ans_network_quantities",
+    "ans_batch_submit", "ans_wait", "ans_matrix_view", "ans_matrix_quantities", "ans_matrix_free",
+    "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
+)
+
+
+class Quantities(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in QUANTITY_NAMES]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n in QUANTITY_NAMES}
+
+
+class AnsError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str):
+        super().__init__(f"{what}: {detail or status_string(code)} (status {code})")
+        self.code = code
+
+
+_lib = None
+_vp = C.c_void_p
+_u64 = C.c_uint64
+
+
+def load(path: str | os.PathLike | None = None):
+    """Load libans.so (building it in-tree first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = buildlib.LIBANS if buildlib.LIBANS.exists() else buildlib.build_ans()
+    lib = C.CDLL(str(path))
+    P = C.POINTER
+    sig = {
+        "ans_ctx_create": ([P(_vp), C.c_int, C.c_size_t, _vp, _vp, _vp], C.c_int),
+        "ans_ctx_destroy": ([_vp], C.c_int),
+        "ans_build_window": ([_vp, _vp, _vp, _u64, P(_vp), _vp], C.c_int),
+        "ans_sum_windows": ([_vp, P(_vp), C.c_size_t, P(_vp), _vp], C.c_int),
+        "ans_network_quantities": ([_vp, _vp, _vp, _vp], C.c_int),
+        "ans_batch_submit": ([_vp, _vp, _vp, P(_u64), C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp), P(_u64), _vp],
+                             C.c_int),
+        "ans_wait": ([_vp, _u64, _u64], C.c_int),
+        "ans_matrix_view": ([_vp, P(_u64), P(_u64), P(_vp), P(_vp), P(_vp), P(_vp)], C.c_int),
+        "ans_matrix_quantities": ([_vp, P(Quantities)], C.c_int),
+        "ans_matrix_free": ([_vp], C.c_int),
+        "ans_status_string": ([C.c_int], C.c_char_p),
+        "ans_last_error": ([_vp], C.c_char_p),
+        "ans_profile_enable": ([_vp, C.c_int], C.c_int),
+        "ans_profile_read": ([_vp, C.c_char_p, C.c_size_t, P(C.c_size_t)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().ans_status_string(code).decode()
+
+
+def _check(rc: int, what: str, ctx=None):
+    if rc != OK:
+        detail = load().ans_last_error(ctx).decode()
+        raise AnsError(rc, what, detail)
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    if x.device.type != "cuda":
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+class _DevView:
+    """Wrap a raw device pointer for torch.as_tensor (CUDA array interface)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True), "version": 3}
+
+
+def _download(ptr: int, n: int, np_dtype) -> np.ndarray:
+    import torch
+    np_dtype = np.dtype(np_dtype)
+    if n == 0:
+        return np.zeros(0, np_dtype)
+    ts = "<i4" if np_dtype.itemsize == 4 else "<i8"
+    t = torch.as_tensor(_DevView(ptr, n, ts), device="cuda")
+    return t.cpu().numpy().view(np_dtype)
+
+
+def _device_tensor(ptr: int, n: int, itemsize: int):
+    import torch
+    ts = "<i4" if itemsize == 4 else "<i8"
+    if n == 0:
+        return torch.zeros(0, dtype=torch.int32 if itemsize == 4 else torch.int64, device="cuda")
+    return torch.as_tensor(_DevView(ptr, n, ts), device="cuda")
+
+
+class Matrix:
+    """A DCSR traffic matrix in device memory (owned; freed by ``free()``)."""
+
+    def __init__(self, handle: int):
+        self._h = _vp(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def view(self):
+        n_r, n_u = _u64(), _u64()
+        p = [_vp() for _ in range(4)]
+        _check(load().ans_matrix_view(self._h, C.byref(n_r), C.byref(n_u), *[C.byref(x) for x in p]), "view")
+        return int(n_r.value), int(n_u.value), [x.value or 0 for x in p]
+
+    @property
+    def nrows(self) -> int:
+        return self.view()[0]
+
+    @property
+    def nnz(self) -> int:
+        return self.view()[1]
+
+    def to_numpy(self):
+        """(row_ids uint32, row_ptr uint64, col_ids uint32, vals uint64) on the host."""
+        nr, nu, (pr, pp, pc, pv) = self.view()
+        return (_download(pr, nr, np.uint32), _download(pp, nr + 1, np.uint64),
+                _download(pc, nu, np.uint32), _download(pv, nu, np.uint64))
+
+    def device_arrays(self):
+        """Zero-copy torch views (int32/int64 reinterpretations) of the four arrays."""
+        nr, nu, (pr, pp, pc, pv) = self.view()
+        return (_device_tensor(pr, nr, 4), _device_tensor(pp, nr + 1, 8),
+                _device_tensor(pc, nu, 4), _device_tensor(pv, nu, 8))
+
+    def quantities(self) -> dict:
+        q = Quantities()
+        _check(load().ans_matrix_quantities(self._h, C.byref(q)), "matrix_quantities")
+        return q.as_dict()
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _check(load().ans_matrix_free(self._h), "matrix_free")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """One ans_ctx: a device, an allocator, a memory budget and scratch."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self._lib = load()
+        h = _vp()
+        _check(self._lib.ans_ctx_create(C.byref(h), int(device), int(budget_bytes), None, None, None), "ctx_create")
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(self._lib.ans_ctx_destroy(self._h), "ctx_destroy")
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points ------------------------------------------------------
+    def build_window(self, src, dst, n: int | None = None, stream=None) -> Matrix:
+        if n is None:
+            n = src.numel()
+        out = _vp()
+        _check(self._lib.ans_build_window(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)), int(n),
+                                          C.byref(out), _vp(_stream(stream))), "build_window", self._h)
+        return Matrix(out.value)
+
+    def sum_windows(self, mats: Sequence[Matrix], stream=None) -> Matrix:
+        arr = (_vp * max(len(mats), 1))(*[m.handle for m in mats])
+        out = _vp()
+        _check(self._lib.ans_sum_windows(self._h, arr, len(mats), C.byref(out), _vp(_stream(stream))),
+               "sum_windows", self._h)
+        return Matrix(out.value)
+
+    def network_quantities(self, m: Matrix, out=None, stream=None) -> dict | None:
+        """Recompute the nine quantities of ``m`` on the device.  With ``out``
+        (a device or pinned uint64 tensor of 9 elements) the call is
+        asynchronous and returns None; otherwise a dict is returned."""
+        if out is not None:
+            _check(self._lib.ans_network_quantities(self._h, m.handle, _vp(out.data_ptr()), _vp(_stream(stream))),
+                   "network_quantities", self._h)
+            return None
+        q = Quantities()
+        _check(self._lib.ans_network_quantities(self._h, m.handle, _vp(C.addressof(q)), _vp(_stream(stream))),
+               "network_quantities", self._h)
+        return q.as_dict()
+
+    def batch_submit(self, src, dst, offsets, flags: int = 0, out=None, stream=None, want_ticket: bool = True):
+        """Analyse windows [offsets[w], offsets[w+1]) of (src, dst).
+
+        ``offsets``: host array-like of nwin + 1 uint64.  ``out``: optional
+        tensor of nwin x 9 int64 (device or pinned host) receiving the
+        quantities.  Returns (per_window matrices or None, sum or None, ticket)."""
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+        nwin = len(offs) - 1
+        per = (_vp * max(nwin, 1))() if flags & BATCH_MATRICES else None
+        sm = _vp() if flags & BATCH_SUM else None
+        tk = _u64() if want_ticket else None
+        outp = _vp(out.data_ptr()) if out is not None else None
+        _check(self._lib.ans_batch_submit(
+            self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)), offs.ctypes.data_as(C.POINTER(_u64)), nwin,
+            int(flags), outp, per, C.byref(sm) if sm is not None else None,
+            C.byref(tk) if tk is not None else None, _vp(_stream(stream))), "batch_submit", self._h)
+        mats = [Matrix(per[i]) for i in range(nwin)] if per is not None else None
+        summ = Matrix(sm.value) if sm is not None else None
+        return mats, summ, (int(tk.value) if tk is not None else None)
+
+    def profile(self, enable: bool = True):
+        _check(self._lib.ans_profile_enable(self._h, 1 if enable else 0), "profile_enable", self._h)
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total ms)} since profiling was enabled."""
+        need = C.c_size_t()
+        _check(self._lib.ans_profile_read(self._h, None, 0, C.byref(need)), "profile_read", self._h)
+        buf = C.create_string_buffer(need.value + 64)
+        _check(self._lib.ans_profile_read(self._h, buf, len(buf), None), "profile_read", self._h)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, n, ms = line.split()
+            out[name] = (int(n), float(ms))
+        return out
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        _check(self._lib.ans_wait(self._h, int(ticket), int(timeout_s * 1e9)), "wait", self._h)
+
+
+def quantities_from_tensor(t) -> list[dict]:
+    """nwin x 9 int64 tensor/array -> list of quantity dicts."""
+    a = t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+    a = a.view(np.uint64).reshape(-1, 9)
+    return [{n: int(v) for n, v in zip(QUANTITY_NAMES, row)} for row in a]

@@ -1,0 +1,1133 @@
+// C ABI of libans.so: contexts, memory budget, scratch, matrices, the batch
+// pipeline and completion tickets.  Host code only; the kernels live in
+// ans_sort.cu and ans_stats.cu.
+//
+// Pipeline of one batch of windows (every window of the batch in one fixed
+// sequence of launches, independent of the number of windows):
+//   pack + digit histograms -> 8 onesweep digit passes -> run-length reduce
+//   to DCSR -> values, row statistics and column-hash inserts -> column scan
+//   [-> time sum: gather links -> histograms -> 8 key/value passes -> value
+//   prefix -> run-length reduce -> statistics -> column scan].
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ans.h"
+#include "ans_internal.cuh"
+
+using namespace ans;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+int fail(int code, const std::string& msg) {
+  t_last_error = msg;
+  return code;
+}
+
+#define ANS_CUDA(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ANS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define ANS_TRY(expr)           \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ != ANS_OK) return rc_; \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr uint64_t kMaxWindow = (1ull << 31) - 1;
+constexpr int kStageSlots = 8;
+constexpr int kErrSlots = 4096;
+
+size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+uint64_t tiles_for(uint64_t n) { return (n + kTile - 1) / kTile; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Two-phase bump layout: add() records sizes, bind() turns offsets into pointers.
+struct Layout {
+  size_t size = 0;
+  size_t add(size_t bytes) {
+    size_t off = size;
+    size = align_up(size + std::max<size_t>(bytes, 1));
+    return off;
+  }
+};
+
+}  // namespace
+
+struct Block;
+
+struct ans_ctx {
+  int device = 0;
+  size_t budget = 0;
+  ans_alloc_fn alloc_fn = nullptr;
+  ans_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  std::mutex mu;
+  size_t live = 0;  // device bytes held: scratch + table + live matrix blocks
+
+  void* scratch = nullptr;
+  size_t scratch_size = 0;
+  // Column hash table (slots and sums), kept all-zero between calls, plus
+  // the device error word.
+  void* table_mem = nullptr;
+  size_t table_slots = 0;
+  uint32_t* d_err = nullptr;
+  void* small_mem = nullptr;
+
+  // Pinned staging ring for plan uploads.
+  struct Stage {
+    void* h = nullptr;
+    size_t size = 0;
+    cudaEvent_t ev = nullptr;
+  } stage[kStageSlots];
+  int stage_next = 0;
+
+  // Completion tickets.
+  uint32_t* h_err_slots = nullptr;  // pinned
+  int err_next = 0;
+  struct Ticket {
+    cudaEvent_t ev;
+    int slot;
+  };
+  std::map<uint64_t, Ticket> tickets;
+  uint64_t next_ticket = 1;
+  cudaStream_t aux = nullptr;  // frees of matrix memory
+
+  // Optional per-kernel timing: CUDA events recorded around each launch on
+  // the launching stream, accumulated by name when read.
+  struct Prof {
+    bool on = false;
+    struct Rec {
+      const char* name;
+      cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> spare;
+    std::map<std::string, std::pair<double, uint64_t>> acc;
+  } prof;
+};
+
+namespace {
+
+cudaEvent_t prof_event(ans_ctx* c) {
+  if (!c->prof.spare.empty()) {
+    cudaEvent_t e = c->prof.spare.back();
+    c->prof.spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Times one kernel launch when profiling is on (records nothing otherwise).
+struct KTime {
+  ans_ctx* c;
+  const char* name;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KTime(ans_ctx* c_, const char* name_, cudaStream_t st_) : c(c_), name(name_), st(st_) {
+    if (!c->prof.on) return;
+    a = prof_event(c);
+    b = prof_event(c);
+    if (a && b) cudaEventRecord(a, st);
+  }
+  ~KTime() {
+    if (!a || !b) return;
+    cudaEventRecord(b, st);
+    c->prof.pending.push_back({name, a, b});
+  }
+};
+
+template <class F>
+cudaError_t timed(ans_ctx* c, const char* name, cudaStream_t st, F&& f) {
+  KTime kt(c, name, st);
+  return f();
+}
+
+void prof_collect(ans_ctx* c) {
+  for (auto& r : c->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      auto& x = c->prof.acc[r.name];
+      x.first += ms;
+      x.second += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->prof.spare.push_back(r.a);
+    c->prof.spare.push_back(r.b);
+  }
+  c->prof.pending.clear();
+}
+
+}  // namespace
+
+// Device memory that holds one or more matrices (one per window of a batch,
+// or a single time sum).
+struct Block {
+  ans_ctx* ctx = nullptr;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  uint32_t nseg = 0;
+  std::vector<uint64_t> base;  // padded start per segment
+  std::vector<uint64_t> cap;   // upper bound on nnz per segment
+  uint32_t* col_ids = nullptr;
+  uint64_t* vals = nullptr;
+  uint32_t* row_ids = nullptr;
+  uint64_t* row_ptr = nullptr;
+  uint64_t* hdr = nullptr;
+  ans_quantities* q = nullptr;
+  uint32_t* status = nullptr;  // device error word captured at completion
+  cudaEvent_t done = nullptr;
+  std::atomic<int> refs{0};
+  std::mutex mu;
+  bool cached = false;
+  std::vector<uint64_t> h_hdr;
+  std::vector<ans_quantities> h_q;
+  uint32_t h_status = 0;
+};
+
+struct ans_matrix {
+  Block* blk;
+  uint32_t seg;
+};
+
+namespace {
+
+int dev_alloc(ans_ctx* c, size_t bytes, cudaStream_t st, void** out) {
+  *out = nullptr;
+  if (bytes == 0) return ANS_OK;
+  if (c->budget && c->live + bytes > c->budget)
+    return fail(ANS_ERR_BUDGET, "memory budget exceeded: holding " + std::to_string(c->live) +
+                                    " bytes, need " + std::to_string(bytes) + " more, budget " +
+                                    std::to_string(c->budget));
+  void* p = nullptr;
+  if (c->alloc_fn) {
+    p = c->alloc_fn(bytes, (void*)st, c->user);
+    if (!p) return fail(ANS_ERR_OOM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ANS_ERR_OOM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " +
+                                   cudaGetErrorString(e));
+    }
+  }
+  c->live += bytes;
+  *out = p;
+  return ANS_OK;
+}
+
+void dev_free(ans_ctx* c, void* p, size_t bytes, cudaStream_t st) {
+  if (!p) return;
+  if (c->free_fn) c->free_fn(p, (void*)st, c->user);
+  else cudaFreeAsync(p, st);
+  c->live -= bytes;
+}
+
+int ensure_scratch(ans_ctx* c, size_t bytes, cudaStream_t st) {
+  if (bytes <= c->scratch_size) return ANS_OK;
+  size_t want = std::max(bytes, c->scratch_size + c->scratch_size / 4);
+  dev_free(c, c->scratch, c->scratch_size, st);
+  c->scratch = nullptr;
+  c->scratch_size = 0;
+  void* p = nullptr;
+  int rc = dev_alloc(c, want, st, &p);
+  if (rc != ANS_OK && want > bytes) rc = dev_alloc(c, bytes, st, &p), want = bytes;
+  if (rc != ANS_OK) return rc;
+  c->scratch = p;
+  c->scratch_size = want;
+  return ANS_OK;
+}
+
+size_t table_bytes(size_t slots) { return slots * 2 * sizeof(unsigned long long); }
+
+int ensure_table(ans_ctx* c, size_t slots, cudaStream_t st) {
+  if (slots <= c->table_slots) return ANS_OK;
+  dev_free(c, c->table_mem, table_bytes(c->table_slots), st);
+  c->table_mem = nullptr;
+  c->table_slots = 0;
+  void* p = nullptr;
+  ANS_TRY(dev_alloc(c, table_bytes(slots), st, &p));
+  ANS_CUDA(cudaMemsetAsync(p, 0, table_bytes(slots), st));
+  c->table_mem = p;
+  c->table_slots = slots;
+  return ANS_OK;
+}
+
+// Copy `bytes` of host data to device `dst` through the pinned ring.
+int upload(ans_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return ANS_OK;
+  ans_ctx::Stage& s = c->stage[c->stage_next];
+  c->stage_next = (c->stage_next + 1) % kStageSlots;
+  ANS_CUDA(cudaEventSynchronize(s.ev));
+  if (s.size < bytes) {
+    if (s.h) ANS_CUDA(cudaFreeHost(s.h));
+    s.h = nullptr;
+    size_t want = std::max<size_t>(align_up(bytes, 1 << 16), 2 * s.size);
+    ANS_CUDA(cudaHostAlloc(&s.h, want, cudaHostAllocDefault));
+    s.size = want;
+  }
+  std::memcpy(s.h, src, bytes);
+  ANS_CUDA(cudaMemcpyAsync(dst, s.h, bytes, cudaMemcpyHostToDevice, st));
+  ANS_CUDA(cudaEventRecord(s.ev, st));
+  return ANS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device layout of a block holding nseg matrices over `pad` padded items.
+struct BlockLayout {
+  size_t col_ids, vals, row_ids, row_ptr, hdr, q, status, total;
+  BlockLayout(uint64_t pad, uint32_t nseg) {
+    Layout L;
+    col_ids = L.add(pad * 4);
+    vals = L.add(pad * 8);
+    row_ids = L.add(pad * 4);
+    row_ptr = L.add((pad + nseg) * 8);
+    hdr = L.add((size_t)nseg * 16);
+    q = L.add((size_t)nseg * sizeof(ans_quantities));
+    status = L.add(8);
+    total = L.size;
+  }
+};
+
+int make_block(ans_ctx* c, uint64_t pad, uint32_t nseg, std::vector<uint64_t> base, std::vector<uint64_t> cap,
+               cudaStream_t st, Block** out) {
+  BlockLayout bl(pad, nseg);
+  void* mem = nullptr;
+  ANS_TRY(dev_alloc(c, bl.total, st, &mem));
+  Block* b = new Block();
+  b->ctx = c;
+  b->mem = mem;
+  b->bytes = bl.total;
+  b->nseg = nseg;
+  b->base = std::move(base);
+  b->cap = std::move(cap);
+  char* m = (char*)mem;
+  b->col_ids = (uint32_t*)(m + bl.col_ids);
+  b->vals = (uint64_t*)(m + bl.vals);
+  b->row_ids = (uint32_t*)(m + bl.row_ids);
+  b->row_ptr = (uint64_t*)(m + bl.row_ptr);
+  b->hdr = (uint64_t*)(m + bl.hdr);
+  b->q = (ans_quantities*)(m + bl.q);
+  b->status = (uint32_t*)(m + bl.status);
+  cudaError_t e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    dev_free(c, mem, bl.total, st);
+    delete b;
+    return fail(ANS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return ANS_OK;
+}
+
+void block_release(Block* b) {
+  if (--b->refs > 0) return;
+  ans_ctx* c = b->ctx;
+  cudaEventSynchronize(b->done);
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    DeviceGuard dg(c->device);
+    dev_free(c, b->mem, b->bytes, c->aux);
+  }
+  cudaEventDestroy(b->done);
+  delete b;
+}
+
+// Discard a block that never left the library (error path).
+void block_discard(Block* b, cudaStream_t st) {
+  if (!b) return;
+  cudaStreamSynchronize(st);
+  dev_free(b->ctx, b->mem, b->bytes, st);
+  cudaEventDestroy(b->done);
+  delete b;
+}
+
+int block_fill_cache(Block* b) {
+  std::lock_guard<std::mutex> g(b->mu);
+  if (b->cached) return ANS_OK;
+  DeviceGuard dg(b->ctx->device);
+  ANS_CUDA(cudaEventSynchronize(b->done));
+  b->h_hdr.resize(2 * (size_t)b->nseg);
+  b->h_q.resize(b->nseg);
+  ANS_CUDA(cudaMemcpy(b->h_hdr.data(), b->hdr, b->h_hdr.size() * 8, cudaMemcpyDeviceToHost));
+  ANS_CUDA(cudaMemcpy(b->h_q.data(), b->q, b->h_q.size() * sizeof(ans_quantities), cudaMemcpyDeviceToHost));
+  ANS_CUDA(cudaMemcpy(&b->h_status, b->status, 4, cudaMemcpyDeviceToHost));
+  b->cached = true;
+  return ANS_OK;
+}
+
+// Everything the statistics phases of one segment set need.
+struct StatsBufs {
+  uint32_t* col_ids;
+  uint64_t* vals;
+  uint32_t* row_ids;
+  uint64_t* row_ptr;
+  uint64_t* hdr;
+  ans_quantities* q;
+};
+
+// Host-side plan of a set of segments.
+struct HostPlan {
+  std::vector<uint64_t> in_off, len, base;
+  std::vector<uint32_t> first_tile;
+  uint64_t pad = 0;   // padded items
+  uint32_t ntiles = 0;
+  void build(const std::vector<uint64_t>& lens, const std::vector<uint64_t>* offs) {
+    const size_t n = lens.size();
+    in_off.assign(n, 0);
+    len = lens;
+    base.resize(n);
+    first_tile.resize(n + 1);
+    uint64_t b = 0, t = 0;
+    for (size_t s = 0; s < n; ++s) {
+      if (offs) in_off[s] = (*offs)[s];
+      base[s] = b;
+      first_tile[s] = (uint32_t)t;
+      const uint64_t k = tiles_for(lens[s]);
+      t += k;
+      b += k * kTile;
+    }
+    first_tile[n] = (uint32_t)t;
+    pad = b;
+    ntiles = (uint32_t)t;
+  }
+};
+
+struct DevPlan {
+  size_t in_off, len, base, first_tile;
+  void reserve(Layout& L, size_t nseg) {
+    in_off = L.add(nseg * 8);
+    len = L.add(nseg * 8);
+    base = L.add(nseg * 8);
+    first_tile = L.add((nseg + 1) * 4);
+  }
+  SegPlan bind(char* m, const HostPlan& hp) const {
+    SegPlan p;
+    p.in_off = (const uint64_t*)(m + in_off);
+    p.len = (const uint64_t*)(m + len);
+    p.base = (const uint64_t*)(m + base);
+    p.first_tile = (const uint32_t*)(m + first_tile);
+    p.nseg = (uint32_t)hp.len.size();
+    p.ntiles = hp.ntiles;
+    return p;
+  }
+};
+
+// Scratch needed by one sort + statistics pipeline over `pad` padded items and
+// `ntiles` tiles.
+struct PipeScratch {
+  size_t keys_a, keys_b, vals_a, vals_b, seg_hist, st0, st1, lb, lb2, tickets, run_start, row_pos, pre;
+  void reserve(Layout& L, uint64_t pad, uint32_t nseg, uint32_t ntiles, bool with_vals) {
+    keys_a = L.add(pad * 8);
+    keys_b = L.add(pad * 8);
+    vals_a = with_vals ? L.add(pad * 8) : 0;
+    vals_b = with_vals ? L.add(pad * 8) : 0;
+    seg_hist = L.add((size_t)nseg * kPasses * kRadix * 4);
+    st0 = L.add((size_t)ntiles * kRadix * 8);
+    st1 = L.add((size_t)ntiles * kRadix * 8);
+    lb = L.add((size_t)ntiles * 8);
+    lb2 = L.add((size_t)ntiles * 8);
+    tickets = L.add(64 * 4);
+    run_start = L.add((pad + nseg) * 8);
+    row_pos = L.add((pad + nseg) * 8);
+    pre = with_vals ? L.add((pad + nseg) * 8) : 0;
+  }
+};
+
+template <typename T>
+T* at(char* m, size_t off) {
+  return reinterpret_cast<T*>(m + off);
+}
+
+// Sort keys (and values) of the segments of `p` in place: 8 stable digit
+// passes ping-ponging between a and b; the result ends in a.
+int sort_segments(ans_ctx* c, const SegPlan& p, uint64_t* ka, uint64_t* kb, uint64_t* va, uint64_t* vb,
+                  const uint32_t* seg_hist, uint64_t* st0, uint64_t* st1, uint32_t* tickets, cudaStream_t st) {
+  for (int pass = 0; pass < kPasses; ++pass) {
+    const bool even = (pass % 2) == 0;
+    KTime kt(c, va ? "onesweep_sum" : "onesweep", st);
+    ANS_CUDA(launch_onesweep(p, pass, even ? ka : kb, even ? kb : ka, va ? (even ? va : vb) : nullptr,
+                             va ? (even ? vb : va) : nullptr, seg_hist, even ? st0 : st1,
+                             even ? st1 : st0, tickets + pass, c->d_err, st));
+  }
+  return ANS_OK;
+}
+
+// Time sum of the matrices described by `mats` (device array of k MatDesc,
+// host capacities `caps`), written into a new block.  Uses scratch laid out
+// by the caller at `m` / `ps` (which must provide vals buffers).
+int sum_pipeline(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k,
+                 const std::vector<uint64_t>& caps, size_t off_gplan, size_t off_splan, size_t off_catoff,
+                 size_t off_lens, size_t off_total, size_t off_q, cudaStream_t st, Block** out_blk) {
+  // gather plan: one segment per matrix, tiles by capacity, lengths from the device
+  HostPlan gp;
+  gp.build(caps, nullptr);
+  uint64_t total_cap = 0;
+  for (uint64_t x : caps) total_cap += x;
+  HostPlan sp;
+  sp.build(std::vector<uint64_t>{total_cap}, nullptr);
+
+  Block* blk = nullptr;
+  ANS_TRY(make_block(c, sp.pad, 1, std::vector<uint64_t>{0}, std::vector<uint64_t>{total_cap}, st, &blk));
+
+  DevPlan gdp{off_gplan, off_gplan + align_up(k * 8), off_gplan + 2 * align_up(k * 8),
+              off_gplan + 3 * align_up(k * 8)};
+  // upload the gather plan (len is overwritten on the device by count_prefix)
+  int rc = ANS_OK;
+  auto up = [&](size_t off, const void* src, size_t bytes) {
+    if (rc == ANS_OK) rc = upload(c, m + off, src, bytes, st);
+  };
+  up(gdp.in_off, gp.in_off.data(), k * 8);
+  up(gdp.base, gp.base.data(), k * 8);
+  up(gdp.first_tile, gp.first_tile.data(), (k + 1) * 4);
+  SegPlan g = gdp.bind(m, gp);
+  g.len = at<uint64_t>(m, off_lens);
+
+  DevPlan sdp{off_splan, off_splan + kAlign, off_splan + 2 * kAlign, off_splan + 3 * kAlign};
+  up(sdp.in_off, sp.in_off.data(), 8);
+  up(sdp.base, sp.base.data(), 8);
+  up(sdp.first_tile, sp.first_tile.data(), 8);
+  if (rc != ANS_OK) {
+    block_discard(blk, st);
+    return rc;
+  }
+  SegPlan s = sdp.bind(m, sp);
+  s.len = at<uint64_t>(m, off_total);
+
+  uint64_t* ka = at<uint64_t>(m, ps.keys_a);
+  uint64_t* kb = at<uint64_t>(m, ps.keys_b);
+  uint64_t* va = at<uint64_t>(m, ps.vals_a);
+  uint64_t* vb = at<uint64_t>(m, ps.vals_b);
+  uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets) + 32;
+
+  auto fail_blk = [&](cudaError_t e, const char* what) {
+    block_discard(blk, st);
+    return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = timed(c, "count_prefix", st, [&] { return launch_count_prefix(d_mats, k, at<uint64_t>(m, off_catoff), at<uint64_t>(m, off_lens),
+                               at<uint64_t>(m, off_total), st); })) != cudaSuccess)
+    return fail_blk(e, "count_prefix");
+  if ((e = timed(c, "gather", st, [&] { return launch_gather(g, d_mats, at<uint64_t>(m, off_catoff), ka, va, st); })) != cudaSuccess)
+    return fail_blk(e, "gather");
+  if ((e = cudaMemsetAsync(seg_hist, 0, kPasses * kRadix * 4, st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = cudaMemsetAsync(m + ps.lb, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = cudaMemsetAsync(m + ps.lb2, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = timed(c, "hist", st, [&] { return launch_hist(s, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); })) != cudaSuccess)
+    return fail_blk(e, "hist");
+  rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
+  if (rc != ANS_OK) {
+    block_discard(blk, st);
+    return rc;
+  }
+  uint64_t* pre = at<uint64_t>(m, ps.pre);
+  if ((e = timed(c, "scan_u64", st, [&] { return launch_scan_u64(s, va, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st); })) !=
+      cudaSuccess)
+    return fail_blk(e, "scan");
+  StatsArgs a;
+  a.plan = s;
+  a.hdr = blk->hdr;
+  a.q = blk->q;
+  a.keys = ka;
+  a.col_ids = blk->col_ids;
+  a.vals = blk->vals;
+  a.row_ids = blk->row_ids;
+  a.row_ptr = blk->row_ptr;
+  a.run_start = at<uint64_t>(m, ps.run_start);
+  a.row_pos = at<uint64_t>(m, ps.row_pos);
+  a.pre = pre;
+  a.lookback = at<uint64_t>(m, ps.lb);
+  a.ticket = tickets + kPasses;
+  a.table = (unsigned long long*)c->table_mem;
+  a.table_sum = a.table + c->table_slots;
+  a.err = c->d_err;
+  a.mode = kModeSum;
+  (void)off_q;
+  if ((e = cudaMemsetAsync(blk->q, 0, sizeof(ans_quantities), st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = timed(c, "rle", st, [&] { return launch_rle(a, st); })) != cudaSuccess) return fail_blk(e, "rle");
+  if ((e = timed(c, "finish", st, [&] { return launch_finish(a, st); })) != cudaSuccess) return fail_blk(e, "finish");
+  if ((e = timed(c, "col_scan", st, [&] { return launch_col_scan(a, st); })) != cudaSuccess) return fail_blk(e, "col_scan");
+  *out_blk = blk;
+  return ANS_OK;
+}
+
+// Snapshot the device error word into `dst` (device); reset_err clears it.
+int capture_err(ans_ctx* c, uint32_t* dst_dev, cudaStream_t st) {
+  ANS_CUDA(cudaMemcpyAsync(dst_dev, c->d_err, 4, cudaMemcpyDeviceToDevice, st));
+  return ANS_OK;
+}
+int reset_err(ans_ctx* c, cudaStream_t st) {
+  ANS_CUDA(cudaMemsetAsync(c->d_err, 0, 4, st));
+  return ANS_OK;
+}
+
+int new_ticket(ans_ctx* c, cudaStream_t st, ans_ticket* out) {
+  ans_ctx::Ticket t;
+  ANS_CUDA(cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming));
+  t.slot = c->err_next;
+  c->err_next = (c->err_next + 1) % kErrSlots;
+  c->h_err_slots[t.slot] = 0;
+  ANS_CUDA(cudaMemcpyAsync(c->h_err_slots + t.slot, c->d_err, 4, cudaMemcpyDeviceToHost, st));
+  ANS_CUDA(cudaEventRecord(t.ev, st));
+  const uint64_t id = c->next_ticket++;
+  c->tickets[id] = t;
+  *out = id;
+  return ANS_OK;
+}
+
+int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n, cudaStream_t st) {
+  if (!out || n == 0) return ANS_OK;
+  ANS_CUDA(cudaMemcpyAsync(out, src, n * sizeof(ans_quantities), cudaMemcpyDefault, st));
+  return ANS_OK;
+}
+
+// The batch pipeline (also serves ans_build_window with nwin == 1).
+int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
+                size_t nwin, uint32_t flags, ans_quantities* out, ans_matrix** per_window, ans_matrix** sum,
+                ans_ticket* ticket, cudaStream_t st) {
+  std::vector<uint64_t> lens(nwin), offs(nwin);
+  for (size_t w = 0; w < nwin; ++w) {
+    if (h_offsets[w + 1] < h_offsets[w]) return fail(ANS_ERR_INVALID_ARG, "offsets must be nondecreasing");
+    lens[w] = h_offsets[w + 1] - h_offsets[w];
+    if (lens[w] > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a window exceeds 2^31 - 1 packets");
+    offs[w] = h_offsets[w];
+  }
+  const uint64_t total = h_offsets[nwin] - h_offsets[0];
+  if (total && (!d_src || !d_dst)) return fail(ANS_ERR_INVALID_ARG, "NULL packet arrays");
+  if (nwin > 0xFFFFFFF0ull) return fail(ANS_ERR_INVALID_ARG, "too many windows");
+  const bool want_mats = (flags & ANS_BATCH_MATRICES) != 0;
+  const bool want_sum = (flags & ANS_BATCH_SUM) != 0;
+  if (want_sum && total > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a time sum is limited to 2^31 - 1 links");
+  const uint32_t nseg = (uint32_t)nwin;
+
+  HostPlan hp;
+  hp.build(lens, &offs);
+  if ((uint64_t)hp.ntiles * kTile != hp.pad) return fail(ANS_ERR_INTERNAL, "plan");
+
+  // ---- scratch layout
+  Layout L;
+  DevPlan dp;
+  dp.reserve(L, nseg);
+  PipeScratch ps;
+  ps.reserve(L, hp.pad, std::max<uint32_t>(nseg, 1), hp.ntiles, want_sum);
+  size_t s_col = 0, s_vals = 0, s_row = 0, s_rp = 0, s_hdr = 0, s_q = 0;
+  if (!want_mats) {
+    s_col = L.add(hp.pad * 4);
+    s_vals = L.add(hp.pad * 8);
+    s_row = L.add(hp.pad * 4);
+    s_rp = L.add((hp.pad + nseg) * 8);
+    s_hdr = L.add((size_t)nseg * 16);
+    s_q = L.add((size_t)nseg * sizeof(ans_quantities));
+  }
+  size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0, off_sq = 0;
+  if (want_sum) {
+    off_mats = L.add((size_t)nseg * sizeof(MatDesc));
+    off_gplan = L.add(4 * align_up((size_t)(nseg + 1) * 8));
+    off_splan = L.add(4 * kAlign);
+    off_catoff = L.add((size_t)nseg * 8);
+    off_lens = L.add((size_t)nseg * 8);
+    off_total = L.add(8);
+    off_sq = L.add(sizeof(ans_quantities));
+  }
+  size_t off_errcap = L.add(8);
+
+  ANS_TRY(ensure_scratch(c, L.size, st));
+  ANS_TRY(ensure_table(c, 2 * std::max<uint64_t>(hp.pad, kTile), st));
+  char* m = (char*)c->scratch;
+
+  Block* blk = nullptr;
+  if (want_mats && nseg > 0) {
+    std::vector<uint64_t> caps(lens);
+    ANS_TRY(make_block(c, hp.pad, nseg, hp.base, caps, st, &blk));
+  }
+  StatsBufs sb;
+  if (blk) {
+    sb = {blk->col_ids, blk->vals, blk->row_ids, blk->row_ptr, blk->hdr, blk->q};
+  } else {
+    sb = {at<uint32_t>(m, s_col), at<uint64_t>(m, s_vals), at<uint32_t>(m, s_row), at<uint64_t>(m, s_rp),
+          at<uint64_t>(m, s_hdr), at<ans_quantities>(m, s_q)};
+  }
+  auto bail = [&](int rc) {
+    block_discard(blk, st);
+    return rc;
+  };
+
+  // ---- plan upload
+  int rc = ANS_OK;
+  if (nseg) {
+    if (rc == ANS_OK) rc = upload(c, m + dp.in_off, hp.in_off.data(), nseg * 8, st);
+    if (rc == ANS_OK) rc = upload(c, m + dp.len, hp.len.data(), nseg * 8, st);
+    if (rc == ANS_OK) rc = upload(c, m + dp.base, hp.base.data(), nseg * 8, st);
+    if (rc == ANS_OK) rc = upload(c, m + dp.first_tile, hp.first_tile.data(), (nseg + 1) * 4, st);
+  }
+  if (rc != ANS_OK) return bail(rc);
+  const SegPlan p = dp.bind(m, hp);
+
+  auto cu = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return ANS_OK;
+    return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  uint64_t* ka = at<uint64_t>(m, ps.keys_a);
+  uint64_t* kb = at<uint64_t>(m, ps.keys_b);
+  uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets);
+  if (nseg) {
+    if ((rc = cu(cudaMemsetAsync(seg_hist, 0, (size_t)nseg * kPasses * kRadix * 4, st), "memset hist"))) return bail(rc);
+    if ((rc = cu(cudaMemsetAsync(sb.q, 0, (size_t)nseg * sizeof(ans_quantities), st), "memset q"))) return bail(rc);
+    if ((rc = cu(cudaMemsetAsync(m + ps.lb, 0, (size_t)hp.ntiles * 8, st), "memset lb"))) return bail(rc);
+    if ((rc = cu(timed(c, "pack_hist", st, [&] { return launch_pack_hist(p, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); }), "pack")))
+      return bail(rc);
+    if ((rc = sort_segments(c, p, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
+                            at<uint64_t>(m, ps.st1), tickets, st)))
+      return bail(rc);
+    StatsArgs a;
+    a.plan = p;
+    a.hdr = sb.hdr;
+    a.q = sb.q;
+    a.keys = ka;
+    a.col_ids = sb.col_ids;
+    a.vals = sb.vals;
+    a.row_ids = sb.row_ids;
+    a.row_ptr = sb.row_ptr;
+    a.run_start = at<uint64_t>(m, ps.run_start);
+    a.row_pos = at<uint64_t>(m, ps.row_pos);
+    a.pre = nullptr;
+    a.lookback = at<uint64_t>(m, ps.lb);
+    a.ticket = tickets + kPasses;
+    a.table = (unsigned long long*)c->table_mem;
+    a.table_sum = a.table + c->table_slots;
+    a.err = c->d_err;
+    a.mode = kModeWindow;
+    if ((rc = cu(timed(c, "empty_fixup", st, [&] { return launch_empty_fixup(a, st); }), "empty"))) return bail(rc);
+    if ((rc = cu(timed(c, "rle", st, [&] { return launch_rle(a, st); }), "rle"))) return bail(rc);
+    if ((rc = cu(timed(c, "finish", st, [&] { return launch_finish(a, st); }), "finish"))) return bail(rc);
+    if ((rc = cu(timed(c, "col_scan", st, [&] { return launch_col_scan(a, st); }), "col_scan"))) return bail(rc);
+  }
+
+  Block* sblk = nullptr;
+  if (want_sum) {
+    std::vector<MatDesc> md(nseg);
+    for (uint32_t s = 0; s < nseg; ++s) {
+      md[s].row_ids = sb.row_ids + hp.base[s];
+      md[s].row_ptr = sb.row_ptr + hp.base[s] + s;
+      md[s].col_ids = sb.col_ids + hp.base[s];
+      md[s].vals = sb.vals + hp.base[s];
+      md[s].hdr = sb.hdr + 2 * (size_t)s;
+    }
+    if (nseg && (rc = upload(c, m + off_mats, md.data(), md.size() * sizeof(MatDesc), st))) return bail(rc);
+    if (nseg == 0) {
+      // an empty batch: an empty sum
+      HostPlan sp;
+      sp.build(std::vector<uint64_t>{0}, nullptr);
+      if ((rc = make_block(c, 0, 1, {0}, {0}, st, &sblk))) return bail(rc);
+      if ((rc = cu(cudaMemsetAsync(sblk->row_ptr, 0, 8, st), "memset"))) return bail(rc);
+      if ((rc = cu(cudaMemsetAsync(sblk->hdr, 0, 16, st), "memset"))) return bail(rc);
+      if ((rc = cu(cudaMemsetAsync(sblk->q, 0, sizeof(ans_quantities), st), "memset"))) return bail(rc);
+    } else {
+      if ((rc = sum_pipeline(c, m, ps, at<MatDesc>(m, off_mats), nseg, lens, off_gplan, off_splan, off_catoff,
+                             off_lens, off_total, off_sq, st, &sblk)))
+        return bail(rc);
+    }
+  }
+
+  // ---- completion
+  if (blk) {
+    if ((rc = capture_err(c, blk->status, st))) return bail(rc);
+  }
+  if (sblk) {
+    if ((rc = capture_err(c, sblk->status, st))) return bail(rc);
+  }
+  (void)off_errcap;
+  if (out) {
+    if ((rc = copy_quantities_out(out, sb.q, nseg, st))) return bail(rc);
+  }
+  if (ticket) {
+    if ((rc = new_ticket(c, st, ticket))) return bail(rc);
+  }
+  if ((rc = reset_err(c, st))) return bail(rc);
+  if (blk) {
+    if ((rc = cu(cudaEventRecord(blk->done, st), "record"))) return bail(rc);
+    blk->refs = (int)nseg;
+    for (uint32_t s = 0; s < nseg; ++s) per_window[s] = new ans_matrix{blk, s};
+  }
+  if (sblk) {
+    ANS_CUDA(cudaEventRecord(sblk->done, st));
+    sblk->refs = 1;
+    *sum = new ans_matrix{sblk, 0};
+  }
+  if (flags & ANS_BATCH_SYNC) ANS_CUDA(cudaStreamSynchronize(st));
+  return ANS_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+const char* ans_status_string(int s) {
+  switch (s) {
+    case ANS_OK: return "ok";
+    case ANS_ERR_INVALID_ARG: return "invalid argument";
+    case ANS_ERR_BUDGET: return "memory budget exceeded";
+    case ANS_ERR_OOM: return "out of device memory";
+    case ANS_ERR_CUDA: return "CUDA error";
+    case ANS_ERR_TIMEOUT: return "timed out";
+    case ANS_ERR_INTERNAL: return "internal error";
+    default: return "unknown status";
+  }
+}
+
+const char* ans_last_error(ans_ctx*) { return t_last_error.c_str(); }
+
+int ans_ctx_create(ans_ctx** out, int device, size_t mem_budget_bytes, ans_alloc_fn alloc, ans_free_fn free_fn,
+                   void* user) {
+  if (!out) return fail(ANS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(ANS_ERR_INVALID_ARG, "give both allocator hooks or neither");
+  int ndev = 0;
+  ANS_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(ANS_ERR_INVALID_ARG, "no such device");
+  DeviceGuard dg(device);
+  ans_ctx* c = new ans_ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  c->alloc_fn = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  auto undo = [&](int rc) {
+    for (auto& s : c->stage)
+      if (s.ev) cudaEventDestroy(s.ev);
+    if (c->h_err_slots) cudaFreeHost(c->h_err_slots);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    delete c;
+    return rc;
+  };
+  for (auto& s : c->stage) {
+    if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess)
+      return undo(fail(ANS_ERR_CUDA, "cudaEventCreate failed"));
+  }
+  if (cudaHostAlloc((void**)&c->h_err_slots, kErrSlots * 4, cudaHostAllocDefault) != cudaSuccess)
+    return undo(fail(ANS_ERR_CUDA, "cudaHostAlloc failed"));
+  std::memset(c->h_err_slots, 0, kErrSlots * 4);
+  if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess)
+    return undo(fail(ANS_ERR_CUDA, "cudaStreamCreate failed"));
+  if (!alloc) {
+    // Keep freed blocks in this process's stream-ordered pool instead of
+    // returning them to the driver at every synchronisation.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
+  void* small = nullptr;
+  int rc = dev_alloc(c, 256, c->aux, &small);
+  if (rc != ANS_OK) return undo(rc);
+  c->small_mem = small;
+  c->d_err = (uint32_t*)small;
+  if (cudaMemsetAsync(small, 0, 256, c->aux) != cudaSuccess || cudaStreamSynchronize(c->aux) != cudaSuccess)
+    return undo(fail(ANS_ERR_CUDA, "initialising the error word failed"));
+  *out = c;
+  return ANS_OK;
+}
+
+int ans_ctx_destroy(ans_ctx* c) {
+  if (!c) return ANS_OK;
+  DeviceGuard dg(c->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : c->tickets) cudaEventDestroy(kv.second.ev);
+  dev_free(c, c->scratch, c->scratch_size, c->aux);
+  dev_free(c, c->table_mem, table_bytes(c->table_slots), c->aux);
+  dev_free(c, c->small_mem, 256, c->aux);
+  cudaStreamSynchronize(c->aux);
+  for (auto& s : c->stage) {
+    if (s.h) cudaFreeHost(s.h);
+    if (s.ev) cudaEventDestroy(s.ev);
+  }
+  if (c->h_err_slots) cudaFreeHost(c->h_err_slots);
+  cudaStreamDestroy(c->aux);
+  delete c;
+  return ANS_OK;
+}
+
+int ans_build_window(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, ans_matrix** out,
+                     void* stream) {
+  if (!c || !out) return fail(ANS_ERR_INVALID_ARG, "NULL context or output");
+  if (n > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a window is limited to 2^31 - 1 packets");
+  *out = nullptr;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  const uint64_t offs[2] = {0, n};
+  return run_windows(c, d_src, d_dst, offs, 1, ANS_BATCH_MATRICES, nullptr, out, nullptr, nullptr,
+                     (cudaStream_t)stream);
+}
+
+int ans_batch_submit(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
+                     size_t nwin, uint32_t flags, ans_quantities* out, ans_matrix** per_window, ans_matrix** sum,
+                     ans_ticket* ticket, void* stream) {
+  if (!c || !h_offsets) return fail(ANS_ERR_INVALID_ARG, "NULL context or offsets");
+  if (flags & ~(ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC))
+    return fail(ANS_ERR_INVALID_ARG, "unknown flag");
+  if ((flags & ANS_BATCH_MATRICES) && !per_window) return fail(ANS_ERR_INVALID_ARG, "per_window is NULL");
+  if ((flags & ANS_BATCH_SUM) && !sum) return fail(ANS_ERR_INVALID_ARG, "sum is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  return run_windows(c, d_src, d_dst, h_offsets, nwin, flags, out, per_window, sum, ticket, (cudaStream_t)stream);
+}
+
+int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_matrix** out, void* stream) {
+  if (!c || !out || (k && !mats)) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  std::vector<uint64_t> caps;
+  std::vector<MatDesc> md;
+  uint64_t total_cap = 0;
+  for (size_t i = 0; i < k; ++i) {
+    const ans_matrix* x = mats[i];
+    if (!x) return fail(ANS_ERR_INVALID_ARG, "NULL matrix");
+    const Block* b = x->blk;
+    if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
+    const uint64_t bs = b->base[x->seg];
+    md.push_back({b->row_ids + bs, b->row_ptr + bs + x->seg, b->col_ids + bs, b->vals + bs, b->hdr + 2 * x->seg});
+    caps.push_back(b->cap[x->seg]);
+    total_cap += b->cap[x->seg];
+    ANS_CUDA(cudaStreamWaitEvent(st, b->done, 0));
+  }
+  if (total_cap > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a time sum is limited to 2^31 - 1 links");
+  Block* sblk = nullptr;
+  if (k == 0 || total_cap == 0) {
+    ANS_TRY(make_block(c, 0, 1, {0}, {0}, st, &sblk));
+    ANS_CUDA(cudaMemsetAsync(sblk->row_ptr, 0, 8, st));
+    ANS_CUDA(cudaMemsetAsync(sblk->hdr, 0, 16, st));
+    ANS_CUDA(cudaMemsetAsync(sblk->q, 0, sizeof(ans_quantities), st));
+    ANS_CUDA(cudaMemsetAsync(sblk->status, 0, 4, st));
+  } else {
+    HostPlan sp;
+    sp.build(std::vector<uint64_t>{total_cap}, nullptr);
+    HostPlan gp;
+    gp.build(caps, nullptr);
+    Layout L;
+    PipeScratch ps;
+    ps.reserve(L, sp.pad, 1, std::max(sp.ntiles, gp.ntiles), true);
+    const size_t off_mats = L.add(k * sizeof(MatDesc));
+    const size_t off_gplan = L.add(4 * align_up((k + 1) * 8));
+    const size_t off_splan = L.add(4 * kAlign);
+    const size_t off_catoff = L.add(k * 8);
+    const size_t off_lens = L.add(k * 8);
+    const size_t off_total = L.add(8);
+    const size_t off_sq = L.add(sizeof(ans_quantities));
+    ANS_TRY(ensure_scratch(c, L.size, st));
+    ANS_TRY(ensure_table(c, 2 * std::max<uint64_t>(sp.pad, kTile), st));
+    char* m = (char*)c->scratch;
+    ANS_TRY(upload(c, m + off_mats, md.data(), k * sizeof(MatDesc), st));
+    ANS_TRY(sum_pipeline(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, caps, off_gplan, off_splan, off_catoff,
+                         off_lens, off_total, off_sq, st, &sblk));
+    int rc = capture_err(c, sblk->status, st);
+    if (rc == ANS_OK) rc = reset_err(c, st);
+    if (rc) {
+      block_discard(sblk, st);
+      return rc;
+    }
+  }
+  ANS_CUDA(cudaEventRecord(sblk->done, st));
+  sblk->refs = 1;
+  *out = new ans_matrix{sblk, 0};
+  return ANS_OK;
+}
+
+int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out, void* stream) {
+  if (!c || !x || !out) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  const Block* b = x->blk;
+  if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
+  ANS_CUDA(cudaStreamWaitEvent(st, b->done, 0));
+  const uint64_t cap = b->cap[x->seg];
+  const uint64_t bs = b->base[x->seg];
+  HostPlan hp;
+  hp.build(std::vector<uint64_t>{cap}, nullptr);
+  Layout L;
+  DevPlan dp;
+  dp.reserve(L, 1);
+  const size_t off_pre = L.add((hp.pad + 1) * 8);
+  const size_t off_lb = L.add((size_t)std::max<uint32_t>(hp.ntiles, 1) * 8);
+  const size_t off_tk = L.add(64 * 4);
+  const size_t off_q = L.add(sizeof(ans_quantities));
+  ANS_TRY(ensure_scratch(c, L.size, st));
+  ANS_TRY(ensure_table(c, 2 * std::max<uint64_t>(hp.pad, kTile), st));
+  char* m = (char*)c->scratch;
+  ANS_TRY(upload(c, m + dp.base, hp.base.data(), 8, st));
+  ANS_TRY(upload(c, m + dp.first_tile, hp.first_tile.data(), 8, st));
+  SegPlan p = dp.bind(m, hp);
+  uint64_t* hdr = b->hdr + 2 * (size_t)x->seg;
+  p.len = hdr + 1;  // nnz, on the device
+  ans_quantities* q = at<ans_quantities>(m, off_q);
+  ANS_CUDA(cudaMemsetAsync(q, 0, sizeof(ans_quantities), st));
+  ANS_CUDA(cudaMemsetAsync(m + off_lb, 0, (size_t)std::max<uint32_t>(hp.ntiles, 1) * 8, st));
+  ANS_CUDA(cudaMemsetAsync(m + off_tk, 0, 64 * 4, st));
+  uint64_t* pre = at<uint64_t>(m, off_pre);
+  if (hp.ntiles) {
+    ANS_CUDA(timed(c, "scan_u64", st, [&] { return launch_scan_u64(p, b->vals + bs, pre, at<uint64_t>(m, off_lb), at<uint32_t>(m, off_tk), c->d_err, st); }));
+    StatsArgs a;
+    a.plan = p;
+    a.hdr = hdr;
+    a.q = q;
+    a.col_ids = b->col_ids + bs;
+    a.vals = b->vals + bs;
+    a.row_ids = b->row_ids + bs;
+    a.row_ptr = b->row_ptr + bs + x->seg;
+    a.pre = pre;
+    a.table = (unsigned long long*)c->table_mem;
+    a.table_sum = a.table + c->table_slots;
+    a.err = c->d_err;
+    a.mode = kModeMatrix;
+    ANS_CUDA(timed(c, "finish", st, [&] { return launch_finish(a, st); }));
+    ANS_CUDA(timed(c, "col_scan", st, [&] { return launch_col_scan(a, st); }));
+  }
+  ANS_CUDA(cudaMemsetAsync(c->d_err, 0, 4, st));
+  ANS_TRY(copy_quantities_out(out, q, 1, st));
+  return ANS_OK;
+}
+
+int ans_wait(ans_ctx* c, ans_ticket t, uint64_t timeout_ns) {
+  if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
+  cudaEvent_t ev;
+  int slot;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->tickets.find(t);
+    if (it == c->tickets.end()) return fail(ANS_ERR_INVALID_ARG, "unknown ticket");
+    ev = it->second.ev;
+    slot = it->second.slot;
+  }
+  DeviceGuard dg(c->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return fail(ANS_ERR_CUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+    const uint64_t el = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+    if (el >= timeout_ns) return fail(ANS_ERR_TIMEOUT, "batch still running");
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  uint32_t err;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    err = c->h_err_slots[slot];
+    cudaEventDestroy(ev);
+    c->tickets.erase(t);
+  }
+  if (err) return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(err) + ")");
+  return ANS_OK;
+}
+
+int ans_matrix_view(const ans_matrix* x, uint64_t* nrows, uint64_t* nnz, const uint32_t** row_ids,
+                    const uint64_t** row_ptr, const uint32_t** col_ids, const uint64_t** vals) {
+  if (!x) return fail(ANS_ERR_INVALID_ARG, "NULL matrix");
+  Block* b = x->blk;
+  ANS_TRY(block_fill_cache(b));
+  if (b->h_status) return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(b->h_status) + ")");
+  const uint64_t bs = b->base[x->seg];
+  if (nrows) *nrows = b->h_hdr[2 * x->seg];
+  if (nnz) *nnz = b->h_hdr[2 * x->seg + 1];
+  if (row_ids) *row_ids = b->row_ids + bs;
+  if (row_ptr) *row_ptr = b->row_ptr + bs + x->seg;
+  if (col_ids) *col_ids = b->col_ids + bs;
+  if (vals) *vals = b->vals + bs;
+  return ANS_OK;
+}
+
+int ans_matrix_quantities(const ans_matrix* x, ans_quantities* out) {
+  if (!x || !out) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  Block* b = x->blk;
+  ANS_TRY(block_fill_cache(b));
+  if (b->h_status) return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(b->h_status) + ")");
+  *out = b->h_q[x->seg];
+  return ANS_OK;
+}
+
+int ans_matrix_free(ans_matrix* x) {
+  if (!x) return ANS_OK;
+  block_release(x->blk);
+  delete x;
+  return ANS_OK;
+}
+
+int ans_profile_enable(ans_ctx* c, int enable) {
+  if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  prof_collect(c);
+  c->prof.acc.clear();
+  c->prof.on = enable != 0;
+  return ANS_OK;
+}
+
+int ans_profile_read(ans_ctx* c, char* buf, size_t buflen, size_t* needed) {
+  if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  prof_collect(c);
+  std::string s;
+  char line[256];
+  for (const auto& kv : c->prof.acc) {
+    std::snprintf(line, sizeof line, "%s %llu %.6f\n", kv.first.c_str(), (unsigned long long)kv.second.second,
+                  kv.second.first);
+    s += line;
+  }
+  if (needed) *needed = s.size() + 1;
+  if (buf && buflen) {
+    const size_t n = std::min(buflen - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return ANS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Internal declarations shared by the CUDA translation units of libans.so.
+//
+// Work is organised in *segments* (one per window, one per time sum, one per
+// matrix) that are cut into fixed tiles of kTile items.  Every segment starts
+// at a multiple of kTile in a padded index space, so tiles never straddle
+// segments and 16-byte vector accesses of scratch are always aligned.  Kernels
+// that carry a running prefix from tile to tile (radix digit offsets, run and
+// row counts, value prefixes) use single-pass decoupled look-back over tile
+// status words; tiles take tickets in launch order so a tile only ever waits
+// for tiles that are already running, and every wait is bounded.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ans.h"
+
+namespace ans {
+
+constexpr int kThreads = 512;                  // threads per tile CTA
+constexpr int kPerThread = 16;                 // items per thread
+constexpr int kTile = kThreads * kPerThread;   // 8192 items per tile
+constexpr int kWarps = kThreads / 32;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kPasses = 64 / kRadixBits;       // LSD passes over a 64-bit key
+
+// Look-back status word: 2 flag bits over a 62-bit value.
+constexpr uint64_t kFlagAgg = 1ull << 62;      // tile aggregate available
+constexpr uint64_t kFlagPre = 2ull << 62;      // inclusive prefix available
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 20;      // polls (about 1 s) before a wait gives up
+
+enum ErrBits : uint32_t {
+  kErrLookback = 1u,   // a look-back wait hit kSpinLimit
+  kErrHashFull = 2u,   // a hash probe sequence exceeded the table
+};
+
+// One entry per segment; device pointers.
+struct SegPlan {
+  const uint64_t* in_off = nullptr;     // first item in the input stream (window path)
+  const uint64_t* len = nullptr;        // items in the segment (may be computed on the device)
+  const uint64_t* base = nullptr;       // padded start, a multiple of kTile
+  const uint32_t* first_tile = nullptr; // nseg + 1 entries
+  uint32_t nseg = 0;
+  uint32_t ntiles = 0;
+};
+
+// Where each phase reads and writes (all device pointers; see the launchers).
+struct StatsArgs {
+  SegPlan plan;
+  uint64_t* hdr = nullptr;        // [nseg][2] = {nrows, nnz}
+  ans_quantities* q = nullptr;    // [nseg]
+  const uint64_t* keys = nullptr; // sorted keys (padded space)
+  uint32_t* col_ids = nullptr;    // at base[s]
+  uint64_t* vals = nullptr;       // at base[s]
+  uint32_t* row_ids = nullptr;    // at base[s]
+  uint64_t* row_ptr = nullptr;    // at base[s] + s  (nrows + 1 entries)
+  uint64_t* run_start = nullptr;  // at base[s] + s  (nnz + 1 entries); null = identity
+  uint64_t* row_pos = nullptr;    // at base[s] + s  (nrows + 1 entries); null = row_ptr
+  const uint64_t* pre = nullptr;  // exclusive value prefix at base[s] + s; null = identity
+  uint64_t* lookback = nullptr;   // [ntiles] status words (zeroed)
+  uint32_t* ticket = nullptr;     // zeroed counter
+  unsigned long long* table = nullptr;  // column hash slots, 2 per padded item, all zero on entry
+  unsigned long long* table_sum = nullptr;
+  uint32_t* err = nullptr;
+  int mode = 0;
+};
+
+enum StatsMode : int {
+  kModeWindow = 0,  // vals = run lengths; row sums = packets per row
+  kModeSum = 1,     // vals = sums of sorted input values; pre = their prefix
+  kModeMatrix = 2,  // vals given; run_start identity; row_pos = row_ptr
+};
+
+// Matrix descriptor for the time-sum gather.
+struct MatDesc {
+  const uint32_t* row_ids;
+  const uint64_t* row_ptr;
+  const uint32_t* col_ids;
+  const uint64_t* vals;
+  const uint64_t* hdr;  // {nrows, nnz}
+};
+
+// ---- launchers (ans_sort.cu) ---------------------------------------------
+// Pack (src, dst) into keys src << 32 | dst, build per-segment digit
+// histograms of all passes, zero the pass-0 status words and the tickets.
+cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32_t* dst,
+                             uint64_t* keys, uint32_t* seg_hist, uint64_t* status0,
+                             uint32_t* tickets, cudaStream_t st);
+// Same for keys that already exist (time sum).
+cudaError_t launch_hist(const SegPlan& p, const uint64_t* keys, uint32_t* seg_hist,
+                        uint64_t* status0, uint32_t* tickets, cudaStream_t st);
+// One onesweep digit pass (stable), optionally carrying uint64 values.
+cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
+                            const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
+                            uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
+                            uint32_t* err, cudaStream_t st);
+// Gather the stored links of k matrices into (key, value) pairs.
+cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,
+                          uint64_t* keys, uint64_t* vals, cudaStream_t st);
+// Exclusive prefix of the matrices' nnz (hdr[1]) -> cat_off, nnz -> lens,
+// their sum -> *total.
+cudaError_t launch_count_prefix(const MatDesc* mats, uint32_t k, uint64_t* cat_off, uint64_t* lens,
+                                uint64_t* total, cudaStream_t st);
+
+// ---- launchers (ans_stats.cu) --------------------------------------------
+// Run-length reduce sorted keys into DCSR structure (col_ids, row_ids,
+// row_ptr) plus run/row start positions; writes hdr.
+cudaError_t launch_rle(const StatsArgs& a, cudaStream_t st);
+// Exclusive prefix of uint64 values per segment (len + 1 entries at base+s).
+cudaError_t launch_scan_u64(const SegPlan& p, const uint64_t* in, uint64_t* out,
+                            uint64_t* lookback, uint32_t* ticket, uint32_t* err, cudaStream_t st);
+// Values, row statistics, link maximum and the column hash inserts.
+cudaError_t launch_finish(const StatsArgs& a, cudaStream_t st);
+// Column statistics from the hash table; clears the table behind itself.
+cudaError_t launch_col_scan(const StatsArgs& a, cudaStream_t st);
+// Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.
+cudaError_t launch_empty_fixup(const StatsArgs& a, cudaStream_t st);
+
+// ---- device helpers --------------------------------------------------------
+#ifdef __CUDACC__
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Segment of a tile: the last s with first_tile[s] <= t (empty segments are
+// skipped because their first_tile equals the next one's).
+__device__ __forceinline__ uint32_t find_seg(const SegPlan& p, uint32_t t) {
+  uint32_t lo = 0, hi = p.nseg;  // first_tile[lo] <= t < first_tile[hi]
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (p.first_tile[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+struct Tile {
+  uint32_t seg, j;     // segment and tile index within it
+  uint64_t len;        // segment length
+  uint64_t base;       // padded segment start
+  uint64_t start;      // first item of the tile within the segment
+  uint32_t count;      // items in this tile (0 if the segment ended before it)
+  uint32_t seg_tiles;  // tiles reserved for the segment
+};
+
+__device__ __forceinline__ Tile make_tile(const SegPlan& p, uint32_t t) {
+  Tile r;
+  r.seg = find_seg(p, t);
+  r.j = t - p.first_tile[r.seg];
+  r.seg_tiles = p.first_tile[r.seg + 1] - p.first_tile[r.seg];
+  r.len = p.len[r.seg];
+  r.base = p.base[r.seg];
+  r.start = (uint64_t)r.j * kTile;
+  r.count = r.len > r.start ? (uint32_t)umin64(kTile, r.len - r.start) : 0u;
+  return r;
+}
+
+// Broadcast a Tile computed by thread 0 through shared memory.
+__device__ __forceinline__ Tile block_tile(const SegPlan& p, uint32_t t, Tile* sm) {
+  if (threadIdx.x == 0) *sm = make_tile(p, t);
+  __syncthreads();
+  return *sm;
+}
+
+// Take a ticket (tiles are processed in ticket order so that look-back only
+// waits on tiles that have started).
+__device__ __forceinline__ uint32_t block_ticket(uint32_t* counter, uint32_t* sm) {
+  if (threadIdx.x == 0) *sm = atomicAdd(counter, 1u);
+  __syncthreads();
+  return *sm;
+}
+
+// Bounded decoupled look-back for one value chain.  `st` points at tile 0 of
+// the chain's status array with `stride` words between consecutive tiles;
+// `first` is the first tile of the segment, `t` this tile (t > first).
+// Returns the exclusive prefix; on timeout flags kErrLookback and returns the
+// partial sum (never larger than the true prefix, so indexes stay in range).
+__device__ __forceinline__ uint64_t lookback(const uint64_t* st, uint32_t stride, uint32_t first,
+                                             uint32_t t, uint32_t* err) {
+  uint64_t excl = 0;
+  uint32_t q = t - 1;
+  uint32_t spins = 0;
+  while (true) {
+    uint64_t v = ld_relaxed(st + (uint64_t)q * stride);
+    uint64_t f = v & ~kValMask;
+    if (f == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(err, (uint32_t)kErrLookback);
+        break;
+      }
+      if (spins > 64) __nanosleep(spins > 4096 ? 1000 : 64);
+      continue;
+    }
+    excl += v & kValMask;
+    if (f == kFlagPre || q == first) break;
+    --q;
+  }
+  return excl;
+}
+
+// Block-wide exclusive scan of one uint32 per thread for the first 256
+// threads (others pass 0 and ignore the result).  `tmp` needs 8 words.
+__device__ __forceinline__ uint32_t scan256_excl(uint32_t v, uint32_t* tmp, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (warp < 8 && lane == 31) tmp[warp] = x;
+  __syncthreads();
+  uint32_t off = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    uint32_t s = tmp[w];
+    off += (w < warp) ? s : 0u;
+    tot += s;
+  }
+  if (total) *total = tot;
+  __syncthreads();
+  return off + x - v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T y = __shfl_xor_sync(0xffffffffu, v, o);
+    v = y > v ? y : v;
+  }
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace ans

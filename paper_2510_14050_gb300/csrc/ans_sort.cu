@@ -1,0 +1,357 @@
+// Segmented onesweep LSD radix sort of packed 64-bit link keys (src << 32 | dst).
+//
+// Building a traffic matrix A(i, j) = #packets i -> j (Table I caption) from
+// raw packets means grouping equal (src, dst) pairs; sorting the packed key
+// puts equal links next to each other in DCSR order (rows = sources
+// ascending, columns ascending within a row, Sec. IV-B).
+//
+// Design (sm_103a):
+//  * one histogram sweep builds the digit counts of all 8 passes for every
+//    segment at once (shared-memory counters; lanes holding identical keys
+//    are merged with __match_any_sync first, which matters for Zipf traffic
+//    where a few links dominate);
+//  * each pass is one kernel: a CTA ranks its 8192-key tile with warp-private
+//    digit counters (warp-aggregated via __match_any_sync), obtains the
+//    tile's global digit offsets by bounded decoupled look-back over the
+//    previous tiles of its segment, reorders the tile in shared memory and
+//    writes runs of equal digits to contiguous addresses;
+//  * loads of the raw (src, dst) stream are 128-bit when the window is
+//    16-byte aligned.
+#include "ans_internal.cuh"
+
+namespace ans {
+
+namespace {
+
+__device__ __forceinline__ void hist_add(uint32_t* h, uint64_t key, bool valid, uint32_t vmask) {
+  if (!valid) return;
+  const uint32_t peers = __match_any_sync(vmask, key);
+  if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) {
+    const uint32_t c = __popc(peers);
+#pragma unroll
+    for (int p = 0; p < kPasses; ++p) atomicAdd(&h[p * kRadix + ((key >> (p * kRadixBits)) & 0xff)], c);
+  }
+}
+
+__device__ __forceinline__ void hist_flush(const uint32_t* h, uint32_t* seg_hist, uint32_t seg) {
+  uint32_t* g = seg_hist + (size_t)seg * kPasses * kRadix;
+  for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) {
+    const uint32_t c = h[i];
+    if (c) atomicAdd(&g[i], c);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_t* __restrict__ src,
+                                                        const uint32_t* __restrict__ dst,
+                                                        uint64_t* __restrict__ keys,
+                                                        uint32_t* __restrict__ seg_hist,
+                                                        uint64_t* __restrict__ status0,
+                                                        uint32_t* __restrict__ tickets) {
+  __shared__ uint32_t h[kPasses * kRadix];
+  __shared__ Tile s_tile;
+  const uint32_t t = blockIdx.x;
+  const Tile tl = block_tile(p, t, &s_tile);
+  for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) h[i] = 0;
+  if (t == 0 && threadIdx.x < 32) tickets[threadIdx.x] = 0;
+  if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  __syncthreads();
+  if (tl.count == 0) return;
+
+  const uint64_t in0 = p.in_off[tl.seg] + tl.start;
+  uint64_t* out = keys + tl.base + tl.start;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool aligned = ((((uintptr_t)(src + in0)) | ((uintptr_t)(dst + in0))) & 15u) == 0;
+
+  if (aligned && tl.count == kTile) {
+    // 128-bit loads: each lane reads 4 consecutive sources and destinations.
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + in0);
+    const uint4* d4 = reinterpret_cast<const uint4*>(dst + in0);
+    ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out);
+#pragma unroll 2
+    for (int i = 0; i < kPerThread / 4; ++i) {
+      const int v = warp * (kPerThread * 8) + i * 32 + lane;  // uint4 index inside the tile
+      const uint4 a = __ldg(s4 + v), b = __ldg(d4 + v);
+      const uint64_t k0 = ((uint64_t)a.x << 32) | b.x, k1 = ((uint64_t)a.y << 32) | b.y;
+      const uint64_t k2 = ((uint64_t)a.z << 32) | b.z, k3 = ((uint64_t)a.w << 32) | b.w;
+      o2[2 * v] = make_ulonglong2(k0, k1);
+      o2[2 * v + 1] = make_ulonglong2(k2, k3);
+      hist_add(h, k0, true, 0xffffffffu);
+      hist_add(h, k1, true, 0xffffffffu);
+      hist_add(h, k2, true, 0xffffffffu);
+      hist_add(h, k3, true, 0xffffffffu);
+    }
+  } else {
+    for (int i = 0; i < kPerThread; ++i) {
+      const uint32_t idx = warp * (kPerThread * 32) + i * 32 + lane;
+      const bool valid = idx < tl.count;
+      const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+      uint64_t key = 0;
+      if (valid) {
+        key = ((uint64_t)src[in0 + idx] << 32) | dst[in0 + idx];
+        out[idx] = key;
+      }
+      hist_add(h, key, valid, vmask);
+    }
+  }
+  __syncthreads();
+  hist_flush(h, seg_hist, tl.seg);
+}
+
+__global__ void __launch_bounds__(kThreads) k_hist(SegPlan p, const uint64_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ seg_hist,
+                                                   uint64_t* __restrict__ status0,
+                                                   uint32_t* __restrict__ tickets) {
+  __shared__ uint32_t h[kPasses * kRadix];
+  __shared__ Tile s_tile;
+  const uint32_t t = blockIdx.x;
+  const Tile tl = block_tile(p, t, &s_tile);
+  for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) h[i] = 0;
+  if (t == 0 && threadIdx.x < 32) tickets[threadIdx.x] = 0;
+  if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  __syncthreads();
+  if (tl.count == 0) return;
+  const uint64_t* in = keys + tl.base + tl.start;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < kPerThread; ++i) {
+    const uint32_t idx = warp * (kPerThread * 32) + i * 32 + lane;
+    const bool valid = idx < tl.count;
+    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    hist_add(h, valid ? in[idx] : 0ull, valid, vmask);
+  }
+  __syncthreads();
+  hist_flush(h, seg_hist, tl.seg);
+}
+
+template <bool kVals>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_onesweep(SegPlan p, int pass, const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
+               const uint64_t* __restrict__ vin, uint64_t* __restrict__ vout,
+               const uint32_t* __restrict__ seg_hist, uint64_t* st_cur, uint64_t* __restrict__ st_next,
+               uint32_t* ticket, uint32_t* err) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* s_vals = s_keys + kTile;
+  uint32_t* s_wc = reinterpret_cast<uint32_t*>(s_keys + (kVals ? 2 : 1) * kTile);  // [kWarps][kRadix+1]
+  __shared__ uint64_t s_gofs[kRadix];
+  __shared__ uint32_t s_dstart[kRadix];
+  __shared__ uint32_t s_tmp[8];
+  __shared__ uint32_t s_ticket;
+  __shared__ Tile s_tile;
+
+  const uint32_t t = block_ticket(ticket, &s_ticket);
+  const Tile tl = block_tile(p, t, &s_tile);
+  if (threadIdx.x < kRadix) st_next[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  if (tl.count == 0) return;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int shift = pass * kRadixBits;
+  uint32_t* wc = s_wc + warp * (kRadix + 1);
+  for (int i = lane; i < kRadix + 1; i += 32) wc[i] = 0;
+  __syncwarp();
+
+  const uint64_t g0 = tl.base + tl.start;
+  const uint32_t wbase = warp * (kPerThread * 32);
+  uint64_t k[kPerThread];
+  uint64_t v[kVals ? kPerThread : 1];
+  uint32_t r[kPerThread];
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const uint32_t idx = wbase + i * 32 + lane;
+    const bool valid = idx < tl.count;
+    k[i] = valid ? kin[g0 + idx] : 0ull;
+    if (kVals) v[i] = valid ? vin[g0 + idx] : 0ull;
+  }
+  // Stable rank inside (warp, digit): lanes with equal digits are merged by
+  // match_any; the lowest lane updates the warp's counter.
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const uint32_t idx = wbase + i * 32 + lane;
+    const uint32_t d = idx < tl.count ? (uint32_t)(k[i] >> shift) & 0xffu : (uint32_t)kRadix;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader) {
+      old = wc[d];
+      wc[d] = old + __popc(peers);
+    }
+    __syncwarp();
+    old = __shfl_sync(0xffffffffu, old, leader);
+    r[i] = old + __popc(peers & lanemask_lt());
+  }
+  __syncthreads();
+
+  // Per digit: exclusive offsets across warps and the tile's count.
+  const int d = threadIdx.x;
+  uint32_t cnt = 0;
+  uint64_t excl = 0;
+  if (d < kRadix) {
+#pragma unroll 4
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = s_wc[w * (kRadix + 1) + d];
+      s_wc[w * (kRadix + 1) + d] = cnt;
+      cnt += c;
+    }
+    uint64_t* my = st_cur + (uint64_t)t * kRadix + d;
+    if (tl.j == 0) {
+      st_relaxed(my, kFlagPre | cnt);
+    } else {
+      st_relaxed(my, kFlagAgg | cnt);
+      excl = lookback(st_cur + d, kRadix, t - tl.j, t, err);
+      st_relaxed(my, kFlagPre | (excl + cnt));
+    }
+  }
+  const uint32_t dstart = scan256_excl(d < kRadix ? cnt : 0u, s_tmp, nullptr);
+  const uint32_t hv = d < kRadix ? seg_hist[((size_t)tl.seg * kPasses + pass) * kRadix + d] : 0u;
+  const uint32_t bstart = scan256_excl(hv, s_tmp, nullptr);
+  if (d < kRadix) {
+    s_dstart[d] = dstart;
+    s_gofs[d] = tl.base + bstart + excl - dstart;  // + position in the sorted tile
+  }
+  __syncthreads();
+
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const uint32_t idx = wbase + i * 32 + lane;
+    if (idx < tl.count) {
+      const uint32_t dg = (uint32_t)(k[i] >> shift) & 0xffu;
+      const uint32_t pos = s_dstart[dg] + wc[dg] + r[i];
+      s_keys[pos] = k[i];
+      if (kVals) s_vals[pos] = v[i];
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < tl.count; i += kThreads) {
+    const uint64_t key = s_keys[i];
+    const uint64_t o = s_gofs[(key >> shift) & 0xffu] + i;
+    kout[o] = key;
+    if (kVals) vout[o] = s_vals[i];
+  }
+}
+
+// One tile per CTA over the stored links of matrix `seg`.
+__global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* __restrict__ mats,
+                                                     const uint64_t* __restrict__ cat_off,
+                                                     uint64_t* __restrict__ keys,
+                                                     uint64_t* __restrict__ vals) {
+  __shared__ Tile s_tile;
+  const Tile tl = block_tile(p, blockIdx.x, &s_tile);
+  if (tl.count == 0) return;
+  const MatDesc m = mats[tl.seg];
+  const uint64_t nrows = m.hdr[0];
+  const uint64_t u0 = tl.start + (uint64_t)threadIdx.x * kPerThread;
+  const uint64_t u1 = umin64(u0 + kPerThread, tl.start + tl.count);
+  if (u0 >= u1) return;
+  // row holding u0: last r with row_ptr[r] <= u0
+  uint64_t lo = 0, hi = nrows;
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (m.row_ptr[mid] <= u0) lo = mid; else hi = mid;
+  }
+  uint64_t r = lo;
+  const uint64_t o = cat_off[tl.seg];
+  for (uint64_t u = u0; u < u1; ++u) {
+    while (m.row_ptr[r + 1] <= u) ++r;
+    keys[o + u] = ((uint64_t)m.row_ids[r] << 32) | m.col_ids[u];
+    vals[o + u] = m.vals[u];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_count_prefix(const MatDesc* __restrict__ mats, uint32_t k,
+                                                       uint64_t* __restrict__ cat_off,
+                                                       uint64_t* __restrict__ lens,
+                                                       uint64_t* __restrict__ total) {
+  __shared__ uint64_t s_w[32];
+  __shared__ uint64_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t c0 = 0; c0 < k; c0 += 1024) {
+    const uint32_t i = c0 + threadIdx.x;
+    const uint64_t v = i < k ? mats[i].hdr[1] : 0ull;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    uint64_t off = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+      off += w < warp ? s_w[w] : 0ull;
+      tot += s_w[w];
+    }
+    const uint64_t carry = s_carry;
+    if (i < k) {
+      cat_off[i] = carry + off + x - v;
+      lens[i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = s_carry;
+}
+
+}  // namespace
+
+static size_t onesweep_smem(bool vals) {
+  return (size_t)kTile * sizeof(uint64_t) * (vals ? 2 : 1) + (size_t)kWarps * (kRadix + 1) * 4;
+}
+
+cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32_t* dst,
+                             uint64_t* keys, uint32_t* seg_hist, uint64_t* status0, uint32_t* tickets,
+                             cudaStream_t st) {
+  if (p.ntiles == 0) return cudaSuccess;
+  k_pack_hist<<<p.ntiles, kThreads, 0, st>>>(p, src, dst, keys, seg_hist, status0, tickets);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist(const SegPlan& p, const uint64_t* keys, uint32_t* seg_hist, uint64_t* status0,
+                        uint32_t* tickets, cudaStream_t st) {
+  if (p.ntiles == 0) return cudaSuccess;
+  k_hist<<<p.ntiles, kThreads, 0, st>>>(p, keys, seg_hist, status0, tickets);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
+                            const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
+                            uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
+                            cudaStream_t st) {
+  if (p.ntiles == 0) return cudaSuccess;
+  static unsigned long long configured = 0;  // one bit per device ordinal
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !((configured >> dev) & 1ull)) {
+    cudaError_t e = cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)onesweep_smem(false));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)onesweep_smem(true));
+    if (e != cudaSuccess) return e;
+    if (dev < 64) configured |= 1ull << dev;
+  }
+  if (vin)
+    k_onesweep<true><<<p.ntiles, kThreads, onesweep_smem(true), st>>>(p, pass, kin, kout, vin, vout,
+                                                                      seg_hist, st_cur, st_next,
+                                                                      ticket, err);
+  else
+    k_onesweep<false><<<p.ntiles, kThreads, onesweep_smem(false), st>>>(
+        p, pass, kin, kout, nullptr, nullptr, seg_hist, st_cur, st_next, ticket, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,
+                          uint64_t* keys, uint64_t* vals, cudaStream_t st) {
+  if (p.ntiles == 0) return cudaSuccess;
+  k_gather<<<p.ntiles, kThreads, 0, st>>>(p, mats, cat_off, keys, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_prefix(const MatDesc* mats, uint32_t k, uint64_t* cat_off, uint64_t* lens,
+                                uint64_t* total, cudaStream_t st) {
+  k_count_prefix<<<1, 1024, 0, st>>>(mats, k, cat_off, lens, total);
+  return cudaGetLastError();
+}
+
+}  // namespace ans

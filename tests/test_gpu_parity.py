@@ -1,0 +1,250 @@
+"""GPU parity: every result of the CUDA path equals the oracle bit for bit.
+
+All inputs are seeded and synthetic; every call goes through the C ABI
+(libans.so) via the ctypes binding.  Tolerance is zero: the outputs are
+integers (DCSR structure, uint64 counts, the nine quantities) and exactly one
+canonical answer exists.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import golden_io
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KT = 8192  # tile size of the kernels: sizes around multiples of it are edge cases
+
+
+@pytest.fixture(scope="module")
+def ans():
+    from paper_2510_14050_gb300 import ans as mod
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(ans):
+    c = ans.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def synth():
+    from paper_2510_14050_gb300 import synth as mod
+    return mod
+
+
+def dev(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+    return torch.from_numpy(a.view(np.int32)).cuda()
+
+
+def assert_dcsr_equal(got, exp: oracle.DCSR, what=""):
+    r, p, c, v = got
+    assert np.array_equal(r, exp.row_ids), f"{what}: row_ids differ"
+    assert np.array_equal(p, exp.row_ptr), f"{what}: row_ptr differ"
+    assert np.array_equal(c, exp.col_ids), f"{what}: col_ids differ"
+    assert np.array_equal(v, exp.vals), f"{what}: vals differ"
+
+
+def check_window(ctx, src, dst, what=""):
+    m = ctx.build_window(dev(src), dev(dst), len(src))
+    exp = oracle.traffic_matrix(src, dst)
+    assert_dcsr_equal(m.to_numpy(), exp, what)
+    q = oracle.network_quantities(exp)
+    assert m.quantities() == q, what
+    assert ctx.network_quantities(m) == q, what
+    return m
+
+
+@pytest.mark.parametrize("name", golden_io.FIXTURES)
+def test_golden_windows(ctx, name):
+    (win,), exp = golden_io.load(name)
+    m = ctx.build_window(dev(win[0]), dev(win[1]), len(win[0]))
+    r, p, c, v = m.to_numpy()
+    assert [int(x) for x in r] == exp["row_ids"] and [int(x) for x in p] == exp["row_ptr"]
+    assert [int(x) for x in c] == exp["col_ids"] and [int(x) for x in v] == exp["vals"]
+    assert m.quantities() == {k: exp[k][0] for k in oracle.QUANTITY_NAMES}
+
+
+def test_golden_time_sum(ctx):
+    wins, exp = golden_io.load("time_sum.txt")
+    mats = [ctx.build_window(dev(s), dev(d), len(s)) for s, d in wins]
+    s = ctx.sum_windows(mats)
+    r, p, c, v = s.to_numpy()
+    assert [int(x) for x in r] == exp["sum_row_ids"] and [int(x) for x in p] == exp["sum_row_ptr"]
+    assert [int(x) for x in c] == exp["sum_col_ids"] and [int(x) for x in v] == exp["sum_vals"]
+    q = {k: exp["sum_" + k][0] for k in oracle.QUANTITY_NAMES}
+    assert s.quantities() == q
+    assert ctx.network_quantities(s) == q
+
+
+def test_empty_and_single(ctx):
+    m = ctx.build_window(dev([0]), dev([0]), 0)
+    assert m.view()[:2] == (0, 0)
+    r, p, c, v = m.to_numpy()
+    assert list(p) == [0]
+    assert m.quantities() == dict.fromkeys(oracle.QUANTITY_NAMES, 0)
+    assert ctx.network_quantities(m) == dict.fromkeys(oracle.QUANTITY_NAMES, 0)
+    check_window(ctx, np.array([0xFFFFFFFF], np.uint32), np.array([0xFFFFFFFF], np.uint32), "single max key")
+    check_window(ctx, np.array([0], np.uint32), np.array([0], np.uint32), "single zero key")
+
+
+@pytest.mark.parametrize("n", [KT - 1, KT, KT + 1, 2 * KT + 7, 5 * KT + 1])
+def test_identical_packets_span_tiles(ctx, n):
+    check_window(ctx, np.full(n, 0xFFFFFFFF, np.uint32), np.full(n, 0xFFFFFFFF, np.uint32), f"identical {n}")
+    check_window(ctx, np.full(n, 9, np.uint32), np.zeros(n, np.uint32), f"identical0 {n}")
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 511, 513, KT - 1, KT, KT + 1, 3 * KT - 5, 40000])
+def test_random_ragged_sizes(ctx, n):
+    rng = np.random.default_rng(n)
+    pool = rng.integers(0, 2**32, size=max(2, n // 5), dtype=np.uint64).astype(np.uint32)
+    pool[0], pool[-1] = 0, 0xFFFFFFFF
+    src = pool[rng.integers(0, len(pool), n)]
+    dst = pool[rng.integers(0, len(pool), n)]
+    check_window(ctx, src, dst, f"random {n}")
+
+
+def test_distinct_star_and_reverse_star(ctx):
+    rng = np.random.default_rng(5)
+    p = 3 * KT + 11
+    src = (rng.permutation(p).astype(np.uint64) * 2654435761 % 2**32).astype(np.uint32)
+    dst = rng.permutation(p).astype(np.uint32)
+    check_window(ctx, src, dst, "distinct")
+    star_d = (np.arange(2 * KT + 3, dtype=np.uint64) * 40503 % 2**32).astype(np.uint32)
+    star_s = np.full(len(star_d), 77, np.uint32)
+    check_window(ctx, star_s, star_d, "star")
+    check_window(ctx, star_d, star_s, "reverse star")
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_unaligned_inputs(ctx, shift):
+    rng = np.random.default_rng(shift)
+    n = 2 * KT + 100
+    src = rng.integers(0, 300, n + shift).astype(np.uint32)
+    dst = rng.integers(0, 300, n + shift).astype(np.uint32)
+    ds, dd = dev(src), dev(dst)
+    m = ctx.build_window(ds[shift:], dd[shift:], n)
+    exp = oracle.traffic_matrix(src[shift:], dst[shift:])
+    assert_dcsr_equal(m.to_numpy(), exp, "unaligned")
+    assert m.quantities() == oracle.network_quantities(exp)
+
+
+def test_cfg1_single_window(ctx, synth):
+    w = synth.generate(1)
+    check_window(ctx, w.src, w.dst, "cfg1")
+
+
+def run_batch(ans, ctx, w, flags):
+    out = torch.zeros((w.nwin, 9), dtype=torch.int64, device="cuda")
+    mats, summ, tk = ctx.batch_submit(dev(w.src), dev(w.dst), w.offsets, flags, out=out)
+    ctx.wait(tk)
+    return mats, summ, ans.quantities_from_tensor(out)
+
+
+def check_batch(ans, ctx, w, check_mats=True, check_sum=True):
+    flags = (ans.BATCH_MATRICES if check_mats else 0) | (ans.BATCH_SUM if check_sum else 0)
+    mats, summ, quants = run_batch(ans, ctx, w, flags)
+    exp_mats, exp_q, exp_sum = oracle.batch(w.src, w.dst, w.offsets, want_sum=check_sum)
+    for i in range(w.nwin):
+        assert quants[i] == exp_q[i], f"window {i}"
+        if check_mats:
+            assert_dcsr_equal(mats[i].to_numpy(), exp_mats[i], f"window {i}")
+            assert mats[i].quantities() == exp_q[i]
+    if check_sum:
+        assert_dcsr_equal(summ.to_numpy(), exp_sum, "sum")
+        sq = oracle.network_quantities(exp_sum)
+        assert summ.quantities() == sq
+        assert ctx.network_quantities(summ) == sq
+    return mats, summ, quants
+
+
+def test_batch_cfg2_full(ans, ctx, synth):
+    w = synth.generate(2)
+    check_batch(ans, ctx, w)
+
+
+def test_batch_cfg3_subset(ans, ctx, synth):
+    w = synth.generate(3, nwin=48)
+    check_batch(ans, ctx, w)
+
+
+def test_batch_cfg4_subset(ans, ctx, synth):
+    w = synth.generate(4, nwin=12)
+    check_batch(ans, ctx, w)
+
+
+def test_batch_cfg5_with_empty_windows(ans, ctx, synth):
+    sizes = synth.window_sizes(5, 20)
+    sizes[[0, 7, 19]] = 0
+    sizes[3] = 1
+    sizes[11] = KT
+    w = synth.generate(5, sizes=sizes)
+    check_batch(ans, ctx, w)
+
+
+def test_empty_batch(ans, ctx):
+    mats, summ, tk = ctx.batch_submit(dev([0]), dev([0]), np.zeros(1, np.uint64),
+                                      ans.BATCH_MATRICES | ans.BATCH_SUM)
+    ctx.wait(tk)
+    assert mats == [] and summ.view()[:2] == (0, 0)
+    assert summ.quantities() == dict.fromkeys(oracle.QUANTITY_NAMES, 0)
+
+
+def test_batched_equals_per_window_and_sum_across_calls(ans, ctx, synth):
+    w = synth.generate(5, nwin=6)
+    mats, summ, quants = run_batch(ans, ctx, w, ans.BATCH_MATRICES | ans.BATCH_SUM)
+    singles = []
+    for i in range(w.nwin):
+        s, d = w.window(i)
+        m = ctx.build_window(dev(s), dev(d), len(s))
+        for a, b in zip(m.to_numpy(), mats[i].to_numpy()):
+            assert np.array_equal(a, b)
+        assert m.quantities() == quants[i]
+        singles.append(m)
+    # a time sum over matrices that came from different calls
+    mixed = ctx.sum_windows(singles[:3] + mats[3:])
+    for a, b in zip(mixed.to_numpy(), summ.to_numpy()):
+        assert np.array_equal(a, b)
+    # summing sums: (A0 + A1) + (A2 + ... ) == total
+    part1 = ctx.sum_windows(mats[:2])
+    part2 = ctx.sum_windows(singles[2:])
+    total = ctx.sum_windows([part1, part2])
+    for a, b in zip(total.to_numpy(), summ.to_numpy()):
+        assert np.array_equal(a, b)
+
+
+def test_quantities_only_batch_matches(ans, ctx, synth):
+    w = synth.generate(3, nwin=20, first_window=100)
+    _, _, quants = run_batch(ans, ctx, w, 0)
+    exp = [oracle.window_quantities(*w.window(i)) for i in range(w.nwin)]
+    assert quants == exp
+
+
+def test_memory_budget_refuses_and_recovers(ans, synth):
+    w = synth.generate(2, nwin=8)
+    c = ans.Context(0, budget_bytes=64 << 20)
+    try:
+        with pytest.raises(ans.AnsError) as ei:
+            c.batch_submit(dev(w.src), dev(w.dst), w.offsets, ans.BATCH_MATRICES)
+        assert ei.value.code == ans.ERR_BUDGET
+        s, d = w.window(0)
+        small = 5000
+        m = c.build_window(dev(s[:small]), dev(d[:small]), small)
+        assert m.quantities() == oracle.window_quantities(s[:small], d[:small])
+        m.free()
+    finally:
+        c.close()
+
+
+def test_invalid_arguments(ans, ctx):
+    with pytest.raises(ans.AnsError) as ei:
+        ctx.batch_submit(dev([1, 2]), dev([1, 2]), np.array([0, 2, 1], np.uint64), 0)
+    assert ei.value.code == ans.ERR_INVALID_ARG
+    with pytest.raises(ans.AnsError) as ei:
+        ctx.wait(123456789)
+    assert ei.value.code == ans.ERR_INVALID_ARG
