@@ -132,7 +132,7 @@ class _DevView:
     """Wrap a raw device pointer for torch.as_tensor (CUDA array interface)."""
 
     def __init__(self, ptr: int, n: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True), "version": 3}
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
 
 
 def _download(ptr: int, n: int, np_dtype) -> np.ndarray:

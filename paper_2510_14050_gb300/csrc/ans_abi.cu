@@ -304,15 +304,6 @@ int upload(ans_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t st
   return ANS_OK;
 }
 
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 // Device layout of a block holding nseg matrices over `pad` padded items.
 struct BlockLayout {
   size_t col_ids, vals, row_ids, row_ptr, hdr, q, status, total;
