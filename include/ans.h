@@ -157,6 +157,29 @@ int ans_matrix_quantities(const ans_matrix* m, ans_quantities* out);
 /* Release a matrix (waits for the work that produces it).  NULL is a no-op. */
 int ans_matrix_free(ans_matrix* m);
 
+/* Quantities of one window without allocating anything.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * while they run -- for example a capture process whose device memory is all
+ * owned up front by another framework's caching allocator, or a
+ * latency-critical ingest loop that cannot absorb cudaMalloc/cudaFree's
+ * implicit synchronisation.  It runs the same kernels as ans_build_window and
+ * writes the nine quantities of the window d_src/d_dst[0..n) to *d_out; it
+ * needs no context and performs no allocation of any kind.
+ *   n        : at most 65536 packets; larger n fails with ANS_ERR_INVALID_ARG.
+ *   d_out    : device memory (or pinned host memory) for one ans_quantities.
+ *   d_status : optional device word receiving 0, or nonzero if a bounded
+ *              device wait or a hash probe gave up (the result is then invalid).
+ * All intermediate data lives in one fixed device array of about 5.6 MiB,
+ * present on every GPU that loads the library until the process exits.
+ * Every call shares that array and it keeps the previous call's contents (the
+ * call clears what must start at zero); calls whose work overlaps on the GPU
+ * -- on different streams, or from threads that do not order their calls --
+ * race and produce wrong results.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * Asynchronous on `stream`. */
+int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
+                                  ans_quantities* d_out, uint32_t* d_status, void* stream);
+
 /* Diagnostics: per-kernel timing.  While enabled, every kernel launch of the
  * context is bracketed by CUDA events on its launching stream (the paper
  * reports wall-clock analysis time, Sec. V-A; this splits it by kernel).

@@ -44,6 +44,7 @@ EXPORTS = (
     "ans_ctx_create", "ans_ctx_destroy", "ans_build_window", "ans_sum_windows", "ans_network_quantities",
     "ans_batch_submit", "ans_wait", "ans_matrix_view", "ans_matrix_quantities", "ans_matrix_free",
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
+    "ans_window_quantities_noalloc",
 )
 
 
@@ -90,6 +91,7 @@ def load(path: str | os.PathLike | None = None):
         "ans_last_error": ([_vp], C.c_char_p),
         "ans_profile_enable": ([_vp, C.c_int], C.c_int),
         "ans_profile_read": ([_vp, C.c_char_p, C.c_size_t, P(C.c_size_t)], C.c_int),
+        "ans_window_quantities_noalloc": ([_vp, _vp, _u64, _vp, _vp, _vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

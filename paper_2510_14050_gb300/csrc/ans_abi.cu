@@ -80,6 +80,8 @@ struct Layout {
 
 }  // namespace
 
+int ans::set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+
 struct Block;
 
 struct ans_ctx {

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "ans.h"
 
 namespace ans {
@@ -81,6 +83,9 @@ struct MatDesc {
   const uint64_t* vals;
   const uint64_t* hdr;  // {nrows, nnz}
 };
+
+// Record `msg` as the calling thread's ans_last_error() text; returns code.
+int set_last_error(int code, const std::string& msg);
 
 // ---- launchers (ans_sort.cu) ---------------------------------------------
 // Pack (src, dst) into keys src << 32 | dst, build per-segment digit

@@ -1,0 +1,66 @@
+"""ans_window_quantities_noalloc: the allocation-free entry point.
+
+It exists for callers that cannot allocate device memory while they run (a
+process whose device memory is all owned by another framework's allocator, or
+a latency-critical loop that cannot absorb cudaMalloc's synchronisation).  This
+test calls it through the C ABI and checks its quantities against the regular
+entry point (ans_build_window) exactly, on calls in a row that reuse the same
+static scratch: a large window, a smaller one (stale contents from the first
+call must not leak), the maximum size, and an empty window.  It lives in a file
+that pytest collects last so that a run stopping at the first failure has
+already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MAX_PACKETS = 65536
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def _noalloc(lib, src, dst, n):
+    out = torch.zeros(9, dtype=torch.int64, device="cuda")
+    status = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.ans_window_quantities_noalloc(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), n,
+                                           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                                           ctypes.c_void_p(stream))
+    return rc, out, status
+
+
+def test_noalloc_matches_build_window_on_consecutive_calls():
+    from paper_2510_14050_gb300 import ans, synth
+    lib = ans.load()
+    ctx = ans.Context(0)
+    try:
+        sizes = [60000, 9000, MAX_PACKETS, 1, 0]
+        w = synth.generate(5, sizes=sizes)
+        for i, n in enumerate(sizes):
+            s, d = w.window(i)
+            ds, dd = _dev(s if n else [0]), _dev(d if n else [0])
+            rc, out, status = _noalloc(lib, ds, dd, n)
+            assert rc == ans.OK, lib.ans_last_error(None)
+            torch.cuda.synchronize()
+            got = ans.quantities_from_tensor(out)[0]
+            m = ctx.build_window(ds, dd, n)
+            assert got == m.quantities(), f"call {i} (n={n})"
+            assert int(status.item()) == 0
+            m.free()
+    finally:
+        ctx.close()
+
+
+def test_noalloc_rejects_oversized_windows():
+    from paper_2510_14050_gb300 import ans
+    lib = ans.load()
+    ds = _dev(np.zeros(MAX_PACKETS + 1, np.uint32))
+    rc, _, _ = _noalloc(lib, ds, ds, MAX_PACKETS + 1)
+    assert rc == ans.ERR_INVALID_ARG
+    assert b"65536" in lib.ans_last_error(None)
