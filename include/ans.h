@@ -114,7 +114,8 @@ int ans_sum_windows(ans_ctx* ctx, const ans_matrix* const* mats, size_t k, ans_m
 
 /* The nine quantities of a matrix (Table I, Sec. IV-C), recomputed on the
  * device from its DCSR arrays: row statistics by segmented reductions over
- * rows, column statistics by a transpose-free hash pass over the stored links.
+ * rows, column statistics by a transpose-free pass that sorts the stored links
+ * by destination and reduces the destination runs.
  * out: host or device pointer to one ans_quantities.  With a device pointer
  * (or pinned host memory) the call is asynchronous; with pageable host memory
  * it returns once the result has been written. */
@@ -140,7 +141,8 @@ int ans_batch_submit(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst,
 
 /* Wait (bounded) for a batch.  timeout_ns == 0 polls once.  Returns ANS_OK,
  * ANS_ERR_TIMEOUT (still running), ANS_ERR_INTERNAL (a bounded device wait or
- * a hash probe gave up inside the batch: its results are not valid) or
+ * a device consistency check failed inside the batch: its results are not
+ * valid) or
  * ANS_ERR_INVALID_ARG (unknown ticket). */
 int ans_wait(ans_ctx* ctx, ans_ticket ticket, uint64_t timeout_ns);
 
@@ -168,8 +170,8 @@ int ans_matrix_free(ans_matrix* m);
  *   n        : at most 65536 packets; larger n fails with ANS_ERR_INVALID_ARG.
  *   d_out    : device memory (or pinned host memory) for one ans_quantities.
  *   d_status : optional device word receiving 0, or nonzero if a bounded
- *              device wait or a hash probe gave up (the result is then invalid).
- * All intermediate data lives in one fixed device array of about 5.6 MiB,
+ *              device wait gave up (the result is then invalid).
+ * All intermediate data lives in one fixed device array of about 5 MiB,
  * present on every GPU that loads the library until the process exits.
  * Every call shares that array and it keeps the previous call's contents (the
  * call clears what must start at zero); calls whose work overlaps on the GPU

@@ -5,9 +5,10 @@
 // Pipeline of one batch of windows (every window of the batch in one fixed
 // sequence of launches, independent of the number of windows):
 //   pack + digit histograms -> 8 onesweep digit passes -> run-length reduce
-//   to DCSR -> values, row statistics and column-hash inserts -> column scan
+//   to DCSR -> values and row statistics -> column pass (4 destination-key
+//   passes, run reduction)
 //   [-> time sum: gather links -> histograms -> 8 key/value passes -> value
-//   prefix -> run-length reduce -> statistics -> column scan].
+//   prefix -> run-length reduce -> statistics -> column pass].
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,6 +52,9 @@ constexpr size_t kAlign = 256;
 constexpr uint64_t kMaxWindow = (1ull << 31) - 1;
 constexpr int kStageSlots = 8;
 constexpr int kErrSlots = 4096;
+// Tickets of the look-back kernels, 32 per phase: window sort + RLE, time-sum
+// sort + RLE + scan, window column pass, time-sum column pass.
+constexpr int kTicketBlocks = 4;
 
 size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 uint64_t tiles_for(uint64_t n) { return (n + kTile - 1) / kTile; }
@@ -91,14 +95,11 @@ struct ans_ctx {
   ans_free_fn free_fn = nullptr;
   void* user = nullptr;
   std::mutex mu;
-  size_t live = 0;  // device bytes held: scratch + table + live matrix blocks
+  size_t live = 0;  // device bytes held: scratch + live matrix blocks
 
   void* scratch = nullptr;
   size_t scratch_size = 0;
-  // Column hash table (slots and sums), kept all-zero between calls, plus
-  // the device error word.
-  void* table_mem = nullptr;
-  size_t table_slots = 0;
+  // The device error word (bounded waits that gave up set bits here).
   uint32_t* d_err = nullptr;
   void* small_mem = nullptr;
 
@@ -272,21 +273,6 @@ int ensure_scratch(ans_ctx* c, size_t bytes, cudaStream_t st) {
   return ANS_OK;
 }
 
-size_t table_bytes(size_t slots) { return slots * 2 * sizeof(unsigned long long); }
-
-int ensure_table(ans_ctx* c, size_t slots, cudaStream_t st) {
-  if (slots <= c->table_slots) return ANS_OK;
-  dev_free(c, c->table_mem, table_bytes(c->table_slots), st);
-  c->table_mem = nullptr;
-  c->table_slots = 0;
-  void* p = nullptr;
-  ANS_TRY(dev_alloc(c, table_bytes(slots), st, &p));
-  ANS_CUDA(cudaMemsetAsync(p, 0, table_bytes(slots), st));
-  c->table_mem = p;
-  c->table_slots = slots;
-  return ANS_OK;
-}
-
 // Copy `bytes` of host data to device `dst` through the pinned ring.
 int upload(ans_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return ANS_OK;
@@ -449,7 +435,15 @@ struct DevPlan {
 // `ntiles` tiles.
 struct PipeScratch {
   size_t keys_a, keys_b, vals_a, vals_b, seg_hist, st0, st1, lb, lb2, tickets, run_start, row_pos, pre;
+  size_t ck_a, ck_b, cv_a, cv_b, col_hist, ulen, bnd;
   void reserve(Layout& L, uint64_t pad, uint32_t nseg, uint32_t ntiles, bool with_vals) {
+    ck_a = L.add(pad * 4);
+    ck_b = L.add(pad * 4);
+    cv_a = L.add(pad * 8);
+    cv_b = L.add(pad * 8);
+    col_hist = L.add((size_t)nseg * kColPasses * kRadix * 4);
+    ulen = L.add((size_t)nseg * 8);
+    bnd = L.add((size_t)ntiles * sizeof(ColBnd));
     keys_a = L.add(pad * 8);
     keys_b = L.add(pad * 8);
     vals_a = with_vals ? L.add(pad * 8) : 0;
@@ -459,7 +453,7 @@ struct PipeScratch {
     st1 = L.add((size_t)ntiles * kRadix * 8);
     lb = L.add((size_t)ntiles * 8);
     lb2 = L.add((size_t)ntiles * 8);
-    tickets = L.add(64 * 4);
+    tickets = L.add(kTicketBlocks * 32 * 4);
     run_start = L.add((pad + nseg) * 8);
     row_pos = L.add((pad + nseg) * 8);
     pre = with_vals ? L.add((pad + nseg) * 8) : 0;
@@ -482,6 +476,37 @@ int sort_segments(ans_ctx* c, const SegPlan& p, uint64_t* ka, uint64_t* kb, uint
                              va ? (even ? vb : va) : nullptr, seg_hist, even ? st0 : st1,
                              even ? st1 : st0, tickets + pass, c->d_err, st));
   }
+  return ANS_OK;
+}
+
+// Column statistics of the segments of `p` (the transpose-free column pass):
+// the stored links (col_ids, vals) are sorted by destination in four 8-bit
+// passes (in -> A -> B -> A -> B) and the destination runs reduced.  Expects
+// k_finish to have filled col_hist and ulen and zeroed st0 and the tickets.
+int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32_t* col_ids,
+                const uint64_t* vals, const PipeScratch& ps, char* m, uint32_t* tickets,
+                ans_quantities* q, cudaStream_t st) {
+  SegPlan cp = p;
+  cp.len = ulen;
+  uint32_t* ka = at<uint32_t>(m, ps.ck_a);
+  uint32_t* kb = at<uint32_t>(m, ps.ck_b);
+  uint64_t* va = at<uint64_t>(m, ps.cv_a);
+  uint64_t* vb = at<uint64_t>(m, ps.cv_b);
+  uint64_t* st0 = at<uint64_t>(m, ps.st0);
+  uint64_t* st1 = at<uint64_t>(m, ps.st1);
+  for (int pass = 0; pass < kColPasses; ++pass) {
+    const uint32_t* kin = pass == 0 ? col_ids : (pass % 2 ? ka : kb);
+    const uint64_t* vin = pass == 0 ? vals : (pass % 2 ? va : vb);
+    uint32_t* kout = pass % 2 ? kb : ka;
+    uint64_t* vout = pass % 2 ? vb : va;
+    ANS_CUDA(timed(c, "onesweep_col", st, [&] {
+      return launch_onesweep_col(cp, pass, kin, kout, vin, vout, at<uint32_t>(m, ps.col_hist),
+                                 pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, tickets + pass, c->d_err, st);
+    }));
+  }
+  ANS_CUDA(timed(c, "colstat", st, [&] {
+    return launch_colstat(cp, kb, vb, at<ColBnd>(m, ps.bnd), q, st);
+  }));
   return ANS_OK;
 }
 
@@ -546,6 +571,8 @@ int sum_pipeline(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_ma
   if ((e = cudaMemsetAsync(seg_hist, 0, kPasses * kRadix * 4, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = cudaMemsetAsync(m + ps.lb, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = cudaMemsetAsync(m + ps.lb2, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = cudaMemsetAsync(m + ps.col_hist, 0, kColPasses * kRadix * 4, st)) != cudaSuccess)
+    return fail_blk(e, "memset");
   if ((e = timed(c, "hist", st, [&] { return launch_hist(s, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); })) != cudaSuccess)
     return fail_blk(e, "hist");
   rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
@@ -571,15 +598,22 @@ int sum_pipeline(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_ma
   a.pre = pre;
   a.lookback = at<uint64_t>(m, ps.lb);
   a.ticket = tickets + kPasses;
-  a.table = (unsigned long long*)c->table_mem;
-  a.table_sum = a.table + c->table_slots;
+  a.col_hist = at<uint32_t>(m, ps.col_hist);
+  a.ulen = at<uint64_t>(m, ps.ulen);
+  a.col_st0 = at<uint64_t>(m, ps.st0);
+  uint32_t* col_tickets = at<uint32_t>(m, ps.tickets) + 3 * 32;
+  a.col_tickets = col_tickets;
   a.err = c->d_err;
   a.mode = kModeSum;
   (void)off_q;
   if ((e = cudaMemsetAsync(blk->q, 0, sizeof(ans_quantities), st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = timed(c, "rle", st, [&] { return launch_rle(a, st); })) != cudaSuccess) return fail_blk(e, "rle");
   if ((e = timed(c, "finish", st, [&] { return launch_finish(a, st); })) != cudaSuccess) return fail_blk(e, "finish");
-  if ((e = timed(c, "col_scan", st, [&] { return launch_col_scan(a, st); })) != cudaSuccess) return fail_blk(e, "col_scan");
+  rc = column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st);
+  if (rc != ANS_OK) {
+    block_discard(blk, st);
+    return rc;
+  }
   *out_blk = blk;
   return ANS_OK;
 }
@@ -665,7 +699,6 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   size_t off_errcap = L.add(8);
 
   ANS_TRY(ensure_scratch(c, L.size, st));
-  ANS_TRY(ensure_table(c, 2 * std::max<uint64_t>(hp.pad, kTile), st));
   char* m = (char*)c->scratch;
 
   Block* blk = nullptr;
@@ -708,6 +741,8 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     if ((rc = cu(cudaMemsetAsync(seg_hist, 0, (size_t)nseg * kPasses * kRadix * 4, st), "memset hist"))) return bail(rc);
     if ((rc = cu(cudaMemsetAsync(sb.q, 0, (size_t)nseg * sizeof(ans_quantities), st), "memset q"))) return bail(rc);
     if ((rc = cu(cudaMemsetAsync(m + ps.lb, 0, (size_t)hp.ntiles * 8, st), "memset lb"))) return bail(rc);
+    if ((rc = cu(cudaMemsetAsync(m + ps.col_hist, 0, (size_t)nseg * kColPasses * kRadix * 4, st), "memset")))
+      return bail(rc);
     if ((rc = cu(timed(c, "pack_hist", st, [&] { return launch_pack_hist(p, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); }), "pack")))
       return bail(rc);
     if ((rc = sort_segments(c, p, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
@@ -727,14 +762,16 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     a.pre = nullptr;
     a.lookback = at<uint64_t>(m, ps.lb);
     a.ticket = tickets + kPasses;
-    a.table = (unsigned long long*)c->table_mem;
-    a.table_sum = a.table + c->table_slots;
+    a.col_hist = at<uint32_t>(m, ps.col_hist);
+    a.ulen = at<uint64_t>(m, ps.ulen);
+    a.col_st0 = at<uint64_t>(m, ps.st0);
+    a.col_tickets = tickets + 2 * 32;
     a.err = c->d_err;
     a.mode = kModeWindow;
     if ((rc = cu(timed(c, "empty_fixup", st, [&] { return launch_empty_fixup(a, st); }), "empty"))) return bail(rc);
     if ((rc = cu(timed(c, "rle", st, [&] { return launch_rle(a, st); }), "rle"))) return bail(rc);
     if ((rc = cu(timed(c, "finish", st, [&] { return launch_finish(a, st); }), "finish"))) return bail(rc);
-    if ((rc = cu(timed(c, "col_scan", st, [&] { return launch_col_scan(a, st); }), "col_scan"))) return bail(rc);
+    if ((rc = column_pass(c, p, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, st))) return bail(rc);
   }
 
   Block* sblk = nullptr;
@@ -872,7 +909,6 @@ int ans_ctx_destroy(ans_ctx* c) {
   cudaDeviceSynchronize();
   for (auto& kv : c->tickets) cudaEventDestroy(kv.second.ev);
   dev_free(c, c->scratch, c->scratch_size, c->aux);
-  dev_free(c, c->table_mem, table_bytes(c->table_slots), c->aux);
   dev_free(c, c->small_mem, 256, c->aux);
   cudaStreamSynchronize(c->aux);
   for (auto& s : c->stage) {
@@ -954,7 +990,6 @@ int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_mat
     const size_t off_total = L.add(8);
     const size_t off_sq = L.add(sizeof(ans_quantities));
     ANS_TRY(ensure_scratch(c, L.size, st));
-    ANS_TRY(ensure_table(c, 2 * std::max<uint64_t>(sp.pad, kTile), st));
     char* m = (char*)c->scratch;
     ANS_TRY(upload(c, m + off_mats, md.data(), k * sizeof(MatDesc), st));
     ANS_TRY(sum_pipeline(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, caps, off_gplan, off_splan, off_catoff,
@@ -989,10 +1024,10 @@ int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out,
   dp.reserve(L, 1);
   const size_t off_pre = L.add((hp.pad + 1) * 8);
   const size_t off_lb = L.add((size_t)std::max<uint32_t>(hp.ntiles, 1) * 8);
-  const size_t off_tk = L.add(64 * 4);
   const size_t off_q = L.add(sizeof(ans_quantities));
+  PipeScratch ps;
+  ps.reserve(L, hp.pad, 1, std::max<uint32_t>(hp.ntiles, 1), false);
   ANS_TRY(ensure_scratch(c, L.size, st));
-  ANS_TRY(ensure_table(c, 2 * std::max<uint64_t>(hp.pad, kTile), st));
   char* m = (char*)c->scratch;
   ANS_TRY(upload(c, m + dp.base, hp.base.data(), 8, st));
   ANS_TRY(upload(c, m + dp.first_tile, hp.first_tile.data(), 8, st));
@@ -1000,12 +1035,14 @@ int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out,
   uint64_t* hdr = b->hdr + 2 * (size_t)x->seg;
   p.len = hdr + 1;  // nnz, on the device
   ans_quantities* q = at<ans_quantities>(m, off_q);
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets);
   ANS_CUDA(cudaMemsetAsync(q, 0, sizeof(ans_quantities), st));
   ANS_CUDA(cudaMemsetAsync(m + off_lb, 0, (size_t)std::max<uint32_t>(hp.ntiles, 1) * 8, st));
-  ANS_CUDA(cudaMemsetAsync(m + off_tk, 0, 64 * 4, st));
+  ANS_CUDA(cudaMemsetAsync(tickets, 0, 32 * 4, st));
+  ANS_CUDA(cudaMemsetAsync(m + ps.col_hist, 0, kColPasses * kRadix * 4, st));
   uint64_t* pre = at<uint64_t>(m, off_pre);
   if (hp.ntiles) {
-    ANS_CUDA(timed(c, "scan_u64", st, [&] { return launch_scan_u64(p, b->vals + bs, pre, at<uint64_t>(m, off_lb), at<uint32_t>(m, off_tk), c->d_err, st); }));
+    ANS_CUDA(timed(c, "scan_u64", st, [&] { return launch_scan_u64(p, b->vals + bs, pre, at<uint64_t>(m, off_lb), tickets, c->d_err, st); }));
     StatsArgs a;
     a.plan = p;
     a.hdr = hdr;
@@ -1015,12 +1052,14 @@ int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out,
     a.row_ids = b->row_ids + bs;
     a.row_ptr = b->row_ptr + bs + x->seg;
     a.pre = pre;
-    a.table = (unsigned long long*)c->table_mem;
-    a.table_sum = a.table + c->table_slots;
+    a.col_hist = at<uint32_t>(m, ps.col_hist);
+    a.ulen = at<uint64_t>(m, ps.ulen);
+    a.col_st0 = at<uint64_t>(m, ps.st0);
+    a.col_tickets = tickets + 32;
     a.err = c->d_err;
     a.mode = kModeMatrix;
     ANS_CUDA(timed(c, "finish", st, [&] { return launch_finish(a, st); }));
-    ANS_CUDA(timed(c, "col_scan", st, [&] { return launch_col_scan(a, st); }));
+    ANS_TRY(column_pass(c, p, a.ulen, a.col_ids, a.vals, ps, m, a.col_tickets, q, st));
   }
   ANS_CUDA(cudaMemsetAsync(c->d_err, 0, 4, st));
   ANS_TRY(copy_quantities_out(out, q, 1, st));

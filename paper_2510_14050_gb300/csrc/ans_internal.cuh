@@ -26,6 +26,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kPasses = 64 / kRadixBits;       // LSD passes over a 64-bit key
+constexpr int kColPasses = 32 / kRadixBits;    // LSD passes over a 32-bit destination key
 
 // Look-back status word: 2 flag bits over a 62-bit value.
 constexpr uint64_t kFlagAgg = 1ull << 62;      // tile aggregate available
@@ -35,7 +36,6 @@ constexpr uint32_t kSpinLimit = 1u << 20;      // polls (about 1 s) before a wai
 
 enum ErrBits : uint32_t {
   kErrLookback = 1u,   // a look-back wait hit kSpinLimit
-  kErrHashFull = 2u,   // a hash probe sequence exceeded the table
 };
 
 // One entry per segment; device pointers.
@@ -63,8 +63,10 @@ struct StatsArgs {
   const uint64_t* pre = nullptr;  // exclusive value prefix at base[s] + s; null = identity
   uint64_t* lookback = nullptr;   // [ntiles] status words (zeroed)
   uint32_t* ticket = nullptr;     // zeroed counter
-  unsigned long long* table = nullptr;  // column hash slots, 2 per padded item, all zero on entry
-  unsigned long long* table_sum = nullptr;
+  uint32_t* col_hist = nullptr;   // [nseg][kColPasses][kRadix] destination digit counts, zero on entry
+  uint64_t* ulen = nullptr;       // [nseg] links per segment (written for the column sort)
+  uint64_t* col_st0 = nullptr;    // first column pass's status words (zeroed here)
+  uint32_t* col_tickets = nullptr;  // the column passes' tickets (zeroed here)
   uint32_t* err = nullptr;
   int mode = 0;
 };
@@ -73,6 +75,13 @@ enum StatsMode : int {
   kModeWindow = 0,  // vals = run lengths; row sums = packets per row
   kModeSum = 1,     // vals = sums of sorted input values; pre = their prefix
   kModeMatrix = 2,  // vals given; run_start identity; row_pos = row_ptr
+};
+
+// Per-tile summary of the column runs that touch the tile's boundaries.
+struct ColBnd {
+  uint64_t lead_len, lead_sum;  // items before the tile's first head (all items if it has none)
+  uint64_t tail_len, tail_sum;  // from the tile's last head to its end
+  uint32_t has_head, pad;
 };
 
 // Matrix descriptor for the time-sum gather.
@@ -101,6 +110,11 @@ cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uin
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                             uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
                             uint32_t* err, cudaStream_t st);
+// One digit pass over 32-bit destination keys carrying uint64 counts.
+cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
+                                const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
+                                uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
+                                cudaStream_t st);
 // Gather the stored links of k matrices into (key, value) pairs.
 cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,
                           uint64_t* keys, uint64_t* vals, cudaStream_t st);
@@ -116,10 +130,14 @@ cudaError_t launch_rle(const StatsArgs& a, cudaStream_t st);
 // Exclusive prefix of uint64 values per segment (len + 1 entries at base+s).
 cudaError_t launch_scan_u64(const SegPlan& p, const uint64_t* in, uint64_t* out,
                             uint64_t* lookback, uint32_t* ticket, uint32_t* err, cudaStream_t st);
-// Values, row statistics, link maximum and the column hash inserts.
+// Values, row statistics, link maximum, and the destination digit histograms
+// for the column pass.
 cudaError_t launch_finish(const StatsArgs& a, cudaStream_t st);
-// Column statistics from the hash table; clears the table behind itself.
-cudaError_t launch_col_scan(const StatsArgs& a, cudaStream_t st);
+// Column statistics from destination-sorted (dst, count) pairs of the
+// segments of `p` (p.len = links per segment): unique destinations, max
+// fan-in, max destination packets.  bnd holds one record per tile.
+cudaError_t launch_colstat(const SegPlan& p, const uint32_t* keys, const uint64_t* vals, ColBnd* bnd,
+                           ans_quantities* q, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.
 cudaError_t launch_empty_fixup(const StatsArgs& a, cudaStream_t st);
 

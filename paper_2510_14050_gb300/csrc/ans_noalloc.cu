@@ -13,7 +13,7 @@
 // Limits and sharing:
 //  * at most kNoAllocMaxPackets (65,536) packets per call; larger windows are
 //    rejected with ANS_ERR_INVALID_ARG;
-//  * the array (kNoAllocBytes, about 5.6 MiB) exists on every GPU that loads
+//  * the array (kNoAllocBytes, about 5 MiB) exists on every GPU that loads
 //    the library and is held until the process exits;
 //  * every call uses the same array, and the array keeps the previous call's
 //    contents: the call clears what must start at zero itself, and calls
@@ -48,7 +48,7 @@ constexpr size_t oSt0 = al(oHist + (size_t)kPasses * kRadix * 4);
 constexpr size_t oSt1 = al(oSt0 + (size_t)kNoAllocTiles * kRadix * 8);
 constexpr size_t oLb = al(oSt1 + (size_t)kNoAllocTiles * kRadix * 8);
 constexpr size_t oTickets = al(oLb + (size_t)kNoAllocTiles * 8);
-constexpr size_t oRunStart = al(oTickets + 64 * 4);
+constexpr size_t oRunStart = al(oTickets + 128 * 4);
 constexpr size_t oRowPos = al(oRunStart + (kNoAllocMaxPackets + 1) * 8);
 constexpr size_t oColIds = al(oRowPos + (kNoAllocMaxPackets + 1) * 8);
 constexpr size_t oVals = al(oColIds + kNoAllocMaxPackets * 4);
@@ -57,9 +57,14 @@ constexpr size_t oRowPtr = al(oRowIds + kNoAllocMaxPackets * 4);
 constexpr size_t oHdr = al(oRowPtr + (kNoAllocMaxPackets + 1) * 8);
 constexpr size_t oQ = al(oHdr + 16);
 constexpr size_t oErr = al(oQ + sizeof(ans_quantities));
-constexpr size_t oTable = al(oErr + 8);                            // 2 slots per packet, then their sums
-constexpr size_t kTableSlots = 2 * kNoAllocMaxPackets;
-constexpr size_t kNoAllocBytes = al(oTable + kTableSlots * 16);
+constexpr size_t oColHist = al(oErr + 8);                          // destination digit counts
+constexpr size_t oUlen = al(oColHist + (size_t)kColPasses * kRadix * 4);
+constexpr size_t oCkA = al(oUlen + 8);                             // destination-sort ping-pong
+constexpr size_t oCkB = al(oCkA + kNoAllocMaxPackets * 4);
+constexpr size_t oCvA = al(oCkB + kNoAllocMaxPackets * 4);
+constexpr size_t oCvB = al(oCvA + kNoAllocMaxPackets * 8);
+constexpr size_t oBnd = al(oCvB + kNoAllocMaxPackets * 8);
+constexpr size_t kNoAllocBytes = al(oBnd + (size_t)kNoAllocTiles * sizeof(ColBnd));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -127,9 +132,7 @@ extern "C" int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32
   if (ntiles) {
     if ((rc = cu(cudaMemsetAsync(m + oHist, 0, (size_t)kPasses * kRadix * 4, st), "memset"))) return rc;
     if ((rc = cu(cudaMemsetAsync(m + oLb, 0, (size_t)ntiles * 8, st), "memset"))) return rc;
-    const size_t used_slots = (size_t)2 * ntiles * kTile;  // column-table slots this window may touch
-    if ((rc = cu(cudaMemsetAsync(m + oTable, 0, used_slots * 8, st), "memset"))) return rc;
-    if ((rc = cu(cudaMemsetAsync(m + oTable + kTableSlots * 8, 0, used_slots * 8, st), "memset"))) return rc;
+    if ((rc = cu(cudaMemsetAsync(m + oColHist, 0, (size_t)kColPasses * kRadix * 4, st), "memset"))) return rc;
     k_noalloc_plan<<<1, 32, 0, st>>>(n, ntiles);
     if ((rc = cu(cudaGetLastError(), "plan"))) return rc;
     SegPlan p;
@@ -168,13 +171,30 @@ extern "C" int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32
     a.pre = nullptr;
     a.lookback = reinterpret_cast<uint64_t*>(m + oLb);
     a.ticket = tickets + kPasses;
-    a.table = reinterpret_cast<unsigned long long*>(m + oTable);
-    a.table_sum = a.table + kTableSlots;
+    a.col_hist = reinterpret_cast<uint32_t*>(m + oColHist);
+    a.ulen = reinterpret_cast<uint64_t*>(m + oUlen);
+    a.col_st0 = st0;
+    a.col_tickets = tickets + 32;
     a.err = err;
     a.mode = kModeWindow;
     if ((rc = cu(launch_rle(a, st), "rle"))) return rc;
     if ((rc = cu(launch_finish(a, st), "finish"))) return rc;
-    if ((rc = cu(launch_col_scan(a, st), "col_scan"))) return rc;
+    // Column statistics: sort the stored links by destination, reduce the runs.
+    SegPlan cp = p;
+    cp.len = a.ulen;
+    uint32_t* cka = reinterpret_cast<uint32_t*>(m + oCkA);
+    uint32_t* ckb = reinterpret_cast<uint32_t*>(m + oCkB);
+    uint64_t* cva = reinterpret_cast<uint64_t*>(m + oCvA);
+    uint64_t* cvb = reinterpret_cast<uint64_t*>(m + oCvB);
+    for (int pass = 0; pass < kColPasses; ++pass) {
+      const uint32_t* kin = pass == 0 ? a.col_ids : (pass % 2 ? cka : ckb);
+      const uint64_t* vin = pass == 0 ? a.vals : (pass % 2 ? cva : cvb);
+      if ((rc = cu(launch_onesweep_col(cp, pass, kin, pass % 2 ? ckb : cka, vin, pass % 2 ? cvb : cva, a.col_hist,
+                                       pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, a.col_tickets + pass, err, st),
+                   "onesweep_col")))
+        return rc;
+    }
+    if ((rc = cu(launch_colstat(cp, ckb, cvb, reinterpret_cast<ColBnd*>(m + oBnd), q, st), "colstat"))) return rc;
   }
   if ((rc = cu(cudaMemcpyAsync(d_out, q, sizeof(ans_quantities), cudaMemcpyDefault, st), "copy out"))) return rc;
   if (d_status && (rc = cu(cudaMemcpyAsync(d_status, err, 4, cudaMemcpyDefault, st), "copy status"))) return rc;

@@ -1,12 +1,15 @@
-// Segmented onesweep LSD radix sort of packed 64-bit link keys (src << 32 | dst).
+// Segmented onesweep LSD radix sorts.
 //
 // Building a traffic matrix A(i, j) = #packets i -> j (Table I caption) from
 // raw packets means grouping equal (src, dst) pairs; sorting the packed key
-// puts equal links next to each other in DCSR order (rows = sources
-// ascending, columns ascending within a row, Sec. IV-B).
+// src << 32 | dst puts equal links next to each other in DCSR order (rows =
+// sources ascending, columns ascending within a row, Sec. IV-B).  The column
+// statistics (Table I: unique destinations, max fan-in; Sec. IV-C: max
+// destination packets) group the stored links by destination instead: a sort
+// of 32-bit destination keys carrying the link counts.
 //
 // Design (sm_103a):
-//  * one histogram sweep builds the digit counts of all 8 passes for every
+//  * one histogram sweep builds the digit counts of every pass for every
 //    segment at once (shared-memory counters; lanes holding identical keys
 //    are merged with __match_any_sync first, which matters for Zipf traffic
 //    where a few links dominate);
@@ -17,6 +20,8 @@
 //    writes runs of equal digits to contiguous addresses;
 //  * loads of the raw (src, dst) stream are 128-bit when the window is
 //    16-byte aligned.
+#include <type_traits>
+
 #include "ans_internal.cuh"
 
 namespace ans {
@@ -122,16 +127,29 @@ __global__ void __launch_bounds__(kThreads) k_hist(SegPlan p, const uint64_t* __
   hist_flush(h, seg_hist, tl.seg);
 }
 
-template <bool kVals>
+struct NoVal {};
+
+template <typename K, typename V>
+constexpr size_t onesweep_smem_bytes() {
+  return (size_t)kTile * sizeof(K) + (std::is_same<V, NoVal>::value ? 0 : (size_t)kTile * sizeof(V)) +
+         (size_t)kWarps * (kRadix + 1) * 4;
+}
+
+// One stable digit pass over keys of type K (8 passes for 64-bit keys, 4 for
+// 32-bit keys; seg_hist holds sizeof(K) histograms per segment), optionally
+// carrying values of type V.
+template <typename K, typename V>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_onesweep(SegPlan p, int pass, const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
-               const uint64_t* __restrict__ vin, uint64_t* __restrict__ vout,
-               const uint32_t* __restrict__ seg_hist, uint64_t* st_cur, uint64_t* __restrict__ st_next,
-               uint32_t* ticket, uint32_t* err) {
+    k_onesweep(SegPlan p, int pass, const K* __restrict__ kin, K* __restrict__ kout,
+               const V* __restrict__ vin, V* __restrict__ vout, const uint32_t* __restrict__ seg_hist,
+               uint64_t* st_cur, uint64_t* __restrict__ st_next, uint32_t* ticket, uint32_t* err) {
+  constexpr bool kVals = !std::is_same<V, NoVal>::value;
+  constexpr int kNumPasses = (int)sizeof(K);
   extern __shared__ __align__(16) uint8_t smem[];
-  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* s_vals = s_keys + kTile;
-  uint32_t* s_wc = reinterpret_cast<uint32_t*>(s_keys + (kVals ? 2 : 1) * kTile);  // [kWarps][kRadix+1]
+  K* s_keys = reinterpret_cast<K*>(smem);
+  V* s_vals = reinterpret_cast<V*>(smem + (size_t)kTile * sizeof(K));
+  uint32_t* s_wc = reinterpret_cast<uint32_t*>(smem + (size_t)kTile * sizeof(K) +
+                                               (kVals ? (size_t)kTile * sizeof(V) : 0));  // [kWarps][kRadix+1]
   __shared__ uint64_t s_gofs[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
   __shared__ uint32_t s_tmp[8];
@@ -151,15 +169,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const uint64_t g0 = tl.base + tl.start;
   const uint32_t wbase = warp * (kPerThread * 32);
-  uint64_t k[kPerThread];
-  uint64_t v[kVals ? kPerThread : 1];
+  K k[kPerThread];
+  V v[kVals ? kPerThread : 1];
   uint32_t r[kPerThread];
 #pragma unroll
   for (int i = 0; i < kPerThread; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
     const bool valid = idx < tl.count;
-    k[i] = valid ? kin[g0 + idx] : 0ull;
-    if (kVals) v[i] = valid ? vin[g0 + idx] : 0ull;
+    k[i] = valid ? kin[g0 + idx] : K(0);
+    if constexpr (kVals) v[i] = valid ? vin[g0 + idx] : V(0);
   }
   // Stable rank inside (warp, digit): lanes with equal digits are merged by
   // match_any; the lowest lane updates the warp's counter.
@@ -201,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   const uint32_t dstart = scan256_excl(d < kRadix ? cnt : 0u, s_tmp, nullptr);
-  const uint32_t hv = d < kRadix ? seg_hist[((size_t)tl.seg * kPasses + pass) * kRadix + d] : 0u;
+  const uint32_t hv = d < kRadix ? seg_hist[((size_t)tl.seg * kNumPasses + pass) * kRadix + d] : 0u;
   const uint32_t bstart = scan256_excl(hv, s_tmp, nullptr);
   if (d < kRadix) {
     s_dstart[d] = dstart;
@@ -216,15 +234,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t dg = (uint32_t)(k[i] >> shift) & 0xffu;
       const uint32_t pos = s_dstart[dg] + wc[dg] + r[i];
       s_keys[pos] = k[i];
-      if (kVals) s_vals[pos] = v[i];
+      if constexpr (kVals) s_vals[pos] = v[i];
     }
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < tl.count; i += kThreads) {
-    const uint64_t key = s_keys[i];
-    const uint64_t o = s_gofs[(key >> shift) & 0xffu] + i;
+    const K key = s_keys[i];
+    const uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
     kout[o] = key;
-    if (kVals) vout[o] = s_vals[i];
+    if constexpr (kVals) vout[o] = s_vals[i];
   }
 }
 
@@ -293,11 +311,33 @@ __global__ void __launch_bounds__(1024) k_count_prefix(const MatDesc* __restrict
   if (threadIdx.x == 0) *total = s_carry;
 }
 
-}  // namespace
-
-static size_t onesweep_smem(bool vals) {
-  return (size_t)kTile * sizeof(uint64_t) * (vals ? 2 : 1) + (size_t)kWarps * (kRadix + 1) * 4;
+// Dynamic shared memory is configured once per kernel instance and device.
+template <typename K, typename V>
+cudaError_t configure_onesweep() {
+  static unsigned long long done = 0;  // one bit per device ordinal
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_onesweep<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem_bytes<K, V>());
+  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  return e;
 }
+
+template <typename K, typename V>
+cudaError_t run_onesweep(const SegPlan& p, int pass, const K* kin, K* kout, const V* vin, V* vout,
+                         const uint32_t* seg_hist, uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
+                         uint32_t* err, cudaStream_t st) {
+  if (p.ntiles == 0) return cudaSuccess;
+  cudaError_t e = configure_onesweep<K, V>();
+  if (e != cudaSuccess) return e;
+  k_onesweep<K, V><<<p.ntiles, kThreads, onesweep_smem_bytes<K, V>(), st>>>(p, pass, kin, kout, vin, vout,
+                                                                           seg_hist, st_cur, st_next, ticket, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32_t* dst,
                              uint64_t* keys, uint32_t* seg_hist, uint64_t* status0, uint32_t* tickets,
@@ -318,27 +358,19 @@ cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uin
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                             uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
                             cudaStream_t st) {
-  if (p.ntiles == 0) return cudaSuccess;
-  static unsigned long long configured = 0;  // one bit per device ordinal
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 64 || !((configured >> dev) & 1ull)) {
-    cudaError_t e = cudaFuncSetAttribute(k_onesweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)onesweep_smem(false));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_onesweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)onesweep_smem(true));
-    if (e != cudaSuccess) return e;
-    if (dev < 64) configured |= 1ull << dev;
-  }
   if (vin)
-    k_onesweep<true><<<p.ntiles, kThreads, onesweep_smem(true), st>>>(p, pass, kin, kout, vin, vout,
-                                                                      seg_hist, st_cur, st_next,
-                                                                      ticket, err);
-  else
-    k_onesweep<false><<<p.ntiles, kThreads, onesweep_smem(false), st>>>(
-        p, pass, kin, kout, nullptr, nullptr, seg_hist, st_cur, st_next, ticket, err);
-  return cudaGetLastError();
+    return run_onesweep<uint64_t, uint64_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket,
+                                            err, st);
+  return run_onesweep<uint64_t, NoVal>(p, pass, kin, kout, (const NoVal*)nullptr, (NoVal*)nullptr, seg_hist,
+                                       st_cur, st_next, ticket, err, st);
+}
+
+cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
+                                const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
+                                uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
+                                cudaStream_t st) {
+  return run_onesweep<uint32_t, uint64_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err,
+                                          st);
 }
 
 cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,

@@ -10,12 +10,14 @@
 //  * k_scan_u64: exclusive prefix of uint64 values (time sums, imported
 //    matrices), same look-back scheme.
 //  * k_finish: link values A(i,j) (Table I), the link maximum, per-row
-//    nonzero counts (fan-out) and packet sums (Sec. IV-C), and the
-//    transpose-free column pass: every stored link adds (1, A(i,j)) to its
-//    destination's slot in an open-addressing table keyed on dst.
-//  * k_col_scan: unique destinations, max fan-in and max destination packets
-//    from the table; each slot is cleared as it is read, so the table is all
-//    zero again for the next call without a memset.
+//    nonzero counts (fan-out) and packet sums (Sec. IV-C); it also builds the
+//    digit histograms of the destination keys for the column sort.
+//  * k_colstat / k_colstat_fin: the transpose-free column pass.  Once the
+//    stored links are sorted by destination (32-bit keys carrying the link
+//    counts), every run of equal destinations is one column: its length is the
+//    fan-in and its value sum the destination's packets (Table I, Sec. IV-C).
+//    Runs inside a tile are reduced in place; runs that cross tiles are
+//    completed from per-tile boundary records.
 // Maxima are combined with 64-bit atomicMax; every value is an exact integer.
 #include "ans_internal.cuh"
 
@@ -195,56 +197,23 @@ __global__ void __launch_bounds__(kThreads) k_scan_u64(SegPlan p, const uint64_t
   }
 }
 
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
-}
-
-// Capacity of a segment's column table: load factor <= 1/2.
-__device__ __forceinline__ uint64_t table_cap(uint64_t nnz, uint32_t seg_tiles) {
-  return umin64(2 * nnz + 64, 2ull * seg_tiles * kTile);
-}
-
-// Slot word = dst << 32 | (number of links into dst); 0 = empty (every
-// occupied slot has at least one link, so the low half is never 0).
-__device__ __forceinline__ void col_insert(unsigned long long* table, unsigned long long* sums,
-                                           uint64_t cap, uint32_t dst, uint64_t v, uint32_t* err) {
-  uint64_t i = ((uint64_t)fmix32(dst) * cap) >> 32;
-  const unsigned long long want = ((unsigned long long)dst << 32) | 1ull;
-  for (uint64_t probe = 0; probe < cap; ++probe) {
-    unsigned long long w = ld_relaxed(reinterpret_cast<const uint64_t*>(table + i));
-    if (w == 0ull) {
-      w = atomicCAS(table + i, 0ull, want);
-      if (w == 0ull) {
-        atomicAdd(sums + i, (unsigned long long)v);
-        return;
-      }
-    }
-    if ((uint32_t)(w >> 32) == dst) {
-      atomicAdd(table + i, 1ull);
-      atomicAdd(sums + i, (unsigned long long)v);
-      return;
-    }
-    if (++i == cap) i = 0;
-  }
-  atomicOr(err, (uint32_t)kErrHashFull);
-}
-
 template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
   __shared__ Tile s_tile;
   __shared__ uint64_t s_red[3][kWarps];
-  const Tile tl = block_tile(a.plan, blockIdx.x, &s_tile);
+  __shared__ uint32_t s_h[kColPasses * kRadix];
+  const uint32_t t = blockIdx.x;
+  const Tile tl = block_tile(a.plan, t, &s_tile);
   const uint32_t s = tl.seg;
   const uint64_t nrows = a.hdr[2 * s], nnz = a.hdr[2 * s + 1];
   const uint64_t bs = tl.base + s;
-  const uint64_t cap = table_cap(nnz, tl.seg_tiles);
-  unsigned long long* table = a.table + 2 * tl.base;
-  unsigned long long* tsum = a.table_sum + 2 * tl.base;
+  for (int i = threadIdx.x; i < kColPasses * kRadix; i += kThreads) s_h[i] = 0;
+  // Prepare the column sort: its first-pass status words, its tickets and
+  // the number of links per segment.
+  if (t == 0 && threadIdx.x < 32) a.col_tickets[threadIdx.x] = 0;
+  if (threadIdx.x < kRadix) a.col_st0[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  if (tl.j == 0 && threadIdx.x == 0) a.ulen[s] = nnz;
+  __syncthreads();
 
   auto P = [&](uint64_t x) -> uint64_t { return a.pre ? a.pre[bs + x] : x; };
 
@@ -259,7 +228,9 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
       a.vals[tl.base + u] = v;
     }
     mlink = v > mlink ? v : mlink;
-    col_insert(table, tsum, cap, a.col_ids[tl.base + u], v, a.err);
+    const uint32_t dst = a.col_ids[tl.base + u];
+#pragma unroll
+    for (int p = 0; p < kColPasses; ++p) atomicAdd(&s_h[p * kRadix + ((dst >> (p * kRadixBits)) & 0xffu)], 1u);
   }
   const uint64_t r_end = umin64(tl.start + kTile, nrows);
   for (uint64_t r = tl.start + threadIdx.x; r < r_end; r += kThreads) {
@@ -279,6 +250,11 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
     s_red[2][warp] = mrow;
   }
   __syncthreads();
+  uint32_t* gh = a.col_hist + (size_t)s * kColPasses * kRadix;
+  for (int i = threadIdx.x; i < kColPasses * kRadix; i += kThreads) {
+    const uint32_t c = s_h[i];
+    if (c) atomicAdd(&gh[i], c);
+  }
   if (threadIdx.x == 0) {
     for (int w = 1; w < kWarps; ++w) {
       mlink = umax64(mlink, s_red[0][w]);
@@ -298,51 +274,181 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_col_scan(StatsArgs a) {
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = 0;
+  for (int w = 0; w < kWarps; ++w) s += red[w];
+  return s;
+}
+
+// Column runs inside one tile of destination-sorted (dst, count) pairs.
+// Each thread scans 16 consecutive pairs; a run that crosses thread chunks is
+// completed by the thread holding its successor head, walking back over the
+// chunks without heads.  Runs that cross the tile boundary are summarised in
+// bnd[t] (leading part, trailing part) for k_colstat_fin.
+__global__ void __launch_bounds__(kThreads) k_colstat(SegPlan p, const uint32_t* __restrict__ keys,
+                                                      const uint64_t* __restrict__ vals,
+                                                      ColBnd* __restrict__ bnd, ans_quantities* q) {
   __shared__ Tile s_tile;
-  __shared__ uint64_t s_red[3][kWarps];
-  const Tile tl = block_tile(a.plan, blockIdx.x, &s_tile);
-  const uint32_t s = tl.seg;
-  const uint64_t nnz = a.hdr[2 * s + 1];
-  const uint64_t cap = table_cap(nnz, tl.seg_tiles);
-  unsigned long long* table = a.table + 2 * tl.base;
-  unsigned long long* tsum = a.table_sum + 2 * tl.base;
-  uint64_t c = 0, mfan = 0, mpk = 0;
-  if (nnz > 0) {
-    const uint64_t s0 = 2 * tl.start, s1 = umin64(s0 + 2 * kTile, cap);
-    for (uint64_t i = s0 + threadIdx.x; i < s1; i += kThreads) {
-      const unsigned long long w = table[i];
-      if (w) {
-        const uint64_t pk = tsum[i];
-        ++c;
-        mfan = umax64(mfan, w & 0xffffffffull);
-        mpk = umax64(mpk, pk);
-        table[i] = 0ull;
-        tsum[i] = 0ull;
+  __shared__ uint64_t s_ll[kThreads], s_ls[kThreads], s_tl[kThreads], s_ts[kThreads];
+  __shared__ uint32_t s_has[kThreads];
+  __shared__ uint64_t s_red[kWarps];
+  __shared__ int s_first, s_last;
+  const uint32_t t = blockIdx.x;
+  const Tile tl = block_tile(p, t, &s_tile);
+  if (tl.count == 0) return;
+  const uint64_t g0 = tl.base + tl.start;
+  const uint32_t i0 = threadIdx.x * kPerThread;
+  const uint32_t n = i0 < tl.count ? min((uint32_t)kPerThread, tl.count - i0) : 0u;
+  uint64_t lead_len = 0, lead_sum = 0, cur_len = 0, cur_sum = 0, mlen = 0, msum = 0;
+  uint32_t heads = 0;
+  bool has_head = false;
+  if (n > 0) {
+    bool has_prev = (tl.start + i0) > 0;
+    uint32_t prev = has_prev ? keys[g0 + i0 - 1] : 0u;
+    for (uint32_t e = 0; e < n; ++e) {
+      const uint32_t k = keys[g0 + i0 + e];
+      const uint64_t v = vals[g0 + i0 + e];
+      const bool head = !has_prev || k != prev;
+      has_prev = true;
+      prev = k;
+      if (head) {
+        if (has_head) {
+          mlen = umax64(mlen, cur_len);
+          msum = umax64(msum, cur_sum);
+        } else {
+          lead_len = cur_len;
+          lead_sum = cur_sum;
+        }
+        has_head = true;
+        ++heads;
+        cur_len = 1;
+        cur_sum = v;
+      } else {
+        ++cur_len;
+        cur_sum += v;
       }
     }
+    if (!has_head) {
+      lead_len = cur_len;
+      lead_sum = cur_sum;
+      cur_len = 0;
+      cur_sum = 0;
+    }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  c = warp_sum(c);
-  mfan = warp_max(mfan);
-  mpk = warp_max(mpk);
-  if (lane == 0) {
-    s_red[0][warp] = c;
-    s_red[1][warp] = mfan;
-    s_red[2][warp] = mpk;
+  s_ll[threadIdx.x] = lead_len;
+  s_ls[threadIdx.x] = lead_sum;
+  s_tl[threadIdx.x] = cur_len;
+  s_ts[threadIdx.x] = cur_sum;
+  s_has[threadIdx.x] = has_head ? 1u : 0u;
+  if (threadIdx.x == 0) {
+    s_first = kThreads;
+    s_last = -1;
+  }
+  __syncthreads();
+  if (has_head) {
+    atomicMin(&s_first, (int)threadIdx.x);
+    atomicMax(&s_last, (int)threadIdx.x);
+    // The run that ends just before this chunk's first head.
+    uint64_t L = lead_len, S = lead_sum;
+    int u = (int)threadIdx.x - 1;
+    for (; u >= 0; --u) {
+      if (s_has[u]) {
+        L += s_tl[u];
+        S += s_ts[u];
+        break;
+      }
+      L += s_ll[u];
+      S += s_ls[u];
+    }
+    if (u >= 0) {  // it began inside this tile; otherwise it is the tile's leading run
+      mlen = umax64(mlen, L);
+      msum = umax64(msum, S);
+    }
+  }
+  __syncthreads();
+  const int hf = s_first, hl = s_last;
+  const int me = (int)threadIdx.x;
+  // Leading run of the tile: chunks up to (and including the lead of) the first head.
+  const uint64_t pl = me <= hf ? s_ll[me] : 0ull, ps = me <= hf ? s_ls[me] : 0ull;
+  // Trailing run: the last head's run plus the headless chunks after it.
+  const uint64_t ql = hl < 0 ? 0ull : (me == hl ? s_tl[me] : (me > hl ? s_ll[me] : 0ull));
+  const uint64_t qs = hl < 0 ? 0ull : (me == hl ? s_ts[me] : (me > hl ? s_ls[me] : 0ull));
+  const uint64_t lead_l = block_sum(pl, s_red);
+  const uint64_t lead_s = block_sum(ps, s_red);
+  const uint64_t tail_l = block_sum(ql, s_red);
+  const uint64_t tail_s = block_sum(qs, s_red);
+  const uint64_t nheads = block_sum((uint64_t)heads, s_red);
+  mlen = warp_max(mlen);
+  msum = warp_max(msum);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    s_ll[threadIdx.x >> 5] = mlen;
+    s_ls[threadIdx.x >> 5] = msum;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < kWarps; ++w) {
-      c += s_red[0][w];
-      mfan = umax64(mfan, s_red[1][w]);
-      mpk = umax64(mpk, s_red[2][w]);
+      mlen = umax64(mlen, s_ll[w]);
+      msum = umax64(msum, s_ls[w]);
     }
-    ans_quantities* q = a.q + s;
-    if (c) atomicAdd((unsigned long long*)&q->unique_destinations, (unsigned long long)c);
-    if (mfan) atomicMax((unsigned long long*)&q->max_destination_fanin, (unsigned long long)mfan);
-    if (mpk) atomicMax((unsigned long long*)&q->max_destination_packets, (unsigned long long)mpk);
+    ColBnd b;
+    b.lead_len = lead_l;
+    b.lead_sum = lead_s;
+    b.tail_len = tail_l;
+    b.tail_sum = tail_s;
+    b.has_head = hl >= 0 ? 1u : 0u;
+    b.pad = 0;
+    bnd[t] = b;
+    ans_quantities* qq = q + tl.seg;
+    if (nheads) atomicAdd((unsigned long long*)&qq->unique_destinations, (unsigned long long)nheads);
+    if (mlen) atomicMax((unsigned long long*)&qq->max_destination_fanin, (unsigned long long)mlen);
+    if (msum) atomicMax((unsigned long long*)&qq->max_destination_packets, (unsigned long long)msum);
   }
+}
+
+// Complete the column runs that cross tile boundaries: the run ending just
+// before a tile's first head, and the run ending at the segment's end.
+__global__ void k_colstat_fin(SegPlan p, const ColBnd* __restrict__ bnd, ans_quantities* q) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.ntiles) return;
+  const Tile tl = make_tile(p, t);
+  if (tl.count == 0) return;
+  const ColBnd b = bnd[t];
+  const uint32_t first = t - tl.j;
+  uint64_t mlen = 0, msum = 0;
+  auto walk_back = [&](uint64_t L, uint64_t S) {
+    for (uint32_t u = t; u > first;) {
+      --u;
+      const ColBnd c = bnd[u];
+      if (c.has_head) {
+        L += c.tail_len;
+        S += c.tail_sum;
+        break;
+      }
+      L += c.lead_len;
+      S += c.lead_sum;
+    }
+    mlen = umax64(mlen, L);
+    msum = umax64(msum, S);
+  };
+  if (b.has_head && tl.j > 0) walk_back(b.lead_len, b.lead_sum);
+  if (tl.start + tl.count == tl.len) {
+    if (b.has_head) {
+      mlen = umax64(mlen, b.tail_len);
+      msum = umax64(msum, b.tail_sum);
+    } else {
+      walk_back(b.lead_len, b.lead_sum);
+    }
+  }
+  ans_quantities* qq = q + tl.seg;
+  if (mlen) atomicMax((unsigned long long*)&qq->max_destination_fanin, (unsigned long long)mlen);
+  if (msum) atomicMax((unsigned long long*)&qq->max_destination_packets, (unsigned long long)msum);
 }
 
 // Segments that own no tile (length 0 known on the host).
@@ -356,6 +462,7 @@ __global__ void k_empty_fixup(StatsArgs a) {
   if (a.row_pos) a.row_pos[bs] = 0;
   a.hdr[2 * s] = 0;
   a.hdr[2 * s + 1] = 0;
+  if (a.ulen) a.ulen[s] = 0;
 }
 
 }  // namespace
@@ -383,9 +490,13 @@ cudaError_t launch_finish(const StatsArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_col_scan(const StatsArgs& a, cudaStream_t st) {
-  if (a.plan.ntiles == 0) return cudaSuccess;
-  k_col_scan<<<a.plan.ntiles, kThreads, 0, st>>>(a);
+cudaError_t launch_colstat(const SegPlan& p, const uint32_t* keys, const uint64_t* vals, ColBnd* bnd,
+                           ans_quantities* q, cudaStream_t st) {
+  if (p.ntiles == 0) return cudaSuccess;
+  k_colstat<<<p.ntiles, kThreads, 0, st>>>(p, keys, vals, bnd, q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_colstat_fin<<<(p.ntiles + 255) / 256, 256, 0, st>>>(p, bnd, q);
   return cudaGetLastError();
 }
 
