@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-per-window", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -232,6 +233,7 @@ def main():
 
     ctx = ans.Context(local)
     stream = torch.cuda.current_stream()
+    tuning = None
     src_h = torch.from_numpy(w.src.view(np.int32)).pin_memory()
     dst_h = torch.from_numpy(w.dst.view(np.int32)).pin_memory()
     src_d = src_h.cuda()
@@ -251,6 +253,8 @@ def main():
             m.free()
         summ.free()
 
+    if not args.no_autotune:
+        tuning = ctx.autotune(src_d, dst_d, w.offsets)
     for _ in range(max(args.warmup, 0)):
         res = step(src_d, dst_d)
         torch.cuda.synchronize()
@@ -388,7 +392,9 @@ def main():
                               "frac": round(path_gbs / peak, 4), "bytes_per_step": alg_bytes},
             "per_window": per_window,
             "batched_over_per_window": (value / per_window["value"]) if per_window else None,
-            "kernel_time_share": kernel_share, "clocks": clk, "cpu_baseline": cpu,
+            "kernel_time_share": kernel_share,
+            "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
+            "tuning": tuning, "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

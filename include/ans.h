@@ -182,6 +182,36 @@ int ans_matrix_free(ans_matrix* m);
 int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                                   ans_quantities* d_out, uint32_t* d_status, void* stream);
 
+/* Launch configuration of the three families of radix passes: the 64-bit link
+ * keys of window sorts (key_*), the 64-bit keys with counts of time sums
+ * (kv_*), and the 32-bit destination keys of the column pass (col_*).
+ * *_threads: threads per 8192-key tile, 512 or 1024.  *_rank: how lanes
+ * holding equal digits find each other, 0 = one __match_any_sync per key,
+ * 1 = eight ballots per key.  *_blocks: CTAs per SM the kernel is compiled
+ * for, 1, or 2 (512 threads only: registers capped at 64).  Results never
+ * depend on the configuration. */
+typedef struct {
+    uint32_t key_threads, key_rank, key_blocks;
+    uint32_t kv_threads, kv_rank, kv_blocks;
+    uint32_t col_threads, col_rank, col_blocks;
+} ans_tuning;
+
+/* Read / set a context's configuration (default: 512 threads, rank 0).
+ * ans_set_tuning fails with ANS_ERR_INVALID_ARG on values other than the
+ * ones listed above. */
+int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);
+int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
+
+/* Autotuner: runs the caller's representative batch (as ans_batch_submit with
+ * per-window matrices and the time sum) once per candidate configuration,
+ * three times each, times every radix pass with CUDA events on `stream`, and
+ * keeps, per family, the configuration with the least total pass time.  The
+ * choice is applied to the context and returned in *chosen (optional).  The
+ * call blocks until the runs have finished; it leaves per-kernel profiling
+ * disabled and its data cleared. */
+int ans_autotune(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
+                 size_t nwin, ans_tuning* chosen, void* stream);
+
 /* Diagnostics: per-kernel timing.  While enabled, every kernel launch of the
  * context is bracketed by CUDA events on its launching stream (the paper
  * reports wall-clock analysis time, Sec. V-A; this splits it by kernel).

@@ -44,7 +44,7 @@ EXPORTS = (
     "ans_ctx_create", "ans_ctx_destroy", "ans_build_window", "ans_sum_windows", "ans_network_quantities",
     "ans_batch_submit", "ans_wait", "ans_matrix_view", "ans_matrix_quantities", "ans_matrix_free",
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
-    "ans_window_quantities_noalloc",
+    "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune",
 )
 
 
@@ -53,6 +53,14 @@ class Quantities(C.Structure):
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n in QUANTITY_NAMES}
+
+
+class Tuning(C.Structure):
+    _fields_ = [(n, C.c_uint32) for n in ("key_threads", "key_rank", "key_blocks", "kv_threads", "kv_rank",
+                                            "kv_blocks", "col_threads", "col_rank", "col_blocks")]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
 class AnsError(RuntimeError):
@@ -92,6 +100,9 @@ def load(path: str | os.PathLike | None = None):
         "ans_profile_enable": ([_vp, C.c_int], C.c_int),
         "ans_profile_read": ([_vp, C.c_char_p, C.c_size_t, P(C.c_size_t)], C.c_int),
         "ans_window_quantities_noalloc": ([_vp, _vp, _u64, _vp, _vp, _vp], C.c_int),
+        "ans_get_tuning": ([_vp, P(Tuning)], C.c_int),
+        "ans_set_tuning": ([_vp, P(Tuning)], C.c_int),
+        "ans_autotune": ([_vp, _vp, _vp, P(_u64), C.c_size_t, P(Tuning), _vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -302,6 +313,25 @@ class Context:
             name, n, ms = line.split()
             out[name] = (int(n), float(ms))
         return out
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(self._lib.ans_get_tuning(self._h, C.byref(t)), "get_tuning", self._h)
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning(**{**self.get_tuning(), **kw})
+        _check(self._lib.ans_set_tuning(self._h, C.byref(t)), "set_tuning", self._h)
+
+    def autotune(self, src, dst, offsets, stream=None) -> dict:
+        """Time the candidate radix-pass configurations on this batch and keep
+        the fastest per pass family; returns the chosen configuration."""
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+        t = Tuning()
+        _check(self._lib.ans_autotune(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)),
+                                      offs.ctypes.data_as(C.POINTER(_u64)), len(offs) - 1, C.byref(t),
+                                      _vp(_stream(stream))), "autotune", self._h)
+        return t.as_dict()
 
     def wait(self, ticket: int, timeout_s: float = 60.0):
         _check(self._lib.ans_wait(self._h, int(ticket), int(timeout_s * 1e9)), "wait", self._h)

@@ -50,7 +50,7 @@ int fail(int code, const std::string& msg) {
 
 constexpr size_t kAlign = 256;
 constexpr uint64_t kMaxWindow = (1ull << 31) - 1;
-constexpr int kStageSlots = 8;
+constexpr int kStageSlots = 16;
 constexpr int kErrSlots = 4096;
 // Tickets of the look-back kernels, 32 per phase: window sort + RLE, time-sum
 // sort + RLE + scan, window column pass, time-sum column pass.
@@ -121,6 +121,10 @@ struct ans_ctx {
   std::map<uint64_t, Ticket> tickets;
   uint64_t next_ticket = 1;
   cudaStream_t aux = nullptr;  // frees of matrix memory
+
+  // Launch configurations of the three families of onesweep passes (set by
+  // ans_set_tuning / ans_autotune).
+  SortCfg cfg_keys, cfg_kv, cfg_col;
 
   // Optional per-kernel timing: CUDA events recorded around each launch on
   // the launching stream, accumulated by name when read.
@@ -273,24 +277,46 @@ int ensure_scratch(ans_ctx* c, size_t bytes, cudaStream_t st) {
   return ANS_OK;
 }
 
-// Copy `bytes` of host data to device `dst` through the pinned ring.
-int upload(ans_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t st) {
-  if (bytes == 0) return ANS_OK;
-  ans_ctx::Stage& s = c->stage[c->stage_next];
-  c->stage_next = (c->stage_next + 1) % kStageSlots;
-  ANS_CUDA(cudaEventSynchronize(s.ev));
-  if (s.size < bytes) {
-    if (s.h) ANS_CUDA(cudaFreeHost(s.h));
-    s.h = nullptr;
-    size_t want = std::max<size_t>(align_up(bytes, 1 << 16), 2 * s.size);
-    ANS_CUDA(cudaHostAlloc(&s.h, want, cudaHostAllocDefault));
-    s.size = want;
+// All the small host arrays of one call (plans, matrix descriptors), staged
+// together in one slot of the context's pinned ring and copied before the
+// call's first kernel.  One slot per call lets kStageSlots calls be in flight
+// before the host waits for the GPU.
+struct UploadSet {
+  struct Item {
+    void* dst;
+    size_t off, bytes;
+  };
+  std::vector<uint8_t> img;
+  std::vector<Item> items;
+  void add(void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return;
+    const size_t off = (img.size() + 15) & ~size_t(15);
+    img.resize(off + bytes);
+    std::memcpy(img.data() + off, src, bytes);
+    items.push_back({dst, off, bytes});
   }
-  std::memcpy(s.h, src, bytes);
-  ANS_CUDA(cudaMemcpyAsync(dst, s.h, bytes, cudaMemcpyHostToDevice, st));
-  ANS_CUDA(cudaEventRecord(s.ev, st));
-  return ANS_OK;
-}
+  int flush(ans_ctx* c, cudaStream_t st) {
+    if (items.empty()) return ANS_OK;
+    ans_ctx::Stage& s = c->stage[c->stage_next];
+    c->stage_next = (c->stage_next + 1) % kStageSlots;
+    ANS_CUDA(cudaEventSynchronize(s.ev));
+    if (s.size < img.size()) {
+      if (s.h) ANS_CUDA(cudaFreeHost(s.h));
+      s.h = nullptr;
+      s.size = 0;
+      const size_t want = std::max<size_t>(align_up(img.size(), 1 << 16), 2 * s.size);
+      ANS_CUDA(cudaHostAlloc(&s.h, want, cudaHostAllocDefault));
+      s.size = want;
+    }
+    std::memcpy(s.h, img.data(), img.size());
+    for (const Item& it : items)
+      ANS_CUDA(cudaMemcpyAsync(it.dst, (char*)s.h + it.off, it.bytes, cudaMemcpyHostToDevice, st));
+    ANS_CUDA(cudaEventRecord(s.ev, st));
+    items.clear();
+    img.clear();
+    return ANS_OK;
+  }
+};
 
 // Device layout of a block holding nseg matrices over `pad` padded items.
 struct BlockLayout {
@@ -474,7 +500,7 @@ int sort_segments(ans_ctx* c, const SegPlan& p, uint64_t* ka, uint64_t* kb, uint
     KTime kt(c, va ? "onesweep_sum" : "onesweep", st);
     ANS_CUDA(launch_onesweep(p, pass, even ? ka : kb, even ? kb : ka, va ? (even ? va : vb) : nullptr,
                              va ? (even ? vb : va) : nullptr, seg_hist, even ? st0 : st1,
-                             even ? st1 : st0, tickets + pass, c->d_err, st));
+                             even ? st1 : st0, tickets + pass, c->d_err, va ? c->cfg_kv : c->cfg_keys, st));
   }
   return ANS_OK;
 }
@@ -501,7 +527,8 @@ int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32
     uint64_t* vout = pass % 2 ? vb : va;
     ANS_CUDA(timed(c, "onesweep_col", st, [&] {
       return launch_onesweep_col(cp, pass, kin, kout, vin, vout, at<uint32_t>(m, ps.col_hist),
-                                 pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, tickets + pass, c->d_err, st);
+                                 pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, tickets + pass, c->d_err, c->cfg_col,
+                                 st);
     }));
   }
   ANS_CUDA(timed(c, "colstat", st, [&] {
@@ -510,46 +537,50 @@ int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32
   return ANS_OK;
 }
 
-// Time sum of the matrices described by `mats` (device array of k MatDesc,
-// host capacities `caps`), written into a new block.  Uses scratch laid out
-// by the caller at `m` / `ps` (which must provide vals buffers).
-int sum_pipeline(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k,
-                 const std::vector<uint64_t>& caps, size_t off_gplan, size_t off_splan, size_t off_catoff,
-                 size_t off_lens, size_t off_total, size_t off_q, cudaStream_t st, Block** out_blk) {
-  // gather plan: one segment per matrix, tiles by capacity, lengths from the device
-  HostPlan gp;
-  gp.build(caps, nullptr);
+// Host half of a time sum over k matrices with capacities `caps`: the gather
+// plan (one segment per matrix, tiles by capacity, lengths filled in on the
+// device), the single-segment sum plan, the output block, and their uploads
+// (added to `us`; the caller flushes it before the first kernel).
+struct SumPlan {
+  HostPlan gp, sp;
+  SegPlan g, s;
+  Block* blk = nullptr;
+};
+
+int sum_prepare(ans_ctx* c, char* m, uint32_t k, const std::vector<uint64_t>& caps, size_t off_gplan,
+                size_t off_splan, size_t off_lens, size_t off_total, UploadSet& us, cudaStream_t st, SumPlan* out) {
+  out->gp.build(caps, nullptr);
   uint64_t total_cap = 0;
   for (uint64_t x : caps) total_cap += x;
-  HostPlan sp;
-  sp.build(std::vector<uint64_t>{total_cap}, nullptr);
-
-  Block* blk = nullptr;
-  ANS_TRY(make_block(c, sp.pad, 1, std::vector<uint64_t>{0}, std::vector<uint64_t>{total_cap}, st, &blk));
-
+  out->sp.build(std::vector<uint64_t>{total_cap}, nullptr);
+  ANS_TRY(make_block(c, out->sp.pad, 1, std::vector<uint64_t>{0}, std::vector<uint64_t>{total_cap}, st, &out->blk));
   DevPlan gdp{off_gplan, off_gplan + align_up(k * 8), off_gplan + 2 * align_up(k * 8),
               off_gplan + 3 * align_up(k * 8)};
-  // upload the gather plan (len is overwritten on the device by count_prefix)
-  int rc = ANS_OK;
-  auto up = [&](size_t off, const void* src, size_t bytes) {
-    if (rc == ANS_OK) rc = upload(c, m + off, src, bytes, st);
-  };
-  up(gdp.in_off, gp.in_off.data(), k * 8);
-  up(gdp.base, gp.base.data(), k * 8);
-  up(gdp.first_tile, gp.first_tile.data(), (k + 1) * 4);
-  SegPlan g = gdp.bind(m, gp);
-  g.len = at<uint64_t>(m, off_lens);
-
+  us.add(m + gdp.in_off, out->gp.in_off.data(), k * 8);
+  us.add(m + gdp.base, out->gp.base.data(), k * 8);
+  us.add(m + gdp.first_tile, out->gp.first_tile.data(), (k + 1) * 4);
+  out->g = gdp.bind(m, out->gp);
+  out->g.len = at<uint64_t>(m, off_lens);
   DevPlan sdp{off_splan, off_splan + kAlign, off_splan + 2 * kAlign, off_splan + 3 * kAlign};
-  up(sdp.in_off, sp.in_off.data(), 8);
-  up(sdp.base, sp.base.data(), 8);
-  up(sdp.first_tile, sp.first_tile.data(), 8);
-  if (rc != ANS_OK) {
-    block_discard(blk, st);
-    return rc;
-  }
-  SegPlan s = sdp.bind(m, sp);
-  s.len = at<uint64_t>(m, off_total);
+  us.add(m + sdp.in_off, out->sp.in_off.data(), 8);
+  us.add(m + sdp.base, out->sp.base.data(), 8);
+  us.add(m + sdp.first_tile, out->sp.first_tile.data(), 8);
+  out->s = sdp.bind(m, out->sp);
+  out->s.len = at<uint64_t>(m, off_total);
+  return ANS_OK;
+}
+
+// Device half of the time sum of the matrices described by `d_mats` (device
+// array of k MatDesc), written into plan->blk.  Uses scratch laid out by the
+// caller at `m` / `ps` (which must provide vals buffers).  On failure the
+// block is discarded.
+int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
+               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st, Block** out_blk) {
+  Block* blk = plan->blk;
+  const HostPlan& sp = plan->sp;
+  const SegPlan& g = plan->g;
+  const SegPlan& s = plan->s;
+  int rc = ANS_OK;
 
   uint64_t* ka = at<uint64_t>(m, ps.keys_a);
   uint64_t* kb = at<uint64_t>(m, ps.keys_b);
@@ -605,7 +636,6 @@ int sum_pipeline(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_ma
   a.col_tickets = col_tickets;
   a.err = c->d_err;
   a.mode = kModeSum;
-  (void)off_q;
   if ((e = cudaMemsetAsync(blk->q, 0, sizeof(ans_quantities), st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = timed(c, "rle", st, [&] { return launch_rle(a, st); })) != cudaSuccess) return fail_blk(e, "rle");
   if ((e = timed(c, "finish", st, [&] { return launch_finish(a, st); })) != cudaSuccess) return fail_blk(e, "finish");
@@ -686,7 +716,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     s_hdr = L.add((size_t)nseg * 16);
     s_q = L.add((size_t)nseg * sizeof(ans_quantities));
   }
-  size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0, off_sq = 0;
+  size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0;
   if (want_sum) {
     off_mats = L.add((size_t)nseg * sizeof(MatDesc));
     off_gplan = L.add(4 * align_up((size_t)(nseg + 1) * 8));
@@ -694,9 +724,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     off_catoff = L.add((size_t)nseg * 8);
     off_lens = L.add((size_t)nseg * 8);
     off_total = L.add(8);
-    off_sq = L.add(sizeof(ans_quantities));
   }
-  size_t off_errcap = L.add(8);
 
   ANS_TRY(ensure_scratch(c, L.size, st));
   char* m = (char*)c->scratch;
@@ -713,20 +741,40 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     sb = {at<uint32_t>(m, s_col), at<uint64_t>(m, s_vals), at<uint32_t>(m, s_row), at<uint64_t>(m, s_rp),
           at<uint64_t>(m, s_hdr), at<ans_quantities>(m, s_q)};
   }
+  SumPlan sump;
+  Block* sblk = nullptr;
   auto bail = [&](int rc) {
     block_discard(blk, st);
+    block_discard(sump.blk, st);
+    block_discard(sblk, st);
     return rc;
   };
 
-  // ---- plan upload
+  // ---- host-side preparation: plans, matrix descriptors and the time-sum
+  // block; every small array goes to the device in one staged upload.
   int rc = ANS_OK;
+  UploadSet us;
   if (nseg) {
-    if (rc == ANS_OK) rc = upload(c, m + dp.in_off, hp.in_off.data(), nseg * 8, st);
-    if (rc == ANS_OK) rc = upload(c, m + dp.len, hp.len.data(), nseg * 8, st);
-    if (rc == ANS_OK) rc = upload(c, m + dp.base, hp.base.data(), nseg * 8, st);
-    if (rc == ANS_OK) rc = upload(c, m + dp.first_tile, hp.first_tile.data(), (nseg + 1) * 4, st);
+    us.add(m + dp.in_off, hp.in_off.data(), nseg * 8);
+    us.add(m + dp.len, hp.len.data(), nseg * 8);
+    us.add(m + dp.base, hp.base.data(), nseg * 8);
+    us.add(m + dp.first_tile, hp.first_tile.data(), (nseg + 1) * 4);
   }
-  if (rc != ANS_OK) return bail(rc);
+  std::vector<MatDesc> md;
+  if (want_sum && nseg) {
+    md.resize(nseg);
+    for (uint32_t s = 0; s < nseg; ++s) {
+      md[s].row_ids = sb.row_ids + hp.base[s];
+      md[s].row_ptr = sb.row_ptr + hp.base[s] + s;
+      md[s].col_ids = sb.col_ids + hp.base[s];
+      md[s].vals = sb.vals + hp.base[s];
+      md[s].hdr = sb.hdr + 2 * (size_t)s;
+    }
+    us.add(m + off_mats, md.data(), md.size() * sizeof(MatDesc));
+    if ((rc = sum_prepare(c, m, nseg, lens, off_gplan, off_splan, off_lens, off_total, us, st, &sump)))
+      return bail(rc);
+  }
+  if ((rc = us.flush(c, st))) return bail(rc);
   const SegPlan p = dp.bind(m, hp);
 
   auto cu = [&](cudaError_t e, const char* what) -> int {
@@ -774,29 +822,17 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     if ((rc = column_pass(c, p, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, st))) return bail(rc);
   }
 
-  Block* sblk = nullptr;
   if (want_sum) {
-    std::vector<MatDesc> md(nseg);
-    for (uint32_t s = 0; s < nseg; ++s) {
-      md[s].row_ids = sb.row_ids + hp.base[s];
-      md[s].row_ptr = sb.row_ptr + hp.base[s] + s;
-      md[s].col_ids = sb.col_ids + hp.base[s];
-      md[s].vals = sb.vals + hp.base[s];
-      md[s].hdr = sb.hdr + 2 * (size_t)s;
-    }
-    if (nseg && (rc = upload(c, m + off_mats, md.data(), md.size() * sizeof(MatDesc), st))) return bail(rc);
     if (nseg == 0) {
       // an empty batch: an empty sum
-      HostPlan sp;
-      sp.build(std::vector<uint64_t>{0}, nullptr);
       if ((rc = make_block(c, 0, 1, {0}, {0}, st, &sblk))) return bail(rc);
       if ((rc = cu(cudaMemsetAsync(sblk->row_ptr, 0, 8, st), "memset"))) return bail(rc);
       if ((rc = cu(cudaMemsetAsync(sblk->hdr, 0, 16, st), "memset"))) return bail(rc);
       if ((rc = cu(cudaMemsetAsync(sblk->q, 0, sizeof(ans_quantities), st), "memset"))) return bail(rc);
     } else {
-      if ((rc = sum_pipeline(c, m, ps, at<MatDesc>(m, off_mats), nseg, lens, off_gplan, off_splan, off_catoff,
-                             off_lens, off_total, off_sq, st, &sblk)))
-        return bail(rc);
+      rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, st, &sblk);
+      sump.blk = nullptr;  // now owned by sblk, or discarded by sum_launch
+      if (rc) return bail(rc);
     }
   }
 
@@ -807,7 +843,6 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   if (sblk) {
     if ((rc = capture_err(c, sblk->status, st))) return bail(rc);
   }
-  (void)off_errcap;
   if (out) {
     if ((rc = copy_quantities_out(out, sb.q, nseg, st))) return bail(rc);
   }
@@ -988,13 +1023,20 @@ int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_mat
     const size_t off_catoff = L.add(k * 8);
     const size_t off_lens = L.add(k * 8);
     const size_t off_total = L.add(8);
-    const size_t off_sq = L.add(sizeof(ans_quantities));
     ANS_TRY(ensure_scratch(c, L.size, st));
     char* m = (char*)c->scratch;
-    ANS_TRY(upload(c, m + off_mats, md.data(), k * sizeof(MatDesc), st));
-    ANS_TRY(sum_pipeline(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, caps, off_gplan, off_splan, off_catoff,
-                         off_lens, off_total, off_sq, st, &sblk));
-    int rc = capture_err(c, sblk->status, st);
+    UploadSet us;
+    us.add(m + off_mats, md.data(), k * sizeof(MatDesc));
+    SumPlan sump;
+    ANS_TRY(sum_prepare(c, m, (uint32_t)k, caps, off_gplan, off_splan, off_lens, off_total, us, st, &sump));
+    int rc = us.flush(c, st);
+    if (rc) {
+      block_discard(sump.blk, st);
+      return rc;
+    }
+    ANS_TRY(sum_launch(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, &sump, off_catoff, off_lens, off_total, st,
+                       &sblk));
+    rc = capture_err(c, sblk->status, st);
     if (rc == ANS_OK) rc = reset_err(c, st);
     if (rc) {
       block_discard(sblk, st);
@@ -1029,8 +1071,10 @@ int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out,
   ps.reserve(L, hp.pad, 1, std::max<uint32_t>(hp.ntiles, 1), false);
   ANS_TRY(ensure_scratch(c, L.size, st));
   char* m = (char*)c->scratch;
-  ANS_TRY(upload(c, m + dp.base, hp.base.data(), 8, st));
-  ANS_TRY(upload(c, m + dp.first_tile, hp.first_tile.data(), 8, st));
+  UploadSet us;
+  us.add(m + dp.base, hp.base.data(), 8);
+  us.add(m + dp.first_tile, hp.first_tile.data(), 8);
+  ANS_TRY(us.flush(c, st));
   SegPlan p = dp.bind(m, hp);
   uint64_t* hdr = b->hdr + 2 * (size_t)x->seg;
   p.len = hdr + 1;  // nnz, on the device
@@ -1159,6 +1203,95 @@ int ans_profile_read(ans_ctx* c, char* buf, size_t buflen, size_t* needed) {
     std::memcpy(buf, s.data(), n);
     buf[n] = 0;
   }
+  return ANS_OK;
+}
+
+int ans_get_tuning(ans_ctx* c, ans_tuning* out) {
+  if (!c || !out) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> g(c->mu);
+  out->key_threads = (uint32_t)c->cfg_keys.threads;
+  out->key_rank = (uint32_t)c->cfg_keys.rank;
+  out->key_blocks = (uint32_t)c->cfg_keys.blocks;
+  out->kv_threads = (uint32_t)c->cfg_kv.threads;
+  out->kv_rank = (uint32_t)c->cfg_kv.rank;
+  out->kv_blocks = (uint32_t)c->cfg_kv.blocks;
+  out->col_threads = (uint32_t)c->cfg_col.threads;
+  out->col_rank = (uint32_t)c->cfg_col.rank;
+  out->col_blocks = (uint32_t)c->cfg_col.blocks;
+  return ANS_OK;
+}
+
+int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
+  if (!c || !t) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  auto ok = [](uint32_t th, uint32_t rk, uint32_t bl) {
+    return (th == 512 || th == 1024) && rk <= 1 && (bl == 1 || (bl == 2 && th == 512));
+  };
+  if (!ok(t->key_threads, t->key_rank, t->key_blocks) || !ok(t->kv_threads, t->kv_rank, t->kv_blocks) ||
+      !ok(t->col_threads, t->col_rank, t->col_blocks))
+    return fail(ANS_ERR_INVALID_ARG, "threads must be 512 or 1024, rank 0 or 1, blocks 1 (or 2 with 512 threads)");
+  std::lock_guard<std::mutex> g(c->mu);
+  c->cfg_keys = SortCfg{(int)t->key_threads, (int)t->key_rank, (int)t->key_blocks};
+  c->cfg_kv = SortCfg{(int)t->kv_threads, (int)t->kv_rank, (int)t->kv_blocks};
+  c->cfg_col = SortCfg{(int)t->col_threads, (int)t->col_rank, (int)t->col_blocks};
+  return ANS_OK;
+}
+
+int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets, size_t nwin,
+                 ans_tuning* chosen, void* stream) {
+  if (!c || !h_offsets || nwin == 0) return fail(ANS_ERR_INVALID_ARG, "NULL argument or empty batch");
+  constexpr int kVariants = 6;
+  const SortCfg variants[kVariants] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankMatch, 2},
+                                       {512, kRankBallot, 2}, {1024, kRankMatch, 1}, {1024, kRankBallot, 1}};
+  double t_keys[kVariants], t_kv[kVariants], t_col[kVariants];
+  std::vector<ans_matrix*> per(nwin, nullptr);
+  auto run_once = [&]() -> int {
+    ans_matrix* sum = nullptr;
+    int rc = ans_batch_submit(c, d_src, d_dst, h_offsets, nwin, ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC,
+                              nullptr, per.data(), &sum, nullptr, stream);
+    if (rc != ANS_OK) return rc;
+    for (auto& m : per) {
+      ans_matrix_free(m);
+      m = nullptr;
+    }
+    ans_matrix_free(sum);
+    return ANS_OK;
+  };
+  for (int v = 0; v < kVariants; ++v) {
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      c->cfg_keys = c->cfg_kv = c->cfg_col = variants[v];
+    }
+    ANS_TRY(run_once());  // first launch of this variant (module load, smem carve-out)
+    ANS_TRY(ans_profile_enable(c, 1));
+    for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
+    std::lock_guard<std::mutex> g(c->mu);
+    DeviceGuard dg(c->device);
+    prof_collect(c);
+    t_keys[v] = c->prof.acc["onesweep"].first;
+    t_kv[v] = c->prof.acc["onesweep_sum"].first;
+    t_col[v] = c->prof.acc["onesweep_col"].first;
+    c->prof.acc.clear();
+    c->prof.on = false;
+  }
+  auto best = [&](const double* t) {
+    int b = 0;
+    for (int v = 1; v < kVariants; ++v)
+      if (t[v] < t[b]) b = v;
+    return variants[b];
+  };
+  ans_tuning res;
+  const SortCfg bk = best(t_keys), bv = best(t_kv), bc = best(t_col);
+  res.key_threads = (uint32_t)bk.threads;
+  res.key_rank = (uint32_t)bk.rank;
+  res.key_blocks = (uint32_t)bk.blocks;
+  res.kv_threads = (uint32_t)bv.threads;
+  res.kv_rank = (uint32_t)bv.rank;
+  res.kv_blocks = (uint32_t)bv.blocks;
+  res.col_threads = (uint32_t)bc.threads;
+  res.col_rank = (uint32_t)bc.rank;
+  res.col_blocks = (uint32_t)bc.blocks;
+  ANS_TRY(ans_set_tuning(c, &res));
+  if (chosen) *chosen = res;
   return ANS_OK;
 }
 

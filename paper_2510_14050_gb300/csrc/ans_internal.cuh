@@ -38,6 +38,17 @@ enum ErrBits : uint32_t {
   kErrLookback = 1u,   // a look-back wait hit kSpinLimit
 };
 
+// How a onesweep pass is launched (chosen per context by the autotuner):
+// threads per 8192-key tile (512 or 1024), how lanes with equal digits are
+// found (one __match_any_sync, or eight ballots), and whether a 512-thread
+// tile is compiled to leave room for two resident CTAs per SM (64 registers).
+enum RankMode : int { kRankMatch = 0, kRankBallot = 1 };
+struct SortCfg {
+  int threads = 512;
+  int rank = kRankMatch;
+  int blocks = 1;
+};
+
 // One entry per segment; device pointers.
 struct SegPlan {
   const uint64_t* in_off = nullptr;     // first item in the input stream (window path)
@@ -109,12 +120,12 @@ cudaError_t launch_hist(const SegPlan& p, const uint64_t* keys, uint32_t* seg_hi
 cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                             uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
-                            uint32_t* err, cudaStream_t st);
+                            uint32_t* err, const SortCfg& cfg, cudaStream_t st);
 // One digit pass over 32-bit destination keys carrying uint64 counts.
 cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
                                 const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                                 uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
-                                cudaStream_t st);
+                                const SortCfg& cfg, cudaStream_t st);
 // Gather the stored links of k matrices into (key, value) pairs.
 cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,
                           uint64_t* keys, uint64_t* vals, cudaStream_t st);

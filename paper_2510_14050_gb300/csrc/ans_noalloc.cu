@@ -153,7 +153,7 @@ extern "C" int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32
     for (int pass = 0; pass < kPasses; ++pass) {
       const bool even = (pass % 2) == 0;
       if ((rc = cu(launch_onesweep(p, pass, even ? ka : kb, even ? kb : ka, nullptr, nullptr, hist,
-                                   even ? st0 : st1, even ? st1 : st0, tickets + pass, err, st),
+                                   even ? st0 : st1, even ? st1 : st0, tickets + pass, err, SortCfg(), st),
                    "onesweep")))
         return rc;
     }
@@ -190,7 +190,8 @@ extern "C" int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32
       const uint32_t* kin = pass == 0 ? a.col_ids : (pass % 2 ? cka : ckb);
       const uint64_t* vin = pass == 0 ? a.vals : (pass % 2 ? cva : cvb);
       if ((rc = cu(launch_onesweep_col(cp, pass, kin, pass % 2 ? ckb : cka, vin, pass % 2 ? cvb : cva, a.col_hist,
-                                       pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, a.col_tickets + pass, err, st),
+                                       pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, a.col_tickets + pass, err,
+                                       SortCfg(), st),
                    "onesweep_col")))
         return rc;
     }

@@ -129,27 +129,48 @@ __global__ void __launch_bounds__(kThreads) k_hist(SegPlan p, const uint64_t* __
 
 struct NoVal {};
 
-template <typename K, typename V>
+template <typename K, typename V, int kT>
 constexpr size_t onesweep_smem_bytes() {
   return (size_t)kTile * sizeof(K) + (std::is_same<V, NoVal>::value ? 0 : (size_t)kTile * sizeof(V)) +
-         (size_t)kWarps * (kRadix + 1) * 4;
+         (size_t)(kT / 32) * (kRadix + 1) * 4;
+}
+
+// Peer mask of lanes holding the same 8-bit digit: one __match_any_sync, or
+// eight ballots (one per digit bit) intersected.  `valid` lanes only.
+template <int kRank>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
+  if constexpr (kRank == kRankMatch) {
+    return __match_any_sync(0xffffffffu, valid ? d : (uint32_t)kRadix);
+  } else {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t ones = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? ones : ~ones;
+    }
+    return peers;
+  }
 }
 
 // One stable digit pass over keys of type K (8 passes for 64-bit keys, 4 for
 // 32-bit keys; seg_hist holds sizeof(K) histograms per segment), optionally
-// carrying values of type V.
-template <typename K, typename V>
-__global__ void __launch_bounds__(kThreads, 1)
+// carrying values of type V.  kT threads share the 8192-key tile (kTile / kT
+// keys each); kRank selects how lanes with equal digits find each other.
+template <typename K, typename V, int kT, int kRank, int kMinB>
+__global__ void __launch_bounds__(kT, kMinB)
     k_onesweep(SegPlan p, int pass, const K* __restrict__ kin, K* __restrict__ kout,
                const V* __restrict__ vin, V* __restrict__ vout, const uint32_t* __restrict__ seg_hist,
                uint64_t* st_cur, uint64_t* __restrict__ st_next, uint32_t* ticket, uint32_t* err) {
   constexpr bool kVals = !std::is_same<V, NoVal>::value;
   constexpr int kNumPasses = (int)sizeof(K);
+  constexpr int kP = kTile / kT;  // keys per thread
+  constexpr int kW = kT / 32;     // warps
   extern __shared__ __align__(16) uint8_t smem[];
   K* s_keys = reinterpret_cast<K*>(smem);
   V* s_vals = reinterpret_cast<V*>(smem + (size_t)kTile * sizeof(K));
   uint32_t* s_wc = reinterpret_cast<uint32_t*>(smem + (size_t)kTile * sizeof(K) +
-                                               (kVals ? (size_t)kTile * sizeof(V) : 0));  // [kWarps][kRadix+1]
+                                               (kVals ? (size_t)kTile * sizeof(V) : 0));  // [kW][kRadix+1]
   __shared__ uint64_t s_gofs[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
   __shared__ uint32_t s_tmp[8];
@@ -168,32 +189,33 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncwarp();
 
   const uint64_t g0 = tl.base + tl.start;
-  const uint32_t wbase = warp * (kPerThread * 32);
-  K k[kPerThread];
-  V v[kVals ? kPerThread : 1];
-  uint32_t r[kPerThread];
+  const uint32_t wbase = warp * (kP * 32);
+  K k[kP];
+  V v[kVals ? kP : 1];
+  uint32_t r[kP];
 #pragma unroll
-  for (int i = 0; i < kPerThread; ++i) {
+  for (int i = 0; i < kP; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
     const bool valid = idx < tl.count;
     k[i] = valid ? kin[g0 + idx] : K(0);
     if constexpr (kVals) v[i] = valid ? vin[g0 + idx] : V(0);
   }
-  // Stable rank inside (warp, digit): lanes with equal digits are merged by
-  // match_any; the lowest lane updates the warp's counter.
+  // Stable rank inside (warp, digit): lanes with equal digits find each other
+  // (digit_peers); the lowest lane updates the warp's counter.
 #pragma unroll
-  for (int i = 0; i < kPerThread; ++i) {
+  for (int i = 0; i < kP; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
-    const uint32_t d = idx < tl.count ? (uint32_t)(k[i] >> shift) & 0xffu : (uint32_t)kRadix;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const bool valid = idx < tl.count;
+    const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & 0xffu : (uint32_t)kRadix;
+    const uint32_t peers = digit_peers<kRank>(d, valid);
     const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
-    if (lane == leader) {
+    if (valid && lane == leader) {
       old = wc[d];
       wc[d] = old + __popc(peers);
     }
     __syncwarp();
-    old = __shfl_sync(0xffffffffu, old, leader);
+    old = __shfl_sync(0xffffffffu, old, valid ? leader : lane);
     r[i] = old + __popc(peers & lanemask_lt());
   }
   __syncthreads();
@@ -204,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t excl = 0;
   if (d < kRadix) {
 #pragma unroll 4
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < kW; ++w) {
       const uint32_t c = s_wc[w * (kRadix + 1) + d];
       s_wc[w * (kRadix + 1) + d] = cnt;
       cnt += c;
@@ -228,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
 
 #pragma unroll
-  for (int i = 0; i < kPerThread; ++i) {
+  for (int i = 0; i < kP; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
     if (idx < tl.count) {
       const uint32_t dg = (uint32_t)(k[i] >> shift) & 0xffu;
@@ -238,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < tl.count; i += kThreads) {
+  for (uint32_t i = threadIdx.x; i < tl.count; i += kT) {
     const K key = s_keys[i];
     const uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
     kout[o] = key;
@@ -312,29 +334,49 @@ __global__ void __launch_bounds__(1024) k_count_prefix(const MatDesc* __restrict
 }
 
 // Dynamic shared memory is configured once per kernel instance and device.
-template <typename K, typename V>
-cudaError_t configure_onesweep() {
+template <typename K, typename V, int kT, int kRank, int kMinB>
+cudaError_t configure_onesweep_variant() {
   static unsigned long long done = 0;  // one bit per device ordinal
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_onesweep<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<K, V>());
+  e = cudaFuncSetAttribute(k_onesweep<K, V, kT, kRank, kMinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem_bytes<K, V, kT>());
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
   return e;
+}
+
+template <typename K, typename V, int kT, int kRank, int kMinB>
+cudaError_t run_onesweep_variant(const SegPlan& p, int pass, const K* kin, K* kout, const V* vin, V* vout,
+                                 const uint32_t* seg_hist, uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
+                                 uint32_t* err, cudaStream_t st) {
+  cudaError_t e = configure_onesweep_variant<K, V, kT, kRank, kMinB>();
+  if (e != cudaSuccess) return e;
+  k_onesweep<K, V, kT, kRank, kMinB><<<p.ntiles, kT, onesweep_smem_bytes<K, V, kT>(), st>>>(
+      p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err);
+  return cudaGetLastError();
 }
 
 template <typename K, typename V>
 cudaError_t run_onesweep(const SegPlan& p, int pass, const K* kin, K* kout, const V* vin, V* vout,
                          const uint32_t* seg_hist, uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
-                         uint32_t* err, cudaStream_t st) {
+                         uint32_t* err, const SortCfg& cfg, cudaStream_t st) {
   if (p.ntiles == 0) return cudaSuccess;
-  cudaError_t e = configure_onesweep<K, V>();
-  if (e != cudaSuccess) return e;
-  k_onesweep<K, V><<<p.ntiles, kThreads, onesweep_smem_bytes<K, V>(), st>>>(p, pass, kin, kout, vin, vout,
-                                                                           seg_hist, st_cur, st_next, ticket, err);
-  return cudaGetLastError();
+#define ANS_OS(T, R, B)                                                                                        \
+  return run_onesweep_variant<K, V, T, R, B>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, \
+                                             err, st)
+  if (cfg.threads == 1024) {
+    if (cfg.rank == kRankBallot) ANS_OS(1024, kRankBallot, 1);
+    ANS_OS(1024, kRankMatch, 1);
+  }
+  if (cfg.blocks == 2) {
+    if (cfg.rank == kRankBallot) ANS_OS(512, kRankBallot, 2);
+    ANS_OS(512, kRankMatch, 2);
+  }
+  if (cfg.rank == kRankBallot) ANS_OS(512, kRankBallot, 1);
+  ANS_OS(512, kRankMatch, 1);
+#undef ANS_OS
 }
 
 }  // namespace
@@ -357,20 +399,20 @@ cudaError_t launch_hist(const SegPlan& p, const uint64_t* keys, uint32_t* seg_hi
 cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                             uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
-                            cudaStream_t st) {
+                            const SortCfg& cfg, cudaStream_t st) {
   if (vin)
     return run_onesweep<uint64_t, uint64_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket,
-                                            err, st);
+                                            err, cfg, st);
   return run_onesweep<uint64_t, NoVal>(p, pass, kin, kout, (const NoVal*)nullptr, (NoVal*)nullptr, seg_hist,
-                                       st_cur, st_next, ticket, err, st);
+                                       st_cur, st_next, ticket, err, cfg, st);
 }
 
 cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
                                 const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                                 uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
-                                cudaStream_t st) {
+                                const SortCfg& cfg, cudaStream_t st) {
   return run_onesweep<uint32_t, uint64_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err,
-                                          st);
+                                          cfg, st);
 }
 
 cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,

@@ -248,3 +248,33 @@ def test_invalid_arguments(ans, ctx):
     with pytest.raises(ans.AnsError) as ei:
         ctx.wait(123456789)
     assert ei.value.code == ans.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("threads,rank,blocks", [(512, 0, 1), (512, 1, 1), (512, 0, 2), (512, 1, 2),
+                                                 (1024, 0, 1), (1024, 1, 1)])
+def test_every_sort_configuration_is_exact(ans, synth, threads, rank, blocks):
+    """Results never depend on the radix-pass launch configuration."""
+    w = synth.generate(5, sizes=[KT * 3 + 17, 0, 40000, 1, 2 * KT])
+    c = ans.Context(0)
+    try:
+        c.set_tuning(key_threads=threads, key_rank=rank, key_blocks=blocks, kv_threads=threads, kv_rank=rank,
+                     kv_blocks=blocks, col_threads=threads, col_rank=rank, col_blocks=blocks)
+        assert c.get_tuning()["kv_threads"] == threads
+        check_batch(ans, c, w)
+    finally:
+        c.close()
+
+
+def test_autotune_picks_valid_configuration(ans, synth):
+    w = synth.generate(2, nwin=4)
+    c = ans.Context(0)
+    try:
+        t = c.autotune(dev(w.src), dev(w.dst), w.offsets)
+        assert t["key_threads"] in (512, 1024) and t["col_rank"] in (0, 1)
+        assert c.get_tuning() == t
+        check_batch(ans, c, w)
+        with pytest.raises(ans.AnsError) as ei:
+            c.set_tuning(key_threads=384)
+        assert ei.value.code == ans.ERR_INVALID_ARG
+    finally:
+        c.close()
