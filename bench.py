@@ -68,6 +68,12 @@ def parse_args():
     ap.add_argument("--no-per-window", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=1e4, help="serving arrivals, windows/s")
+    ap.add_argument("--serve-windows", type=int, default=20000)
+    ap.add_argument("--serve-budget-gib", type=float, default=64.0)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="only serving: every rate of 1e3..1e5 windows/s x budgets 32/64/128 GiB, one line each")
     return ap.parse_args()
 
 
@@ -145,6 +151,28 @@ def algorithmic_bytes(sizes, quants, sum_q):
     return b
 
 
+def run_serving(local, rate, n, budget_gib, pool=None, seed=0):
+    """Open-loop Poisson arrivals of serving-size windows (P uniform in
+    [2^12, 2^17], traffic as the 64-window batch) through the
+    continuous-batching server; latency from arrival to quantities on the host,
+    H2D included.  Running 1-minute and 1-hour tumbling sums stay resident."""
+    from paper_2510_14050_gb300 import serve
+    pool = pool or serve.pool_source(512, seed=seed)
+    npool = pool.offsets.size - 1
+    srv = serve.Server(device=local, slots=4, budget_bytes=int(budget_gib * (1 << 30)), max_batch_windows=256,
+                       max_batch_packets=1 << 24, bucket_seconds=(60.0, 3600.0))
+    try:
+        warm_t, warm_o = serve.poisson_schedule(rate, min(n, 200), npool, seed=seed + 1)
+        srv.serve(pool, warm_t, warm_o)
+        arr, order = serve.poisson_schedule(rate, n, npool, seed=seed)
+        st = srv.serve(pool, arr, order)
+        out = {"lambda_windows_per_s": rate, "budget_gib": budget_gib, "slots": 4, **st.summary(),
+               "offered_packets_per_s": float(np.diff(pool.offsets)[order].sum() / max(arr[-1], 1e-9))}
+    finally:
+        srv.close()
+    return out, pool
+
+
 def oracle_step(w):
     import oracle
     oracle.batch(w.src, w.dst, w.offsets, want_sum=True)
@@ -208,6 +236,15 @@ def main():
     from paper_2510_14050_gb300 import ans, synth
 
     torch.cuda.set_device(local)
+    if args.serve_sweep:
+        if rank == 0:
+            pool = None
+            for budget in (32.0, 64.0, 128.0):
+                for rate in (1e3, 3e3, 1e4, 3e4, 1e5):
+                    n = max(args.serve_windows, int(min(rate * 10.0, 200000)))
+                    res, pool = run_serving(local, rate, n, budget, pool)
+                    print(json.dumps({"metric": "serving window latency", "unit": "ms", **res}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -380,6 +417,10 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {n_used} of {nwin} windows + their time sum ({dt:.1f} s, numpy, 1 thread)"}
 
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving, _ = run_serving(local, args.serve_rate, args.serve_windows, args.serve_budget_gib)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -394,7 +435,7 @@ def main():
             "batched_over_per_window": (value / per_window["value"]) if per_window else None,
             "kernel_time_share": kernel_share,
             "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
-            "tuning": tuning, "clocks": clk, "cpu_baseline": cpu,
+            "tuning": tuning, "serving": serving, "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -156,8 +156,18 @@ int ans_matrix_view(const ans_matrix* m, uint64_t* nrows, uint64_t* nnz, const u
  * the matrix is complete). */
 int ans_matrix_quantities(const ans_matrix* m, ans_quantities* out);
 
-/* Release a matrix (waits for the work that produces it).  NULL is a no-op. */
+/* Release a matrix.  Waits for the work that produces it and for every
+ * library call that reads it (ans_sum_windows, ans_network_quantities) to
+ * finish, so a matrix may be freed right after enqueueing such a call, on any
+ * stream.  Work of the caller's own that reads the matrix must be complete.
+ * NULL is a no-op. */
 int ans_matrix_free(ans_matrix* m);
+
+/* A second handle to the same matrix (no copy): the memory is released when
+ * every handle has been freed.  Serves data structures that hold one matrix
+ * in several places, e.g. a batch sum that belongs to a one-minute and a
+ * one-hour running sum. */
+int ans_matrix_retain(const ans_matrix* m, ans_matrix** out);
 
 /* Quantities of one window without allocating anything.  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory
@@ -181,6 +191,14 @@ int ans_matrix_free(ans_matrix* m);
  * Asynchronous on `stream`. */
 int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                                   ans_quantities* d_out, uint32_t* d_status, void* stream);
+
+/* Memory accounting for admission control.  ans_ctx_memory reports the
+ * device bytes the context holds now (scratch plus live matrices) and its
+ * budget (0 = none).  ans_batch_bytes gives the additional device bytes that
+ * ans_batch_submit with these offsets and flags would allocate if called now
+ * (scratch growth plus output matrices); nothing is allocated. */
+int ans_ctx_memory(ans_ctx* ctx, size_t* live_bytes, size_t* budget_bytes);
+int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32_t flags, size_t* bytes);
 
 /* Launch configuration of the three families of radix passes: the 64-bit link
  * keys of window sorts (key_*), the 64-bit keys with counts of time sums

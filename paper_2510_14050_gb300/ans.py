@@ -44,7 +44,8 @@ EXPORTS = (
     "ans_ctx_create", "ans_ctx_destroy", "ans_build_window", "ans_sum_windows", "ans_network_quantities",
     "ans_batch_submit", "ans_wait", "ans_matrix_view", "ans_matrix_quantities", "ans_matrix_free",
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
-    "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune",
+    "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
+    "ans_ctx_memory", "ans_batch_bytes",
 )
 
 
@@ -95,6 +96,7 @@ def load(path: str | os.PathLike | None = None):
         "ans_matrix_view": ([_vp, P(_u64), P(_u64), P(_vp), P(_vp), P(_vp), P(_vp)], C.c_int),
         "ans_matrix_quantities": ([_vp, P(Quantities)], C.c_int),
         "ans_matrix_free": ([_vp], C.c_int),
+        "ans_matrix_retain": ([_vp, P(_vp)], C.c_int),
         "ans_status_string": ([C.c_int], C.c_char_p),
         "ans_last_error": ([_vp], C.c_char_p),
         "ans_profile_enable": ([_vp, C.c_int], C.c_int),
@@ -103,6 +105,8 @@ def load(path: str | os.PathLike | None = None):
         "ans_get_tuning": ([_vp, P(Tuning)], C.c_int),
         "ans_set_tuning": ([_vp, P(Tuning)], C.c_int),
         "ans_autotune": ([_vp, _vp, _vp, P(_u64), C.c_size_t, P(Tuning), _vp], C.c_int),
+        "ans_ctx_memory": ([_vp, P(C.c_size_t), P(C.c_size_t)], C.c_int),
+        "ans_batch_bytes": ([_vp, P(_u64), C.c_size_t, C.c_uint32, P(C.c_size_t)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -206,6 +210,12 @@ class Matrix:
         q = Quantities()
         _check(load().ans_matrix_quantities(self._h, C.byref(q)), "matrix_quantities")
         return q.as_dict()
+
+    def retain(self) -> "Matrix":
+        """A second handle to the same device matrix (no copy)."""
+        out = _vp()
+        _check(load().ans_matrix_retain(self._h, C.byref(out)), "matrix_retain")
+        return Matrix(out.value)
 
     def free(self):
         if self._h is not None and self._h.value:
@@ -313,6 +323,20 @@ class Context:
             name, n, ms = line.split()
             out[name] = (int(n), float(ms))
         return out
+
+    def memory(self) -> tuple[int, int]:
+        """(device bytes held now, budget) of this context."""
+        live, budget = C.c_size_t(), C.c_size_t()
+        _check(self._lib.ans_ctx_memory(self._h, C.byref(live), C.byref(budget)), "ctx_memory", self._h)
+        return int(live.value), int(budget.value)
+
+    def batch_bytes(self, offsets, flags: int = 0) -> int:
+        """Additional device bytes batch_submit(offsets, flags) would allocate now."""
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+        out = C.c_size_t()
+        _check(self._lib.ans_batch_bytes(self._h, offs.ctypes.data_as(C.POINTER(_u64)), len(offs) - 1, int(flags),
+                                         C.byref(out)), "batch_bytes", self._h)
+        return int(out.value)
 
     def get_tuning(self) -> dict:
         t = Tuning()

@@ -218,6 +218,7 @@ struct Block {
   cudaEvent_t done = nullptr;
   std::atomic<int> refs{0};
   std::mutex mu;
+  std::vector<cudaEvent_t> readers;  // completion of library calls that read the block
   bool cached = false;
   std::vector<uint64_t> h_hdr;
   std::vector<ans_quantities> h_q;
@@ -364,10 +365,32 @@ int make_block(ans_ctx* c, uint64_t pad, uint32_t nseg, std::vector<uint64_t> ba
   return ANS_OK;
 }
 
+// Note that work just enqueued on `st` reads block b: freeing b waits for it.
+int note_read(Block* b, cudaStream_t st) {
+  cudaEvent_t ev = nullptr;
+  ANS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, st);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return fail(ANS_ERR_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+  }
+  std::lock_guard<std::mutex> g(b->mu);
+  b->readers.push_back(ev);
+  return ANS_OK;
+}
+
 void block_release(Block* b) {
   if (--b->refs > 0) return;
   ans_ctx* c = b->ctx;
   cudaEventSynchronize(b->done);
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    for (cudaEvent_t ev : b->readers) {
+      cudaEventSynchronize(ev);
+      cudaEventDestroy(ev);
+    }
+    b->readers.clear();
+  }
   {
     std::lock_guard<std::mutex> g(c->mu);
     DeviceGuard dg(c->device);
@@ -678,6 +701,37 @@ int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n
   return ANS_OK;
 }
 
+// Scratch layout of one batch (shared by run_windows and ans_batch_bytes).
+struct WinLayout {
+  DevPlan dp;
+  PipeScratch ps;
+  size_t s_col = 0, s_vals = 0, s_row = 0, s_rp = 0, s_hdr = 0, s_q = 0;
+  size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0;
+  size_t size = 0;
+  void reserve(const HostPlan& hp, uint32_t nseg, bool want_mats, bool want_sum) {
+    Layout L;
+    dp.reserve(L, nseg);
+    ps.reserve(L, hp.pad, std::max<uint32_t>(nseg, 1), hp.ntiles, want_sum);
+    if (!want_mats) {  // the DCSR arrays are intermediate: keep them in scratch
+      s_col = L.add(hp.pad * 4);
+      s_vals = L.add(hp.pad * 8);
+      s_row = L.add(hp.pad * 4);
+      s_rp = L.add((hp.pad + nseg) * 8);
+      s_hdr = L.add((size_t)nseg * 16);
+      s_q = L.add((size_t)nseg * sizeof(ans_quantities));
+    }
+    if (want_sum) {
+      off_mats = L.add((size_t)nseg * sizeof(MatDesc));
+      off_gplan = L.add(4 * align_up((size_t)(nseg + 1) * 8));
+      off_splan = L.add(4 * kAlign);
+      off_catoff = L.add((size_t)nseg * 8);
+      off_lens = L.add((size_t)nseg * 8);
+      off_total = L.add(8);
+    }
+    size = L.size;
+  }
+};
+
 // The batch pipeline (also serves ans_build_window with nwin == 1).
 int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
                 size_t nwin, uint32_t flags, ans_quantities* out, ans_matrix** per_window, ans_matrix** sum,
@@ -702,31 +756,16 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   if ((uint64_t)hp.ntiles * kTile != hp.pad) return fail(ANS_ERR_INTERNAL, "plan");
 
   // ---- scratch layout
-  Layout L;
-  DevPlan dp;
-  dp.reserve(L, nseg);
-  PipeScratch ps;
-  ps.reserve(L, hp.pad, std::max<uint32_t>(nseg, 1), hp.ntiles, want_sum);
-  size_t s_col = 0, s_vals = 0, s_row = 0, s_rp = 0, s_hdr = 0, s_q = 0;
-  if (!want_mats) {
-    s_col = L.add(hp.pad * 4);
-    s_vals = L.add(hp.pad * 8);
-    s_row = L.add(hp.pad * 4);
-    s_rp = L.add((hp.pad + nseg) * 8);
-    s_hdr = L.add((size_t)nseg * 16);
-    s_q = L.add((size_t)nseg * sizeof(ans_quantities));
-  }
-  size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0;
-  if (want_sum) {
-    off_mats = L.add((size_t)nseg * sizeof(MatDesc));
-    off_gplan = L.add(4 * align_up((size_t)(nseg + 1) * 8));
-    off_splan = L.add(4 * kAlign);
-    off_catoff = L.add((size_t)nseg * 8);
-    off_lens = L.add((size_t)nseg * 8);
-    off_total = L.add(8);
-  }
+  WinLayout wl;
+  wl.reserve(hp, nseg, want_mats, want_sum);
+  const DevPlan& dp = wl.dp;
+  const PipeScratch& ps = wl.ps;
+  const size_t s_col = wl.s_col, s_vals = wl.s_vals, s_row = wl.s_row, s_rp = wl.s_rp, s_hdr = wl.s_hdr,
+               s_q = wl.s_q;
+  const size_t off_mats = wl.off_mats, off_gplan = wl.off_gplan, off_splan = wl.off_splan,
+               off_catoff = wl.off_catoff, off_lens = wl.off_lens, off_total = wl.off_total;
 
-  ANS_TRY(ensure_scratch(c, L.size, st));
+  ANS_TRY(ensure_scratch(c, wl.size, st));
   char* m = (char*)c->scratch;
 
   Block* blk = nullptr;
@@ -997,8 +1036,17 @@ int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_mat
     if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
     const uint64_t bs = b->base[x->seg];
     md.push_back({b->row_ids + bs, b->row_ptr + bs + x->seg, b->col_ids + bs, b->vals + bs, b->hdr + 2 * x->seg});
-    caps.push_back(b->cap[x->seg]);
-    total_cap += b->cap[x->seg];
+    // An input that has already been computed contributes its actual link
+    // count to the output's capacity; one still running contributes its bound.
+    uint64_t cap = b->cap[x->seg];
+    if (cudaEventQuery(b->done) == cudaSuccess) {
+      ANS_TRY(block_fill_cache(const_cast<Block*>(b)));
+      cap = std::min<uint64_t>(cap, b->h_hdr[2 * (size_t)x->seg + 1]);
+    } else {
+      cudaGetLastError();
+    }
+    caps.push_back(cap);
+    total_cap += cap;
     ANS_CUDA(cudaStreamWaitEvent(st, b->done, 0));
   }
   if (total_cap > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a time sum is limited to 2^31 - 1 links");
@@ -1043,6 +1091,7 @@ int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_mat
       return rc;
     }
   }
+  for (size_t i = 0; i < k; ++i) ANS_TRY(note_read(mats[i]->blk, st));
   ANS_CUDA(cudaEventRecord(sblk->done, st));
   sblk->refs = 1;
   *out = new ans_matrix{sblk, 0};
@@ -1106,6 +1155,7 @@ int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out,
     ANS_TRY(column_pass(c, p, a.ulen, a.col_ids, a.vals, ps, m, a.col_tickets, q, st));
   }
   ANS_CUDA(cudaMemsetAsync(c->d_err, 0, 4, st));
+  ANS_TRY(note_read(const_cast<Block*>(b), st));
   ANS_TRY(copy_quantities_out(out, q, 1, st));
   return ANS_OK;
 }
@@ -1175,6 +1225,13 @@ int ans_matrix_free(ans_matrix* x) {
   return ANS_OK;
 }
 
+int ans_matrix_retain(const ans_matrix* x, ans_matrix** out) {
+  if (!x || !out) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  ++x->blk->refs;
+  *out = new ans_matrix{x->blk, x->seg};
+  return ANS_OK;
+}
+
 int ans_profile_enable(ans_ctx* c, int enable) {
   if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
   std::lock_guard<std::mutex> g(c->mu);
@@ -1203,6 +1260,38 @@ int ans_profile_read(ans_ctx* c, char* buf, size_t buflen, size_t* needed) {
     std::memcpy(buf, s.data(), n);
     buf[n] = 0;
   }
+  return ANS_OK;
+}
+
+int ans_ctx_memory(ans_ctx* c, size_t* live_bytes, size_t* budget_bytes) {
+  if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
+  std::lock_guard<std::mutex> g(c->mu);
+  if (live_bytes) *live_bytes = c->live;
+  if (budget_bytes) *budget_bytes = c->budget;
+  return ANS_OK;
+}
+
+int ans_batch_bytes(ans_ctx* c, const uint64_t* h_offsets, size_t nwin, uint32_t flags, size_t* bytes) {
+  if (!c || !h_offsets || !bytes) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  std::vector<uint64_t> lens(nwin);
+  uint64_t total = 0;
+  for (size_t w = 0; w < nwin; ++w) {
+    if (h_offsets[w + 1] < h_offsets[w]) return fail(ANS_ERR_INVALID_ARG, "offsets must be nondecreasing");
+    lens[w] = h_offsets[w + 1] - h_offsets[w];
+    total += lens[w];
+  }
+  HostPlan hp;
+  hp.build(lens, nullptr);
+  const bool want_mats = (flags & ANS_BATCH_MATRICES) != 0, want_sum = (flags & ANS_BATCH_SUM) != 0;
+  WinLayout wl;
+  wl.reserve(hp, (uint32_t)nwin, want_mats, want_sum);
+  size_t need = 0;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (wl.size > c->scratch_size)  // the scratch is replaced by a larger one
+    need += std::max(wl.size, c->scratch_size + c->scratch_size / 4) - c->scratch_size;
+  if (want_mats && nwin) need += BlockLayout(hp.pad, (uint32_t)nwin).total;
+  if (want_sum) need += BlockLayout((total + kTile - 1) / kTile * kTile, 1).total;
+  *bytes = need;
   return ANS_OK;
 }
 

@@ -1,0 +1,333 @@
+"""Continuous-batching server for windows of packet pairs.
+
+Windows arrive on an open-loop schedule (arrival times in seconds).  The
+server admits whatever has arrived into the next free slot -- one slot is one
+library context with its own CUDA stream and device input buffers -- so
+batches overlap on the GPU.  Each batch is one ``ans_batch_submit`` (the nine
+quantities of every window plus the batch's time sum).  Admission is by
+device-memory budget: a batch is submitted only if the bytes held by all of
+the server's contexts plus the bytes the library says the batch would
+allocate (``ans_batch_bytes``) stay within the budget; otherwise it waits for
+running batches to complete (an admission stall).  Window latency runs from
+the window's arrival to its quantities being visible on the host; it includes
+the host-to-device copy of its packets.
+
+Running time sums (Table I: A_t summed over t) are kept resident on the
+device per tumbling bucket of the arrival clock (``bucket_seconds``, e.g. one
+minute and one hour).  A worker thread owns them: each bucket holds a few
+partial sums of geometrically growing size, and a completed batch's sum is
+merged (``ans_sum_windows``) with the newest partial while they are of similar
+size, so the resident set stays small and each link is re-merged O(log n)
+times.  The worker waits for each merge before the next one, so every output
+is sized by its inputs' actual link counts.  ``bucket_sum()`` merges a
+bucket's partials into one matrix.
+"""
+from __future__ import annotations
+
+import queue as _queue
+import threading
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import ans
+
+
+@dataclass
+class WindowSource:
+    """Packets of the windows to serve: window i is [offsets[i], offsets[i+1])
+    of (src, dst), uint32 numpy arrays in host memory."""
+    src: np.ndarray
+    dst: np.ndarray
+    offsets: np.ndarray
+
+    def size(self, i: int) -> int:
+        return int(self.offsets[i + 1] - self.offsets[i])
+
+
+@dataclass
+class ServeStats:
+    latencies_s: np.ndarray
+    quantities: np.ndarray          # [n, 9] uint64 per served window, in arrival order
+    packets: int
+    wall_s: float
+    batches: int
+    admission_stalls: int
+    max_queue: int
+
+    def percentile_ms(self, q: float) -> float:
+        return float(np.percentile(self.latencies_s, q) * 1e3) if len(self.latencies_s) else 0.0
+
+    def summary(self) -> dict:
+        return {
+            "windows": int(len(self.latencies_s)),
+            "p50_ms": round(self.percentile_ms(50), 4),
+            "p99_ms": round(self.percentile_ms(99), 4),
+            "max_ms": round(float(self.latencies_s.max() * 1e3) if len(self.latencies_s) else 0.0, 4),
+            "sustained_packets_per_s": self.packets / self.wall_s if self.wall_s > 0 else 0.0,
+            "batches": self.batches,
+            "admission_stalls": self.admission_stalls,
+            "max_queue": self.max_queue,
+        }
+
+
+class SumKeeper:
+    """Resident tumbling time sums, maintained by a worker thread."""
+
+    def __init__(self, device: int, budget_bytes: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.ctx = ans.Context(device, budget_bytes=budget_bytes)
+        self.stream = torch.cuda.Stream(device=device)
+        self.buckets = {}      # (level, index) -> [(nnz, Matrix)], newest last
+        self.lock = threading.Lock()
+        self.q = _queue.Queue()
+        self.error = None
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def add(self, keys, batch_sum):
+        """Hand a completed batch's sum to its buckets: keys[level] is the
+        bucket index at each level."""
+        self.q.put((tuple(keys), batch_sum))
+
+    def _run(self):
+        self.torch.cuda.set_device(self.device)
+        while True:
+            item = self.q.get()
+            try:
+                if item is None:
+                    return
+                keys, mat = item
+                # every level holds its own handle to the same batch sum
+                handles = [mat] + [mat.retain() for _ in keys[1:]]
+                for level, (idx, h) in enumerate(zip(keys, handles)):
+                    self._insert((level, idx), h)
+            except Exception as e:  # surfaced by drain()
+                self.error = e
+            finally:
+                self.q.task_done()
+
+    def _insert(self, key, mat):
+        with self.lock:
+            parts = self.buckets.setdefault(key, [])
+            parts.append((mat.nnz, mat))
+            while len(parts) >= 2 and parts[-2][0] <= 2 * parts[-1][0]:
+                (_, m1), (_, m2) = parts[-2], parts[-1]
+                merged = self.ctx.sum_windows([m1, m2], stream=self.stream)
+                m1.free()
+                m2.free()
+                self.stream.synchronize()
+                parts[-2:] = [(merged.nnz, merged)]
+
+    def drain(self):
+        self.q.join()
+        if self.error is not None:
+            raise self.error
+
+    def bucket_sum(self, key):
+        self.drain()
+        with self.lock:
+            parts = self.buckets.get(key)
+            if not parts:
+                return None
+            mats = [m for _, m in parts]
+            merged = self.ctx.sum_windows(mats, stream=self.stream) if len(mats) > 1 else mats[0]
+            if len(mats) > 1:
+                for m in mats:
+                    m.free()
+            self.stream.synchronize()
+            parts[:] = [(merged.nnz, merged)]
+            return merged
+
+    def memory(self) -> int:
+        return self.ctx.memory()[0]
+
+    def close(self):
+        self.q.put(None)
+        self.thread.join()
+        for parts in self.buckets.values():
+            for _, m in parts:
+                m.free()
+        self.buckets = {}
+        self.ctx.close()
+
+
+class Server:
+    def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int = 64 << 30,
+                 max_batch_windows: int = 256, max_batch_packets: int = 1 << 24,
+                 bucket_seconds=(60.0, 3600.0), keep_sums: bool = True):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.max_batch_windows = max_batch_windows
+        self.max_batch_packets = max_batch_packets
+        self.bucket_seconds = tuple(bucket_seconds)
+        self.keep_sums = keep_sums
+        self.budget = budget_bytes
+        self.slots = []
+        for _ in range(slots):
+            ctx = ans.Context(device, budget_bytes=budget_bytes)
+            st = torch.cuda.Stream(device=device)
+            self.slots.append({
+                "ctx": ctx, "stream": st,
+                "src": torch.empty(max_batch_packets, dtype=torch.int32, device=f"cuda:{device}"),
+                "dst": torch.empty(max_batch_packets, dtype=torch.int32, device=f"cuda:{device}"),
+                "h_src": torch.empty(max_batch_packets, dtype=torch.int32).pin_memory(),
+                "h_dst": torch.empty(max_batch_packets, dtype=torch.int32).pin_memory(),
+                "q_dev": torch.empty((max_batch_windows, 9), dtype=torch.int64, device=f"cuda:{device}"),
+                "q_host": torch.empty((max_batch_windows, 9), dtype=torch.int64).pin_memory(),
+                "inflight": None,
+            })
+        self.sums = SumKeeper(device, budget_bytes) if keep_sums else None
+
+    def live_bytes(self) -> int:
+        """Device bytes held by all of the server's contexts."""
+        return sum(s["ctx"].memory()[0] for s in self.slots) + (self.sums.memory() if self.sums else 0)
+
+    def bucket_sum(self, level: int, idx: int):
+        """One matrix: the time sum of every served window whose arrival falls
+        in bucket idx of bucket_seconds[level] (None if there is none)."""
+        return self.sums.bucket_sum((level, idx)) if self.sums else None
+
+    def close(self):
+        if self.sums is not None:
+            self.sums.close()
+        for s in self.slots:
+            s["ctx"].close()
+
+    def serve(self, source: WindowSource, arrivals: np.ndarray, order=None) -> ServeStats:
+        """Serve windows order[k] (default k) arriving at arrivals[k] seconds
+        after the start; returns latencies and quantities in arrival order."""
+        torch = self.torch
+        n = len(arrivals)
+        order = np.arange(n) if order is None else np.asarray(order)
+        lat = np.zeros(n)
+        quants = np.zeros((n, 9), dtype=np.uint64)
+        batches = stalls = max_q = 0
+        packets = 0
+        next_k = 0             # next arrival not yet admitted
+        queue = []             # arrived, not yet submitted (indices into arrivals)
+        flags = ans.BATCH_SUM if self.keep_sums else 0
+        t0 = time.perf_counter()
+
+        def bucket_ids(k):
+            return tuple(int(arrivals[k] // w) for w in self.bucket_seconds)
+
+        def complete(slot):
+            nonlocal packets
+            job = slot["inflight"]
+            slot["inflight"] = None
+            job["event"].synchronize()
+            t_done = time.perf_counter() - t0
+            qh = slot["q_host"][: len(job["ks"])].numpy().view(np.uint64)
+            for j, k in enumerate(job["ks"]):
+                lat[k] = t_done - arrivals[k]
+                quants[k] = qh[j]
+            packets += job["packets"]
+            if job["sum"] is not None:
+                self.sums.add(job["buckets"], job["sum"])
+
+        def batch_offsets(ks):
+            offs = np.zeros(len(ks) + 1, dtype=np.uint64)
+            np.cumsum([source.size(int(order[k])) for k in ks], out=offs[1:])
+            return offs
+
+        def submit(slot, ks, offs):
+            ctx, st = slot["ctx"], slot["stream"]
+            hs, hd = slot["h_src"].numpy().view(np.uint32), slot["h_dst"].numpy().view(np.uint32)
+            for j, k in enumerate(ks):
+                w = int(order[k])
+                a, b = int(source.offsets[w]), int(source.offsets[w + 1])
+                hs[int(offs[j]):int(offs[j + 1])] = source.src[a:b]
+                hd[int(offs[j]):int(offs[j + 1])] = source.dst[a:b]
+            pos = int(offs[-1])
+            with torch.cuda.stream(st):
+                slot["src"][:pos].copy_(slot["h_src"][:pos], non_blocking=True)
+                slot["dst"][:pos].copy_(slot["h_dst"][:pos], non_blocking=True)
+                _, summ, _ = ctx.batch_submit(slot["src"], slot["dst"], offs, flags, out=slot["q_dev"],
+                                              stream=st, want_ticket=False)
+                slot["q_host"][: len(ks)].copy_(slot["q_dev"][: len(ks)], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            slot["inflight"] = {"ks": list(ks), "event": ev, "sum": summ, "packets": pos,
+                                "buckets": bucket_ids(ks[0])}
+
+        stalled_head = -1
+        while True:
+            now = time.perf_counter() - t0
+            while next_k < n and arrivals[next_k] <= now:
+                queue.append(next_k)
+                next_k += 1
+            max_q = max(max_q, len(queue))
+            progressed = False
+            for slot in self.slots:
+                job = slot["inflight"]
+                if job is not None and job["event"].query():
+                    complete(slot)
+                    progressed = True
+            for slot in self.slots:
+                if not queue:
+                    break
+                if slot["inflight"] is not None:
+                    continue
+                # continuous batching: take what has arrived, one time bucket per batch
+                ks, pk = [], 0
+                b0 = bucket_ids(queue[0])
+                for k in queue:
+                    sz = source.size(int(order[k]))
+                    if ks and (len(ks) >= self.max_batch_windows or pk + sz > self.max_batch_packets
+                               or bucket_ids(k) != b0):
+                        break
+                    ks.append(k)
+                    pk += sz
+                offs = batch_offsets(ks)
+                need = slot["ctx"].batch_bytes(offs, flags)
+                if self.live_bytes() + need > self.budget:
+                    if stalled_head != ks[0]:
+                        stalls += 1
+                        stalled_head = ks[0]
+                    if all(s["inflight"] is None for s in self.slots):
+                        if self.sums is not None:
+                            self.sums.drain()  # merges may still release memory
+                            if self.live_bytes() + need <= self.budget:
+                                continue
+                        raise RuntimeError(f"a batch of {len(ks)} windows needs {need} bytes and does not fit in "
+                                           f"the {self.budget}-byte budget with nothing running")
+                    break  # wait for running batches to release memory
+                submit(slot, ks, offs)
+                del queue[: len(ks)]
+                batches += 1
+                progressed = True
+            if next_k >= n and not queue and all(s["inflight"] is None for s in self.slots):
+                break
+            if not progressed:
+                if next_k < n and not queue:
+                    wait = arrivals[next_k] - (time.perf_counter() - t0)
+                    if wait > 2e-4:
+                        time.sleep(min(wait - 1e-4, 2e-3))
+                else:
+                    time.sleep(2e-5)
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize(self.device)
+        return ServeStats(latencies_s=lat, quantities=quants, packets=packets, wall_s=wall, batches=batches,
+                          admission_stalls=stalls, max_queue=max_q)
+
+
+def pool_source(nwin: int, seed: int = 0) -> WindowSource:
+    """A pool of serving-size windows: P uniform in [2^12, 2^17], traffic as
+    the 64-window batch (Zipf sources/destinations, 5% bursts)."""
+    from . import synth
+    w = synth.generate(5, nwin=nwin, seed=seed)
+    return WindowSource(w.src, w.dst, w.offsets)
+
+
+def poisson_schedule(rate: float, n: int, pool: int, seed: int = 0):
+    """Arrival times (s) of n windows at `rate` windows/s, and which pool
+    window each one carries."""
+    from . import synth
+    t = synth.arrivals(rate, n, seed=seed)
+    order = (np.arange(n) * 7919) % pool
+    return t, order
