@@ -620,15 +620,18 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
   if ((e = timed(c, "count_prefix", st, [&] { return launch_count_prefix(d_mats, k, at<uint64_t>(m, off_catoff), at<uint64_t>(m, off_lens),
                                at<uint64_t>(m, off_total), st); })) != cudaSuccess)
     return fail_blk(e, "count_prefix");
-  if ((e = timed(c, "gather", st, [&] { return launch_gather(g, d_mats, at<uint64_t>(m, off_catoff), ka, va, st); })) != cudaSuccess)
-    return fail_blk(e, "gather");
   if ((e = cudaMemsetAsync(seg_hist, 0, kPasses * kRadix * 4, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = cudaMemsetAsync(m + ps.lb, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = cudaMemsetAsync(m + ps.lb2, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = cudaMemsetAsync(m + ps.col_hist, 0, kColPasses * kRadix * 4, st)) != cudaSuccess)
     return fail_blk(e, "memset");
-  if ((e = timed(c, "hist", st, [&] { return launch_hist(s, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); })) != cudaSuccess)
-    return fail_blk(e, "hist");
+  // gather fills the sum segment's histograms and zeroes its first status
+  // words (the gather plan has at least as many tiles as the sum plan)
+  if ((e = timed(c, "gather", st, [&] {
+         return launch_gather(g, d_mats, at<uint64_t>(m, off_catoff), ka, va, seg_hist, at<uint64_t>(m, ps.st0),
+                              tickets, st);
+       })) != cudaSuccess)
+    return fail_blk(e, "gather");
   rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
   if (rc != ANS_OK) {
     block_discard(blk, st);

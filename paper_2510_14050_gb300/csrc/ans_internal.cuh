@@ -113,9 +113,6 @@ int set_last_error(int code, const std::string& msg);
 cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32_t* dst,
                              uint64_t* keys, uint32_t* seg_hist, uint64_t* status0,
                              uint32_t* tickets, cudaStream_t st);
-// Same for keys that already exist (time sum).
-cudaError_t launch_hist(const SegPlan& p, const uint64_t* keys, uint32_t* seg_hist,
-                        uint64_t* status0, uint32_t* tickets, cudaStream_t st);
 // One onesweep digit pass (stable), optionally carrying uint64 values.
 cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
@@ -126,9 +123,13 @@ cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin,
                                 const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                                 uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
                                 const SortCfg& cfg, cudaStream_t st);
-// Gather the stored links of k matrices into (key, value) pairs.
-cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,
-                          uint64_t* keys, uint64_t* vals, cudaStream_t st);
+// Gather the stored links of k matrices into (key, value) pairs at their
+// concatenation offsets, accumulating the time-sum segment's digit histograms
+// (sum_hist, zeroed by the caller) and zeroing the sum sort's first status
+// words and tickets.  status0 needs p.ntiles * kRadix words.
+cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off, uint64_t* keys,
+                          uint64_t* vals, uint32_t* sum_hist, uint64_t* status0, uint32_t* tickets,
+                          cudaStream_t st);
 // Exclusive prefix of the matrices' nnz (hdr[1]) -> cat_off, nnz -> lens,
 // their sum -> *total.
 cudaError_t launch_count_prefix(const MatDesc* mats, uint32_t k, uint64_t* cat_off, uint64_t* lens,

@@ -102,31 +102,6 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
   hist_flush(h, seg_hist, tl.seg);
 }
 
-__global__ void __launch_bounds__(kThreads) k_hist(SegPlan p, const uint64_t* __restrict__ keys,
-                                                   uint32_t* __restrict__ seg_hist,
-                                                   uint64_t* __restrict__ status0,
-                                                   uint32_t* __restrict__ tickets) {
-  __shared__ uint32_t h[kPasses * kRadix];
-  __shared__ Tile s_tile;
-  const uint32_t t = blockIdx.x;
-  const Tile tl = block_tile(p, t, &s_tile);
-  for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) h[i] = 0;
-  if (t == 0 && threadIdx.x < 32) tickets[threadIdx.x] = 0;
-  if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
-  __syncthreads();
-  if (tl.count == 0) return;
-  const uint64_t* in = keys + tl.base + tl.start;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < kPerThread; ++i) {
-    const uint32_t idx = warp * (kPerThread * 32) + i * 32 + lane;
-    const bool valid = idx < tl.count;
-    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-    hist_add(h, valid ? in[idx] : 0ull, valid, vmask);
-  }
-  __syncthreads();
-  hist_flush(h, seg_hist, tl.seg);
-}
-
 struct NoVal {};
 
 template <typename K, typename V, int kT>
@@ -268,32 +243,81 @@ __global__ void __launch_bounds__(kT, kMinB)
   }
 }
 
-// One tile per CTA over the stored links of matrix `seg`.
-__global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* __restrict__ mats,
-                                                     const uint64_t* __restrict__ cat_off,
-                                                     uint64_t* __restrict__ keys,
-                                                     uint64_t* __restrict__ vals) {
-  __shared__ Tile s_tile;
-  const Tile tl = block_tile(p, blockIdx.x, &s_tile);
-  if (tl.count == 0) return;
-  const MatDesc m = mats[tl.seg];
-  const uint64_t nrows = m.hdr[0];
-  const uint64_t u0 = tl.start + (uint64_t)threadIdx.x * kPerThread;
-  const uint64_t u1 = umin64(u0 + kPerThread, tl.start + tl.count);
-  if (u0 >= u1) return;
-  // row holding u0: last r with row_ptr[r] <= u0
+// Last row r of matrix m with row_ptr[r] <= u.
+__device__ __forceinline__ uint64_t row_of(const MatDesc& m, uint64_t nrows, uint64_t u) {
   uint64_t lo = 0, hi = nrows;
   while (hi - lo > 1) {
     const uint64_t mid = (lo + hi) >> 1;
-    if (m.row_ptr[mid] <= u0) lo = mid; else hi = mid;
+    if (m.row_ptr[mid] <= u) lo = mid; else hi = mid;
   }
-  uint64_t r = lo;
-  const uint64_t o = cat_off[tl.seg];
-  for (uint64_t u = u0; u < u1; ++u) {
-    while (m.row_ptr[r + 1] <= u) ++r;
-    keys[o + u] = ((uint64_t)m.row_ids[r] << 32) | m.col_ids[u];
-    vals[o + u] = m.vals[u];
+  return lo;
+}
+
+constexpr size_t kGatherSmem = 2 * (size_t)(kTile + 1) * sizeof(uint32_t);
+
+// One tile per CTA over the stored links of matrix `seg`: writes the links as
+// (src << 32 | dst, count) at the matrix's offset in the concatenation and
+// accumulates the digit histograms of the single time-sum segment.  The rows
+// that cover the tile (at most one per link) are staged in shared memory, so
+// each link finds its row by a binary search there.  Also zeroes the sum
+// sort's first status words and tickets (k_hist's other duties).
+__global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* __restrict__ mats,
+                                                     const uint64_t* __restrict__ cat_off,
+                                                     uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
+                                                     uint32_t* __restrict__ sum_hist,
+                                                     uint64_t* __restrict__ status0,
+                                                     uint32_t* __restrict__ tickets) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* s_rp = reinterpret_cast<uint32_t*>(smem);  // row starts relative to the tile, rows r0..r1+1
+  uint32_t* s_ri = s_rp + kTile + 1;                    // row ids of rows r0..r1
+  __shared__ uint32_t h[kPasses * kRadix];
+  __shared__ Tile s_tile;
+  __shared__ uint64_t s_r0;
+  __shared__ uint32_t s_nr;
+  const uint32_t t = blockIdx.x;
+  const Tile tl = block_tile(p, t, &s_tile);
+  for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) h[i] = 0;
+  if (t == 0 && threadIdx.x < 32) tickets[threadIdx.x] = 0;
+  if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  if (tl.count == 0) return;
+  const MatDesc m = mats[tl.seg];
+  if (threadIdx.x == 0) {
+    const uint64_t nrows = m.hdr[0];
+    const uint64_t r0 = row_of(m, nrows, tl.start);
+    const uint64_t r1 = row_of(m, nrows, tl.start + tl.count - 1);
+    s_r0 = r0;
+    s_nr = (uint32_t)(r1 - r0 + 1);
   }
+  __syncthreads();
+  const uint64_t r0 = s_r0;
+  const uint32_t nr = s_nr;
+  for (uint32_t i = threadIdx.x; i <= nr; i += kThreads) {
+    const uint64_t rp = m.row_ptr[r0 + i];
+    s_rp[i] = rp <= tl.start ? 0u : (uint32_t)umin64(rp - tl.start, tl.count);
+    if (i < nr) s_ri[i] = m.row_ids[r0 + i];
+  }
+  __syncthreads();
+  const uint64_t o = cat_off[tl.seg] + tl.start;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = 0; it < kPerThread; ++it) {
+    const uint32_t i = warp * (kPerThread * 32) + it * 32 + lane;
+    const bool valid = i < tl.count;
+    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    uint64_t key = 0;
+    if (valid) {
+      uint32_t lo = 0, hi = nr;  // last row r with s_rp[r] <= i
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_rp[mid] <= i) lo = mid; else hi = mid;
+      }
+      key = ((uint64_t)s_ri[lo] << 32) | m.col_ids[tl.start + i];
+      keys[o + i] = key;
+      vals[o + i] = m.vals[tl.start + i];
+    }
+    hist_add(h, key, valid, vmask);
+  }
+  __syncthreads();
+  hist_flush(h, sum_hist, 0);
 }
 
 __global__ void __launch_bounds__(1024) k_count_prefix(const MatDesc* __restrict__ mats, uint32_t k,
@@ -389,12 +413,6 @@ cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32
   return cudaGetLastError();
 }
 
-cudaError_t launch_hist(const SegPlan& p, const uint64_t* keys, uint32_t* seg_hist, uint64_t* status0,
-                        uint32_t* tickets, cudaStream_t st) {
-  if (p.ntiles == 0) return cudaSuccess;
-  k_hist<<<p.ntiles, kThreads, 0, st>>>(p, keys, seg_hist, status0, tickets);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
@@ -415,10 +433,20 @@ cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin,
                                           cfg, st);
 }
 
-cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off,
-                          uint64_t* keys, uint64_t* vals, cudaStream_t st) {
+cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off, uint64_t* keys,
+                          uint64_t* vals, uint32_t* sum_hist, uint64_t* status0, uint32_t* tickets,
+                          cudaStream_t st) {
   if (p.ntiles == 0) return cudaSuccess;
-  k_gather<<<p.ntiles, kThreads, 0, st>>>(p, mats, cat_off, keys, vals);
+  static unsigned long long configured = 0;  // one bit per device ordinal
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !((configured >> dev) & 1ull)) {
+    e = cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGatherSmem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) configured |= 1ull << dev;
+  }
+  k_gather<<<p.ntiles, kThreads, kGatherSmem, st>>>(p, mats, cat_off, keys, vals, sum_hist, status0, tickets);
   return cudaGetLastError();
 }
 
