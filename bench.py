@@ -50,10 +50,10 @@ WORKLOADS = {
 }
 DEFAULT_NWIN = {2: 64, 3: 1024, 4: 8192}
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_onesweep launch on
-# the 64-window batch (profiles/onesweep_cfg2.md); None until captured for the
-# current kernel.
-ONESWEEP_NCU_TRAFFIC = None
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_onesweep launch
+# (64-bit link keys, first digit pass) on the 64-window batch, cold cache; set
+# to None whenever that kernel changes until it is captured again.
+ONESWEEP_NCU_TRAFFIC = 90465792  # 68153088 + 22312704 B, pass 0, cold cache
 
 
 def parse_args():
@@ -68,6 +68,8 @@ def parse_args():
     ap.add_argument("--no-per-window", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="fix radix-pass launch shapes instead of autotuning, e.g. key=512,0,2;kv=512,0,1")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=1e4, help="serving arrivals, windows/s")
     ap.add_argument("--serve-windows", type=int, default=20000)
@@ -290,7 +292,15 @@ def main():
             m.free()
         summ.free()
 
-    if not args.no_autotune:
+    if args.tuning:
+        kw = {}
+        for part in args.tuning.split(";"):
+            fam, vals = part.split("=")
+            for field, v in zip(("threads", "rank", "blocks"), vals.split(",")):
+                kw[f"{fam.strip()}_{field}"] = int(v)
+        ctx.set_tuning(**kw)
+        tuning = ctx.get_tuning()
+    elif not args.no_autotune:
         tuning = ctx.autotune(src_d, dst_d, w.offsets)
     for _ in range(max(args.warmup, 0)):
         res = step(src_d, dst_d)
