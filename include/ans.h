@@ -91,8 +91,12 @@ typedef void (*ans_free_fn)(void* ptr, void* stream, void* user);
 int ans_ctx_create(ans_ctx** out, int device, size_t mem_budget_bytes,
                    ans_alloc_fn alloc, ans_free_fn free_fn, void* user);
 
-/* Wait for the context's outstanding work and release its scratch.  Matrices
- * created from it must be freed before the context is destroyed. */
+/* Wait for the context's outstanding work and release its scratch and
+ * tickets; the handle is invalid afterwards.  Matrices created from the
+ * context stay valid: the context's remaining state (its free hook and user
+ * pointer included, which must stay usable) is released with the last of
+ * them.  Destroying a context twice is ANS_ERR_INVALID_ARG (while matrices
+ * keep it alive) or undefined. */
 int ans_ctx_destroy(ans_ctx* ctx);
 
 /* Traffic matrix of one window (Table I caption): A(i,j) = #{k : d_src[k] == i,
@@ -206,15 +210,26 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * *_threads: threads per 8192-key tile, 512 or 1024.  *_rank: how lanes
  * holding equal digits find each other, 0 = one __match_any_sync per key,
  * 1 = eight ballots per key.  *_blocks: CTAs per SM the kernel is compiled
- * for, 1, or 2 (512 threads only: registers capped at 64).  Results never
+ * for, 1, or 2 (512 threads only: registers capped at 64).
+ * win_path: how window keys are sorted, 0 = on chip, one 8-CTA thread-block
+ * cluster per window of at most 2^17 packets sorting it in distributed shared
+ * memory (larger windows, and every window when the device cannot host such
+ * a cluster, take the key_* passes), 1 = the key_* passes for every window.
+ * win_threads (512 or 1024) and win_rank (as *_rank) configure the cluster
+ * kernel.  sum_path: how time sums order the links of their input matrices,
+ * 0 = ceil(log2 k) rounds of pairwise merges of the matrices' already sorted
+ * links, 1 = the kv_* radix passes over all gathered links.  Results never
  * depend on the configuration. */
 typedef struct {
     uint32_t key_threads, key_rank, key_blocks;
     uint32_t kv_threads, kv_rank, kv_blocks;
     uint32_t col_threads, col_rank, col_blocks;
+    uint32_t win_path, win_threads, win_rank;
+    uint32_t sum_path;
 } ans_tuning;
 
-/* Read / set a context's configuration (default: 512 threads, rank 0).
+/* Read / set a context's configuration (default: 512 threads, rank 0, one
+ * block; win_path 1, win_threads 1024, win_rank 0; sum_path 0).
  * ans_set_tuning fails with ANS_ERR_INVALID_ARG on values other than the
  * ones listed above. */
 int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);
@@ -223,8 +238,11 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
 /* Autotuner: runs the caller's representative batch (as ans_batch_submit with
  * per-window matrices and the time sum) once per candidate configuration,
  * three times each, times every radix pass with CUDA events on `stream`, and
- * keeps, per family, the configuration with the least total pass time.  The
- * choice is applied to the context and returned in *chosen (optional).  The
+ * keeps, per family, the configuration with the least total pass time; it
+ * then times the on-chip window sort (win_path 0, three cluster
+ * configurations) and keeps it if the batch's windows sort faster that way
+ * than by the best key passes plus their histogram sweep, and likewise picks
+ * the faster sum_path.  The choice is applied to the context and returned in *chosen (optional).  The
  * call blocks until the runs have finished; it leaves per-kernel profiling
  * disabled and its data cleared. */
 int ans_autotune(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,

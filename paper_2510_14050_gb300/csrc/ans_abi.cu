@@ -96,6 +96,10 @@ struct ans_ctx {
   void* user = nullptr;
   std::mutex mu;
   size_t live = 0;  // device bytes held: scratch + live matrix blocks
+  // Lifetime: matrix blocks keep the context alive; ans_ctx_destroy releases
+  // what only calls need and the last block to go frees the rest.
+  size_t blocks = 0;
+  bool closed = false;
 
   void* scratch = nullptr;
   size_t scratch_size = 0;
@@ -125,6 +129,16 @@ struct ans_ctx {
   // Launch configurations of the three families of onesweep passes (set by
   // ans_set_tuning / ans_autotune).
   SortCfg cfg_keys, cfg_kv, cfg_col;
+  // Window sort: 0 = on chip (one 8-CTA cluster per window of at most
+  // kClusterWindowMax packets; larger windows take the onesweep passes),
+  // 1 = onesweep passes for every window (the default: faster on every
+  // workload measured so far).  cfg_win: the cluster kernel's threads and
+  // ranking mode.
+  int win_path = 1;
+  SortCfg cfg_win{1024, kRankMatch, 1};
+  // Time sum: 0 = merge the matrices' sorted links pairwise, 1 = radix-sort
+  // the gathered links (kv passes).
+  int sum_path = 0;
 
   // Optional per-kernel timing: CUDA events recorded around each launch on
   // the launching stream, accumulated by name when read.
@@ -361,6 +375,7 @@ int make_block(ans_ctx* c, uint64_t pad, uint32_t nseg, std::vector<uint64_t> ba
     delete b;
     return fail(ANS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
   }
+  ++c->blocks;  // callers hold c->mu
   *out = b;
   return ANS_OK;
 }
@@ -379,6 +394,8 @@ int note_read(Block* b, cudaStream_t st) {
   return ANS_OK;
 }
 
+void ctx_finalize(ans_ctx* c);
+
 void block_release(Block* b) {
   if (--b->refs > 0) return;
   ans_ctx* c = b->ctx;
@@ -391,13 +408,29 @@ void block_release(Block* b) {
     }
     b->readers.clear();
   }
+  bool last = false;
   {
     std::lock_guard<std::mutex> g(c->mu);
     DeviceGuard dg(c->device);
     dev_free(c, b->mem, b->bytes, c->aux);
+    cudaEventDestroy(b->done);
+    last = --c->blocks == 0 && c->closed;
   }
-  cudaEventDestroy(b->done);
   delete b;
+  if (last) ctx_finalize(c);
+}
+
+// Free what the context kept for its live matrices, and the context.
+void ctx_finalize(ans_ctx* c) {
+  DeviceGuard dg(c->device);
+  cudaStreamSynchronize(c->aux);
+  for (auto& s : c->stage) {
+    if (s.h) cudaFreeHost(s.h);
+    if (s.ev) cudaEventDestroy(s.ev);
+  }
+  if (c->h_err_slots) cudaFreeHost(c->h_err_slots);
+  cudaStreamDestroy(c->aux);
+  delete c;
 }
 
 // Discard a block that never left the library (error path).
@@ -406,6 +439,7 @@ void block_discard(Block* b, cudaStream_t st) {
   cudaStreamSynchronize(st);
   dev_free(b->ctx, b->mem, b->bytes, st);
   cudaEventDestroy(b->done);
+  --b->ctx->blocks;  // callers hold the context's lock and keep it open
   delete b;
 }
 
@@ -456,6 +490,26 @@ struct HostPlan {
     }
     first_tile[n] = (uint32_t)t;
     pad = b;
+    ntiles = (uint32_t)t;
+  }
+  // The segments `ids` of `all`, keeping their padded starts (so a pass over
+  // this plan writes where one over `all` would).
+  void subset(const HostPlan& all, const std::vector<uint32_t>& ids) {
+    const size_t n = ids.size();
+    in_off.resize(n);
+    len.resize(n);
+    base.resize(n);
+    first_tile.resize(n + 1);
+    uint64_t t = 0;
+    for (size_t i = 0; i < n; ++i) {
+      in_off[i] = all.in_off[ids[i]];
+      len[i] = all.len[ids[i]];
+      base[i] = all.base[ids[i]];
+      first_tile[i] = (uint32_t)t;
+      t += tiles_for(len[i]);
+    }
+    first_tile[n] = (uint32_t)t;
+    pad = all.pad;
     ntiles = (uint32_t)t;
   }
 };
@@ -625,27 +679,43 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
   if ((e = cudaMemsetAsync(m + ps.lb2, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = cudaMemsetAsync(m + ps.col_hist, 0, kColPasses * kRadix * 4, st)) != cudaSuccess)
     return fail_blk(e, "memset");
-  // gather fills the sum segment's histograms and zeroes its first status
-  // words (the gather plan has at least as many tiles as the sum plan)
+  // gather (with the radix path: also the sum segment's histograms) zeroes
+  // the sort's first status words (the gather plan has at least as many
+  // tiles as the sum plan) and tickets
+  const bool merge = c->sum_path == 0;
+  const uint64_t* cat_off = at<uint64_t>(m, off_catoff);
   if ((e = timed(c, "gather", st, [&] {
-         return launch_gather(g, d_mats, at<uint64_t>(m, off_catoff), ka, va, seg_hist, at<uint64_t>(m, ps.st0),
+         return launch_gather(g, d_mats, cat_off, ka, va, merge ? nullptr : seg_hist, at<uint64_t>(m, ps.st0),
                               tickets, st);
        })) != cudaSuccess)
     return fail_blk(e, "gather");
-  rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
-  if (rc != ANS_OK) {
-    block_discard(blk, st);
-    return rc;
+  uint64_t *fk = ka, *fv = va;  // the sorted links
+  if (merge) {
+    uint64_t *ok = kb, *ov = vb;
+    for (int round = 0; (1ull << round) < k; ++round) {
+      if ((e = timed(c, "merge", st, [&] {
+             return launch_merge(cat_off, k, sp.pad, round, fk, fv, ok, ov, st);
+           })) != cudaSuccess)
+        return fail_blk(e, "merge");
+      std::swap(fk, ok);
+      std::swap(fv, ov);
+    }
+  } else {
+    rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
+    if (rc != ANS_OK) {
+      block_discard(blk, st);
+      return rc;
+    }
   }
   uint64_t* pre = at<uint64_t>(m, ps.pre);
-  if ((e = timed(c, "scan_u64", st, [&] { return launch_scan_u64(s, va, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st); })) !=
+  if ((e = timed(c, "scan_u64", st, [&] { return launch_scan_u64(s, fv, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st); })) !=
       cudaSuccess)
     return fail_blk(e, "scan");
   StatsArgs a;
   a.plan = s;
   a.hdr = blk->hdr;
   a.q = blk->q;
-  a.keys = ka;
+  a.keys = fk;
   a.col_ids = blk->col_ids;
   a.vals = blk->vals;
   a.row_ids = blk->row_ids;
@@ -706,7 +776,8 @@ int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n
 
 // Scratch layout of one batch (shared by run_windows and ans_batch_bytes).
 struct WinLayout {
-  DevPlan dp;
+  DevPlan dp, dp_big;  // every window; the windows sorted by onesweep passes
+  size_t off_small = 0;  // ids of the windows sorted on chip
   PipeScratch ps;
   size_t s_col = 0, s_vals = 0, s_row = 0, s_rp = 0, s_hdr = 0, s_q = 0;
   size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0;
@@ -714,6 +785,8 @@ struct WinLayout {
   void reserve(const HostPlan& hp, uint32_t nseg, bool want_mats, bool want_sum) {
     Layout L;
     dp.reserve(L, nseg);
+    dp_big.reserve(L, nseg);
+    off_small = L.add((size_t)nseg * 4);
     ps.reserve(L, hp.pad, std::max<uint32_t>(nseg, 1), hp.ntiles, want_sum);
     if (!want_mats) {  // the DCSR arrays are intermediate: keep them in scratch
       s_col = L.add(hp.pad * 4);
@@ -727,7 +800,7 @@ struct WinLayout {
       off_mats = L.add((size_t)nseg * sizeof(MatDesc));
       off_gplan = L.add(4 * align_up((size_t)(nseg + 1) * 8));
       off_splan = L.add(4 * kAlign);
-      off_catoff = L.add((size_t)nseg * 8);
+      off_catoff = L.add(((size_t)nseg + 1) * 8);
       off_lens = L.add((size_t)nseg * 8);
       off_total = L.add(8);
     }
@@ -757,6 +830,18 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   HostPlan hp;
   hp.build(lens, &offs);
   if ((uint64_t)hp.ntiles * kTile != hp.pad) return fail(ANS_ERR_INTERNAL, "plan");
+  // Which windows are sorted on chip (one cluster each) and which by the
+  // onesweep passes.
+  std::vector<uint32_t> small_ids, big_ids;
+  const int win_path = c->win_path;  // the caller holds c->mu
+  const SortCfg cfg_win = c->cfg_win;
+  const bool on_chip = win_path == 0 && cluster_sort_clusters(c->device) > 0;
+  for (uint32_t s = 0; s < nseg; ++s) {
+    if (on_chip && lens[s] <= kClusterWindowMax) small_ids.push_back(s);
+    else big_ids.push_back(s);
+  }
+  HostPlan hp_big;
+  hp_big.subset(hp, big_ids);
 
   // ---- scratch layout
   WinLayout wl;
@@ -802,6 +887,14 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     us.add(m + dp.base, hp.base.data(), nseg * 8);
     us.add(m + dp.first_tile, hp.first_tile.data(), (nseg + 1) * 4);
   }
+  if (!small_ids.empty()) us.add(m + wl.off_small, small_ids.data(), small_ids.size() * 4);
+  if (!big_ids.empty()) {
+    const size_t nb = big_ids.size();
+    us.add(m + wl.dp_big.in_off, hp_big.in_off.data(), nb * 8);
+    us.add(m + wl.dp_big.len, hp_big.len.data(), nb * 8);
+    us.add(m + wl.dp_big.base, hp_big.base.data(), nb * 8);
+    us.add(m + wl.dp_big.first_tile, hp_big.first_tile.data(), (nb + 1) * 4);
+  }
   std::vector<MatDesc> md;
   if (want_sum && nseg) {
     md.resize(nseg);
@@ -828,16 +921,28 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
   uint32_t* tickets = at<uint32_t>(m, ps.tickets);
   if (nseg) {
-    if ((rc = cu(cudaMemsetAsync(seg_hist, 0, (size_t)nseg * kPasses * kRadix * 4, st), "memset hist"))) return bail(rc);
     if ((rc = cu(cudaMemsetAsync(sb.q, 0, (size_t)nseg * sizeof(ans_quantities), st), "memset q"))) return bail(rc);
     if ((rc = cu(cudaMemsetAsync(m + ps.lb, 0, (size_t)hp.ntiles * 8, st), "memset lb"))) return bail(rc);
     if ((rc = cu(cudaMemsetAsync(m + ps.col_hist, 0, (size_t)nseg * kColPasses * kRadix * 4, st), "memset")))
       return bail(rc);
-    if ((rc = cu(timed(c, "pack_hist", st, [&] { return launch_pack_hist(p, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); }), "pack")))
-      return bail(rc);
-    if ((rc = sort_segments(c, p, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
-                            at<uint64_t>(m, ps.st1), tickets, st)))
-      return bail(rc);
+    if (!small_ids.empty()) {
+      const uint32_t* ids = small_ids.size() == nseg ? nullptr : at<uint32_t>(m, wl.off_small);
+      if ((rc = cu(timed(c, "cluster_sort", st, [&] {
+                     return launch_cluster_sort(p, ids, (uint32_t)small_ids.size(), d_src, d_dst, ka, tickets,
+                                                cfg_win, st);
+                   }), "cluster sort")))
+        return bail(rc);
+    }
+    if (!big_ids.empty()) {
+      const SegPlan pb = wl.dp_big.bind(m, hp_big);
+      const size_t nb = big_ids.size();
+      if ((rc = cu(cudaMemsetAsync(seg_hist, 0, nb * kPasses * kRadix * 4, st), "memset hist"))) return bail(rc);
+      if ((rc = cu(timed(c, "pack_hist", st, [&] { return launch_pack_hist(pb, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); }), "pack")))
+        return bail(rc);
+      if ((rc = sort_segments(c, pb, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
+                              at<uint64_t>(m, ps.st1), tickets, st)))
+        return bail(rc);
+    }
     StatsArgs a;
     a.plan = p;
     a.hdr = sb.hdr;
@@ -982,19 +1087,30 @@ int ans_ctx_create(ans_ctx** out, int device, size_t mem_budget_bytes, ans_alloc
 
 int ans_ctx_destroy(ans_ctx* c) {
   if (!c) return ANS_OK;
-  DeviceGuard dg(c->device);
-  cudaDeviceSynchronize();
-  for (auto& kv : c->tickets) cudaEventDestroy(kv.second.ev);
-  dev_free(c, c->scratch, c->scratch_size, c->aux);
-  dev_free(c, c->small_mem, 256, c->aux);
-  cudaStreamSynchronize(c->aux);
-  for (auto& s : c->stage) {
-    if (s.h) cudaFreeHost(s.h);
-    if (s.ev) cudaEventDestroy(s.ev);
+  bool last = false;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (c->closed) return fail(ANS_ERR_INVALID_ARG, "context already destroyed");
+    DeviceGuard dg(c->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : c->tickets) cudaEventDestroy(kv.second.ev);
+    c->tickets.clear();
+    dev_free(c, c->scratch, c->scratch_size, c->aux);
+    c->scratch = nullptr;
+    c->scratch_size = 0;
+    dev_free(c, c->small_mem, 256, c->aux);
+    c->small_mem = nullptr;
+    for (auto& kv : c->prof.pending) {
+      cudaEventDestroy(kv.a);
+      cudaEventDestroy(kv.b);
+    }
+    c->prof.pending.clear();
+    for (cudaEvent_t e : c->prof.spare) cudaEventDestroy(e);
+    c->prof.spare.clear();
+    c->closed = true;
+    last = c->blocks == 0;
   }
-  if (c->h_err_slots) cudaFreeHost(c->h_err_slots);
-  cudaStreamDestroy(c->aux);
-  delete c;
+  if (last) ctx_finalize(c);
   return ANS_OK;
 }
 
@@ -1071,7 +1187,7 @@ int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_mat
     const size_t off_mats = L.add(k * sizeof(MatDesc));
     const size_t off_gplan = L.add(4 * align_up((k + 1) * 8));
     const size_t off_splan = L.add(4 * kAlign);
-    const size_t off_catoff = L.add(k * 8);
+    const size_t off_catoff = L.add((k + 1) * 8);
     const size_t off_lens = L.add(k * 8);
     const size_t off_total = L.add(8);
     ANS_TRY(ensure_scratch(c, L.size, st));
@@ -1310,6 +1426,10 @@ int ans_get_tuning(ans_ctx* c, ans_tuning* out) {
   out->col_threads = (uint32_t)c->cfg_col.threads;
   out->col_rank = (uint32_t)c->cfg_col.rank;
   out->col_blocks = (uint32_t)c->cfg_col.blocks;
+  out->win_path = (uint32_t)c->win_path;
+  out->win_threads = (uint32_t)c->cfg_win.threads;
+  out->win_rank = (uint32_t)c->cfg_win.rank;
+  out->sum_path = (uint32_t)c->sum_path;
   return ANS_OK;
 }
 
@@ -1321,7 +1441,13 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   if (!ok(t->key_threads, t->key_rank, t->key_blocks) || !ok(t->kv_threads, t->kv_rank, t->kv_blocks) ||
       !ok(t->col_threads, t->col_rank, t->col_blocks))
     return fail(ANS_ERR_INVALID_ARG, "threads must be 512 or 1024, rank 0 or 1, blocks 1 (or 2 with 512 threads)");
+  if (t->win_path > 1 || !ok(t->win_threads, t->win_rank, 1))
+    return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
+  if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
   std::lock_guard<std::mutex> g(c->mu);
+  c->win_path = (int)t->win_path;
+  c->cfg_win = SortCfg{(int)t->win_threads, (int)t->win_rank, 1};
+  c->sum_path = (int)t->sum_path;
   c->cfg_keys = SortCfg{(int)t->key_threads, (int)t->key_rank, (int)t->key_blocks};
   c->cfg_kv = SortCfg{(int)t->kv_threads, (int)t->kv_rank, (int)t->kv_blocks};
   c->cfg_col = SortCfg{(int)t->col_threads, (int)t->col_rank, (int)t->col_blocks};
@@ -1334,7 +1460,8 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   constexpr int kVariants = 6;
   const SortCfg variants[kVariants] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankMatch, 2},
                                        {512, kRankBallot, 2}, {1024, kRankMatch, 1}, {1024, kRankBallot, 1}};
-  double t_keys[kVariants], t_kv[kVariants], t_col[kVariants];
+  double t_keys[kVariants], t_kv[kVariants], t_col[kVariants], t_pack[kVariants], t_gather[kVariants];
+
   std::vector<ans_matrix*> per(nwin, nullptr);
   auto run_once = [&]() -> int {
     ans_matrix* sum = nullptr;
@@ -1352,6 +1479,8 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     {
       std::lock_guard<std::mutex> g(c->mu);
       c->cfg_keys = c->cfg_kv = c->cfg_col = variants[v];
+      c->win_path = 1;  // time the key passes on every window
+      c->sum_path = 1;  // and the kv passes on the time sum
     }
     ANS_TRY(run_once());  // first launch of this variant (module load, smem carve-out)
     ANS_TRY(ans_profile_enable(c, 1));
@@ -1362,8 +1491,68 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     t_keys[v] = c->prof.acc["onesweep"].first;
     t_kv[v] = c->prof.acc["onesweep_sum"].first;
     t_col[v] = c->prof.acc["onesweep_col"].first;
+    t_pack[v] = c->prof.acc["pack_hist"].first;
+    t_gather[v] = c->prof.acc["gather"].first;
     c->prof.acc.clear();
     c->prof.on = false;
+  }
+  // The on-chip window sort (for windows that fit a cluster) against the
+  // fastest key passes: total window-sort time of the batch either way.
+  int bk_i = 0;
+  for (int v = 1; v < kVariants; ++v)
+    if (t_keys[v] + t_pack[v] < t_keys[bk_i] + t_pack[bk_i]) bk_i = v;
+  double best_win = t_keys[bk_i] + t_pack[bk_i];
+  int win_path = 1;
+  SortCfg win_cfg{1024, kRankMatch, 1};
+  if (cluster_sort_clusters(c->device) > 0) {
+    const SortCfg wv[3] = {{1024, kRankMatch, 1}, {1024, kRankBallot, 1}, {512, kRankMatch, 1}};
+    for (const SortCfg& w : wv) {
+      {
+        std::lock_guard<std::mutex> g(c->mu);
+        c->cfg_keys = variants[bk_i];
+        c->win_path = 0;
+        c->cfg_win = w;
+      }
+      ANS_TRY(run_once());
+      ANS_TRY(ans_profile_enable(c, 1));
+      for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
+      std::lock_guard<std::mutex> g(c->mu);
+      DeviceGuard dg(c->device);
+      prof_collect(c);
+      const double t = c->prof.acc["cluster_sort"].first + c->prof.acc["onesweep"].first +
+                       c->prof.acc["pack_hist"].first;
+      c->prof.acc.clear();
+      c->prof.on = false;
+      if (t < best_win) {
+        best_win = t;
+        win_path = 0;
+        win_cfg = w;
+      }
+    }
+  }
+
+  // Time sums: pairwise merges against the fastest kv passes (each with its
+  // gather, which builds digit histograms only for the radix passes).
+  int bv_i = 0;
+  for (int v = 1; v < kVariants; ++v)
+    if (t_kv[v] + t_gather[v] < t_kv[bv_i] + t_gather[bv_i]) bv_i = v;
+  int sum_path = 1;
+  {
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      c->win_path = 1;
+      c->sum_path = 0;
+    }
+    ANS_TRY(run_once());
+    ANS_TRY(ans_profile_enable(c, 1));
+    for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
+    std::lock_guard<std::mutex> g(c->mu);
+    DeviceGuard dg(c->device);
+    prof_collect(c);
+    const double t = c->prof.acc["merge"].first + c->prof.acc["gather"].first;
+    c->prof.acc.clear();
+    c->prof.on = false;
+    if (t < t_kv[bv_i] + t_gather[bv_i]) sum_path = 0;
   }
   auto best = [&](const double* t) {
     int b = 0;
@@ -1371,7 +1560,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       if (t[v] < t[b]) b = v;
     return variants[b];
   };
-  ans_tuning res;
+  ans_tuning res{};
   const SortCfg bk = best(t_keys), bv = best(t_kv), bc = best(t_col);
   res.key_threads = (uint32_t)bk.threads;
   res.key_rank = (uint32_t)bk.rank;
@@ -1382,6 +1571,10 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   res.col_threads = (uint32_t)bc.threads;
   res.col_rank = (uint32_t)bc.rank;
   res.col_blocks = (uint32_t)bc.blocks;
+  res.win_path = (uint32_t)win_path;
+  res.win_threads = (uint32_t)win_cfg.threads;
+  res.win_rank = (uint32_t)win_cfg.rank;
+  res.sum_path = (uint32_t)sum_path;
   ANS_TRY(ans_set_tuning(c, &res));
   if (chosen) *chosen = res;
   return ANS_OK;

@@ -27,6 +27,8 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kPasses = 64 / kRadixBits;       // LSD passes over a 64-bit key
 constexpr int kColPasses = 32 / kRadixBits;    // LSD passes over a 32-bit destination key
+constexpr int kWindowCluster = 8;              // CTAs of the on-chip window sort's cluster
+constexpr uint32_t kClusterWindowMax = 1u << 17;  // largest window sorted on chip (1 MiB of keys)
 
 // Look-back status word: 2 flag bits over a 62-bit value.
 constexpr uint64_t kFlagAgg = 1ull << 62;      // tile aggregate available
@@ -125,15 +127,34 @@ cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin,
                                 const SortCfg& cfg, cudaStream_t st);
 // Gather the stored links of k matrices into (key, value) pairs at their
 // concatenation offsets, accumulating the time-sum segment's digit histograms
-// (sum_hist, zeroed by the caller) and zeroing the sum sort's first status
-// words and tickets.  status0 needs p.ntiles * kRadix words.
+// (sum_hist, zeroed by the caller; null: none) and zeroing the sum sort's
+// first status words and tickets.  status0 needs p.ntiles * kRadix words.
 cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off, uint64_t* keys,
                           uint64_t* vals, uint32_t* sum_hist, uint64_t* status0, uint32_t* tickets,
                           cudaStream_t st);
-// Exclusive prefix of the matrices' nnz (hdr[1]) -> cat_off, nnz -> lens,
-// their sum -> *total.
+// Exclusive prefix of the matrices' nnz (hdr[1]) -> cat_off[0..k), nnz ->
+// lens, their sum -> *total and cat_off[k].
 cudaError_t launch_count_prefix(const MatDesc* mats, uint32_t k, uint64_t* cat_off, uint64_t* lens,
                                 uint64_t* total, cudaStream_t st);
+
+// ---- launchers (ans_cluster.cu) ------------------------------------------
+// Sort the keys src << 32 | dst of every segment seg_ids[0..nclusters) (or
+// 0..nclusters if seg_ids is null; each at most kClusterWindowMax items) on
+// chip, one 8-CTA cluster per segment, writing them to keys at base[s]; also
+// zeroes tickets[0..32).  cfg.threads is 512 or 1024, cfg.rank as for onesweep.
+cudaError_t launch_cluster_sort(const SegPlan& p, const uint32_t* seg_ids, uint32_t nclusters, const uint32_t* src,
+                                const uint32_t* dst, uint64_t* keys, uint32_t* tickets, const SortCfg& cfg,
+                                cudaStream_t st);
+// Clusters of the window sort that fit on `device` at once (0: unavailable).
+int cluster_sort_clusters(int device);
+
+// ---- launchers (ans_merge.cu) --------------------------------------------
+// One round of pairwise merges of sorted (key, value) runs: runs of 2^round
+// matrices of the concatenation described by cat_off (k + 1 starts on the
+// device) are merged pairwise from kin/vin into kout/vout at the same
+// offsets.  total_cap bounds cat_off[k] (it sizes the grid).
+cudaError_t launch_merge(const uint64_t* cat_off, uint32_t k, uint64_t total_cap, int round, const uint64_t* kin,
+                         const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st);
 
 // ---- launchers (ans_stats.cu) --------------------------------------------
 // Run-length reduce sorted keys into DCSR structure (col_ids, row_ids,
@@ -271,6 +292,24 @@ __device__ __forceinline__ uint32_t scan256_excl(uint32_t v, uint32_t* tmp, uint
   if (total) *total = tot;
   __syncthreads();
   return off + x - v;
+}
+
+// Peer mask of lanes holding the same 8-bit digit: one __match_any_sync, or
+// eight ballots (one per digit bit) intersected.  `valid` lanes only.
+template <int kRank>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
+  if constexpr (kRank == kRankMatch) {
+    return __match_any_sync(0xffffffffu, valid ? d : (uint32_t)kRadix);
+  } else {
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t ones = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? ones : ~ones;
+    }
+    return peers;
+  }
 }
 
 template <typename T>

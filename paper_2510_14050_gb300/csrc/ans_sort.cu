@@ -110,24 +110,6 @@ constexpr size_t onesweep_smem_bytes() {
          (size_t)(kT / 32) * (kRadix + 1) * 4;
 }
 
-// Peer mask of lanes holding the same 8-bit digit: one __match_any_sync, or
-// eight ballots (one per digit bit) intersected.  `valid` lanes only.
-template <int kRank>
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
-  if constexpr (kRank == kRankMatch) {
-    return __match_any_sync(0xffffffffu, valid ? d : (uint32_t)kRadix);
-  } else {
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
-      const uint32_t bit = (d >> b) & 1u;
-      const uint32_t ones = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? ones : ~ones;
-    }
-    return peers;
-  }
-}
-
 // One stable digit pass over keys of type K (8 passes for 64-bit keys, 4 for
 // 32-bit keys; seg_hist holds sizeof(K) histograms per segment), optionally
 // carrying values of type V.  kT threads share the 8192-key tile (kTile / kT
@@ -256,8 +238,9 @@ __device__ __forceinline__ uint64_t row_of(const MatDesc& m, uint64_t nrows, uin
 constexpr size_t kGatherSmem = 2 * (size_t)(kTile + 1) * sizeof(uint32_t);
 
 // One tile per CTA over the stored links of matrix `seg`: writes the links as
-// (src << 32 | dst, count) at the matrix's offset in the concatenation and
-// accumulates the digit histograms of the single time-sum segment.  The rows
+// (src << 32 | dst, count) at the matrix's offset in the concatenation and,
+// unless sum_hist is null, accumulates the digit histograms of the single
+// time-sum segment.  The rows
 // that cover the tile (at most one per link) are staged in shared memory, so
 // each link finds its row by a binary search there.  Also zeroes the sum
 // sort's first status words and tickets (k_hist's other duties).
@@ -314,8 +297,9 @@ __global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* _
       keys[o + i] = key;
       vals[o + i] = m.vals[tl.start + i];
     }
-    hist_add(h, key, valid, vmask);
+    if (sum_hist) hist_add(h, key, valid, vmask);
   }
+  if (!sum_hist) return;
   __syncthreads();
   hist_flush(h, sum_hist, 0);
 }
@@ -354,7 +338,10 @@ __global__ void __launch_bounds__(1024) k_count_prefix(const MatDesc* __restrict
     if (threadIdx.x == 0) s_carry = carry + tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *total = s_carry;
+  if (threadIdx.x == 0) {
+    *total = s_carry;
+    cat_off[k] = s_carry;
+  }
 }
 
 // Dynamic shared memory is configured once per kernel instance and device.

@@ -258,7 +258,7 @@ def test_every_sort_configuration_is_exact(ans, synth, threads, rank, blocks):
     c = ans.Context(0)
     try:
         c.set_tuning(key_threads=threads, key_rank=rank, key_blocks=blocks, kv_threads=threads, kv_rank=rank,
-                     kv_blocks=blocks, col_threads=threads, col_rank=rank, col_blocks=blocks)
+                     kv_blocks=blocks, col_threads=threads, col_rank=rank, col_blocks=blocks, win_path=1)
         assert c.get_tuning()["kv_threads"] == threads
         check_batch(ans, c, w)
     finally:
@@ -278,3 +278,84 @@ def test_autotune_picks_valid_configuration(ans, synth):
         assert ei.value.code == ans.ERR_INVALID_ARG
     finally:
         c.close()
+
+
+# Windows sorted on chip by one 8-CTA cluster (at most 2^17 packets, spread
+# over the CTAs in power-of-two slices of 512 .. 16384 keys) next to windows
+# that take the onesweep passes, in one batch.
+CLUSTER_SIZES = [0, 1, 511, 512, 513, 4095, 4097, 16383, 16384, 16385, 65539, 131071, 131072, 131073, 200000]
+
+
+@pytest.mark.parametrize("path,threads,rank", [(0, 1024, 0), (0, 1024, 1), (0, 512, 0), (0, 512, 1), (1, 1024, 0)])
+def test_window_sort_paths_are_exact(ans, synth, path, threads, rank):
+    w = synth.generate(5, sizes=CLUSTER_SIZES)
+    c = ans.Context(0)
+    try:
+        c.set_tuning(win_path=path, win_threads=threads, win_rank=rank)
+        assert c.get_tuning()["win_path"] == path
+        check_batch(ans, c, w)
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("n", [1 << 17, (1 << 17) - 1])
+def test_window_sort_degenerate_windows(ans, n, path):
+    """Every key equal (one digit in every pass), and one source to n distinct
+    destinations (all keys share the upper four digits), on both window
+    paths."""
+    c = ans.Context(0)
+    try:
+        c.set_tuning(win_path=path)
+        z = np.full(n, 0xDEADBEEF, np.uint32)
+        check_window(c, z, z, "identical").free()
+        rng = np.random.default_rng(n)
+        d = rng.permutation(np.arange(n, dtype=np.uint64) * 7919 % (1 << 32)).astype(np.uint32)
+        check_window(c, np.full(n, 5, np.uint32), d, "star").free()
+        check_window(c, d, np.full(n, 0xFFFFFFFF, np.uint32), "reverse star").free()
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("sum_path", [0, 1])
+@pytest.mark.parametrize("nwin", [1, 2, 3, 5, 8, 13])
+def test_time_sum_paths_are_exact(ans, synth, sum_path, nwin):
+    """Time sums by pairwise merges (0) and by radix passes (1), for window
+    counts that leave odd runs and empty windows at every merge round."""
+    sizes = [(i * 7919) % 30000 if i % 4 != 2 else 0 for i in range(nwin)]
+    sizes[0] = max(sizes[0], 3)
+    w = synth.generate(5, sizes=sizes, first_window=nwin)
+    c = ans.Context(0)
+    try:
+        c.set_tuning(sum_path=sum_path)
+        mats, summ, _ = check_batch(ans, c, w)
+        # sums of sums and of matrices in another order
+        exp = oracle.sum_matrices([oracle.traffic_matrix(*w.window(i)) for i in range(nwin)])
+        half = c.sum_windows(mats[::2])
+        rest = c.sum_windows(mats[1::2]) if nwin > 1 else None
+        total = c.sum_windows([half, rest] if rest is not None else [half])
+        assert_dcsr_equal(total.to_numpy(), exp, "sum of sums")
+        rev = c.sum_windows(mats[::-1])
+        assert_dcsr_equal(rev.to_numpy(), exp, "reversed")
+    finally:
+        c.close()
+
+
+def test_matrices_outlive_their_context(ans, synth):
+    """A matrix stays readable after ans_ctx_destroy; the last matrix freed
+    releases the context's remaining state."""
+    w = synth.generate(5, sizes=[5000, 7000])
+    c = ans.Context(0)
+    mats, summ, _ = c.batch_submit(dev(w.src), dev(w.dst), w.offsets, ans.BATCH_MATRICES | ans.BATCH_SUM,
+                                   want_ticket=False)
+    single = c.build_window(dev(w.window(0)[0]), dev(w.window(0)[1]), 5000)
+    c.close()
+    for i, m in enumerate(mats):
+        exp = oracle.traffic_matrix(*w.window(i))
+        assert_dcsr_equal(m.to_numpy(), exp, f"window {i}")
+        assert m.quantities() == oracle.network_quantities(exp)
+        m.free()
+    assert_dcsr_equal(summ.to_numpy(), oracle.sum_matrices([oracle.traffic_matrix(*w.window(i)) for i in range(2)]))
+    summ.free()
+    assert_dcsr_equal(single.to_numpy(), oracle.traffic_matrix(*w.window(0)))
+    single.free()
