@@ -69,7 +69,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default=None,
-                    help="fix radix-pass launch shapes instead of autotuning, e.g. key=512,0,2;kv=512,0,1")
+                    help="fix launch shapes and paths instead of autotuning, e.g. key=512,0,2;kv=512,0,1;agg_path=1")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=1e4, help="serving arrivals, windows/s")
     ap.add_argument("--serve-windows", type=int, default=20000)
@@ -296,8 +296,12 @@ def main():
         kw = {}
         for part in args.tuning.split(";"):
             fam, vals = part.split("=")
+            fam = fam.strip()
+            if fam.endswith("_path"):  # e.g. agg_path=1
+                kw[fam] = int(vals)
+                continue
             for field, v in zip(("threads", "rank", "blocks"), vals.split(",")):
-                kw[f"{fam.strip()}_{field}"] = int(v)
+                kw[f"{fam}_{field}"] = int(v)
         ctx.set_tuning(**kw)
         tuning = ctx.get_tuning()
     elif not args.no_autotune:

@@ -218,18 +218,23 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * win_threads (512 or 1024) and win_rank (as *_rank) configure the cluster
  * kernel.  sum_path: how time sums order the links of their input matrices,
  * 0 = ceil(log2 k) rounds of pairwise merges of the matrices' already sorted
- * links, 1 = the kv_* radix passes over all gathered links.  Results never
- * depend on the configuration. */
+ * links, 1 = the kv_* radix passes over all gathered links.  agg_path: how
+ * a window's equal packets are grouped, 0 = sorting every packet's link key,
+ * 1 = counting links in a per-window hash table (2^k >= 2 x packets slots of
+ * 12 bytes, kept by the context between calls) and sorting only the distinct
+ * links with their counts (kv_* passes); worth it when windows repeat links
+ * heavily.  Results never depend on the configuration. */
 typedef struct {
     uint32_t key_threads, key_rank, key_blocks;
     uint32_t kv_threads, kv_rank, kv_blocks;
     uint32_t col_threads, col_rank, col_blocks;
     uint32_t win_path, win_threads, win_rank;
     uint32_t sum_path;
+    uint32_t agg_path;
 } ans_tuning;
 
 /* Read / set a context's configuration (default: 512 threads, rank 0, one
- * block; win_path 1, win_threads 1024, win_rank 0; sum_path 0).
+ * block; win_path 1, win_threads 1024, win_rank 0; sum_path 0; agg_path 0).
  * ans_set_tuning fails with ANS_ERR_INVALID_ARG on values other than the
  * ones listed above. */
 int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);
@@ -241,8 +246,9 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
  * keeps, per family, the configuration with the least total pass time; it
  * then times the on-chip window sort (win_path 0, three cluster
  * configurations) and keeps it if the batch's windows sort faster that way
- * than by the best key passes plus their histogram sweep, and likewise picks
- * the faster sum_path.  The choice is applied to the context and returned in *chosen (optional).  The
+ * than by the best key passes plus their histogram sweep, likewise picks the
+ * faster sum_path, and finally the agg_path with the smaller total kernel
+ * time of the whole batch.  The choice is applied to the context and returned in *chosen (optional).  The
  * call blocks until the runs have finished; it leaves per-kernel profiling
  * disabled and its data cleared. */
 int ans_autotune(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,

@@ -139,6 +139,14 @@ struct ans_ctx {
   // Time sum: 0 = merge the matrices' sorted links pairwise, 1 = radix-sort
   // the gathered links (kv passes).
   int sum_path = 0;
+  // Window aggregation: 0 = sort every packet's key, 1 = count links in
+  // per-window hash tables and sort the distinct links.  The tables live in
+  // their own arena, left empty by every call that used them (hash_dirty
+  // marks one that may not have been).
+  int agg_path = 0;
+  void* hash_mem = nullptr;
+  size_t hash_slots = 0;
+  bool hash_dirty = false;
 
   // Optional per-kernel timing: CUDA events recorded around each launch on
   // the launching stream, accumulated by name when read.
@@ -289,6 +297,27 @@ int ensure_scratch(ans_ctx* c, size_t bytes, cudaStream_t st) {
   if (rc != ANS_OK) return rc;
   c->scratch = p;
   c->scratch_size = want;
+  return ANS_OK;
+}
+
+// The hash tables' arena: `slots` slots of (uint64 key, uint32 count), all
+// empty (keys all ones, counts 0) when this returns.
+int ensure_hash(ans_ctx* c, size_t slots, cudaStream_t st) {
+  if (slots > c->hash_slots) {
+    dev_free(c, c->hash_mem, c->hash_slots * 12, st);
+    c->hash_mem = nullptr;
+    c->hash_slots = 0;
+    void* p = nullptr;
+    ANS_TRY(dev_alloc(c, slots * 12, st, &p));
+    c->hash_mem = p;
+    c->hash_slots = slots;
+    c->hash_dirty = true;
+  }
+  if (c->hash_dirty) {
+    ANS_CUDA(cudaMemsetAsync(c->hash_mem, 0xff, c->hash_slots * 8, st));
+    ANS_CUDA(cudaMemsetAsync((char*)c->hash_mem + c->hash_slots * 8, 0, c->hash_slots * 4, st));
+    c->hash_dirty = false;
+  }
   return ANS_OK;
 }
 
@@ -571,10 +600,11 @@ T* at(char* m, size_t off) {
 // Sort keys (and values) of the segments of `p` in place: 8 stable digit
 // passes ping-ponging between a and b; the result ends in a.
 int sort_segments(ans_ctx* c, const SegPlan& p, uint64_t* ka, uint64_t* kb, uint64_t* va, uint64_t* vb,
-                  const uint32_t* seg_hist, uint64_t* st0, uint64_t* st1, uint32_t* tickets, cudaStream_t st) {
+                  const uint32_t* seg_hist, uint64_t* st0, uint64_t* st1, uint32_t* tickets, cudaStream_t st,
+                  const char* name = nullptr) {
   for (int pass = 0; pass < kPasses; ++pass) {
     const bool even = (pass % 2) == 0;
-    KTime kt(c, va ? "onesweep_sum" : "onesweep", st);
+    KTime kt(c, name ? name : va ? "onesweep_sum" : "onesweep", st);
     ANS_CUDA(launch_onesweep(p, pass, even ? ka : kb, even ? kb : ka, va ? (even ? va : vb) : nullptr,
                              va ? (even ? vb : va) : nullptr, seg_hist, even ? st0 : st1,
                              even ? st1 : st0, tickets + pass, c->d_err, va ? c->cfg_kv : c->cfg_keys, st));
@@ -774,20 +804,45 @@ int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n
   return ANS_OK;
 }
 
+// Hash path: window s gets a table of 2^lg[s] >= 2 * lens[s] slots (at
+// least one tile; none for an empty window); `tab` lays the tables out as
+// segments of the arena.
+void plan_tables(const std::vector<uint64_t>& lens, std::vector<uint32_t>* lg, HostPlan* tab) {
+  std::vector<uint64_t> slots(lens.size());
+  lg->resize(lens.size());
+  for (size_t s = 0; s < lens.size(); ++s) {
+    uint32_t l = 13;  // kTile slots
+    while ((1ull << l) < 2 * lens[s]) ++l;
+    (*lg)[s] = l;
+    slots[s] = lens[s] ? (1ull << l) : 0;
+  }
+  tab->build(slots, nullptr);
+}
+
 // Scratch layout of one batch (shared by run_windows and ans_batch_bytes).
 struct WinLayout {
   DevPlan dp, dp_big;  // every window; the windows sorted by onesweep passes
   size_t off_small = 0;  // ids of the windows sorted on chip
+  DevPlan dp_tab;        // hash path: the windows' tables as segments
+  size_t off_tlg = 0, off_special = 0, off_hulen = 0, off_nclaim = 0, off_claims = 0;
   PipeScratch ps;
   size_t s_col = 0, s_vals = 0, s_row = 0, s_rp = 0, s_hdr = 0, s_q = 0;
   size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0;
   size_t size = 0;
-  void reserve(const HostPlan& hp, uint32_t nseg, bool want_mats, bool want_sum) {
+  void reserve(const HostPlan& hp, uint32_t nseg, bool want_mats, bool want_sum, bool hash = false) {
     Layout L;
     dp.reserve(L, nseg);
     dp_big.reserve(L, nseg);
     off_small = L.add((size_t)nseg * 4);
-    ps.reserve(L, hp.pad, std::max<uint32_t>(nseg, 1), hp.ntiles, want_sum);
+    if (hash) {
+      dp_tab.reserve(L, nseg);
+      off_tlg = L.add((size_t)nseg * 4);
+      off_special = L.add((size_t)nseg * 8);
+      off_hulen = L.add((size_t)nseg * 8);
+      off_nclaim = L.add((size_t)nseg * 8);
+      off_claims = L.add(hp.pad * 4);
+    }
+    ps.reserve(L, hp.pad, std::max<uint32_t>(nseg, 1), hp.ntiles, want_sum || hash);
     if (!want_mats) {  // the DCSR arrays are intermediate: keep them in scratch
       s_col = L.add(hp.pad * 4);
       s_vals = L.add(hp.pad * 8);
@@ -842,10 +897,16 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   }
   HostPlan hp_big;
   hp_big.subset(hp, big_ids);
+  // Hash path: one table per window of 2^lg >= 2 * packets slots (at least
+  // one tile; none for an empty window), as segments of the table arena.
+  const bool hash = c->agg_path == 1 && nseg > 0;
+  HostPlan hp_tab;
+  std::vector<uint32_t> tab_lg;
+  if (hash) plan_tables(lens, &tab_lg, &hp_tab);
 
   // ---- scratch layout
   WinLayout wl;
-  wl.reserve(hp, nseg, want_mats, want_sum);
+  wl.reserve(hp, nseg, want_mats, want_sum, hash);
   const DevPlan& dp = wl.dp;
   const PipeScratch& ps = wl.ps;
   const size_t s_col = wl.s_col, s_vals = wl.s_vals, s_row = wl.s_row, s_rp = wl.s_rp, s_hdr = wl.s_hdr,
@@ -854,6 +915,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
                off_catoff = wl.off_catoff, off_lens = wl.off_lens, off_total = wl.off_total;
 
   ANS_TRY(ensure_scratch(c, wl.size, st));
+  if (hash) ANS_TRY(ensure_hash(c, hp_tab.pad, st));
   char* m = (char*)c->scratch;
 
   Block* blk = nullptr;
@@ -888,7 +950,11 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     us.add(m + dp.first_tile, hp.first_tile.data(), (nseg + 1) * 4);
   }
   if (!small_ids.empty()) us.add(m + wl.off_small, small_ids.data(), small_ids.size() * 4);
-  if (!big_ids.empty()) {
+  if (hash) {
+    us.add(m + wl.dp_tab.base, hp_tab.base.data(), nseg * 8);
+    us.add(m + wl.off_tlg, tab_lg.data(), nseg * 4);
+  }
+  if (!hash && !big_ids.empty()) {
     const size_t nb = big_ids.size();
     us.add(m + wl.dp_big.in_off, hp_big.in_off.data(), nb * 8);
     us.add(m + wl.dp_big.len, hp_big.len.data(), nb * 8);
@@ -925,7 +991,49 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     if ((rc = cu(cudaMemsetAsync(m + ps.lb, 0, (size_t)hp.ntiles * 8, st), "memset lb"))) return bail(rc);
     if ((rc = cu(cudaMemsetAsync(m + ps.col_hist, 0, (size_t)nseg * kColPasses * kRadix * 4, st), "memset")))
       return bail(rc);
-    if (!small_ids.empty()) {
+    SegPlan pw = p;  // the plan of the statistics phases
+    int mode = kModeWindow;
+    uint64_t* pre = nullptr;
+    if (hash) {
+      HashTabs h;
+      h.keys = (uint64_t*)c->hash_mem;
+      h.cnt = (uint32_t*)((char*)c->hash_mem + c->hash_slots * 8);
+      h.off = at<uint64_t>(m, wl.dp_tab.base);
+      h.lg = at<uint32_t>(m, wl.off_tlg);
+      h.special = at<uint64_t>(m, wl.off_special);
+      h.claims = at<uint32_t>(m, wl.off_claims);
+      h.nclaim = at<uint64_t>(m, wl.off_nclaim);
+      uint64_t* hulen = at<uint64_t>(m, wl.off_hulen);
+      uint64_t* va = at<uint64_t>(m, ps.vals_a);
+      uint64_t* vb = at<uint64_t>(m, ps.vals_b);
+      pre = at<uint64_t>(m, ps.pre);
+      if ((rc = cu(cudaMemsetAsync(h.special, 0, (size_t)nseg * 8, st), "memset"))) return bail(rc);
+      if ((rc = cu(cudaMemsetAsync(h.nclaim, 0, (size_t)nseg * 8, st), "memset"))) return bail(rc);
+      if ((rc = cu(cudaMemsetAsync(hulen, 0, (size_t)nseg * 8, st), "memset"))) return bail(rc);
+      if ((rc = cu(cudaMemsetAsync(seg_hist, 0, (size_t)nseg * kPasses * kRadix * 4, st), "memset"))) return bail(rc);
+      if ((rc = cu(cudaMemsetAsync(m + ps.lb2, 0, (size_t)hp.ntiles * 8, st), "memset"))) return bail(rc);
+      c->hash_dirty = true;  // until the compaction that empties the tables is queued
+      if ((rc = cu(timed(c, "hash_insert", st, [&] { return launch_hash_insert(p, d_src, d_dst, h, c->d_err, st); }),
+                   "hash insert")))
+        return bail(rc);
+      SegPlan pc = p;
+      pc.len = h.nclaim;
+      if ((rc = cu(timed(c, "hash_compact", st, [&] {
+                     return launch_hash_compact(pc, h, hulen, ka, va, seg_hist, at<uint64_t>(m, ps.st0), tickets, st);
+                   }), "hash compact")))
+        return bail(rc);
+      c->hash_dirty = false;
+      pw.len = hulen;
+      if ((rc = sort_segments(c, pw, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1),
+                              tickets, st, "onesweep_hash")))
+        return bail(rc);
+      if ((rc = cu(timed(c, "scan_u64", st, [&] {
+                     return launch_scan_u64(pw, va, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st);
+                   }), "scan")))
+        return bail(rc);
+      mode = kModeSum;
+    }
+    if (!hash && !small_ids.empty()) {
       const uint32_t* ids = small_ids.size() == nseg ? nullptr : at<uint32_t>(m, wl.off_small);
       if ((rc = cu(timed(c, "cluster_sort", st, [&] {
                      return launch_cluster_sort(p, ids, (uint32_t)small_ids.size(), d_src, d_dst, ka, tickets,
@@ -933,7 +1041,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
                    }), "cluster sort")))
         return bail(rc);
     }
-    if (!big_ids.empty()) {
+    if (!hash && !big_ids.empty()) {
       const SegPlan pb = wl.dp_big.bind(m, hp_big);
       const size_t nb = big_ids.size();
       if ((rc = cu(cudaMemsetAsync(seg_hist, 0, nb * kPasses * kRadix * 4, st), "memset hist"))) return bail(rc);
@@ -944,7 +1052,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         return bail(rc);
     }
     StatsArgs a;
-    a.plan = p;
+    a.plan = pw;
     a.hdr = sb.hdr;
     a.q = sb.q;
     a.keys = ka;
@@ -954,7 +1062,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     a.row_ptr = sb.row_ptr;
     a.run_start = at<uint64_t>(m, ps.run_start);
     a.row_pos = at<uint64_t>(m, ps.row_pos);
-    a.pre = nullptr;
+    a.pre = pre;
     a.lookback = at<uint64_t>(m, ps.lb);
     a.ticket = tickets + kPasses;
     a.col_hist = at<uint32_t>(m, ps.col_hist);
@@ -962,11 +1070,11 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     a.col_st0 = at<uint64_t>(m, ps.st0);
     a.col_tickets = tickets + 2 * 32;
     a.err = c->d_err;
-    a.mode = kModeWindow;
+    a.mode = mode;
     if ((rc = cu(timed(c, "empty_fixup", st, [&] { return launch_empty_fixup(a, st); }), "empty"))) return bail(rc);
     if ((rc = cu(timed(c, "rle", st, [&] { return launch_rle(a, st); }), "rle"))) return bail(rc);
     if ((rc = cu(timed(c, "finish", st, [&] { return launch_finish(a, st); }), "finish"))) return bail(rc);
-    if ((rc = column_pass(c, p, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, st))) return bail(rc);
+    if ((rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, st))) return bail(rc);
   }
 
   if (want_sum) {
@@ -1100,6 +1208,9 @@ int ans_ctx_destroy(ans_ctx* c) {
     c->scratch_size = 0;
     dev_free(c, c->small_mem, 256, c->aux);
     c->small_mem = nullptr;
+    dev_free(c, c->hash_mem, c->hash_slots * 12, c->aux);
+    c->hash_mem = nullptr;
+    c->hash_slots = 0;
     for (auto& kv : c->prof.pending) {
       cudaEventDestroy(kv.a);
       cudaEventDestroy(kv.b);
@@ -1402,12 +1513,19 @@ int ans_batch_bytes(ans_ctx* c, const uint64_t* h_offsets, size_t nwin, uint32_t
   HostPlan hp;
   hp.build(lens, nullptr);
   const bool want_mats = (flags & ANS_BATCH_MATRICES) != 0, want_sum = (flags & ANS_BATCH_SUM) != 0;
-  WinLayout wl;
-  wl.reserve(hp, (uint32_t)nwin, want_mats, want_sum);
-  size_t need = 0;
   std::lock_guard<std::mutex> g(c->mu);
+  const bool hash = c->agg_path == 1 && nwin > 0;
+  WinLayout wl;
+  wl.reserve(hp, (uint32_t)nwin, want_mats, want_sum, hash);
+  size_t need = 0;
   if (wl.size > c->scratch_size)  // the scratch is replaced by a larger one
     need += std::max(wl.size, c->scratch_size + c->scratch_size / 4) - c->scratch_size;
+  if (hash) {
+    std::vector<uint32_t> lg;
+    HostPlan tab;
+    plan_tables(lens, &lg, &tab);
+    if (tab.pad > c->hash_slots) need += (tab.pad - c->hash_slots) * 12;  // the arena is replaced
+  }
   if (want_mats && nwin) need += BlockLayout(hp.pad, (uint32_t)nwin).total;
   if (want_sum) need += BlockLayout((total + kTile - 1) / kTile * kTile, 1).total;
   *bytes = need;
@@ -1430,6 +1548,7 @@ int ans_get_tuning(ans_ctx* c, ans_tuning* out) {
   out->win_threads = (uint32_t)c->cfg_win.threads;
   out->win_rank = (uint32_t)c->cfg_win.rank;
   out->sum_path = (uint32_t)c->sum_path;
+  out->agg_path = (uint32_t)c->agg_path;
   return ANS_OK;
 }
 
@@ -1444,10 +1563,12 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   if (t->win_path > 1 || !ok(t->win_threads, t->win_rank, 1))
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
   if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
+  if (t->agg_path > 1) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0 or 1");
   std::lock_guard<std::mutex> g(c->mu);
   c->win_path = (int)t->win_path;
   c->cfg_win = SortCfg{(int)t->win_threads, (int)t->win_rank, 1};
   c->sum_path = (int)t->sum_path;
+  c->agg_path = (int)t->agg_path;
   c->cfg_keys = SortCfg{(int)t->key_threads, (int)t->key_rank, (int)t->key_blocks};
   c->cfg_kv = SortCfg{(int)t->kv_threads, (int)t->kv_rank, (int)t->kv_blocks};
   c->cfg_col = SortCfg{(int)t->col_threads, (int)t->col_rank, (int)t->col_blocks};
@@ -1481,6 +1602,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       c->cfg_keys = c->cfg_kv = c->cfg_col = variants[v];
       c->win_path = 1;  // time the key passes on every window
       c->sum_path = 1;  // and the kv passes on the time sum
+      c->agg_path = 0;
     }
     ANS_TRY(run_once());  // first launch of this variant (module load, smem carve-out)
     ANS_TRY(ans_profile_enable(c, 1));
@@ -1554,6 +1676,33 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     c->prof.on = false;
     if (t < t_kv[bv_i] + t_gather[bv_i]) sum_path = 0;
   }
+  // Window aggregation: hash counting against sorting every packet, by the
+  // whole batch's kernel time with everything else as chosen.
+  int agg_path = 0;
+  {
+    double tot[2] = {0, 0};
+    for (int a = 0; a < 2; ++a) {
+      {
+        std::lock_guard<std::mutex> g(c->mu);
+        c->cfg_keys = variants[bk_i];
+        c->cfg_kv = variants[bv_i];
+        c->win_path = win_path;
+        c->cfg_win = win_cfg;
+        c->sum_path = sum_path;
+        c->agg_path = a;
+      }
+      ANS_TRY(run_once());
+      ANS_TRY(ans_profile_enable(c, 1));
+      for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
+      std::lock_guard<std::mutex> g(c->mu);
+      DeviceGuard dg(c->device);
+      prof_collect(c);
+      for (const auto& kv : c->prof.acc) tot[a] += kv.second.first;
+      c->prof.acc.clear();
+      c->prof.on = false;
+    }
+    agg_path = tot[1] < tot[0] ? 1 : 0;
+  }
   auto best = [&](const double* t) {
     int b = 0;
     for (int v = 1; v < kVariants; ++v)
@@ -1561,7 +1710,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     return variants[b];
   };
   ans_tuning res{};
-  const SortCfg bk = best(t_keys), bv = best(t_kv), bc = best(t_col);
+  const SortCfg bk = variants[bk_i], bv = variants[bv_i], bc = best(t_col);
   res.key_threads = (uint32_t)bk.threads;
   res.key_rank = (uint32_t)bk.rank;
   res.key_blocks = (uint32_t)bk.blocks;
@@ -1575,6 +1724,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   res.win_threads = (uint32_t)win_cfg.threads;
   res.win_rank = (uint32_t)win_cfg.rank;
   res.sum_path = (uint32_t)sum_path;
+  res.agg_path = (uint32_t)agg_path;
   ANS_TRY(ans_set_tuning(c, &res));
   if (chosen) *chosen = res;
   return ANS_OK;

@@ -38,6 +38,7 @@ constexpr uint32_t kSpinLimit = 1u << 20;      // polls (about 1 s) before a wai
 
 enum ErrBits : uint32_t {
   kErrLookback = 1u,   // a look-back wait hit kSpinLimit
+  kErrHashFull = 2u,   // a hash probe sequence found no free slot
 };
 
 // How a onesweep pass is launched (chosen per context by the autotuner):
@@ -97,6 +98,21 @@ struct ColBnd {
   uint32_t has_head, pad;
 };
 
+// Per-window hash tables of the hash aggregation path (device pointers):
+// window s owns slots [off[s], off[s] + 2^lg[s]) of keys/cnt; special[s]
+// counts the all-ones key, which marks empty slots; the slots window s
+// claimed are listed at claims + base[s] (its padded start), nclaim[s] of
+// them.
+struct HashTabs {
+  uint64_t* keys = nullptr;
+  uint32_t* cnt = nullptr;
+  const uint64_t* off = nullptr;
+  const uint32_t* lg = nullptr;
+  uint64_t* special = nullptr;
+  uint32_t* claims = nullptr;
+  uint64_t* nclaim = nullptr;
+};
+
 // Matrix descriptor for the time-sum gather.
 struct MatDesc {
   const uint32_t* row_ids;
@@ -147,6 +163,19 @@ cudaError_t launch_cluster_sort(const SegPlan& p, const uint32_t* seg_ids, uint3
                                 cudaStream_t st);
 // Clusters of the window sort that fit on `device` at once (0: unavailable).
 int cluster_sort_clusters(int device);
+
+// ---- launchers (ans_hash.cu) ---------------------------------------------
+// Count the packets of every window of `p` into its hash table (tables clean
+// on entry; special and nclaim zeroed), listing the claimed slots.
+cudaError_t launch_hash_insert(const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HashTabs& h,
+                               uint32_t* err, cudaStream_t st);
+// pc: the window plan with len = h.nclaim.  Move every window's (key, count)
+// pairs out of its table to okeys/ovals at base[s], their number to ulen[s],
+// their digit histograms to seg_hist (zeroed); empties the claimed slots;
+// zeroes the first status words of pc's tiles and tickets[0..32).
+cudaError_t launch_hash_compact(const SegPlan& pc, const HashTabs& h, uint64_t* ulen, uint64_t* okeys,
+                                uint64_t* ovals, uint32_t* seg_hist, uint64_t* status0, uint32_t* tickets,
+                                cudaStream_t st);
 
 // ---- launchers (ans_merge.cu) --------------------------------------------
 // One round of pairwise merges of sorted (key, value) runs: runs of 2^round

@@ -359,3 +359,40 @@ def test_matrices_outlive_their_context(ans, synth):
     summ.free()
     assert_dcsr_equal(single.to_numpy(), oracle.traffic_matrix(*w.window(0)))
     single.free()
+
+
+def _dup_heavy_window(n, links, seed):
+    """n packets drawn from `links` distinct (src, dst) pairs, the all-ones
+    pair (the hash tables' empty marker) among them."""
+    rng = np.random.default_rng(seed)
+    s = rng.integers(0, 1 << 32, links, dtype=np.uint64).astype(np.uint32)
+    d = rng.integers(0, 1 << 32, links, dtype=np.uint64).astype(np.uint32)
+    s[0] = d[0] = 0xFFFFFFFF
+    pick = rng.integers(0, links, n)
+    return s[pick], d[pick]
+
+
+@pytest.mark.parametrize("agg_path", [0, 1])
+def test_aggregation_paths_are_exact(ans, synth, agg_path):
+    """Sorting every packet (0) and hash counting then sorting the distinct
+    links (1) give the same DCSR and quantities: mixed window sizes (empty,
+    ragged, larger than 2^17), heavy duplication with the all-ones key, all
+    packets equal, all distinct."""
+    w = synth.generate(5, sizes=[0, 1, 8191, 8193, 40000, 0, 131072, 150001], first_window=7)
+    c = ans.Context(0)
+    try:
+        c.set_tuning(agg_path=agg_path)
+        assert c.get_tuning()["agg_path"] == agg_path
+        for _ in range(2):  # the second call reuses the (emptied) tables
+            check_batch(ans, c, w)
+        for n, links in [(100000, 37), (65536, 1), (20000, 20000)]:
+            s, d = _dup_heavy_window(n, links, n + links)
+            check_window(c, s, d, f"{n}/{links}").free()
+        z = np.full(50000, 0xFFFFFFFF, np.uint32)
+        check_window(c, z, z, "all ones").free()
+        perm = np.random.default_rng(1).permutation(1 << 16).astype(np.uint32)
+        check_window(c, perm, perm[::-1].copy(), "distinct").free()
+        w3 = synth.generate(3, nwin=6, first_window=40)
+        check_batch(ans, c, w3)
+    finally:
+        c.close()
