@@ -42,13 +42,14 @@ FLUSH_BYTES = 512 << 20  # > 129 MB L2
 FALLBACK_HBM_GBS = 6800.0
 
 WORKLOADS = {
+    1: "1 window x 2^17 packets; src, dst Zipf(1.2)/2^16; DCSR + 9 quantities (the plain single-window case)",
     2: "64 windows x 2^17 packets (8.4M pairs); src Zipf(1.1)/2^20, dst Zipf(1.3)/2^22, 5% bursts of 2..100; "
        "per-window DCSR + 9 quantities + 64-window time sum",
     3: "1024 windows, P loguniform [2^10, 2^20]; heavy hitter 10%, scanners, rest Zipf(1.1)/2^24; "
        "per-window DCSR + 9 quantities + time sum",
     4: "2^13 windows x 2^17 (2^30 pairs); src, dst Zipf(1.05) over 2^32; per-window DCSR + quantities + time sum",
 }
-DEFAULT_NWIN = {2: 64, 3: 1024, 4: 8192}
+DEFAULT_NWIN = {1: 1, 2: 64, 3: 1024, 4: 8192}
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_onesweep launch
 # (64-bit link keys, first digit pass) on the 64-window batch, cold cache; set
