@@ -298,8 +298,8 @@ def main():
         for part in args.tuning.split(";"):
             fam, vals = part.split("=")
             fam = fam.strip()
-            if fam.endswith("_path"):  # e.g. agg_path=1
-                kw[fam] = int(vals)
+            if fam.endswith("_path"):  # e.g. agg_path=1; graph_path=0 sets graph
+                kw["graph" if fam == "graph_path" else fam] = int(vals)
                 continue
             for field, v in zip(("threads", "rank", "blocks"), vals.split(",")):
                 kw[f"{fam}_{field}"] = int(v)

@@ -223,7 +223,11 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * 1 = counting links in a per-window hash table (2^k >= 2 x packets slots of
  * 12 bytes, kept by the context between calls) and sorting only the distinct
  * links with their counts (kv_* passes); worth it when windows repeat links
- * heavily.  Results never depend on the configuration. */
+ * heavily.  graph: 1 = a batch's launch sequence is recorded into a CUDA
+ * graph and replayed through a cached executable graph of the same shape
+ * (updated in place with the call's pointers), 0 = launched directly; per-
+ * kernel profiling always launches directly.  Results never depend on the
+ * configuration. */
 typedef struct {
     uint32_t key_threads, key_rank, key_blocks;
     uint32_t kv_threads, kv_rank, kv_blocks;
@@ -231,10 +235,12 @@ typedef struct {
     uint32_t win_path, win_threads, win_rank;
     uint32_t sum_path;
     uint32_t agg_path;
+    uint32_t graph;
 } ans_tuning;
 
 /* Read / set a context's configuration (default: 512 threads, rank 0, one
- * block; win_path 1, win_threads 1024, win_rank 0; sum_path 0; agg_path 0).
+ * block; win_path 1, win_threads 1024, win_rank 0; sum_path 0; agg_path 0;
+ * graph 1).
  * ans_set_tuning fails with ANS_ERR_INVALID_ARG on values other than the
  * ones listed above. */
 int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);

@@ -144,6 +144,13 @@ struct ans_ctx {
   // their own arena, left empty by every call that used them (hash_dirty
   // marks one that may not have been).
   int agg_path = 0;
+  // Batches replay their launch sequence as a CUDA graph (graph = 1): it is
+  // captured on `cap` each call and applied to a cached executable graph of
+  // the same shape by cudaGraphExecUpdate (re-instantiated if the topology
+  // changed).  Off while per-kernel profiling is on.
+  int graph = 1;
+  cudaStream_t cap = nullptr;
+  std::map<std::string, cudaGraphExec_t> graphs;
   void* hash_mem = nullptr;
   size_t hash_slots = 0;
   bool hash_dirty = false;
@@ -679,10 +686,10 @@ int sum_prepare(ans_ctx* c, char* m, uint32_t k, const std::vector<uint64_t>& ca
 
 // Device half of the time sum of the matrices described by `d_mats` (device
 // array of k MatDesc), written into plan->blk.  Uses scratch laid out by the
-// caller at `m` / `ps` (which must provide vals buffers).  On failure the
-// block is discarded.
+// caller at `m` / `ps` (which must provide vals buffers).  Only queues work
+// on `st` (it may be capturing); on failure the caller discards plan->blk.
 int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
-               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st, Block** out_blk) {
+               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st) {
   Block* blk = plan->blk;
   const HostPlan& sp = plan->sp;
   const SegPlan& g = plan->g;
@@ -697,17 +704,16 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
   uint32_t* tickets = at<uint32_t>(m, ps.tickets) + 32;
 
   auto fail_blk = [&](cudaError_t e, const char* what) {
-    block_discard(blk, st);
     return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
   cudaError_t e;
   if ((e = timed(c, "count_prefix", st, [&] { return launch_count_prefix(d_mats, k, at<uint64_t>(m, off_catoff), at<uint64_t>(m, off_lens),
                                at<uint64_t>(m, off_total), st); })) != cudaSuccess)
     return fail_blk(e, "count_prefix");
-  if ((e = cudaMemsetAsync(seg_hist, 0, kPasses * kRadix * 4, st)) != cudaSuccess) return fail_blk(e, "memset");
-  if ((e = cudaMemsetAsync(m + ps.lb, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
-  if ((e = cudaMemsetAsync(m + ps.lb2, 0, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
-  if ((e = cudaMemsetAsync(m + ps.col_hist, 0, kColPasses * kRadix * 4, st)) != cudaSuccess)
+  if ((e = launch_zero(seg_hist, kPasses * kRadix * 4, st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = launch_zero(m + ps.lb, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = launch_zero(m + ps.lb2, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = launch_zero(m + ps.col_hist, kColPasses * kRadix * 4, st)) != cudaSuccess)
     return fail_blk(e, "memset");
   // gather (with the radix path: also the sum segment's histograms) zeroes
   // the sort's first status words (the gather plan has at least as many
@@ -732,10 +738,7 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
     }
   } else {
     rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
-    if (rc != ANS_OK) {
-      block_discard(blk, st);
-      return rc;
-    }
+    if (rc != ANS_OK) return rc;
   }
   uint64_t* pre = at<uint64_t>(m, ps.pre);
   if ((e = timed(c, "scan_u64", st, [&] { return launch_scan_u64(s, fv, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st); })) !=
@@ -762,16 +765,10 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
   a.col_tickets = col_tickets;
   a.err = c->d_err;
   a.mode = kModeSum;
-  if ((e = cudaMemsetAsync(blk->q, 0, sizeof(ans_quantities), st)) != cudaSuccess) return fail_blk(e, "memset");
+  if ((e = launch_zero(blk->q, sizeof(ans_quantities), st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = timed(c, "rle", st, [&] { return launch_rle(a, st); })) != cudaSuccess) return fail_blk(e, "rle");
   if ((e = timed(c, "finish", st, [&] { return launch_finish(a, st); })) != cudaSuccess) return fail_blk(e, "finish");
-  rc = column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st);
-  if (rc != ANS_OK) {
-    block_discard(blk, st);
-    return rc;
-  }
-  *out_blk = blk;
-  return ANS_OK;
+  return column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st);
 }
 
 // Snapshot the device error word into `dst` (device); reset_err clears it.
@@ -801,6 +798,61 @@ int new_ticket(ans_ctx* c, cudaStream_t st, ans_ticket* out) {
 int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n, cudaStream_t st) {
   if (!out || n == 0) return ANS_OK;
   ANS_CUDA(cudaMemcpyAsync(out, src, n * sizeof(ans_quantities), cudaMemcpyDefault, st));
+  return ANS_OK;
+}
+
+// Key of the cached executable graph for a batch: what decides its topology
+// and kernel functions (the launch sequence zeroes scratch with kernels, so
+// sizes only change node parameters, which cudaGraphExecUpdate applies).
+std::string launch_sig(uint32_t flags, bool any_tiles, bool any_small, bool any_big, int rounds, const ans_ctx* c) {
+  std::string k = std::to_string(flags) + "/" + std::to_string(any_tiles) + std::to_string(any_small) +
+                  std::to_string(any_big) + "/" + std::to_string(rounds) + "/" + std::to_string(c->win_path) +
+                  std::to_string(c->sum_path) + std::to_string(c->agg_path);
+  for (const SortCfg* f : {&c->cfg_keys, &c->cfg_kv, &c->cfg_col, &c->cfg_win})
+    k += "/" + std::to_string(f->threads) + std::to_string(f->rank) + std::to_string(f->blocks);
+  return k;
+}
+
+// Run `fn(stream)` (which only queues work) on `st`, directly or through the
+// context's graph cache.
+template <typename F>
+int run_launches(ans_ctx* c, cudaStream_t st, const std::string& key, F&& fn) {
+  if (!c->graph || c->prof.on) return fn(st);
+  if (!c->cap) ANS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  ANS_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  const int rc = fn(c->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (rc != ANS_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != ANS_OK ? rc : fail(ANS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end()) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(it->second, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(it->second);
+      c->graphs.erase(it);
+      it = c->graphs.end();
+    }
+  }
+  if (it == c->graphs.end()) {
+    if (c->graphs.size() >= 8) {  // keep a few shapes
+      cudaGraphExecDestroy(c->graphs.begin()->second);
+      c->graphs.erase(c->graphs.begin());
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(ANS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    it = c->graphs.emplace(key, ex).first;
+  }
+  cudaGraphDestroy(g);
+  ANS_CUDA(cudaGraphLaunch(it->second, st));
   return ANS_OK;
 }
 
@@ -982,113 +1034,130 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     if (e == cudaSuccess) return ANS_OK;
     return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
-  uint64_t* ka = at<uint64_t>(m, ps.keys_a);
-  uint64_t* kb = at<uint64_t>(m, ps.keys_b);
-  uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
-  uint32_t* tickets = at<uint32_t>(m, ps.tickets);
-  if (nseg) {
-    if ((rc = cu(cudaMemsetAsync(sb.q, 0, (size_t)nseg * sizeof(ans_quantities), st), "memset q"))) return bail(rc);
-    if ((rc = cu(cudaMemsetAsync(m + ps.lb, 0, (size_t)hp.ntiles * 8, st), "memset lb"))) return bail(rc);
-    if ((rc = cu(cudaMemsetAsync(m + ps.col_hist, 0, (size_t)nseg * kColPasses * kRadix * 4, st), "memset")))
-      return bail(rc);
-    SegPlan pw = p;  // the plan of the statistics phases
-    int mode = kModeWindow;
-    uint64_t* pre = nullptr;
-    if (hash) {
-      HashTabs h;
-      h.keys = (uint64_t*)c->hash_mem;
-      h.cnt = (uint32_t*)((char*)c->hash_mem + c->hash_slots * 8);
-      h.off = at<uint64_t>(m, wl.dp_tab.base);
-      h.lg = at<uint32_t>(m, wl.off_tlg);
-      h.special = at<uint64_t>(m, wl.off_special);
-      h.claims = at<uint32_t>(m, wl.off_claims);
-      h.nclaim = at<uint64_t>(m, wl.off_nclaim);
-      uint64_t* hulen = at<uint64_t>(m, wl.off_hulen);
-      uint64_t* va = at<uint64_t>(m, ps.vals_a);
-      uint64_t* vb = at<uint64_t>(m, ps.vals_b);
-      pre = at<uint64_t>(m, ps.pre);
-      if ((rc = cu(cudaMemsetAsync(h.special, 0, (size_t)nseg * 8, st), "memset"))) return bail(rc);
-      if ((rc = cu(cudaMemsetAsync(h.nclaim, 0, (size_t)nseg * 8, st), "memset"))) return bail(rc);
-      if ((rc = cu(cudaMemsetAsync(hulen, 0, (size_t)nseg * 8, st), "memset"))) return bail(rc);
-      if ((rc = cu(cudaMemsetAsync(seg_hist, 0, (size_t)nseg * kPasses * kRadix * 4, st), "memset"))) return bail(rc);
-      if ((rc = cu(cudaMemsetAsync(m + ps.lb2, 0, (size_t)hp.ntiles * 8, st), "memset"))) return bail(rc);
-      c->hash_dirty = true;  // until the compaction that empties the tables is queued
-      if ((rc = cu(timed(c, "hash_insert", st, [&] { return launch_hash_insert(p, d_src, d_dst, h, c->d_err, st); }),
-                   "hash insert")))
-        return bail(rc);
-      SegPlan pc = p;
-      pc.len = h.nclaim;
-      if ((rc = cu(timed(c, "hash_compact", st, [&] {
-                     return launch_hash_compact(pc, h, hulen, ka, va, seg_hist, at<uint64_t>(m, ps.st0), tickets, st);
-                   }), "hash compact")))
-        return bail(rc);
-      c->hash_dirty = false;
-      pw.len = hulen;
-      if ((rc = sort_segments(c, pw, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1),
-                              tickets, st, "onesweep_hash")))
-        return bail(rc);
-      if ((rc = cu(timed(c, "scan_u64", st, [&] {
-                     return launch_scan_u64(pw, va, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st);
-                   }), "scan")))
-        return bail(rc);
-      mode = kModeSum;
-    }
-    if (!hash && !small_ids.empty()) {
-      const uint32_t* ids = small_ids.size() == nseg ? nullptr : at<uint32_t>(m, wl.off_small);
-      if ((rc = cu(timed(c, "cluster_sort", st, [&] {
-                     return launch_cluster_sort(p, ids, (uint32_t)small_ids.size(), d_src, d_dst, ka, tickets,
-                                                cfg_win, st);
-                   }), "cluster sort")))
-        return bail(rc);
-    }
-    if (!hash && !big_ids.empty()) {
-      const SegPlan pb = wl.dp_big.bind(m, hp_big);
-      const size_t nb = big_ids.size();
-      if ((rc = cu(cudaMemsetAsync(seg_hist, 0, nb * kPasses * kRadix * 4, st), "memset hist"))) return bail(rc);
-      if ((rc = cu(timed(c, "pack_hist", st, [&] { return launch_pack_hist(pb, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st); }), "pack")))
-        return bail(rc);
-      if ((rc = sort_segments(c, pb, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
-                              at<uint64_t>(m, ps.st1), tickets, st)))
-        return bail(rc);
-    }
-    StatsArgs a;
-    a.plan = pw;
-    a.hdr = sb.hdr;
-    a.q = sb.q;
-    a.keys = ka;
-    a.col_ids = sb.col_ids;
-    a.vals = sb.vals;
-    a.row_ids = sb.row_ids;
-    a.row_ptr = sb.row_ptr;
-    a.run_start = at<uint64_t>(m, ps.run_start);
-    a.row_pos = at<uint64_t>(m, ps.row_pos);
-    a.pre = pre;
-    a.lookback = at<uint64_t>(m, ps.lb);
-    a.ticket = tickets + kPasses;
-    a.col_hist = at<uint32_t>(m, ps.col_hist);
-    a.ulen = at<uint64_t>(m, ps.ulen);
-    a.col_st0 = at<uint64_t>(m, ps.st0);
-    a.col_tickets = tickets + 2 * 32;
-    a.err = c->d_err;
-    a.mode = mode;
-    if ((rc = cu(timed(c, "empty_fixup", st, [&] { return launch_empty_fixup(a, st); }), "empty"))) return bail(rc);
-    if ((rc = cu(timed(c, "rle", st, [&] { return launch_rle(a, st); }), "rle"))) return bail(rc);
-    if ((rc = cu(timed(c, "finish", st, [&] { return launch_finish(a, st); }), "finish"))) return bail(rc);
-    if ((rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, st))) return bail(rc);
+  // Empty batch with a time sum: an empty sum matrix.
+  if (want_sum && nseg == 0) {
+    if ((rc = make_block(c, 0, 1, {0}, {0}, st, &sblk))) return bail(rc);
   }
-
-  if (want_sum) {
-    if (nseg == 0) {
-      // an empty batch: an empty sum
-      if ((rc = make_block(c, 0, 1, {0}, {0}, st, &sblk))) return bail(rc);
-      if ((rc = cu(cudaMemsetAsync(sblk->row_ptr, 0, 8, st), "memset"))) return bail(rc);
-      if ((rc = cu(cudaMemsetAsync(sblk->hdr, 0, 16, st), "memset"))) return bail(rc);
-      if ((rc = cu(cudaMemsetAsync(sblk->q, 0, sizeof(ans_quantities), st), "memset"))) return bail(rc);
-    } else {
-      rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, st, &sblk);
-      sump.blk = nullptr;  // now owned by sblk, or discarded by sum_launch
-      if (rc) return bail(rc);
+  // ---- the launch sequence (every kernel and memset of the batch), run on
+  // `ls`: the caller's stream, or a capture stream when it is recorded into a
+  // CUDA graph.  Host-side state is only read here.
+  auto launch_all = [&](cudaStream_t ls) -> int {
+    int rc = ANS_OK;
+    uint64_t* ka = at<uint64_t>(m, ps.keys_a);
+    uint64_t* kb = at<uint64_t>(m, ps.keys_b);
+    uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
+    uint32_t* tickets = at<uint32_t>(m, ps.tickets);
+    if (nseg) {
+      if ((rc = cu(launch_zero(sb.q, (size_t)nseg * sizeof(ans_quantities), ls), "memset q"))) return rc;
+      if ((rc = cu(launch_zero(m + ps.lb, (size_t)hp.ntiles * 8, ls), "memset lb"))) return rc;
+      if ((rc = cu(launch_zero(m + ps.col_hist, (size_t)nseg * kColPasses * kRadix * 4, ls), "memset")))
+        return rc;
+      SegPlan pw = p;  // the plan of the statistics phases
+      int mode = kModeWindow;
+      uint64_t* pre = nullptr;
+      if (hash) {
+        HashTabs h;
+        h.keys = (uint64_t*)c->hash_mem;
+        h.cnt = (uint32_t*)((char*)c->hash_mem + c->hash_slots * 8);
+        h.off = at<uint64_t>(m, wl.dp_tab.base);
+        h.lg = at<uint32_t>(m, wl.off_tlg);
+        h.special = at<uint64_t>(m, wl.off_special);
+        h.claims = at<uint32_t>(m, wl.off_claims);
+        h.nclaim = at<uint64_t>(m, wl.off_nclaim);
+        uint64_t* hulen = at<uint64_t>(m, wl.off_hulen);
+        uint64_t* va = at<uint64_t>(m, ps.vals_a);
+        uint64_t* vb = at<uint64_t>(m, ps.vals_b);
+        pre = at<uint64_t>(m, ps.pre);
+        if ((rc = cu(launch_zero(h.special, (size_t)nseg * 8, ls), "memset"))) return rc;
+        if ((rc = cu(launch_zero(h.nclaim, (size_t)nseg * 8, ls), "memset"))) return rc;
+        if ((rc = cu(launch_zero(hulen, (size_t)nseg * 8, ls), "memset"))) return rc;
+        if ((rc = cu(launch_zero(seg_hist, (size_t)nseg * kPasses * kRadix * 4, ls), "memset"))) return rc;
+        if ((rc = cu(launch_zero(m + ps.lb2, (size_t)hp.ntiles * 8, ls), "memset"))) return rc;
+        c->hash_dirty = true;  // until the compaction that empties the tables is queued
+        if ((rc = cu(timed(c, "hash_insert", ls, [&] { return launch_hash_insert(p, d_src, d_dst, h, c->d_err, ls); }),
+                     "hash insert")))
+          return rc;
+        SegPlan pc = p;
+        pc.len = h.nclaim;
+        if ((rc = cu(timed(c, "hash_compact", ls, [&] {
+                       return launch_hash_compact(pc, h, hulen, ka, va, seg_hist, at<uint64_t>(m, ps.st0), tickets, ls);
+                     }), "hash compact")))
+          return rc;
+        c->hash_dirty = false;
+        pw.len = hulen;
+        if ((rc = sort_segments(c, pw, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1),
+                                tickets, ls, "onesweep_hash")))
+          return rc;
+        if ((rc = cu(timed(c, "scan_u64", ls, [&] {
+                       return launch_scan_u64(pw, va, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, ls);
+                     }), "scan")))
+          return rc;
+        mode = kModeSum;
+      }
+      if (!hash && !small_ids.empty()) {
+        const uint32_t* ids = small_ids.size() == nseg ? nullptr : at<uint32_t>(m, wl.off_small);
+        if ((rc = cu(timed(c, "cluster_sort", ls, [&] {
+                       return launch_cluster_sort(p, ids, (uint32_t)small_ids.size(), d_src, d_dst, ka, tickets,
+                                                  cfg_win, ls);
+                     }), "cluster sort")))
+          return rc;
+      }
+      if (!hash && !big_ids.empty()) {
+        const SegPlan pb = wl.dp_big.bind(m, hp_big);
+        const size_t nb = big_ids.size();
+        if ((rc = cu(launch_zero(seg_hist, nb * kPasses * kRadix * 4, ls), "memset hist"))) return rc;
+        if ((rc = cu(timed(c, "pack_hist", ls, [&] { return launch_pack_hist(pb, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, ls); }), "pack")))
+          return rc;
+        if ((rc = sort_segments(c, pb, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
+                                at<uint64_t>(m, ps.st1), tickets, ls)))
+          return rc;
+      }
+      StatsArgs a;
+      a.plan = pw;
+      a.hdr = sb.hdr;
+      a.q = sb.q;
+      a.keys = ka;
+      a.col_ids = sb.col_ids;
+      a.vals = sb.vals;
+      a.row_ids = sb.row_ids;
+      a.row_ptr = sb.row_ptr;
+      a.run_start = at<uint64_t>(m, ps.run_start);
+      a.row_pos = at<uint64_t>(m, ps.row_pos);
+      a.pre = pre;
+      a.lookback = at<uint64_t>(m, ps.lb);
+      a.ticket = tickets + kPasses;
+      a.col_hist = at<uint32_t>(m, ps.col_hist);
+      a.ulen = at<uint64_t>(m, ps.ulen);
+      a.col_st0 = at<uint64_t>(m, ps.st0);
+      a.col_tickets = tickets + 2 * 32;
+      a.err = c->d_err;
+      a.mode = mode;
+      if ((rc = cu(timed(c, "empty_fixup", ls, [&] { return launch_empty_fixup(a, ls); }), "empty"))) return rc;
+      if ((rc = cu(timed(c, "rle", ls, [&] { return launch_rle(a, ls); }), "rle"))) return rc;
+      if ((rc = cu(timed(c, "finish", ls, [&] { return launch_finish(a, ls); }), "finish"))) return rc;
+      if ((rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls))) return rc;
     }
+
+    if (want_sum) {
+      if (nseg == 0) {
+        // an empty batch: an empty sum (its block is made before the launches)
+        if ((rc = cu(launch_zero(sblk->row_ptr, 8, ls), "memset"))) return rc;
+        if ((rc = cu(launch_zero(sblk->hdr, 16, ls), "memset"))) return rc;
+        if ((rc = cu(launch_zero(sblk->q, sizeof(ans_quantities), ls), "memset"))) return rc;
+      } else {
+        rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, ls);
+        if (rc) return rc;
+      }
+    }
+    return ANS_OK;
+  };
+  int rounds = 0;
+  while ((1ull << rounds) < nseg) ++rounds;
+  const std::string sig = launch_sig(flags, hp.ntiles > 0, !small_ids.empty(), !big_ids.empty(), rounds, c);
+  if ((rc = run_launches(c, st, sig, launch_all))) return bail(rc);
+  if (sump.blk) {  // the time sum's block is filled
+    sblk = sump.blk;
+    sump.blk = nullptr;
   }
 
   // ---- completion
@@ -1211,6 +1280,10 @@ int ans_ctx_destroy(ans_ctx* c) {
     dev_free(c, c->hash_mem, c->hash_slots * 12, c->aux);
     c->hash_mem = nullptr;
     c->hash_slots = 0;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    if (c->cap) cudaStreamDestroy(c->cap);
+    c->cap = nullptr;
     for (auto& kv : c->prof.pending) {
       cudaEventDestroy(kv.a);
       cudaEventDestroy(kv.b);
@@ -1312,8 +1385,12 @@ int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_mat
       block_discard(sump.blk, st);
       return rc;
     }
-    ANS_TRY(sum_launch(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, &sump, off_catoff, off_lens, off_total, st,
-                       &sblk));
+    rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, &sump, off_catoff, off_lens, off_total, st);
+    if (rc) {
+      block_discard(sump.blk, st);
+      return rc;
+    }
+    sblk = sump.blk;
     rc = capture_err(c, sblk->status, st);
     if (rc == ANS_OK) rc = reset_err(c, st);
     if (rc) {
@@ -1549,6 +1626,7 @@ int ans_get_tuning(ans_ctx* c, ans_tuning* out) {
   out->win_rank = (uint32_t)c->cfg_win.rank;
   out->sum_path = (uint32_t)c->sum_path;
   out->agg_path = (uint32_t)c->agg_path;
+  out->graph = (uint32_t)c->graph;
   return ANS_OK;
 }
 
@@ -1564,11 +1642,13 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
   if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
   if (t->agg_path > 1) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0 or 1");
+  if (t->graph > 1) return fail(ANS_ERR_INVALID_ARG, "graph must be 0 or 1");
   std::lock_guard<std::mutex> g(c->mu);
   c->win_path = (int)t->win_path;
   c->cfg_win = SortCfg{(int)t->win_threads, (int)t->win_rank, 1};
   c->sum_path = (int)t->sum_path;
   c->agg_path = (int)t->agg_path;
+  c->graph = (int)t->graph;
   c->cfg_keys = SortCfg{(int)t->key_threads, (int)t->key_rank, (int)t->key_blocks};
   c->cfg_kv = SortCfg{(int)t->kv_threads, (int)t->kv_rank, (int)t->kv_blocks};
   c->cfg_col = SortCfg{(int)t->col_threads, (int)t->col_rank, (int)t->col_blocks};
@@ -1725,6 +1805,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   res.win_rank = (uint32_t)win_cfg.rank;
   res.sum_path = (uint32_t)sum_path;
   res.agg_path = (uint32_t)agg_path;
+  res.graph = (uint32_t)c->graph;
   ANS_TRY(ans_set_tuning(c, &res));
   if (chosen) *chosen = res;
   return ANS_OK;

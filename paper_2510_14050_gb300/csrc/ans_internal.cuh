@@ -200,6 +200,8 @@ cudaError_t launch_finish(const StatsArgs& a, cudaStream_t st);
 // fan-in, max destination packets.  bnd holds one record per tile.
 cudaError_t launch_colstat(const SegPlan& p, const uint32_t* keys, const uint64_t* vals, ColBnd* bnd,
                            ans_quantities* q, cudaStream_t st);
+// Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.
 cudaError_t launch_empty_fixup(const StatsArgs& a, cudaStream_t st);
 

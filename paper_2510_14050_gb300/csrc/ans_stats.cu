@@ -465,7 +465,24 @@ __global__ void k_empty_fixup(StatsArgs a) {
   if (a.ulen) a.ulen[s] = 0;
 }
 
+// Zero `bytes` bytes at p (4-byte aligned): a kernel instead of a memset so
+// that a recorded launch sequence keeps its topology when sizes change.
+__global__ void k_zero(uint32_t* __restrict__ p, size_t words, uint8_t* __restrict__ tail, uint32_t ntail) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) p[i] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x < ntail) tail[threadIdx.x] = 0;
+}
+
 }  // namespace
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) {
+  const size_t words = bytes / 4;
+  const uint32_t ntail = (uint32_t)(bytes % 4);
+  const size_t want = (words + 1023) / 1024;
+  const unsigned blocks = (unsigned)(want < 1 ? 1 : (want > 2048 ? 2048 : want));
+  k_zero<<<blocks, 256, 0, st>>>((uint32_t*)p, words, (uint8_t*)p + words * 4, ntail);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rle(const StatsArgs& a, cudaStream_t st) {
   if (a.plan.ntiles == 0) return cudaSuccess;

@@ -396,3 +396,25 @@ def test_aggregation_paths_are_exact(ans, synth, agg_path):
         check_batch(ans, c, w3)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_graph_replay_follows_each_call(ans, synth, graph):
+    """With graph replay, a cached executable graph is reused for batches of
+    the same shape: each call's own inputs and outputs must be the ones used
+    (new device buffers, different packets, same shape), across shape
+    changes and back."""
+    a1 = synth.generate(5, sizes=[3000, 0, 20000, 8192], first_window=1)
+    a2 = synth.generate(5, sizes=[3000, 0, 20000, 8192], first_window=11)  # same shape, other packets
+    b = synth.generate(2, nwin=5, first_window=3)
+    c = ans.Context(0)
+    try:
+        c.set_tuning(graph=graph)
+        for w in (a1, b, a2, a1, a2, b, a1):
+            check_batch(ans, c, w)
+        # quantities-only calls of the same windows, into caller-owned outputs
+        for w in (a2, a1):
+            _, _, quants = run_batch(ans, c, w, 0)
+            assert quants == [oracle.window_quantities(*w.window(i)) for i in range(w.nwin)]
+    finally:
+        c.close()
