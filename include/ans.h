@@ -223,7 +223,7 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * 1 = counting links in a per-window hash table (2^k >= 2 x packets slots of
  * 12 bytes, kept by the context between calls) and sorting only the distinct
  * links with their counts (kv_* passes); worth it when windows repeat links
- * heavily.  graph: 1 = a batch's launch sequence is recorded into a CUDA
+ * heavily.  Setting agg_path 0 waits for the device and releases the tables.  graph: 1 = a batch's launch sequence is recorded into a CUDA
  * graph and replayed through a cached executable graph of the same shape
  * (updated in place with the call's pointers), 0 = launched directly; per-
  * kernel profiling always launches directly.  Results never depend on the
@@ -254,7 +254,9 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
  * configurations) and keeps it if the batch's windows sort faster that way
  * than by the best key passes plus their histogram sweep, likewise picks the
  * faster sum_path, and finally the agg_path with the smaller total kernel
- * time of the whole batch.  The choice is applied to the context and returned in *chosen (optional).  The
+ * time of the whole batch.  An optional path whose trial cannot get its
+ * device memory (ANS_ERR_OOM / ANS_ERR_BUDGET) is skipped; the call fails
+ * with ANS_ERR_OOM only if the default paths do not fit.  The choice is applied to the context and returned in *chosen (optional).  The
  * call blocks until the runs have finished; it leaves per-kernel profiling
  * disabled and its data cleared. */
 int ans_autotune(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,

@@ -274,6 +274,16 @@ int dev_alloc(ans_ctx* c, size_t bytes, cudaStream_t st, void** out) {
     if (!p) return fail(ANS_ERR_OOM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
   } else {
     cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e == cudaErrorMemoryAllocation) {
+      // The pool keeps freed memory (release threshold: unlimited); return it
+      // to the device once everything queued has finished, and retry.
+      cudaGetLastError();
+      cudaMemPool_t pool = nullptr;
+      if (cudaDeviceSynchronize() == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess)
+        cudaMemPoolTrimTo(pool, 0);
+      cudaGetLastError();
+      e = cudaMallocAsync(&p, bytes, st);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(ANS_ERR_OOM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " +
@@ -623,9 +633,11 @@ int sort_segments(ans_ctx* c, const SegPlan& p, uint64_t* ka, uint64_t* kb, uint
 // the stored links (col_ids, vals) are sorted by destination in four 8-bit
 // passes (in -> A -> B -> A -> B) and the destination runs reduced.  Expects
 // k_finish to have filled col_hist and ulen and zeroed st0 and the tickets.
+// With vals32 (window matrices, whose counts fit 31 bits; k_finish wrote the
+// copy into the value buffer B) the passes carry uint32 counts.
 int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32_t* col_ids,
                 const uint64_t* vals, const PipeScratch& ps, char* m, uint32_t* tickets,
-                ans_quantities* q, cudaStream_t st) {
+                ans_quantities* q, cudaStream_t st, bool vals32 = false) {
   SegPlan cp = p;
   cp.len = ulen;
   uint32_t* ka = at<uint32_t>(m, ps.ck_a);
@@ -634,27 +646,30 @@ int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32
   uint64_t* vb = at<uint64_t>(m, ps.cv_b);
   uint64_t* st0 = at<uint64_t>(m, ps.st0);
   uint64_t* st1 = at<uint64_t>(m, ps.st1);
+  uint32_t* hist = at<uint32_t>(m, ps.col_hist);
   for (int pass = 0; pass < kColPasses; ++pass) {
     const uint32_t* kin = pass == 0 ? col_ids : (pass % 2 ? ka : kb);
-    const uint64_t* vin = pass == 0 ? vals : (pass % 2 ? va : vb);
     uint32_t* kout = pass % 2 ? kb : ka;
-    uint64_t* vout = pass % 2 ? vb : va;
     ANS_CUDA(timed(c, "onesweep_col", st, [&] {
-      return launch_onesweep_col(cp, pass, kin, kout, vin, vout, at<uint32_t>(m, ps.col_hist),
-                                 pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, tickets + pass, c->d_err, c->cfg_col,
-                                 st);
+      if (vals32) {  // B (the copy, then pass 2's output) -> A -> B
+        const uint32_t* vin = (const uint32_t*)(pass % 2 ? va : vb);
+        uint32_t* vout = (uint32_t*)(pass % 2 ? vb : va);
+        return launch_onesweep_col32(cp, pass, kin, kout, vin, vout, hist, pass % 2 ? st1 : st0,
+                                     pass % 2 ? st0 : st1, tickets + pass, c->d_err, c->cfg_col, st);
+      }
+      const uint64_t* vin = pass == 0 ? vals : (pass % 2 ? va : vb);
+      uint64_t* vout = pass % 2 ? vb : va;
+      return launch_onesweep_col(cp, pass, kin, kout, vin, vout, hist, pass % 2 ? st1 : st0, pass % 2 ? st0 : st1,
+                                 tickets + pass, c->d_err, c->cfg_col, st);
     }));
   }
   ANS_CUDA(timed(c, "colstat", st, [&] {
+    if (vals32) return launch_colstat32(cp, kb, (const uint32_t*)vb, at<ColBnd>(m, ps.bnd), q, st);
     return launch_colstat(cp, kb, vb, at<ColBnd>(m, ps.bnd), q, st);
   }));
   return ANS_OK;
 }
 
-// Host half of a time sum over k matrices with capacities `caps`: the gather
-// plan (one segment per matrix, tiles by capacity, lengths filled in on the
-// device), the single-segment sum plan, the output block, and their uploads
-// (added to `us`; the caller flushes it before the first kernel).
 struct SumPlan {
   HostPlan gp, sp;
   SegPlan g, s;
@@ -1124,6 +1139,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       a.run_start = at<uint64_t>(m, ps.run_start);
       a.row_pos = at<uint64_t>(m, ps.row_pos);
       a.pre = pre;
+      a.vals32 = (uint32_t*)at<uint64_t>(m, ps.cv_b);  // window counts fit 31 bits
       a.lookback = at<uint64_t>(m, ps.lb);
       a.ticket = tickets + kPasses;
       a.col_hist = at<uint32_t>(m, ps.col_hist);
@@ -1135,7 +1151,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       if ((rc = cu(timed(c, "empty_fixup", ls, [&] { return launch_empty_fixup(a, ls); }), "empty"))) return rc;
       if ((rc = cu(timed(c, "rle", ls, [&] { return launch_rle(a, ls); }), "rle"))) return rc;
       if ((rc = cu(timed(c, "finish", ls, [&] { return launch_finish(a, ls); }), "finish"))) return rc;
-      if ((rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls))) return rc;
+      if ((rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls, true))) return rc;
     }
 
     if (want_sum) {
@@ -1649,6 +1665,13 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   c->sum_path = (int)t->sum_path;
   c->agg_path = (int)t->agg_path;
   c->graph = (int)t->graph;
+  if (c->agg_path == 0 && c->hash_mem) {  // the hash tables are no longer needed
+    DeviceGuard dg(c->device);
+    ANS_CUDA(cudaDeviceSynchronize());
+    dev_free(c, c->hash_mem, c->hash_slots * 12, c->aux);
+    c->hash_mem = nullptr;
+    c->hash_slots = 0;
+  }
   c->cfg_keys = SortCfg{(int)t->key_threads, (int)t->key_rank, (int)t->key_blocks};
   c->cfg_kv = SortCfg{(int)t->kv_threads, (int)t->kv_rank, (int)t->kv_blocks};
   c->cfg_col = SortCfg{(int)t->col_threads, (int)t->col_rank, (int)t->col_blocks};
@@ -1661,8 +1684,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   constexpr int kVariants = 6;
   const SortCfg variants[kVariants] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankMatch, 2},
                                        {512, kRankBallot, 2}, {1024, kRankMatch, 1}, {1024, kRankBallot, 1}};
-  double t_keys[kVariants], t_kv[kVariants], t_col[kVariants], t_pack[kVariants], t_gather[kVariants];
-
+  using Prof = std::map<std::string, double>;
   std::vector<ans_matrix*> per(nwin, nullptr);
   auto run_once = [&]() -> int {
     ans_matrix* sum = nullptr;
@@ -1676,55 +1698,90 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     ans_matrix_free(sum);
     return ANS_OK;
   };
-  for (int v = 0; v < kVariants; ++v) {
+  // One trial: apply `set` to the context, run the batch once untimed (module
+  // load, shared-memory carve-out), then twice with per-kernel timing; the
+  // kernel totals go to *out.  A trial that cannot get its memory (a path the
+  // device cannot hold for this batch) reports false instead of failing.
+  auto trial = [&](auto&& set, Prof* out, bool* ran) -> int {
     {
       std::lock_guard<std::mutex> g(c->mu);
-      c->cfg_keys = c->cfg_kv = c->cfg_col = variants[v];
-      c->win_path = 1;  // time the key passes on every window
-      c->sum_path = 1;  // and the kv passes on the time sum
-      c->agg_path = 0;
+      set();
     }
-    ANS_TRY(run_once());  // first launch of this variant (module load, smem carve-out)
-    ANS_TRY(ans_profile_enable(c, 1));
-    for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
+    *ran = false;
+    int rc = run_once();
+    if (rc == ANS_OK) {
+      ANS_TRY(ans_profile_enable(c, 1));
+      for (int rep = 0; rep < 2 && rc == ANS_OK; ++rep) rc = run_once();
+    }
     std::lock_guard<std::mutex> g(c->mu);
     DeviceGuard dg(c->device);
     prof_collect(c);
-    t_keys[v] = c->prof.acc["onesweep"].first;
-    t_kv[v] = c->prof.acc["onesweep_sum"].first;
-    t_col[v] = c->prof.acc["onesweep_col"].first;
-    t_pack[v] = c->prof.acc["pack_hist"].first;
-    t_gather[v] = c->prof.acc["gather"].first;
+    out->clear();
+    for (const auto& kv : c->prof.acc) (*out)[kv.first] = kv.second.first;
     c->prof.acc.clear();
     c->prof.on = false;
+    if (rc == ANS_ERR_OOM || rc == ANS_ERR_BUDGET) return ANS_OK;
+    if (rc == ANS_OK) *ran = true;
+    return rc;
+  };
+  auto total = [](const Prof& p) {
+    double t = 0;
+    for (const auto& kv : p) t += kv.second;
+    return t;
+  };
+  auto get = [](const Prof& p, const char* k) {
+    auto it = p.find(k);
+    return it == p.end() ? 0.0 : it->second;
+  };
+  constexpr double kNever = 1e300;
+
+  // Radix-pass launch shapes, per family, on the paths that use them all.
+  double t_keys[kVariants], t_kv[kVariants], t_col[kVariants];
+  for (int v = 0; v < kVariants; ++v) {
+    Prof pr;
+    bool ran = false;
+    ANS_TRY(trial([&] {
+      c->cfg_keys = c->cfg_kv = c->cfg_col = variants[v];
+      c->win_path = 1;  // the key passes on every window
+      c->sum_path = 1;  // the kv passes on the time sum
+      c->agg_path = 0;
+    }, &pr, &ran));
+    if (!ran) return fail(ANS_ERR_OOM, "autotune: the batch does not fit the device with the default paths");
+    t_keys[v] = get(pr, "onesweep") + get(pr, "pack_hist");
+    t_kv[v] = get(pr, "onesweep_sum") + get(pr, "gather");
+    t_col[v] = get(pr, "onesweep_col");
   }
-  // The on-chip window sort (for windows that fit a cluster) against the
-  // fastest key passes: total window-sort time of the batch either way.
-  int bk_i = 0;
-  for (int v = 1; v < kVariants; ++v)
-    if (t_keys[v] + t_pack[v] < t_keys[bk_i] + t_pack[bk_i]) bk_i = v;
-  double best_win = t_keys[bk_i] + t_pack[bk_i];
+  auto best = [&](const double* t) {
+    int b = 0;
+    for (int v = 1; v < kVariants; ++v)
+      if (t[v] < t[b]) b = v;
+    return b;
+  };
+  const int bk_i = best(t_keys), bv_i = best(t_kv), bc_i = best(t_col);
+  auto base = [&] {
+    c->cfg_keys = variants[bk_i];
+    c->cfg_kv = variants[bv_i];
+    c->cfg_col = variants[bc_i];
+  };
+
+  // The on-chip window sort (windows that fit a cluster) against the key
+  // passes plus their histogram sweep.
   int win_path = 1;
   SortCfg win_cfg{1024, kRankMatch, 1};
+  double best_win = t_keys[bk_i];
   if (cluster_sort_clusters(c->device) > 0) {
     const SortCfg wv[3] = {{1024, kRankMatch, 1}, {1024, kRankBallot, 1}, {512, kRankMatch, 1}};
     for (const SortCfg& w : wv) {
-      {
-        std::lock_guard<std::mutex> g(c->mu);
-        c->cfg_keys = variants[bk_i];
+      Prof pr;
+      bool ran = false;
+      ANS_TRY(trial([&] {
+        base();
         c->win_path = 0;
         c->cfg_win = w;
-      }
-      ANS_TRY(run_once());
-      ANS_TRY(ans_profile_enable(c, 1));
-      for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
-      std::lock_guard<std::mutex> g(c->mu);
-      DeviceGuard dg(c->device);
-      prof_collect(c);
-      const double t = c->prof.acc["cluster_sort"].first + c->prof.acc["onesweep"].first +
-                       c->prof.acc["pack_hist"].first;
-      c->prof.acc.clear();
-      c->prof.on = false;
+        c->sum_path = 1;
+        c->agg_path = 0;
+      }, &pr, &ran));
+      const double t = ran ? get(pr, "cluster_sort") + get(pr, "onesweep") + get(pr, "pack_hist") : kNever;
       if (t < best_win) {
         best_win = t;
         win_path = 0;
@@ -1733,64 +1790,43 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     }
   }
 
-  // Time sums: pairwise merges against the fastest kv passes (each with its
-  // gather, which builds digit histograms only for the radix passes).
-  int bv_i = 0;
-  for (int v = 1; v < kVariants; ++v)
-    if (t_kv[v] + t_gather[v] < t_kv[bv_i] + t_gather[bv_i]) bv_i = v;
+  // Time sums: pairwise merges against the kv passes (each with its gather).
   int sum_path = 1;
   {
-    {
-      std::lock_guard<std::mutex> g(c->mu);
-      c->win_path = 1;
+    Prof pr;
+    bool ran = false;
+    ANS_TRY(trial([&] {
+      base();
+      c->win_path = win_path;
+      c->cfg_win = win_cfg;
       c->sum_path = 0;
-    }
-    ANS_TRY(run_once());
-    ANS_TRY(ans_profile_enable(c, 1));
-    for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
-    std::lock_guard<std::mutex> g(c->mu);
-    DeviceGuard dg(c->device);
-    prof_collect(c);
-    const double t = c->prof.acc["merge"].first + c->prof.acc["gather"].first;
-    c->prof.acc.clear();
-    c->prof.on = false;
-    if (t < t_kv[bv_i] + t_gather[bv_i]) sum_path = 0;
+      c->agg_path = 0;
+    }, &pr, &ran));
+    if (ran && get(pr, "merge") + get(pr, "gather") < t_kv[bv_i]) sum_path = 0;
   }
+
   // Window aggregation: hash counting against sorting every packet, by the
   // whole batch's kernel time with everything else as chosen.
   int agg_path = 0;
   {
-    double tot[2] = {0, 0};
+    double tot[2] = {kNever, kNever};
     for (int a = 0; a < 2; ++a) {
-      {
-        std::lock_guard<std::mutex> g(c->mu);
-        c->cfg_keys = variants[bk_i];
-        c->cfg_kv = variants[bv_i];
+      Prof pr;
+      bool ran = false;
+      ANS_TRY(trial([&] {
+        base();
         c->win_path = win_path;
         c->cfg_win = win_cfg;
         c->sum_path = sum_path;
         c->agg_path = a;
-      }
-      ANS_TRY(run_once());
-      ANS_TRY(ans_profile_enable(c, 1));
-      for (int rep = 0; rep < 2; ++rep) ANS_TRY(run_once());
-      std::lock_guard<std::mutex> g(c->mu);
-      DeviceGuard dg(c->device);
-      prof_collect(c);
-      for (const auto& kv : c->prof.acc) tot[a] += kv.second.first;
-      c->prof.acc.clear();
-      c->prof.on = false;
+      }, &pr, &ran));
+      if (ran) tot[a] = total(pr);
     }
     agg_path = tot[1] < tot[0] ? 1 : 0;
   }
-  auto best = [&](const double* t) {
-    int b = 0;
-    for (int v = 1; v < kVariants; ++v)
-      if (t[v] < t[b]) b = v;
-    return variants[b];
-  };
+
   ans_tuning res{};
-  const SortCfg bk = variants[bk_i], bv = variants[bv_i], bc = best(t_col);
+  const SortCfg bk = variants[bk_i], bv = variants[bv_i], bc = variants[bc_i];
   res.key_threads = (uint32_t)bk.threads;
   res.key_rank = (uint32_t)bk.rank;
   res.key_blocks = (uint32_t)bk.blocks;

@@ -70,6 +70,7 @@ struct StatsArgs {
   const uint64_t* keys = nullptr; // sorted keys (padded space)
   uint32_t* col_ids = nullptr;    // at base[s]
   uint64_t* vals = nullptr;       // at base[s]
+  uint32_t* vals32 = nullptr;     // optional uint32 copy of vals (column pass input), at base[s]
   uint32_t* row_ids = nullptr;    // at base[s]
   uint64_t* row_ptr = nullptr;    // at base[s] + s  (nrows + 1 entries)
   uint64_t* run_start = nullptr;  // at base[s] + s  (nnz + 1 entries); null = identity
@@ -141,6 +142,11 @@ cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin,
                                 const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                                 uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
                                 const SortCfg& cfg, cudaStream_t st);
+// The same with uint32 counts (window matrices: every count fits 31 bits).
+cudaError_t launch_onesweep_col32(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
+                                  const uint32_t* vin, uint32_t* vout, const uint32_t* seg_hist,
+                                  uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
+                                  const SortCfg& cfg, cudaStream_t st);
 // Gather the stored links of k matrices into (key, value) pairs at their
 // concatenation offsets, accumulating the time-sum segment's digit histograms
 // (sum_hist, zeroed by the caller; null: none) and zeroing the sum sort's
@@ -200,6 +206,8 @@ cudaError_t launch_finish(const StatsArgs& a, cudaStream_t st);
 // fan-in, max destination packets.  bnd holds one record per tile.
 cudaError_t launch_colstat(const SegPlan& p, const uint32_t* keys, const uint64_t* vals, ColBnd* bnd,
                            ans_quantities* q, cudaStream_t st);
+cudaError_t launch_colstat32(const SegPlan& p, const uint32_t* keys, const uint32_t* vals, ColBnd* bnd,
+                             ans_quantities* q, cudaStream_t st);
 // Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.

@@ -412,6 +412,14 @@ cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uin
                                        st_cur, st_next, ticket, err, cfg, st);
 }
 
+cudaError_t launch_onesweep_col32(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
+                                  const uint32_t* vin, uint32_t* vout, const uint32_t* seg_hist,
+                                  uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
+                                  const SortCfg& cfg, cudaStream_t st) {
+  return run_onesweep<uint32_t, uint32_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err,
+                                          cfg, st);
+}
+
 cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
                                 const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                                 uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,

@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
     } else {
       v = P(a.run_start[bs + u + 1]) - P(a.run_start[bs + u]);
       a.vals[tl.base + u] = v;
+      if (a.vals32) a.vals32[tl.base + u] = (uint32_t)v;
     }
     mlink = v > mlink ? v : mlink;
     const uint32_t dst = a.col_ids[tl.base + u];
@@ -291,8 +292,9 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 // completed by the thread holding its successor head, walking back over the
 // chunks without heads.  Runs that cross the tile boundary are summarised in
 // bnd[t] (leading part, trailing part) for k_colstat_fin.
+template <typename V>
 __global__ void __launch_bounds__(kThreads) k_colstat(SegPlan p, const uint32_t* __restrict__ keys,
-                                                      const uint64_t* __restrict__ vals,
+                                                      const V* __restrict__ vals,
                                                       ColBnd* __restrict__ bnd, ans_quantities* q) {
   __shared__ Tile s_tile;
   __shared__ uint64_t s_ll[kThreads], s_ls[kThreads], s_tl[kThreads], s_ts[kThreads];
@@ -507,14 +509,25 @@ cudaError_t launch_finish(const StatsArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_colstat(const SegPlan& p, const uint32_t* keys, const uint64_t* vals, ColBnd* bnd,
-                           ans_quantities* q, cudaStream_t st) {
+template <typename V>
+cudaError_t run_colstat(const SegPlan& p, const uint32_t* keys, const V* vals, ColBnd* bnd, ans_quantities* q,
+                        cudaStream_t st) {
   if (p.ntiles == 0) return cudaSuccess;
-  k_colstat<<<p.ntiles, kThreads, 0, st>>>(p, keys, vals, bnd, q);
+  k_colstat<V><<<p.ntiles, kThreads, 0, st>>>(p, keys, vals, bnd, q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_colstat_fin<<<(p.ntiles + 255) / 256, 256, 0, st>>>(p, bnd, q);
   return cudaGetLastError();
+}
+
+cudaError_t launch_colstat(const SegPlan& p, const uint32_t* keys, const uint64_t* vals, ColBnd* bnd,
+                           ans_quantities* q, cudaStream_t st) {
+  return run_colstat(p, keys, vals, bnd, q, st);
+}
+
+cudaError_t launch_colstat32(const SegPlan& p, const uint32_t* keys, const uint32_t* vals, ColBnd* bnd,
+                             ans_quantities* q, cudaStream_t st) {
+  return run_colstat(p, keys, vals, bnd, q, st);
 }
 
 cudaError_t launch_empty_fixup(const StatsArgs& a, cudaStream_t st) {
