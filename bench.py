@@ -236,7 +236,7 @@ def main():
 
     import torch
 
-    from paper_2510_14050_gb300 import ans, synth
+    from paper_2510_14050_gb300 import ans, replicas, synth
 
     torch.cuda.set_device(local)
     if args.serve_sweep:
@@ -259,15 +259,11 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dist, "cuda")
 
     cfg = args.config
     nwin = args.nwin or DEFAULT_NWIN[cfg]
-    w = synth.generate(cfg, nwin=nwin, first_window=rank * nwin)
+    w = synth.generate(cfg, nwin=nwin, first_window=replicas.first_window(rank, nwin))
     total = w.total
     sizes = np.diff(w.offsets)
 
@@ -339,7 +335,8 @@ def main():
         release(r)
     keep = []
     t_ms = max_over_ranks(sum(step_ms))
-    value = total * args.steps * world / (t_ms / 1e3)
+    job_total = replicas.sum_over_ranks(total, dist, "cuda")  # packets of one step, all ranks
+    value = replicas.job_rate(job_total * args.steps, t_ms / 1e3)
 
     # ---- dominant kernel and roofline
     peak, peak_kind = hbm_peak()
@@ -392,7 +389,7 @@ def main():
         e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs2))
         for r in keep:
             release(r)
-        e2e = {"value": total * args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
+        e2e = {"value": replicas.job_rate(job_total * args.steps, e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 72 * nwin}
 
     # ---- the plain per-window method on the same GPU
@@ -422,7 +419,7 @@ def main():
         pw_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs3))
         for r in keep:
             release(r)
-        per_window = {"value": total * k2 * world / (pw_ms / 1e3), "unit": UNIT, "steps": k2,
+        per_window = {"value": replicas.job_rate(job_total * k2, pw_ms / 1e3), "unit": UNIT, "steps": k2,
                       "ms_per_step": pw_ms / k2, "launches": f"{nwin} x ans_build_window + ans_sum_windows"}
 
     # ---- CPU oracle baseline (rank 0, N=1 only)
