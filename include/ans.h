@@ -272,6 +272,23 @@ int ans_autotune(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, con
 int ans_profile_enable(ans_ctx* ctx, int enable);
 int ans_profile_read(ans_ctx* ctx, char* buf, size_t buflen, size_t* needed);
 
+/* Import a traffic matrix given as DCSR -- the paper's own input form, the
+ * flat containers of Sec. IV-B (row ids; row pointers, the prefix of the
+ * per-row degrees; column ids, the edges; uint64 values, the weights) -- as
+ * a matrix of the context, so that ans_network_quantities, ans_sum_windows
+ * and the views work on it.  nrows rows, nnz links; row_ids[nrows],
+ * row_ptr[nrows + 1], col_ids[nnz], vals[nnz], in device or host memory
+ * (copied; the caller keeps ownership).  The input must be canonical: row
+ * ids strictly ascending, row_ptr from 0 to nnz and strictly increasing (no
+ * empty stored row), column ids strictly ascending within a row, no zero
+ * value.  The call checks this on the device and waits for the check; the
+ * quantities are then computed asynchronously on `stream`.  Errors:
+ * ANS_ERR_INVALID_ARG (NULL arrays, nnz > 2^31 - 1, not canonical),
+ * ANS_ERR_BUDGET, ANS_ERR_OOM, ANS_ERR_CUDA. */
+int ans_matrix_import(ans_ctx* ctx, uint64_t nrows, uint64_t nnz, const uint32_t* row_ids,
+                      const uint64_t* row_ptr, const uint32_t* col_ids, const uint64_t* vals,
+                      ans_matrix** out, void* stream);
+
 /* Static description of a status code. */
 const char* ans_status_string(int status);
 

@@ -45,7 +45,7 @@ EXPORTS = (
     "ans_batch_submit", "ans_wait", "ans_matrix_view", "ans_matrix_quantities", "ans_matrix_free",
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
     "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
-    "ans_ctx_memory", "ans_batch_bytes",
+    "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import",
 )
 
 
@@ -109,6 +109,7 @@ def load(path: str | os.PathLike | None = None):
         "ans_autotune": ([_vp, _vp, _vp, P(_u64), C.c_size_t, P(Tuning), _vp], C.c_int),
         "ans_ctx_memory": ([_vp, P(C.c_size_t), P(C.c_size_t)], C.c_int),
         "ans_batch_bytes": ([_vp, P(_u64), C.c_size_t, C.c_uint32, P(C.c_size_t)], C.c_int),
+        "ans_matrix_import": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, P(_vp), _vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -269,6 +270,34 @@ class Context:
         out = _vp()
         _check(self._lib.ans_build_window(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)), int(n),
                                           C.byref(out), _vp(_stream(stream))), "build_window", self._h)
+        return Matrix(out.value)
+
+    def import_matrix(self, row_ids, row_ptr, col_ids, vals, stream=None) -> Matrix:
+        """A matrix of this context from DCSR arrays (CUDA tensors, or host
+        numpy arrays / CPU tensors: uint32 row ids and column ids, uint64 row
+        pointers and values; int32/int64 tensors are taken bit for bit).
+        The arrays are copied; non-canonical input raises ERR_INVALID_ARG."""
+        keep = []
+
+        def ptr(x, dt):
+            if hasattr(x, "data_ptr"):  # torch tensor, device or host
+                if not x.is_contiguous():
+                    raise ValueError("expected a contiguous tensor")
+                keep.append(x)
+                return x.data_ptr() if x.numel() else None
+            a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+            keep.append(a)
+            return a.ctypes.data if a.size else None
+
+        nrows = len(row_ids)
+        nnz = len(col_ids)
+        if len(row_ptr) != nrows + 1 or len(vals) != nnz:
+            raise ValueError("row_ptr needs nrows + 1 entries and vals nnz")
+        out = _vp()
+        _check(self._lib.ans_matrix_import(self._h, nrows, nnz, _vp(ptr(row_ids, np.uint32)),
+                                           _vp(ptr(row_ptr, np.uint64)), _vp(ptr(col_ids, np.uint32)),
+                                           _vp(ptr(vals, np.uint64)), C.byref(out), _vp(_stream(stream))),
+               "matrix_import", self._h)
         return Matrix(out.value)
 
     def sum_windows(self, mats: Sequence[Matrix], stream=None) -> Matrix:

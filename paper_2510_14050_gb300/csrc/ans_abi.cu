@@ -1204,6 +1204,62 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   return ANS_OK;
 }
 
+// The nine quantities of matrix (b, seg) recomputed from its stored DCSR
+// into the device array q (kModeMatrix pipeline: value prefix, row
+// statistics, column pass).  The caller holds c->mu and has ordered `st`
+// after the matrix's completion.
+int matrix_stats(ans_ctx* c, const Block* b, uint32_t seg, ans_quantities* q_out, cudaStream_t st) {
+  const uint64_t cap = b->cap[seg];
+  const uint64_t bs = b->base[seg];
+  HostPlan hp;
+  hp.build(std::vector<uint64_t>{cap}, nullptr);
+  Layout L;
+  DevPlan dp;
+  dp.reserve(L, 1);
+  const size_t off_pre = L.add((hp.pad + 1) * 8);
+  const size_t off_lb = L.add((size_t)std::max<uint32_t>(hp.ntiles, 1) * 8);
+  const size_t off_q = L.add(sizeof(ans_quantities));
+  PipeScratch ps;
+  ps.reserve(L, hp.pad, 1, std::max<uint32_t>(hp.ntiles, 1), false);
+  ANS_TRY(ensure_scratch(c, L.size, st));
+  char* m = (char*)c->scratch;
+  UploadSet us;
+  us.add(m + dp.base, hp.base.data(), 8);
+  us.add(m + dp.first_tile, hp.first_tile.data(), 8);
+  ANS_TRY(us.flush(c, st));
+  SegPlan p = dp.bind(m, hp);
+  uint64_t* hdr = b->hdr + 2 * (size_t)seg;
+  p.len = hdr + 1;  // nnz, on the device
+  ans_quantities* q = at<ans_quantities>(m, off_q);
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets);
+  ANS_CUDA(cudaMemsetAsync(q, 0, sizeof(ans_quantities), st));
+  ANS_CUDA(cudaMemsetAsync(m + off_lb, 0, (size_t)std::max<uint32_t>(hp.ntiles, 1) * 8, st));
+  ANS_CUDA(cudaMemsetAsync(tickets, 0, 32 * 4, st));
+  ANS_CUDA(cudaMemsetAsync(m + ps.col_hist, 0, kColPasses * kRadix * 4, st));
+  uint64_t* pre = at<uint64_t>(m, off_pre);
+  if (hp.ntiles) {
+    ANS_CUDA(timed(c, "scan_u64", st, [&] { return launch_scan_u64(p, b->vals + bs, pre, at<uint64_t>(m, off_lb), tickets, c->d_err, st); }));
+    StatsArgs a;
+    a.plan = p;
+    a.hdr = hdr;
+    a.q = q;
+    a.col_ids = b->col_ids + bs;
+    a.vals = b->vals + bs;
+    a.row_ids = b->row_ids + bs;
+    a.row_ptr = b->row_ptr + bs + seg;
+    a.pre = pre;
+    a.col_hist = at<uint32_t>(m, ps.col_hist);
+    a.ulen = at<uint64_t>(m, ps.ulen);
+    a.col_st0 = at<uint64_t>(m, ps.st0);
+    a.col_tickets = tickets + 32;
+    a.err = c->d_err;
+    a.mode = kModeMatrix;
+    ANS_CUDA(timed(c, "finish", st, [&] { return launch_finish(a, st); }));
+    ANS_TRY(column_pass(c, p, a.ulen, a.col_ids, a.vals, ps, m, a.col_tickets, q, st));
+  }
+  return copy_quantities_out(q_out, q, 1, st);
+}
+
 }  // namespace
 
 // =========================================================================
@@ -1429,59 +1485,63 @@ int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out,
   const Block* b = x->blk;
   if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
   ANS_CUDA(cudaStreamWaitEvent(st, b->done, 0));
-  const uint64_t cap = b->cap[x->seg];
-  const uint64_t bs = b->base[x->seg];
-  HostPlan hp;
-  hp.build(std::vector<uint64_t>{cap}, nullptr);
-  Layout L;
-  DevPlan dp;
-  dp.reserve(L, 1);
-  const size_t off_pre = L.add((hp.pad + 1) * 8);
-  const size_t off_lb = L.add((size_t)std::max<uint32_t>(hp.ntiles, 1) * 8);
-  const size_t off_q = L.add(sizeof(ans_quantities));
-  PipeScratch ps;
-  ps.reserve(L, hp.pad, 1, std::max<uint32_t>(hp.ntiles, 1), false);
-  ANS_TRY(ensure_scratch(c, L.size, st));
-  char* m = (char*)c->scratch;
-  UploadSet us;
-  us.add(m + dp.base, hp.base.data(), 8);
-  us.add(m + dp.first_tile, hp.first_tile.data(), 8);
-  ANS_TRY(us.flush(c, st));
-  SegPlan p = dp.bind(m, hp);
-  uint64_t* hdr = b->hdr + 2 * (size_t)x->seg;
-  p.len = hdr + 1;  // nnz, on the device
-  ans_quantities* q = at<ans_quantities>(m, off_q);
-  uint32_t* tickets = at<uint32_t>(m, ps.tickets);
-  ANS_CUDA(cudaMemsetAsync(q, 0, sizeof(ans_quantities), st));
-  ANS_CUDA(cudaMemsetAsync(m + off_lb, 0, (size_t)std::max<uint32_t>(hp.ntiles, 1) * 8, st));
-  ANS_CUDA(cudaMemsetAsync(tickets, 0, 32 * 4, st));
-  ANS_CUDA(cudaMemsetAsync(m + ps.col_hist, 0, kColPasses * kRadix * 4, st));
-  uint64_t* pre = at<uint64_t>(m, off_pre);
-  if (hp.ntiles) {
-    ANS_CUDA(timed(c, "scan_u64", st, [&] { return launch_scan_u64(p, b->vals + bs, pre, at<uint64_t>(m, off_lb), tickets, c->d_err, st); }));
-    StatsArgs a;
-    a.plan = p;
-    a.hdr = hdr;
-    a.q = q;
-    a.col_ids = b->col_ids + bs;
-    a.vals = b->vals + bs;
-    a.row_ids = b->row_ids + bs;
-    a.row_ptr = b->row_ptr + bs + x->seg;
-    a.pre = pre;
-    a.col_hist = at<uint32_t>(m, ps.col_hist);
-    a.ulen = at<uint64_t>(m, ps.ulen);
-    a.col_st0 = at<uint64_t>(m, ps.st0);
-    a.col_tickets = tickets + 32;
-    a.err = c->d_err;
-    a.mode = kModeMatrix;
-    ANS_CUDA(timed(c, "finish", st, [&] { return launch_finish(a, st); }));
-    ANS_TRY(column_pass(c, p, a.ulen, a.col_ids, a.vals, ps, m, a.col_tickets, q, st));
-  }
+  ANS_TRY(matrix_stats(c, b, x->seg, out, st));
   ANS_CUDA(cudaMemsetAsync(c->d_err, 0, 4, st));
   ANS_TRY(note_read(const_cast<Block*>(b), st));
-  ANS_TRY(copy_quantities_out(out, q, 1, st));
   return ANS_OK;
 }
+
+int ans_matrix_import(ans_ctx* c, uint64_t nrows, uint64_t nnz, const uint32_t* row_ids, const uint64_t* row_ptr,
+                      const uint32_t* col_ids, const uint64_t* vals, ans_matrix** out, void* stream) {
+  if (!c || !out) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (nnz > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "an imported matrix is limited to 2^31 - 1 links");
+  if (nrows > nnz) return fail(ANS_ERR_INVALID_ARG, "more rows than links (every stored row is nonempty)");
+  if (!row_ptr || (nnz && (!row_ids || !col_ids || !vals))) return fail(ANS_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  Block* b = nullptr;
+  const uint64_t pad = tiles_for(nnz) * kTile;
+  ANS_TRY(make_block(c, pad, 1, std::vector<uint64_t>{0}, std::vector<uint64_t>{nnz}, st, &b));
+  auto bail = [&](int rc) {
+    block_discard(b, st);
+    return rc;
+  };
+  auto cu = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return ANS_OK;
+    return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  int rc = ANS_OK;
+  const uint64_t hdr[2] = {nrows, nnz};
+  UploadSet us;
+  us.add(b->hdr, hdr, 16);
+  if ((rc = us.flush(c, st))) return bail(rc);
+  if ((rc = cu(cudaMemcpyAsync(b->row_ptr, row_ptr, (nrows + 1) * 8, cudaMemcpyDefault, st), "copy row_ptr")))
+    return bail(rc);
+  if (nnz) {
+    if ((rc = cu(cudaMemcpyAsync(b->row_ids, row_ids, nrows * 4, cudaMemcpyDefault, st), "copy row_ids")) ||
+        (rc = cu(cudaMemcpyAsync(b->col_ids, col_ids, nnz * 4, cudaMemcpyDefault, st), "copy col_ids")) ||
+        (rc = cu(cudaMemcpyAsync(b->vals, vals, nnz * 8, cudaMemcpyDefault, st), "copy vals")))
+      return bail(rc);
+  }
+  // Canonical DCSR or nothing: the statistics kernels index by row_ptr.
+  if ((rc = cu(cudaMemsetAsync(b->status, 0, 4, st), "memset"))) return bail(rc);
+  if ((rc = cu(launch_check_dcsr(nrows, nnz, b->row_ids, b->row_ptr, b->col_ids, b->vals, b->status, st), "check")))
+    return bail(rc);
+  uint32_t bad = 0;
+  if ((rc = cu(cudaMemcpyAsync(&bad, b->status, 4, cudaMemcpyDeviceToHost, st), "copy")) ||
+      (rc = cu(cudaStreamSynchronize(st), "sync")))
+    return bail(rc);
+  if (bad) return bail(fail(ANS_ERR_INVALID_ARG, "not canonical DCSR (check code " + std::to_string(bad) + ")"));
+  if ((rc = matrix_stats(c, b, 0, b->q, st))) return bail(rc);
+  if ((rc = capture_err(c, b->status, st)) || (rc = reset_err(c, st))) return bail(rc);
+  if ((rc = cu(cudaEventRecord(b->done, st), "record"))) return bail(rc);
+  b->refs = 1;
+  *out = new ans_matrix{b, 0};
+  return ANS_OK;
+}
+
 
 int ans_wait(ans_ctx* c, ans_ticket t, uint64_t timeout_ns) {
   if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");

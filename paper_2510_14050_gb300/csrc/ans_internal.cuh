@@ -208,6 +208,9 @@ cudaError_t launch_colstat(const SegPlan& p, const uint32_t* keys, const uint64_
                            ans_quantities* q, cudaStream_t st);
 cudaError_t launch_colstat32(const SegPlan& p, const uint32_t* keys, const uint32_t* vals, ColBnd* bnd,
                              ans_quantities* q, cudaStream_t st);
+// Canonical-DCSR check of an imported matrix; ORs failure bits into *bad.
+cudaError_t launch_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* row_ids, const uint64_t* row_ptr,
+                              const uint32_t* col_ids, const uint64_t* vals, uint32_t* bad, cudaStream_t st);
 // Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.

@@ -475,7 +475,47 @@ __global__ void k_zero(uint32_t* __restrict__ p, size_t words, uint8_t* __restri
   if (blockIdx.x == 0 && threadIdx.x < ntail) tail[threadIdx.x] = 0;
 }
 
+// Canonical-DCSR check of an imported matrix (Sec. IV-B containers; rows
+// ascending, every stored row nonempty, columns ascending within a row, no
+// stored zero).  Sets bits of *bad: 1 row_ptr does not run from 0 to nnz,
+// 2 a row is empty or row_ptr decreases, 4 row ids not strictly ascending,
+// 8 a zero value, 16 columns not strictly ascending within a row.
+__global__ void k_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* __restrict__ row_ids,
+                             const uint64_t* __restrict__ row_ptr, const uint32_t* __restrict__ col_ids,
+                             const uint64_t* __restrict__ vals, uint32_t* bad) {
+  const uint64_t n = nrows + 1 > nnz ? nrows + 1 : nnz;
+  uint32_t f = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (i == 0 && (row_ptr[0] != 0 || row_ptr[nrows] != nnz)) f |= 1u;
+    if (i < nrows) {
+      if (row_ptr[i] >= row_ptr[i + 1]) f |= 2u;
+      if (i + 1 < nrows && row_ids[i] >= row_ids[i + 1]) f |= 4u;
+    }
+    if (i < nnz) {
+      if (vals[i] == 0) f |= 8u;
+      if (i + 1 < nnz && col_ids[i] >= col_ids[i + 1]) {  // then i + 1 must start a row
+        uint64_t lo = 0, hi = nrows + 1;                    // first r with row_ptr[r] >= i + 1
+        while (lo < hi) {
+          const uint64_t mid = (lo + hi) >> 1;
+          if (row_ptr[mid] < i + 1) lo = mid + 1; else hi = mid;
+        }
+        if (lo > nrows || row_ptr[lo] != i + 1) f |= 16u;
+      }
+    }
+  }
+  if (f) atomicOr(bad, f);
+}
+
 }  // namespace
+
+cudaError_t launch_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* row_ids, const uint64_t* row_ptr,
+                              const uint32_t* col_ids, const uint64_t* vals, uint32_t* bad, cudaStream_t st) {
+  const uint64_t n = nrows + 1 > nnz ? nrows + 1 : nnz;
+  const uint64_t want = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(want > 4096 ? 4096 : want);
+  k_check_dcsr<<<blocks, 256, 0, st>>>(nrows, nnz, row_ids, row_ptr, col_ids, vals, bad);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) {
   const size_t words = bytes / 4;

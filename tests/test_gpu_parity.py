@@ -418,3 +418,60 @@ def test_graph_replay_follows_each_call(ans, synth, graph):
             assert quants == [oracle.window_quantities(*w.window(i)) for i in range(w.nwin)]
     finally:
         c.close()
+
+
+def test_import_dcsr_quantities_and_sums(ans, ctx, synth):
+    """Matrices given as DCSR (the paper's input form) get the oracle's
+    quantities, read back unchanged, and sum with built windows."""
+    w = synth.generate(2, nwin=3, first_window=50)
+    exp = [oracle.traffic_matrix(*w.window(i)) for i in range(3)]
+    imported = []
+    for i, e in enumerate(exp):
+        if i == 0:  # host arrays
+            m = ctx.import_matrix(e.row_ids, e.row_ptr, e.col_ids, e.vals)
+        else:       # device tensors
+            t = [torch.from_numpy(np.ascontiguousarray(a).view(np.int32 if a.dtype == np.uint32 else np.int64)).cuda()
+                 for a in (e.row_ids, e.row_ptr, e.col_ids, e.vals)]
+            m = ctx.import_matrix(*t)
+        assert_dcsr_equal(m.to_numpy(), e, f"import {i}")
+        assert m.quantities() == oracle.network_quantities(e)
+        assert ctx.network_quantities(m) == oracle.network_quantities(e)
+        imported.append(m)
+    built = ctx.build_window(dev(w.window(2)[0]), dev(w.window(2)[1]), int(w.offsets[3] - w.offsets[2]))
+    s = ctx.sum_windows(imported[:2] + [built])
+    assert_dcsr_equal(s.to_numpy(), oracle.sum_matrices(exp), "sum")
+    for m in imported + [built, s]:
+        m.free()
+    empty = ctx.import_matrix(np.zeros(0, np.uint32), np.zeros(1, np.uint64), np.zeros(0, np.uint32),
+                              np.zeros(0, np.uint64))
+    assert empty.quantities() == dict.fromkeys(oracle.QUANTITY_NAMES, 0)
+    empty.free()
+
+
+@pytest.mark.parametrize("case", ["row_ptr_start", "empty_row", "rows_unsorted", "zero_value", "cols_unsorted",
+                                  "cols_equal", "row_ptr_end"])
+def test_import_rejects_non_canonical_dcsr(ans, ctx, case):
+    r = np.array([1, 5, 9], np.uint32)
+    p = np.array([0, 2, 3, 5], np.uint64)
+    c = np.array([3, 7, 2, 0, 4], np.uint32)
+    v = np.array([1, 2, 3, 4, 5], np.uint64)
+    m = ctx.import_matrix(r, p, c, v)  # canonical: accepted
+    m.free()
+    r, p, c, v = r.copy(), p.copy(), c.copy(), v.copy()
+    if case == "row_ptr_start":
+        p[0] = 1
+    elif case == "empty_row":
+        p[1] = 0
+    elif case == "rows_unsorted":
+        r[1], r[2] = 9, 5
+    elif case == "zero_value":
+        v[3] = 0
+    elif case == "cols_unsorted":
+        c[0], c[1] = 7, 3
+    elif case == "cols_equal":
+        c[4] = 0
+    elif case == "row_ptr_end":
+        p[3] = 4
+    with pytest.raises(ans.AnsError) as ei:
+        ctx.import_matrix(r, p, c, v)
+    assert ei.value.code == ans.ERR_INVALID_ARG
