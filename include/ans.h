@@ -209,14 +209,15 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * (kv_*), and the 32-bit destination keys of the column pass (col_*).
  * *_threads: threads per 8192-key tile, 512 or 1024.  *_rank: how lanes
  * holding equal digits find each other, 0 = one __match_any_sync per key,
- * 1 = eight ballots per key.  *_blocks: CTAs per SM the kernel is compiled
+ * 1 = eight ballots per key, 2 = a per-warp shared-memory table (each lane
+ * ORs its bit into its digit's entry, which also carries the digit's count).  *_blocks: CTAs per SM the kernel is compiled
  * for, 1, or 2 (512 threads only: registers capped at 64).
  * win_path: how window keys are sorted, 0 = on chip, one 8-CTA thread-block
  * cluster per window of at most 2^17 packets sorting it in distributed shared
  * memory (larger windows, and every window when the device cannot host such
  * a cluster, take the key_* passes), 1 = the key_* passes for every window.
- * win_threads (512 or 1024) and win_rank (as *_rank) configure the cluster
- * kernel.  sum_path: how time sums order the links of their input matrices,
+ * win_threads (512 or 1024) and win_rank (0 or 1, as *_rank) configure the
+ * cluster kernel.  sum_path: how time sums order the links of their input matrices,
  * 0 = ceil(log2 k) rounds of pairwise merges of the matrices' already sorted
  * links, 1 = the kv_* radix passes over all gathered links.  agg_path: how
  * a window's equal packets are grouped, 0 = sorting every packet's link key,

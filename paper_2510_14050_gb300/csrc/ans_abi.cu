@@ -1709,12 +1709,12 @@ int ans_get_tuning(ans_ctx* c, ans_tuning* out) {
 int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   if (!c || !t) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
   auto ok = [](uint32_t th, uint32_t rk, uint32_t bl) {
-    return (th == 512 || th == 1024) && rk <= 1 && (bl == 1 || (bl == 2 && th == 512));
+    return (th == 512 || th == 1024) && rk <= 2 && (bl == 1 || (bl == 2 && th == 512));
   };
   if (!ok(t->key_threads, t->key_rank, t->key_blocks) || !ok(t->kv_threads, t->kv_rank, t->kv_blocks) ||
       !ok(t->col_threads, t->col_rank, t->col_blocks))
-    return fail(ANS_ERR_INVALID_ARG, "threads must be 512 or 1024, rank 0 or 1, blocks 1 (or 2 with 512 threads)");
-  if (t->win_path > 1 || !ok(t->win_threads, t->win_rank, 1))
+    return fail(ANS_ERR_INVALID_ARG, "threads must be 512 or 1024, rank 0, 1 or 2, blocks 1 (or 2 with 512 threads)");
+  if (t->win_path > 1 || t->win_rank > 1 || !ok(t->win_threads, t->win_rank, 1))
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
   if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
   if (t->agg_path > 1) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0 or 1");
@@ -1741,9 +1741,10 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
 int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets, size_t nwin,
                  ans_tuning* chosen, void* stream) {
   if (!c || !h_offsets || nwin == 0) return fail(ANS_ERR_INVALID_ARG, "NULL argument or empty batch");
-  constexpr int kVariants = 6;
-  const SortCfg variants[kVariants] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankMatch, 2},
-                                       {512, kRankBallot, 2}, {1024, kRankMatch, 1}, {1024, kRankBallot, 1}};
+  constexpr int kVariants = 9;
+  const SortCfg variants[kVariants] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankTable, 1},
+                                       {512, kRankMatch, 2}, {512, kRankBallot, 2}, {512, kRankTable, 2},
+                                       {1024, kRankMatch, 1}, {1024, kRankBallot, 1}, {1024, kRankTable, 1}};
   using Prof = std::map<std::string, double>;
   std::vector<ans_matrix*> per(nwin, nullptr);
   auto run_once = [&]() -> int {

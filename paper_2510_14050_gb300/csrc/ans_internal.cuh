@@ -43,9 +43,11 @@ enum ErrBits : uint32_t {
 
 // How a onesweep pass is launched (chosen per context by the autotuner):
 // threads per 8192-key tile (512 or 1024), how lanes with equal digits are
-// found (one __match_any_sync, or eight ballots), and whether a 512-thread
-// tile is compiled to leave room for two resident CTAs per SM (64 registers).
-enum RankMode : int { kRankMatch = 0, kRankBallot = 1 };
+// found (one __match_any_sync; eight ballots; or a per-warp shared-memory
+// table where each lane ORs its bit into its digit's entry, which also holds
+// the digit's running count), and whether a 512-thread tile is compiled to
+// leave room for two resident CTAs per SM (64 registers).
+enum RankMode : int { kRankMatch = 0, kRankBallot = 1, kRankTable = 2 };
 struct SortCfg {
   int threads = 512;
   int rank = kRankMatch;

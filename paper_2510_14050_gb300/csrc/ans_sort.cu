@@ -104,10 +104,17 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
 
 struct NoVal {};
 
-template <typename K, typename V, int kT>
+// Per-warp digit counters: kRadix + 1 uint32 counters, or (table ranking)
+// kRadix uint64 entries {count << 32 | lanes holding the digit}.
+template <int kRank>
+constexpr size_t warp_counter_bytes() {
+  return kRank == kRankTable ? (size_t)kRadix * 8 : (size_t)(kRadix + 1) * 4;
+}
+
+template <typename K, typename V, int kT, int kRank>
 constexpr size_t onesweep_smem_bytes() {
   return (size_t)kTile * sizeof(K) + (std::is_same<V, NoVal>::value ? 0 : (size_t)kTile * sizeof(V)) +
-         (size_t)(kT / 32) * (kRadix + 1) * 4;
+         (size_t)(kT / 32) * warp_counter_bytes<kRank>();
 }
 
 // One stable digit pass over keys of type K (8 passes for 64-bit keys, 4 for
@@ -126,8 +133,9 @@ __global__ void __launch_bounds__(kT, kMinB)
   extern __shared__ __align__(16) uint8_t smem[];
   K* s_keys = reinterpret_cast<K*>(smem);
   V* s_vals = reinterpret_cast<V*>(smem + (size_t)kTile * sizeof(K));
-  uint32_t* s_wc = reinterpret_cast<uint32_t*>(smem + (size_t)kTile * sizeof(K) +
-                                               (kVals ? (size_t)kTile * sizeof(V) : 0));  // [kW][kRadix+1]
+  uint8_t* s_cnt = smem + (size_t)kTile * sizeof(K) + (kVals ? (size_t)kTile * sizeof(V) : 0);
+  uint32_t* s_wc = reinterpret_cast<uint32_t*>(s_cnt);   // [kW][kRadix+1] (match / ballot ranking)
+  uint64_t* s_tab = reinterpret_cast<uint64_t*>(s_cnt);  // [kW][kRadix]   (table ranking)
   __shared__ uint64_t s_gofs[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
   __shared__ uint32_t s_tmp[8];
@@ -142,7 +150,12 @@ __global__ void __launch_bounds__(kT, kMinB)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int shift = pass * kRadixBits;
   uint32_t* wc = s_wc + warp * (kRadix + 1);
-  for (int i = lane; i < kRadix + 1; i += 32) wc[i] = 0;
+  uint64_t* tab = s_tab + warp * kRadix;
+  if constexpr (kRank == kRankTable) {
+    for (int i = lane; i < kRadix; i += 32) tab[i] = 0;
+  } else {
+    for (int i = lane; i < kRadix + 1; i += 32) wc[i] = 0;
+  }
   __syncwarp();
 
   const uint64_t g0 = tl.base + tl.start;
@@ -163,17 +176,32 @@ __global__ void __launch_bounds__(kT, kMinB)
   for (int i = 0; i < kP; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
     const bool valid = idx < tl.count;
-    const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & 0xffu : (uint32_t)kRadix;
-    const uint32_t peers = digit_peers<kRank>(d, valid);
-    const int leader = __ffs(peers) - 1;
-    uint32_t old = 0;
-    if (valid && lane == leader) {
-      old = wc[d];
-      wc[d] = old + __popc(peers);
+    if constexpr (kRank == kRankTable) {
+      // Each lane sets its bit in its digit's entry; every lane then reads
+      // the entry (the lanes sharing its digit, and the digit's count so
+      // far), and the lowest of them advances the count and clears the bits.
+      const uint32_t d = (uint32_t)(k[i] >> shift) & 0xffu;
+      if (valid) atomicOr(reinterpret_cast<unsigned int*>(tab + d), 1u << lane);
+      __syncwarp();
+      const uint64_t e = valid ? tab[d] : 0ull;
+      __syncwarp();
+      const uint32_t peers = (uint32_t)e, old = (uint32_t)(e >> 32);
+      if (valid && lane == __ffs(peers) - 1) tab[d] = (uint64_t)(old + __popc(peers)) << 32;
+      __syncwarp();
+      r[i] = old + __popc(peers & lanemask_lt());
+    } else {
+      const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & 0xffu : (uint32_t)kRadix;
+      const uint32_t peers = digit_peers<kRank>(d, valid);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (valid && lane == leader) {
+        old = wc[d];
+        wc[d] = old + __popc(peers);
+      }
+      __syncwarp();
+      old = __shfl_sync(0xffffffffu, old, valid ? leader : lane);
+      r[i] = old + __popc(peers & lanemask_lt());
     }
-    __syncwarp();
-    old = __shfl_sync(0xffffffffu, old, valid ? leader : lane);
-    r[i] = old + __popc(peers & lanemask_lt());
   }
   __syncthreads();
 
@@ -184,9 +212,15 @@ __global__ void __launch_bounds__(kT, kMinB)
   if (d < kRadix) {
 #pragma unroll 4
     for (int w = 0; w < kW; ++w) {
-      const uint32_t c = s_wc[w * (kRadix + 1) + d];
-      s_wc[w * (kRadix + 1) + d] = cnt;
-      cnt += c;
+      if constexpr (kRank == kRankTable) {
+        const uint32_t c = (uint32_t)(s_tab[w * kRadix + d] >> 32);
+        s_tab[w * kRadix + d] = (uint64_t)cnt << 32;
+        cnt += c;
+      } else {
+        const uint32_t c = s_wc[w * (kRadix + 1) + d];
+        s_wc[w * (kRadix + 1) + d] = cnt;
+        cnt += c;
+      }
     }
     uint64_t* my = st_cur + (uint64_t)t * kRadix + d;
     if (tl.j == 0) {
@@ -211,7 +245,8 @@ __global__ void __launch_bounds__(kT, kMinB)
     const uint32_t idx = wbase + i * 32 + lane;
     if (idx < tl.count) {
       const uint32_t dg = (uint32_t)(k[i] >> shift) & 0xffu;
-      const uint32_t pos = s_dstart[dg] + wc[dg] + r[i];
+      const uint32_t woff = kRank == kRankTable ? (uint32_t)(tab[dg] >> 32) : wc[dg];
+      const uint32_t pos = s_dstart[dg] + woff + r[i];
       s_keys[pos] = k[i];
       if constexpr (kVals) s_vals[pos] = v[i];
     }
@@ -353,7 +388,7 @@ cudaError_t configure_onesweep_variant() {
   if (e != cudaSuccess) return e;
   if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
   e = cudaFuncSetAttribute(k_onesweep<K, V, kT, kRank, kMinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<K, V, kT>());
+                           (int)onesweep_smem_bytes<K, V, kT, kRank>());
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
   return e;
 }
@@ -364,7 +399,7 @@ cudaError_t run_onesweep_variant(const SegPlan& p, int pass, const K* kin, K* ko
                                  uint32_t* err, cudaStream_t st) {
   cudaError_t e = configure_onesweep_variant<K, V, kT, kRank, kMinB>();
   if (e != cudaSuccess) return e;
-  k_onesweep<K, V, kT, kRank, kMinB><<<p.ntiles, kT, onesweep_smem_bytes<K, V, kT>(), st>>>(
+  k_onesweep<K, V, kT, kRank, kMinB><<<p.ntiles, kT, onesweep_smem_bytes<K, V, kT, kRank>(), st>>>(
       p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err);
   return cudaGetLastError();
 }
@@ -379,13 +414,16 @@ cudaError_t run_onesweep(const SegPlan& p, int pass, const K* kin, K* kout, cons
                                              err, st)
   if (cfg.threads == 1024) {
     if (cfg.rank == kRankBallot) ANS_OS(1024, kRankBallot, 1);
+    if (cfg.rank == kRankTable) ANS_OS(1024, kRankTable, 1);
     ANS_OS(1024, kRankMatch, 1);
   }
   if (cfg.blocks == 2) {
     if (cfg.rank == kRankBallot) ANS_OS(512, kRankBallot, 2);
+    if (cfg.rank == kRankTable) ANS_OS(512, kRankTable, 2);
     ANS_OS(512, kRankMatch, 2);
   }
   if (cfg.rank == kRankBallot) ANS_OS(512, kRankBallot, 1);
+  if (cfg.rank == kRankTable) ANS_OS(512, kRankTable, 1);
   ANS_OS(512, kRankMatch, 1);
 #undef ANS_OS
 }

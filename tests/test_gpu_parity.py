@@ -250,8 +250,8 @@ def test_invalid_arguments(ans, ctx):
     assert ei.value.code == ans.ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("threads,rank,blocks", [(512, 0, 1), (512, 1, 1), (512, 0, 2), (512, 1, 2),
-                                                 (1024, 0, 1), (1024, 1, 1)])
+@pytest.mark.parametrize("threads,rank,blocks", [(512, 0, 1), (512, 1, 1), (512, 2, 1), (512, 0, 2), (512, 1, 2),
+                                                 (512, 2, 2), (1024, 0, 1), (1024, 1, 1), (1024, 2, 1)])
 def test_every_sort_configuration_is_exact(ans, synth, threads, rank, blocks):
     """Results never depend on the radix-pass launch configuration."""
     w = synth.generate(5, sizes=[KT * 3 + 17, 0, 40000, 1, 2 * KT])
