@@ -154,6 +154,40 @@ def algorithmic_bytes(sizes, quants, sum_q):
     return b
 
 
+def kernel_bytes_per_step(name, sizes, quants, sum_q, tuning):
+    """Algorithmic bytes one step's launches of kernel family `name` move
+    (reads + writes each item needs once per pass; DESIGN lists the rules).
+    P = packets (split by window-sort path), U/R = links/rows of the windows,
+    Us/Rs = links/rows of the time sum."""
+    cluster_max = 1 << 17
+    on_chip = bool(tuning) and tuning.get("win_path") == 0
+    p_cl = sum(int(p) for p in sizes if on_chip and p <= cluster_max)
+    p_all = sum(int(p) for p in sizes)
+    p_os = p_all - p_cl
+    u = sum(q["unique_links"] for q in quants)
+    r = sum(q["unique_sources"] for q in quants)
+    us = sum_q["unique_links"] if sum_q else 0
+    rs = sum_q["unique_sources"] if sum_q else 0
+    rounds = max(1, (len(sizes) - 1).bit_length()) if len(sizes) > 1 else 0
+    rules = {
+        "pack_hist": 16 * p_os,                        # read pairs, write keys
+        "onesweep": 8 * 16 * p_os,                     # 8 passes: read + write a key
+        "cluster_sort": 16 * p_cl,                     # read pairs, write sorted keys
+        "hash_insert": 8 * p_all,                      # read pairs
+        "hash_compact": 32 * u,                        # slot in, (key, count) out
+        "onesweep_hash": 8 * 32 * u,                   # 8 passes over (key, count)
+        "rle": 8 * p_all + 12 * u + 20 * r + 8 * u + 12 * us + 20 * rs,
+        "finish": 32 * u + 32 * r + 28 * us + 32 * rs,
+        "onesweep_col": 4 * 16 * u + 4 * 24 * us,      # (dst, u32 count) / (dst, u64 count)
+        "colstat": 8 * u + 12 * us,
+        "gather": 28 * u,                              # link + its row in, (key, count) out
+        "merge": rounds * 32 * u,                      # each round: read both runs, write the merge
+        "onesweep_sum": 8 * 32 * u,                    # 8 passes over (key, count)
+        "scan_u64": 16 * u,
+    }
+    return rules.get(name)
+
+
 def run_serving(local, rate, n, budget_gib, pool=None, seed=0):
     """Open-loop Poisson arrivals of serving-size windows (P uniform in
     [2^12, 2^17], traffic as the 64-window batch) through the
@@ -307,6 +341,8 @@ def main():
         res = step(src_d, dst_d)
         torch.cuda.synchronize()
         release(res)
+    if tuning is None:
+        tuning = ctx.get_tuning()
     quants = ans.quantities_from_tensor(q_dev)
     res = step(src_d, dst_d)
     torch.cuda.synchronize()
@@ -346,12 +382,14 @@ def main():
     if dom is not None:
         name, (n_l, ms_l) = dom
         mean_ms = ms_l / n_l
-        if name == "onesweep":
-            per_launch = 16 * total        # read + write every key of the batch once
-            unit_desc = "16 B per packet per digit pass"
-        else:
-            per_launch = alg_bytes
-            unit_desc = "whole-step algorithmic bytes"
+        per_step = kernel_bytes_per_step(name, sizes, quants, sum_q, tuning)
+        per_launch = int(per_step / (n_l / args.steps)) if per_step is not None else alg_bytes
+        unit_desc = {"onesweep": "16 B per packet per digit pass",
+                     "merge": "32 B per window link per merge round",
+                     "onesweep_sum": "32 B per window link per digit pass",
+                     "onesweep_col": "16 B per window link (u32 count) / 24 B per time-sum link per digit pass",
+                     "cluster_sort": "16 B per packet"}.get(name, "per-kernel algorithmic bytes" if per_step
+                                                            else "whole-step algorithmic bytes")
         ach = per_launch / (mean_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": ONESWEEP_NCU_TRAFFIC if name == "onesweep" else None,
