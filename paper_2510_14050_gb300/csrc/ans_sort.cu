@@ -46,17 +46,27 @@ __device__ __forceinline__ void hist_flush(const uint32_t* h, uint32_t* seg_hist
   }
 }
 
+// Digit counts of one key (count c) into one of kHistCopies histogram copies
+// (a warp's copy is warp % kHistCopies, which spreads the shared-memory
+// atomics of a CTA's warps).
+constexpr int kHistCopies = 4;
+__device__ __forceinline__ void hist_add_plain(uint32_t* h, uint64_t key, uint32_t c) {
+#pragma unroll
+  for (int p = 0; p < kPasses; ++p) atomicAdd(&h[p * kRadix + ((key >> (p * kRadixBits)) & 0xff)], c);
+}
+
 __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_t* __restrict__ src,
                                                         const uint32_t* __restrict__ dst,
                                                         uint64_t* __restrict__ keys,
                                                         uint32_t* __restrict__ seg_hist,
                                                         uint64_t* __restrict__ status0,
                                                         uint32_t* __restrict__ tickets) {
-  __shared__ uint32_t h[kPasses * kRadix];
+  __shared__ uint32_t hc[kHistCopies][kPasses * kRadix];
+  uint32_t* h = hc[0];
   __shared__ Tile s_tile;
   const uint32_t t = blockIdx.x;
   const Tile tl = block_tile(p, t, &s_tile);
-  for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) h[i] = 0;
+  for (int i = threadIdx.x; i < kHistCopies * kPasses * kRadix; i += kThreads) (&hc[0][0])[i] = 0;
   if (t == 0 && threadIdx.x < 32) tickets[threadIdx.x] = 0;
   if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
   __syncthreads();
@@ -80,10 +90,14 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
       const uint64_t k2 = ((uint64_t)a.z << 32) | b.z, k3 = ((uint64_t)a.w << 32) | b.w;
       o2[2 * v] = make_ulonglong2(k0, k1);
       o2[2 * v + 1] = make_ulonglong2(k2, k3);
-      hist_add(h, k0, true, 0xffffffffu);
-      hist_add(h, k1, true, 0xffffffffu);
-      hist_add(h, k2, true, 0xffffffffu);
-      hist_add(h, k3, true, 0xffffffffu);
+      // The four keys are consecutive packets: equal neighbours (bursts of
+      // one link) are counted once.
+      uint32_t* hw = hc[warp % kHistCopies];
+      uint32_t c = 1;
+      if (k1 == k0) ++c; else { hist_add_plain(hw, k0, c); c = 1; }
+      if (k2 == k1) ++c; else { hist_add_plain(hw, k1, c); c = 1; }
+      if (k3 == k2) ++c; else { hist_add_plain(hw, k2, c); c = 1; }
+      hist_add_plain(hw, k3, c);
     }
   } else {
     for (int i = 0; i < kPerThread; ++i) {
@@ -97,6 +111,13 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
       }
       hist_add(h, key, valid, vmask);
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 1; k < kHistCopies; ++k) c += hc[k][i];
+    h[i] += c;
   }
   __syncthreads();
   hist_flush(h, seg_hist, tl.seg);
