@@ -1,0 +1,149 @@
+"""Out-of-core ingest: windows held in host memory, more of them than the
+device budget holds at once, analysed batch by batch with the host-to-device
+copy of the next batch overlapped with the analysis of the current one.
+
+This is the paper's sub-partitioning into b_n batches (Sec. III-C) in the
+other direction: there, a device's partition is split so that each batch
+fits; here the host stream is split into batches of at most
+``batch_packets`` packets (whole windows; a larger window forms a batch of
+its own).  Two slots -- each a library context with its own CUDA stream,
+device input buffers and pinned staging buffers -- alternate: while one
+slot's batch is analysed, the other slot's next batch is staged and copied.
+Each batch yields its windows' nine quantities; with ``want_sum`` the time
+sum of all windows (Table I: A_t summed over t) is kept on the device and
+folded batch by batch (``ans_sum_windows``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import ans
+
+
+def plan_batches(offsets: np.ndarray, batch_packets: int) -> list[tuple[int, int]]:
+    """Consecutive window ranges [w0, w1) of at most batch_packets packets
+    each (a window larger than that alone)."""
+    offsets = np.asarray(offsets, dtype=np.uint64)
+    nwin = len(offsets) - 1
+    out = []
+    w0 = 0
+    while w0 < nwin:
+        w1 = w0 + 1
+        while w1 < nwin and int(offsets[w1 + 1] - offsets[w0]) <= batch_packets:
+            w1 += 1
+        out.append((w0, w1))
+        w0 = w1
+    return out
+
+
+@dataclass
+class StreamResult:
+    quantities: np.ndarray  # [nwin, 9] uint64, in window order
+    sum: "ans.Matrix | None"  # the time sum of every window (device-resident), or None
+    batches: int
+    seconds: float
+
+
+def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
+                   want_sum: bool = True, device: int = 0, budget_bytes: int = 0) -> StreamResult:
+    """Analyse every window [offsets[w], offsets[w+1]) of the host arrays
+    src/dst in batches of at most batch_packets packets, two batches in
+    flight.  src/dst: uint32 numpy arrays (staged through pinned buffers) or
+    pinned int32 CPU tensors (copied to the device directly).  Returns the
+    quantities of every window and, with want_sum, their time sum."""
+    import time
+
+    import torch
+
+    offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    nwin = len(offsets) - 1
+    pinned = hasattr(src, "is_pinned") and src.is_pinned() and dst.is_pinned()
+    if not pinned:
+        src = np.ascontiguousarray(src, dtype=np.uint32)
+        dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    plan = plan_batches(offsets, batch_packets)
+    cap = max([int(offsets[b] - offsets[a]) for a, b in plan] + [1])
+    cap_w = max([b - a for a, b in plan] + [1])
+    dev = f"cuda:{device}"
+    slots = []
+    for _ in range(2):
+        slots.append({
+            "ctx": ans.Context(device, budget_bytes=budget_bytes),
+            "stream": torch.cuda.Stream(device=device),
+            "src": torch.empty(cap, dtype=torch.int32, device=dev),
+            "dst": torch.empty(cap, dtype=torch.int32, device=dev),
+            "h_src": None if pinned else torch.empty(cap, dtype=torch.int32).pin_memory(),
+            "h_dst": None if pinned else torch.empty(cap, dtype=torch.int32).pin_memory(),
+            "q": torch.empty((cap_w, 9), dtype=torch.int64, device=dev),
+            "h_q": torch.empty((cap_w, 9), dtype=torch.int64).pin_memory(),
+            "done": None, "pending": None,
+        })
+    quant = np.zeros((nwin, 9), dtype=np.uint64)
+    # Partial time sums as a binary counter: (level, matrix), levels strictly
+    # decreasing; two partials of one level merge into the next level, so
+    # each link is re-merged O(log batches) times.
+    partials: list[tuple[int, "ans.Matrix"]] = []
+    retired: list["ans.Matrix"] = []  # merged inputs, freed once later work has passed them
+    t0 = time.perf_counter()
+
+    def finish(slot):
+        """Collect a slot's previous batch: its quantities and its sum."""
+        if slot["pending"] is None:
+            return
+        (w0, w1), bsum = slot["pending"]
+        slot["done"].synchronize()
+        for m in retired:
+            m.free()
+        retired.clear()
+        quant[w0:w1] = slot["h_q"][: w1 - w0].numpy().view(np.uint64)
+        if bsum is not None:
+            partials.append((0, bsum))
+            while len(partials) >= 2 and partials[-1][0] == partials[-2][0]:
+                (lv, b), (_, a) = partials.pop(), partials.pop()
+                partials.append((lv + 1, slot["ctx"].sum_windows([a, b], stream=slot["stream"])))
+                retired.extend((a, b))
+        slot["pending"] = None
+
+    try:
+        for i, (w0, w1) in enumerate(plan):
+            slot = slots[i % 2]
+            finish(slot)  # the slot's buffers are free again
+            p0, p1 = int(offsets[w0]), int(offsets[w1])
+            n = p1 - p0
+            st = slot["stream"]
+            if pinned:
+                h_src, h_dst = src[p0:p1], dst[p0:p1]
+            else:  # stage into pinned memory (host copy), then copy asynchronously
+                slot["h_src"][:n].numpy().view(np.uint32)[:] = src[p0:p1]
+                slot["h_dst"][:n].numpy().view(np.uint32)[:] = dst[p0:p1]
+                h_src, h_dst = slot["h_src"][:n], slot["h_dst"][:n]
+            with torch.cuda.stream(st):
+                slot["src"][:n].copy_(h_src, non_blocking=True)
+                slot["dst"][:n].copy_(h_dst, non_blocking=True)
+            flags = ans.BATCH_SUM if want_sum else 0
+            _, bsum, _ = slot["ctx"].batch_submit(slot["src"], slot["dst"], offsets[w0:w1 + 1] - offsets[w0], flags,
+                                                  out=slot["q"], stream=st, want_ticket=False)
+            with torch.cuda.stream(st):
+                slot["h_q"][: w1 - w0].copy_(slot["q"][: w1 - w0], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            slot["done"] = ev
+            slot["pending"] = ((w0, w1), bsum)
+        for i in range(len(plan), len(plan) + 2):
+            finish(slots[i % 2])
+        total_sum = None
+        if partials:
+            mats = [m for _, m in partials]
+            total_sum = mats[0] if len(mats) == 1 else slots[0]["ctx"].sum_windows(mats, stream=slots[0]["stream"])
+            if len(mats) > 1:
+                retired.extend(mats)
+        torch.cuda.synchronize(device)
+        for m in retired:
+            m.free()
+        seconds = time.perf_counter() - t0
+        return StreamResult(quant, total_sum, len(plan), seconds)
+    finally:
+        for s in slots:
+            s["ctx"].close()
