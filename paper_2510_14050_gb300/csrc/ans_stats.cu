@@ -289,8 +289,8 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 
 // Column runs inside one tile of destination-sorted (dst, count) pairs.
 // Each thread scans 16 consecutive pairs; a run that crosses thread chunks is
-// completed by the thread holding its successor head, walking back over the
-// chunks without heads.  Runs that cross the tile boundary are summarised in
+// completed by the thread holding its successor head, from a segmented scan
+// over the chunks.  Runs that cross the tile boundary are summarised in
 // bnd[t] (leading part, trailing part) for k_colstat_fin.
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_colstat(SegPlan p, const uint32_t* __restrict__ keys,
@@ -298,7 +298,8 @@ __global__ void __launch_bounds__(kThreads) k_colstat(SegPlan p, const uint32_t*
                                                       ColBnd* __restrict__ bnd, ans_quantities* q) {
   __shared__ Tile s_tile;
   __shared__ uint64_t s_ll[kThreads], s_ls[kThreads], s_tl[kThreads], s_ts[kThreads];
-  __shared__ uint32_t s_has[kThreads];
+  __shared__ uint32_t s_wf[kWarps];
+  __shared__ uint64_t s_wl[kWarps], s_ws[kWarps];
   __shared__ uint64_t s_red[kWarps];
   __shared__ int s_first, s_last;
   const uint32_t t = blockIdx.x;
@@ -347,7 +348,6 @@ __global__ void __launch_bounds__(kThreads) k_colstat(SegPlan p, const uint32_t*
   s_ls[threadIdx.x] = lead_sum;
   s_tl[threadIdx.x] = cur_len;
   s_ts[threadIdx.x] = cur_sum;
-  s_has[threadIdx.x] = has_head ? 1u : 0u;
   if (threadIdx.x == 0) {
     s_first = kThreads;
     s_last = -1;
@@ -356,21 +356,65 @@ __global__ void __launch_bounds__(kThreads) k_colstat(SegPlan p, const uint32_t*
   if (has_head) {
     atomicMin(&s_first, (int)threadIdx.x);
     atomicMax(&s_last, (int)threadIdx.x);
-    // The run that ends just before this chunk's first head.
-    uint64_t L = lead_len, S = lead_sum;
-    int u = (int)threadIdx.x - 1;
-    for (; u >= 0; --u) {
-      if (s_has[u]) {
-        L += s_tl[u];
-        S += s_ts[u];
-        break;
+  }
+  // The run that ends just before this chunk's first head began at the last
+  // head of an earlier chunk: a segmented exclusive scan over the chunks of
+  // (has a head, its tail if so else the whole chunk) gives its length and
+  // sum up to this chunk (operator: (f1, v1) + (f2, v2) = (f1 | f2, f2 ? v2 :
+  // v1 + v2)), warp by warp with shuffles, then across warps.
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool f = has_head;
+    uint64_t vl = has_head ? cur_len : lead_len, vs = has_head ? cur_sum : lead_sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const bool pf = __shfl_up_sync(0xffffffffu, f, o);
+      const uint64_t pl = __shfl_up_sync(0xffffffffu, vl, o), ps = __shfl_up_sync(0xffffffffu, vs, o);
+      if (lane >= o) {
+        if (!f) {
+          vl += pl;
+          vs += ps;
+        }
+        f = f || pf;
       }
-      L += s_ll[u];
-      S += s_ls[u];
     }
-    if (u >= 0) {  // it began inside this tile; otherwise it is the tile's leading run
-      mlen = umax64(mlen, L);
-      msum = umax64(msum, S);
+    // exclusive within the warp
+    bool xf = __shfl_up_sync(0xffffffffu, f, 1);
+    uint64_t xl = __shfl_up_sync(0xffffffffu, vl, 1), xs = __shfl_up_sync(0xffffffffu, vs, 1);
+    if (lane == 0) {
+      xf = false;
+      xl = xs = 0;
+    }
+    if (lane == 31) {
+      s_wf[warp] = f ? 1u : 0u;
+      s_wl[warp] = vl;
+      s_ws[warp] = vs;
+    }
+    __syncthreads();
+    // prefix of the earlier warps
+    bool pf = false;
+    uint64_t pl = 0, ps = 0;
+    for (int w = 0; w < warp; ++w) {
+      if (s_wf[w]) {
+        pl = s_wl[w];
+        ps = s_ws[w];
+      } else {
+        pl += s_wl[w];
+        ps += s_ws[w];
+      }
+      pf = pf || s_wf[w];
+    }
+    if (xf) {
+      pl = xl;
+      ps = xs;
+    } else {
+      pl += xl;
+      ps += xs;
+    }
+    pf = pf || xf;
+    if (has_head && pf) {  // it began inside this tile; otherwise it is the tile's leading run
+      mlen = umax64(mlen, pl + lead_len);
+      msum = umax64(msum, ps + lead_sum);
     }
   }
   __syncthreads();
