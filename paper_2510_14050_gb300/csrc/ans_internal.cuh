@@ -286,6 +286,22 @@ __device__ __forceinline__ uint32_t block_ticket(uint32_t* counter, uint32_t* sm
   return *sm;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T y = __shfl_xor_sync(0xffffffffu, v, o);
+    v = y > v ? y : v;
+  }
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Bounded decoupled look-back for one value chain.  `st` points at tile 0 of
 // the chain's status array with `stride` words between consecutive tiles;
 // `first` is the first tile of the segment, `t` this tile (t > first).
@@ -312,6 +328,38 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* st, uint32_t stride
     --q;
   }
   return excl;
+}
+
+// The same for a whole warp (all 32 lanes call it; every lane gets the
+// result): lane i reads the status of tile q - i, so one round trip covers 32
+// predecessors.  The nearest tile with its inclusive prefix ends the walk
+// (tiles before `first` count as such a tile with value 0); if a nearer tile
+// has not published yet, the window is read again.
+__device__ __forceinline__ uint64_t warp_lookback(const uint64_t* st, uint32_t stride, uint32_t first, uint32_t t,
+                                                  uint32_t* err) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint64_t excl = 0;
+  uint32_t q = t - 1;  // newest tile not yet added; q >= first
+  uint32_t spins = 0;
+  while (true) {
+    const uint64_t v = lane <= q - first ? ld_relaxed(st + (uint64_t)(q - lane) * stride) : kFlagPre;
+    const uint64_t f = v & ~kValMask;
+    const uint32_t pre = __ballot_sync(0xffffffffu, f == kFlagPre);
+    const uint32_t none = __ballot_sync(0xffffffffu, f == 0);
+    const int p = pre ? __ffs(pre) - 1 : 32;              // nearest tile with its prefix
+    const uint32_t upto = p == 32 ? 0xffffffffu : (2u << p) - 1u;  // lanes 0..p
+    if (none & upto) {                                     // a nearer tile is not ready
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicOr(err, (uint32_t)kErrLookback);
+        return excl;
+      }
+      if (spins > 64) __nanosleep(spins > 4096 ? 1000 : 64);
+      continue;
+    }
+    excl += warp_sum((uint64_t)(lane <= (uint32_t)p ? (v & kValMask) : 0ull));
+    if (p < 32) return excl;
+    q -= 32;  // 32 aggregates added; look further back
+  }
 }
 
 // Block-wide exclusive scan of one uint32 per thread for the first 256
@@ -354,22 +402,6 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
     }
     return peers;
   }
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    T y = __shfl_xor_sync(0xffffffffu, v, o);
-    v = y > v ? y : v;
-  }
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
 }
 
 #endif  // __CUDACC__

@@ -83,35 +83,41 @@ __global__ void __launch_bounds__(kThreads) k_rle(StatsArgs a) {
     s_wr[warp] = nr;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {  // the tile's counts, then the look-back by the whole warp
     uint32_t th = 0, tr = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t x = s_wh[w], y = s_wr[w];
-      s_wh[w] = th;
-      s_wr[w] = tr;
-      th += x;
-      tr += y;
+    if (lane == 0) {
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t x = s_wh[w], y = s_wr[w];
+        s_wh[w] = th;
+        s_wr[w] = tr;
+        th += x;
+        tr += y;
+      }
     }
+    th = __shfl_sync(0xffffffffu, th, 0);
+    tr = __shfl_sync(0xffffffffu, tr, 0);
     const uint64_t agg = ((uint64_t)th << 31) | tr;
     uint64_t* my = a.lookback + t;
     uint64_t excl = 0;
     if (tl.j == 0) {
-      st_relaxed(my, kFlagPre | agg);
+      if (lane == 0) st_relaxed(my, kFlagPre | agg);
     } else {
-      st_relaxed(my, kFlagAgg | agg);
-      excl = lookback(a.lookback, 1, t - tl.j, t, a.err);
-      st_relaxed(my, kFlagPre | (excl + agg));
+      if (lane == 0) st_relaxed(my, kFlagAgg | agg);
+      excl = warp_lookback(a.lookback, 1, t - tl.j, t, a.err);
+      if (lane == 0) st_relaxed(my, kFlagPre | (excl + agg));
     }
-    const uint64_t eh = excl >> 31, er = excl & kLow31;
-    s_eh = eh;
-    s_er = er;
-    if (tl.start + tl.count == tl.len) {  // last tile: terminators and header
-      const uint64_t u = eh + th, r = er + tr;
-      if (a.run_start) a.run_start[bs + u] = tl.len;
-      if (a.row_pos) a.row_pos[bs + r] = tl.len;
-      a.row_ptr[bs + r] = u;
-      a.hdr[2 * tl.seg] = r;
-      a.hdr[2 * tl.seg + 1] = u;
+    if (lane == 0) {
+      const uint64_t eh = excl >> 31, er = excl & kLow31;
+      s_eh = eh;
+      s_er = er;
+      if (tl.start + tl.count == tl.len) {  // last tile: terminators and header
+        const uint64_t u = eh + th, r = er + tr;
+        if (a.run_start) a.run_start[bs + u] = tl.len;
+        if (a.row_pos) a.row_pos[bs + r] = tl.len;
+        a.row_ptr[bs + r] = u;
+        a.hdr[2 * tl.seg] = r;
+        a.hdr[2 * tl.seg + 1] = u;
+      }
     }
   }
   __syncthreads();
@@ -169,24 +175,29 @@ __global__ void __launch_bounds__(kThreads) k_scan_u64(SegPlan p, const uint64_t
   }
   if (lane == 0) s_w[warp] = run;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {  // the tile's total, then the look-back by the whole warp
     uint64_t tot = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      const uint64_t x = s_w[w];
-      s_w[w] = tot;
-      tot += x;
+    if (lane == 0) {
+      for (int w = 0; w < kWarps; ++w) {
+        const uint64_t x = s_w[w];
+        s_w[w] = tot;
+        tot += x;
+      }
     }
+    tot = __shfl_sync(0xffffffffu, tot, 0);
     uint64_t* my = lookback_st + t;
     uint64_t excl = 0;
     if (tl.j == 0) {
-      st_relaxed(my, kFlagPre | (tot & kValMask));
+      if (lane == 0) st_relaxed(my, kFlagPre | (tot & kValMask));
     } else {
-      st_relaxed(my, kFlagAgg | (tot & kValMask));
-      excl = lookback(lookback_st, 1, t - tl.j, t, err);
-      st_relaxed(my, kFlagPre | ((excl + tot) & kValMask));
+      if (lane == 0) st_relaxed(my, kFlagAgg | (tot & kValMask));
+      excl = warp_lookback(lookback_st, 1, t - tl.j, t, err);
+      if (lane == 0) st_relaxed(my, kFlagPre | ((excl + tot) & kValMask));
     }
-    s_excl = excl;
-    if (tl.start + tl.count == tl.len) out[bs + tl.len] = excl + tot;
+    if (lane == 0) {
+      s_excl = excl;
+      if (tl.start + tl.count == tl.len) out[bs + tl.len] = excl + tot;
+    }
   }
   __syncthreads();
   const uint64_t off = s_excl + s_w[warp];
