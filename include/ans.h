@@ -143,6 +143,20 @@ int ans_batch_submit(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst,
                      const uint64_t* h_offsets, size_t nwin, uint32_t flags, ans_quantities* out,
                      ans_matrix** per_window, ans_matrix** sum, ans_ticket* ticket, void* stream);
 
+/* The same analysis with every window in its own arrays: window w is
+ * srcs[w][0..lens[w]) and dsts[w][0..lens[w]), in device memory, in
+ * page-locked host memory (read by the kernels directly over the host link,
+ * no staging copy: the serving path for windows that arrive in pinned
+ * buffers), or in any host memory if the device reads pageable memory
+ * (cudaDevAttrPageableMemoryAccess).  srcs, dsts and lens are host arrays of
+ * nwin entries, read during the call; the windows' arrays must stay valid
+ * until the batch completes.  Every other argument, result and error as
+ * ans_batch_submit; ANS_ERR_INVALID_ARG also for a window the device cannot
+ * read. */
+int ans_batch_submit_windows(ans_ctx* ctx, const uint32_t* const* srcs, const uint32_t* const* dsts,
+                             const uint64_t* lens, size_t nwin, uint32_t flags, ans_quantities* out,
+                             ans_matrix** per_window, ans_matrix** sum, ans_ticket* ticket, void* stream);
+
 /* Wait (bounded) for a batch.  timeout_ns == 0 polls once.  Returns ANS_OK,
  * ANS_ERR_TIMEOUT (still running), ANS_ERR_INTERNAL (a bounded device wait or
  * a device consistency check failed inside the batch: its results are not

@@ -45,7 +45,7 @@ EXPORTS = (
     "ans_batch_submit", "ans_wait", "ans_matrix_view", "ans_matrix_quantities", "ans_matrix_free",
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
     "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
-    "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import",
+    "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import", "ans_batch_submit_windows",
 )
 
 
@@ -110,6 +110,8 @@ def load(path: str | os.PathLike | None = None):
         "ans_ctx_memory": ([_vp, P(C.c_size_t), P(C.c_size_t)], C.c_int),
         "ans_batch_bytes": ([_vp, P(_u64), C.c_size_t, C.c_uint32, P(C.c_size_t)], C.c_int),
         "ans_matrix_import": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, P(_vp), _vp], C.c_int),
+        "ans_batch_submit_windows": ([_vp, P(_vp), P(_vp), P(_u64), C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp),
+                                      P(_u64), _vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -336,6 +338,37 @@ class Context:
             self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)), offs.ctypes.data_as(C.POINTER(_u64)), nwin,
             int(flags), outp, per, C.byref(sm) if sm is not None else None,
             C.byref(tk) if tk is not None else None, _vp(_stream(stream))), "batch_submit", self._h)
+        mats = [Matrix(per[i]) for i in range(nwin)] if per is not None else None
+        summ = Matrix(sm.value) if sm is not None else None
+        return mats, summ, (int(tk.value) if tk is not None else None)
+
+    def batch_submit_windows(self, windows, flags: int = 0, out=None, stream=None, want_ticket: bool = True):
+        """As batch_submit, with every window in its own arrays: ``windows`` is
+        a sequence of (src, dst) pairs -- int32 tensors of equal length on the
+        device or in pinned host memory (read in place), or (src_ptr, dst_ptr,
+        n) triples of raw addresses."""
+        nwin = len(windows)
+        srcs = (_vp * max(nwin, 1))()
+        dsts = (_vp * max(nwin, 1))()
+        lens = np.zeros(max(nwin, 1), dtype=np.uint64)
+        for i, w in enumerate(windows):
+            if len(w) == 3:
+                srcs[i], dsts[i], lens[i] = w[0], w[1], int(w[2])
+            else:
+                a, b = w
+                if a.numel() != b.numel():
+                    raise ValueError("src and dst of a window differ in length")
+                if not (a.is_contiguous() and b.is_contiguous()):
+                    raise ValueError("expected contiguous tensors")
+                srcs[i], dsts[i], lens[i] = a.data_ptr(), b.data_ptr(), a.numel()
+        per = (_vp * max(nwin, 1))() if flags & BATCH_MATRICES else None
+        sm = _vp() if flags & BATCH_SUM else None
+        tk = _u64() if want_ticket else None
+        outp = _vp(out.data_ptr()) if out is not None else None
+        _check(self._lib.ans_batch_submit_windows(
+            self._h, srcs, dsts, lens.ctypes.data_as(C.POINTER(_u64)), nwin, int(flags), outp, per,
+            C.byref(sm) if sm is not None else None, C.byref(tk) if tk is not None else None,
+            _vp(_stream(stream))), "batch_submit_windows", self._h)
         mats = [Matrix(per[i]) for i in range(nwin)] if per is not None else None
         summ = Matrix(sm.value) if sm is not None else None
         return mats, summ, (int(tk.value) if tk is not None else None)

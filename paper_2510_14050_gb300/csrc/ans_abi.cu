@@ -144,6 +144,7 @@ struct ans_ctx {
   // their own arena, left empty by every call that used them (hash_dirty
   // marks one that may not have been).
   int agg_path = 0;
+  int pageable = -1;  // does the device read pageable host memory (-1: not asked yet)
   // Batches replay their launch sequence as a CUDA graph (graph = 1): it is
   // captured on `cap` each call and applied to a cached executable graph of
   // the same shape by cudaGraphExecUpdate (re-instantiated if the topology
@@ -516,6 +517,7 @@ struct StatsBufs {
 // Host-side plan of a set of segments.
 struct HostPlan {
   std::vector<uint64_t> in_off, len, base;
+  std::vector<uint64_t> src_at, dst_at;  // per-window array addresses (empty: one input stream)
   std::vector<uint32_t> first_tile;
   uint64_t pad = 0;   // padded items
   uint32_t ntiles = 0;
@@ -547,8 +549,14 @@ struct HostPlan {
     base.resize(n);
     first_tile.resize(n + 1);
     uint64_t t = 0;
+    src_at.clear();
+    dst_at.clear();
     for (size_t i = 0; i < n; ++i) {
       in_off[i] = all.in_off[ids[i]];
+      if (!all.src_at.empty()) {
+        src_at.push_back(all.src_at[ids[i]]);
+        dst_at.push_back(all.dst_at[ids[i]]);
+      }
       len[i] = all.len[ids[i]];
       base[i] = all.base[ids[i]];
       first_tile[i] = (uint32_t)t;
@@ -562,15 +570,26 @@ struct HostPlan {
 
 struct DevPlan {
   size_t in_off, len, base, first_tile;
-  void reserve(Layout& L, size_t nseg) {
+  size_t src_at = 0, dst_at = 0;
+  bool addrs = false;
+  void reserve(Layout& L, size_t nseg, bool with_addrs = false) {
     in_off = L.add(nseg * 8);
     len = L.add(nseg * 8);
     base = L.add(nseg * 8);
     first_tile = L.add((nseg + 1) * 4);
+    addrs = with_addrs;
+    if (addrs) {
+      src_at = L.add(nseg * 8);
+      dst_at = L.add(nseg * 8);
+    }
   }
   SegPlan bind(char* m, const HostPlan& hp) const {
     SegPlan p;
     p.in_off = (const uint64_t*)(m + in_off);
+    if (addrs) {
+      p.src_at = (const uint64_t*)(m + src_at);
+      p.dst_at = (const uint64_t*)(m + dst_at);
+    }
     p.len = (const uint64_t*)(m + len);
     p.base = (const uint64_t*)(m + base);
     p.first_tile = (const uint32_t*)(m + first_tile);
@@ -898,8 +917,9 @@ struct WinLayout {
   size_t size = 0;
   void reserve(const HostPlan& hp, uint32_t nseg, bool want_mats, bool want_sum, bool hash = false) {
     Layout L;
-    dp.reserve(L, nseg);
-    dp_big.reserve(L, nseg);
+    const bool addrs = !hp.src_at.empty();
+    dp.reserve(L, nseg, addrs);
+    dp_big.reserve(L, nseg, addrs);
     off_small = L.add((size_t)nseg * 4);
     if (hash) {
       dp_tab.reserve(L, nseg);
@@ -933,7 +953,8 @@ struct WinLayout {
 // The batch pipeline (also serves ans_build_window with nwin == 1).
 int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
                 size_t nwin, uint32_t flags, ans_quantities* out, ans_matrix** per_window, ans_matrix** sum,
-                ans_ticket* ticket, cudaStream_t st) {
+                ans_ticket* ticket, cudaStream_t st, const uint32_t* const* h_srcs = nullptr,
+                const uint32_t* const* h_dsts = nullptr) {
   std::vector<uint64_t> lens(nwin), offs(nwin);
   for (size_t w = 0; w < nwin; ++w) {
     if (h_offsets[w + 1] < h_offsets[w]) return fail(ANS_ERR_INVALID_ARG, "offsets must be nondecreasing");
@@ -942,7 +963,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     offs[w] = h_offsets[w];
   }
   const uint64_t total = h_offsets[nwin] - h_offsets[0];
-  if (total && (!d_src || !d_dst)) return fail(ANS_ERR_INVALID_ARG, "NULL packet arrays");
+  if (total && !h_srcs && (!d_src || !d_dst)) return fail(ANS_ERR_INVALID_ARG, "NULL packet arrays");
   if (nwin > 0xFFFFFFF0ull) return fail(ANS_ERR_INVALID_ARG, "too many windows");
   const bool want_mats = (flags & ANS_BATCH_MATRICES) != 0;
   const bool want_sum = (flags & ANS_BATCH_SUM) != 0;
@@ -952,6 +973,14 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   HostPlan hp;
   hp.build(lens, &offs);
   if ((uint64_t)hp.ntiles * kTile != hp.pad) return fail(ANS_ERR_INTERNAL, "plan");
+  if (h_srcs) {  // every window's own arrays
+    hp.src_at.resize(nwin);
+    hp.dst_at.resize(nwin);
+    for (size_t w = 0; w < nwin; ++w) {
+      hp.src_at[w] = (uint64_t)(uintptr_t)h_srcs[w];
+      hp.dst_at[w] = (uint64_t)(uintptr_t)h_dsts[w];
+    }
+  }
   // Which windows are sorted on chip (one cluster each) and which by the
   // onesweep passes.
   std::vector<uint32_t> small_ids, big_ids;
@@ -1015,6 +1044,10 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     us.add(m + dp.len, hp.len.data(), nseg * 8);
     us.add(m + dp.base, hp.base.data(), nseg * 8);
     us.add(m + dp.first_tile, hp.first_tile.data(), (nseg + 1) * 4);
+    if (dp.addrs) {
+      us.add(m + dp.src_at, hp.src_at.data(), nseg * 8);
+      us.add(m + dp.dst_at, hp.dst_at.data(), nseg * 8);
+    }
   }
   if (!small_ids.empty()) us.add(m + wl.off_small, small_ids.data(), small_ids.size() * 4);
   if (hash) {
@@ -1027,6 +1060,10 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     us.add(m + wl.dp_big.len, hp_big.len.data(), nb * 8);
     us.add(m + wl.dp_big.base, hp_big.base.data(), nb * 8);
     us.add(m + wl.dp_big.first_tile, hp_big.first_tile.data(), (nb + 1) * 4);
+    if (wl.dp_big.addrs) {
+      us.add(m + wl.dp_big.src_at, hp_big.src_at.data(), nb * 8);
+      us.add(m + wl.dp_big.dst_at, hp_big.dst_at.data(), nb * 8);
+    }
   }
   std::vector<MatDesc> md;
   if (want_sum && nseg) {
@@ -1393,6 +1430,47 @@ int ans_batch_submit(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, c
   std::lock_guard<std::mutex> g(c->mu);
   DeviceGuard dg(c->device);
   return run_windows(c, d_src, d_dst, h_offsets, nwin, flags, out, per_window, sum, ticket, (cudaStream_t)stream);
+}
+
+int ans_batch_submit_windows(ans_ctx* c, const uint32_t* const* srcs, const uint32_t* const* dsts,
+                             const uint64_t* lens, size_t nwin, uint32_t flags, ans_quantities* out,
+                             ans_matrix** per_window, ans_matrix** sum, ans_ticket* ticket, void* stream) {
+  if (!c || (nwin && (!srcs || !dsts || !lens))) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  if (flags & ~(ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC))
+    return fail(ANS_ERR_INVALID_ARG, "unknown flag");
+  if ((flags & ANS_BATCH_MATRICES) && !per_window) return fail(ANS_ERR_INVALID_ARG, "per_window is NULL");
+  if ((flags & ANS_BATCH_SUM) && !sum) return fail(ANS_ERR_INVALID_ARG, "sum is NULL");
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  // Every nonempty window's arrays must be readable by the device: device or
+  // page-locked host memory, or any host memory where the device reads
+  // pageable memory.
+  if (c->pageable < 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, c->device) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    c->pageable = v ? 1 : 0;
+  }
+  std::vector<uint64_t> offs(nwin + 1, 0);
+  for (size_t w = 0; w < nwin; ++w) {
+    offs[w + 1] = offs[w] + lens[w];
+    if (!lens[w]) continue;
+    if (!srcs[w] || !dsts[w]) return fail(ANS_ERR_INVALID_ARG, "NULL packet arrays of a nonempty window");
+    if (!c->pageable) {
+      for (const void* ptr : {(const void*)srcs[w], (const void*)dsts[w]}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type == cudaMemoryTypeUnregistered) {
+          cudaGetLastError();
+          return fail(ANS_ERR_INVALID_ARG, "window " + std::to_string(w) +
+                                               ": packet arrays in pageable host memory this device cannot read");
+        }
+      }
+    }
+  }
+  return run_windows(c, nullptr, nullptr, offs.data(), nwin, flags, out, per_window, sum, ticket,
+                     (cudaStream_t)stream, srcs, dsts);
 }
 
 int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_matrix** out, void* stream) {

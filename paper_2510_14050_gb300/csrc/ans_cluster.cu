@@ -118,11 +118,14 @@ __global__ void __launch_bounds__(kCT, 1)
 
   uint64_t k[kP];
   {
-    const uint64_t in0 = p.in_off[seg] + lo;
+    const uint32_t *ws, *wd;
+    window_inputs(p, seg, src, dst, &ws, &wd);
+    ws += lo;
+    wd += lo;
 #pragma unroll
     for (int i = 0; i < kP; ++i) {
       const uint32_t idx = wbase + i * 32 + lane;
-      k[i] = idx < cnt ? ((uint64_t)__ldg(src + in0 + idx) << 32) | __ldg(dst + in0 + idx) : 0ull;
+      k[i] = idx < cnt ? ((uint64_t)__ldg(ws + idx) << 32) | __ldg(wd + idx) : 0ull;
     }
   }
 

@@ -77,7 +77,10 @@ __global__ void __launch_bounds__(kThreads) k_hash_insert(SegPlan p, const uint3
   if (tl.count == 0) return;
   if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
-  const uint64_t in0 = p.in_off[tl.seg] + tl.start;
+  const uint32_t *ws, *wd;
+  window_inputs(p, tl.seg, src, dst, &ws, &wd);
+  ws += tl.start;
+  wd += tl.start;
   uint64_t* keys = h.keys + h.off[tl.seg];
   uint32_t* cnt = h.cnt + h.off[tl.seg];
   const uint32_t mask = (uint32_t)((1ull << h.lg[tl.seg]) - 1);
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k_hash_insert(SegPlan p, const uint3
     const bool valid = idx < tl.count;
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     if (!valid) continue;
-    const uint64_t key = ((uint64_t)__ldg(src + in0 + idx) << 32) | __ldg(dst + in0 + idx);
+    const uint64_t key = ((uint64_t)__ldg(ws + idx) << 32) | __ldg(wd + idx);
     const uint32_t peers = __match_any_sync(vmask, key);
     if (lane != __ffs(peers) - 1) continue;
     const uint32_t c = __popc(peers);

@@ -57,6 +57,8 @@ struct SortCfg {
 // One entry per segment; device pointers.
 struct SegPlan {
   const uint64_t* in_off = nullptr;     // first item in the input stream (window path)
+  const uint64_t* src_at = nullptr;     // or: per-segment addresses of the src / dst arrays
+  const uint64_t* dst_at = nullptr;     //     (device-accessible; then in_off is unused)
   const uint64_t* len = nullptr;        // items in the segment (may be computed on the device)
   const uint64_t* base = nullptr;       // padded start, a multiple of kTile
   const uint32_t* first_tile = nullptr; // nseg + 1 entries
@@ -248,6 +250,19 @@ __device__ __forceinline__ uint32_t find_seg(const SegPlan& p, uint32_t t) {
     if (p.first_tile[mid] <= t) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// Window `seg`'s packet arrays: its own addresses when the plan has them,
+// else its offset into the one input stream (src, dst).
+__device__ __forceinline__ void window_inputs(const SegPlan& p, uint32_t seg, const uint32_t* src,
+                                              const uint32_t* dst, const uint32_t** ws, const uint32_t** wd) {
+  if (p.src_at) {
+    *ws = reinterpret_cast<const uint32_t*>(p.src_at[seg]);
+    *wd = reinterpret_cast<const uint32_t*>(p.dst_at[seg]);
+  } else {
+    *ws = src + p.in_off[seg];
+    *wd = dst + p.in_off[seg];
+  }
 }
 
 struct Tile {

@@ -72,15 +72,18 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
   __syncthreads();
   if (tl.count == 0) return;
 
-  const uint64_t in0 = p.in_off[tl.seg] + tl.start;
+  const uint32_t *ws, *wd;
+  window_inputs(p, tl.seg, src, dst, &ws, &wd);
+  ws += tl.start;
+  wd += tl.start;
   uint64_t* out = keys + tl.base + tl.start;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool aligned = ((((uintptr_t)(src + in0)) | ((uintptr_t)(dst + in0))) & 15u) == 0;
+  const bool aligned = ((((uintptr_t)ws) | ((uintptr_t)wd)) & 15u) == 0;
 
   if (aligned && tl.count == kTile) {
     // 128-bit loads: each lane reads 4 consecutive sources and destinations.
-    const uint4* s4 = reinterpret_cast<const uint4*>(src + in0);
-    const uint4* d4 = reinterpret_cast<const uint4*>(dst + in0);
+    const uint4* s4 = reinterpret_cast<const uint4*>(ws);
+    const uint4* d4 = reinterpret_cast<const uint4*>(wd);
     ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out);
 #pragma unroll 2
     for (int i = 0; i < kPerThread / 4; ++i) {
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
       const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
       uint64_t key = 0;
       if (valid) {
-        key = ((uint64_t)src[in0 + idx] << 32) | dst[in0 + idx];
+        key = ((uint64_t)ws[idx] << 32) | wd[idx];
         out[idx] = key;
       }
       hist_add(h, key, valid, vmask);

@@ -10,7 +10,10 @@ the server's contexts plus the bytes the library says the batch would
 allocate (``ans_batch_bytes``) stay within the budget; otherwise it waits for
 running batches to complete (an admission stall).  Window latency runs from
 the window's arrival to its quantities being visible on the host; it includes
-the host-to-device copy of its packets.
+moving its packets to the device: by default the windows sit in page-locked
+host memory and the batch's kernels read them there
+(``ans_batch_submit_windows``, no staging copy); with ``zero_copy=False``
+they are staged into a slot's pinned buffer and copied.
 
 Running time sums (Table I: A_t summed over t) are kept resident on the
 device per tumbling bucket of the arrival clock (``bucket_seconds``, e.g. one
@@ -96,19 +99,40 @@ class SumKeeper:
     def _run(self):
         self.torch.cuda.set_device(self.device)
         while True:
-            item = self.q.get()
+            # Everything queued so far is handled together: the batch sums
+            # bound for one bucket are first summed in one call, so the
+            # number of merges follows the worker's wake-ups, not the batches.
+            items = [self.q.get()]
+            while True:
+                try:
+                    items.append(self.q.get_nowait())
+                except _queue.Empty:
+                    break
             try:
-                if item is None:
-                    return
-                keys, mat = item
-                # every level holds its own handle to the same batch sum
-                handles = [mat] + [mat.retain() for _ in keys[1:]]
-                for level, (idx, h) in enumerate(zip(keys, handles)):
-                    self._insert((level, idx), h)
+                groups = {}
+                for item in items:
+                    if item is None:
+                        continue
+                    keys, mat = item
+                    # every level holds its own handle to the same batch sum
+                    handles = [mat] + [mat.retain() for _ in keys[1:]]
+                    for level, (idx, h) in enumerate(zip(keys, handles)):
+                        groups.setdefault((level, idx), []).append(h)
+                for key, mats in groups.items():
+                    if len(mats) > 1:
+                        merged = self.ctx.sum_windows(mats, stream=self.stream)
+                        for m in mats:
+                            m.free()
+                        self.stream.synchronize()
+                        mats = [merged]
+                    self._insert(key, mats[0])
             except Exception as e:  # surfaced by drain()
                 self.error = e
             finally:
-                self.q.task_done()
+                for _ in items:
+                    self.q.task_done()
+            if any(item is None for item in items):
+                return
 
     def _insert(self, key, mat):
         with self.lock:
@@ -158,7 +182,7 @@ class SumKeeper:
 class Server:
     def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int = 64 << 30,
                  max_batch_windows: int = 256, max_batch_packets: int = 1 << 24,
-                 bucket_seconds=(60.0, 3600.0), keep_sums: bool = True):
+                 bucket_seconds=(60.0, 3600.0), keep_sums: bool = True, zero_copy: bool = True):
         import torch
         self.torch = torch
         self.device = device
@@ -166,6 +190,7 @@ class Server:
         self.max_batch_packets = max_batch_packets
         self.bucket_seconds = tuple(bucket_seconds)
         self.keep_sums = keep_sums
+        self.zero_copy = zero_copy
         self.budget = budget_bytes
         self.slots = []
         for _ in range(slots):
@@ -211,6 +236,10 @@ class Server:
         next_k = 0             # next arrival not yet admitted
         queue = []             # arrived, not yet submitted (indices into arrivals)
         flags = ans.BATCH_SUM if self.keep_sums else 0
+        if self.zero_copy:
+            # windows arrive in page-locked host memory; the kernels read them there
+            pin_src = torch.from_numpy(source.src.view(np.int32)).pin_memory()
+            pin_dst = torch.from_numpy(source.dst.view(np.int32)).pin_memory()
         t0 = time.perf_counter()
 
         def bucket_ids(k):
@@ -237,6 +266,21 @@ class Server:
 
         def submit(slot, ks, offs):
             ctx, st = slot["ctx"], slot["stream"]
+            if self.zero_copy:
+                wins = []
+                for k in ks:
+                    w = int(order[k])
+                    a, b = int(source.offsets[w]), int(source.offsets[w + 1])
+                    wins.append((pin_src.data_ptr() + 4 * a, pin_dst.data_ptr() + 4 * a, b - a))
+                with torch.cuda.stream(st):
+                    _, summ, _ = ctx.batch_submit_windows(wins, flags, out=slot["q_dev"], stream=st,
+                                                          want_ticket=False)
+                    slot["q_host"][: len(ks)].copy_(slot["q_dev"][: len(ks)], non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(st)
+                slot["inflight"] = {"ks": list(ks), "event": ev, "sum": summ, "packets": int(offs[-1]),
+                                    "buckets": bucket_ids(ks[0])}
+                return
             hs, hd = slot["h_src"].numpy().view(np.uint32), slot["h_dst"].numpy().view(np.uint32)
             for j, k in enumerate(ks):
                 w = int(order[k])

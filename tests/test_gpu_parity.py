@@ -475,3 +475,39 @@ def test_import_rejects_non_canonical_dcsr(ans, ctx, case):
     with pytest.raises(ans.AnsError) as ei:
         ctx.import_matrix(r, p, c, v)
     assert ei.value.code == ans.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("where", ["device", "pinned", "mixed"])
+def test_batch_of_scattered_windows(ans, ctx, synth, where):
+    """Windows in their own arrays -- device tensors, pinned host tensors read
+    in place by the kernels, or both in one batch -- give the oracle's
+    matrices, quantities and time sum; unaligned starts and empty windows
+    included."""
+    w = synth.generate(5, sizes=[40000, 0, 8193, 131072, 3, 200001], first_window=77)
+    wins = []
+    for i in range(w.nwin):
+        s, d = w.window(i)
+        pad = i % 3  # start some windows off a 16-byte boundary
+        st = torch.from_numpy(np.concatenate([np.zeros(pad, np.uint32), s]).view(np.int32))[pad:]
+        dt = torch.from_numpy(np.concatenate([np.zeros(pad, np.uint32), d]).view(np.int32))[pad:]
+        on_dev = where == "device" or (where == "mixed" and i % 2 == 0)
+        if on_dev:
+            st, dt = st.cuda(), dt.cuda()
+        else:
+            base_s = torch.zeros(len(s) + pad, dtype=torch.int32).pin_memory()
+            base_d = torch.zeros(len(d) + pad, dtype=torch.int32).pin_memory()
+            base_s[pad:] = st
+            base_d[pad:] = dt
+            st, dt = base_s[pad:], base_d[pad:]
+        wins.append((st, dt))
+    out = torch.zeros((w.nwin, 9), dtype=torch.int64, device="cuda")
+    mats, summ, tk = ctx.batch_submit_windows(wins, ans.BATCH_MATRICES | ans.BATCH_SUM, out=out)
+    ctx.wait(tk)
+    exp_mats, exp_q, exp_sum = oracle.batch(w.src, w.dst, w.offsets, want_sum=True)
+    got_q = ans.quantities_from_tensor(out)
+    for i in range(w.nwin):
+        assert got_q[i] == exp_q[i], f"window {i}"
+        assert_dcsr_equal(mats[i].to_numpy(), exp_mats[i], f"window {i}")
+        mats[i].free()
+    assert_dcsr_equal(summ.to_numpy(), exp_sum, "sum")
+    summ.free()

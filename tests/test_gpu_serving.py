@@ -21,8 +21,8 @@ def _alone(ctx, src, dst):
     return q
 
 
-@pytest.mark.parametrize("slots,budget", [(3, 48 << 30), (2, 3 << 30)])
-def test_alone_equals_mix_and_bucket_sums(slots, budget):
+@pytest.mark.parametrize("slots,budget,zero_copy", [(3, 48 << 30, True), (2, 3 << 30, True), (2, 3 << 30, False)])
+def test_alone_equals_mix_and_bucket_sums(slots, budget, zero_copy):
     from paper_2510_14050_gb300 import ans, serve, synth
     pool = 24
     src = serve.pool_source(pool, seed=3)
@@ -30,7 +30,7 @@ def test_alone_equals_mix_and_bucket_sums(slots, budget):
     arrivals = np.sort(synth.arrivals(4000.0, n, seed=5))
     order = (np.arange(n) * 5) % pool
     srv = serve.Server(device=0, slots=slots, budget_bytes=budget, max_batch_windows=7,
-                       max_batch_packets=1 << 21, bucket_seconds=(0.005, 0.02))
+                       max_batch_packets=1 << 21, bucket_seconds=(0.005, 0.02), zero_copy=zero_copy)
     try:
         stats = srv.serve(src, arrivals, order)
         assert stats.batches >= 2
