@@ -116,6 +116,17 @@ int ans_build_window(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst,
 int ans_sum_windows(ans_ctx* ctx, const ans_matrix* const* mats, size_t k, ans_matrix** out,
                     void* stream);
 
+/* Signed time sum: out = sum_i signs[i] * A_i with signs[i] = +1 or -1 --
+ * the exact update of a sliding time sum (Table I's A_t summed over t) when
+ * windows leave it.  Links whose counts cancel are dropped, so the result is
+ * canonical DCSR again.  Every combined count must be >= 0 (and every
+ * count and partial sum below 2^61): a negative one makes ans_matrix_view /
+ * ans_matrix_quantities of the result return ANS_ERR_INVALID_ARG.  With a -1 sign the call waits for the combination
+ * (the cancelled links are compacted out in a second pass).  Arguments,
+ * ownership and other errors as ans_sum_windows. */
+int ans_combine(ans_ctx* ctx, const ans_matrix* const* mats, const int* signs, size_t k, ans_matrix** out,
+                void* stream);
+
 /* The nine quantities of a matrix (Table I, Sec. IV-C), recomputed on the
  * device from its DCSR arrays: row statistics by segmented reductions over
  * rows, column statistics by a transpose-free pass that sorts the stored links

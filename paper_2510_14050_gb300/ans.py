@@ -45,7 +45,7 @@ EXPORTS = (
     "ans_batch_submit", "ans_wait", "ans_matrix_view", "ans_matrix_quantities", "ans_matrix_free",
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
     "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
-    "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import", "ans_batch_submit_windows",
+    "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import", "ans_batch_submit_windows", "ans_combine",
 )
 
 
@@ -110,6 +110,7 @@ def load(path: str | os.PathLike | None = None):
         "ans_ctx_memory": ([_vp, P(C.c_size_t), P(C.c_size_t)], C.c_int),
         "ans_batch_bytes": ([_vp, P(_u64), C.c_size_t, C.c_uint32, P(C.c_size_t)], C.c_int),
         "ans_matrix_import": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, P(_vp), _vp], C.c_int),
+        "ans_combine": ([_vp, P(_vp), P(C.c_int), C.c_size_t, P(_vp), _vp], C.c_int),
         "ans_batch_submit_windows": ([_vp, P(_vp), P(_vp), P(_u64), C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp),
                                       P(_u64), _vp], C.c_int),
     }
@@ -300,6 +301,17 @@ class Context:
                                            _vp(ptr(row_ptr, np.uint64)), _vp(ptr(col_ids, np.uint32)),
                                            _vp(ptr(vals, np.uint64)), C.byref(out), _vp(_stream(stream))),
                "matrix_import", self._h)
+        return Matrix(out.value)
+
+    def combine(self, mats: Sequence[Matrix], signs: Sequence[int], stream=None) -> Matrix:
+        """sum_i signs[i] * mats[i] (signs +1 / -1); cancelled links are dropped."""
+        arr = (_vp * max(len(mats), 1))(*[m.handle for m in mats])
+        sg = (C.c_int * max(len(signs), 1))(*[int(x) for x in signs])
+        if len(signs) != len(mats):
+            raise ValueError("one sign per matrix")
+        out = _vp()
+        _check(self._lib.ans_combine(self._h, arr, sg, len(mats), C.byref(out), _vp(_stream(stream))),
+               "combine", self._h)
         return Matrix(out.value)
 
     def sum_windows(self, mats: Sequence[Matrix], stream=None) -> Matrix:

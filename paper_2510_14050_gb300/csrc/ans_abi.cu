@@ -504,6 +504,14 @@ int block_fill_cache(Block* b) {
   return ANS_OK;
 }
 
+// The device-side outcome recorded with a block's results.
+int block_status(const Block* b) {
+  if (!b->h_status) return ANS_OK;
+  if (b->h_status == kErrNegative)
+    return fail(ANS_ERR_INVALID_ARG, "a signed combination left a negative count");
+  return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(b->h_status) + ")");
+}
+
 // Everything the statistics phases of one segment set need.
 struct StatsBufs {
   uint32_t* col_ids;
@@ -722,6 +730,9 @@ int sum_prepare(ans_ctx* c, char* m, uint32_t k, const std::vector<uint64_t>& ca
 // array of k MatDesc), written into plan->blk.  Uses scratch laid out by the
 // caller at `m` / `ps` (which must provide vals buffers).  Only queues work
 // on `st` (it may be capturing); on failure the caller discards plan->blk.
+int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s, const uint64_t* fk,
+                   const uint64_t* fv, Block* blk, cudaStream_t st);
+
 int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
                size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st) {
   Block* blk = plan->blk;
@@ -774,6 +785,20 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
     rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
     if (rc != ANS_OK) return rc;
   }
+  return links_to_block(c, m, ps, s, fk, fv, blk, st);
+}
+
+// From sorted (key, value) links (equal keys adjacent) of the single segment
+// of `s` to a DCSR block: value prefix, run-length reduction, values as
+// prefix differences, row statistics and the column pass (the time sum's
+// statistics half).  Only queues work on `st`.
+int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s, const uint64_t* fk,
+                   const uint64_t* fv, Block* blk, cudaStream_t st) {
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets) + 32;
+  auto fail_blk = [&](cudaError_t e, const char* what) {
+    return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e;
   uint64_t* pre = at<uint64_t>(m, ps.pre);
   if ((e = timed(c, "scan_u64", st, [&] { return launch_scan_u64(s, fv, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st); })) !=
       cudaSuccess)
@@ -1297,6 +1322,168 @@ int matrix_stats(ans_ctx* c, const Block* b, uint32_t seg, ans_quantities* q_out
   return copy_quantities_out(q_out, q, 1, st);
 }
 
+// Drop the stored zeros of a signed combination: the links of `blk` (one
+// matrix, at most cap links) are gathered as (key, value), the nonzero ones
+// compacted in order, and the statistics rebuilt into a new block *out.  A
+// negative count sets kErrNegative in the context's error word.
+int drop_zeros(ans_ctx* c, Block* blk, uint64_t cap, cudaStream_t st, Block** out) {
+  *out = nullptr;
+  HostPlan sp;
+  sp.build(std::vector<uint64_t>{cap}, nullptr);
+  Layout L;
+  PipeScratch ps;
+  ps.reserve(L, sp.pad, 1, std::max<uint32_t>(sp.ntiles, 1), true);
+  const size_t off_mats = L.add(sizeof(MatDesc));
+  const size_t off_gplan = L.add(4 * align_up(2 * 8));
+  const size_t off_splan = L.add(4 * kAlign);
+  const size_t off_catoff = L.add(2 * 8);
+  const size_t off_lens = L.add(8);
+  const size_t off_total = L.add(8);
+  const size_t off_count = L.add(8);
+  ANS_TRY(ensure_scratch(c, L.size, st));
+  char* m = (char*)c->scratch;
+  MatDesc md{blk->row_ids, blk->row_ptr, blk->col_ids, blk->vals, blk->hdr};
+  UploadSet us;
+  us.add(m + off_mats, &md, sizeof(MatDesc));
+  SumPlan plan;
+  ANS_TRY(sum_prepare(c, m, 1, std::vector<uint64_t>{cap}, off_gplan, off_splan, off_lens, off_total, us, st, &plan));
+  auto bail = [&](int rc) {
+    block_discard(plan.blk, st);
+    return rc;
+  };
+  int rc = us.flush(c, st);
+  if (rc) return bail(rc);
+  auto cu = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return ANS_OK;
+    return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  uint64_t* ka = at<uint64_t>(m, ps.keys_a);
+  uint64_t* kb = at<uint64_t>(m, ps.keys_b);
+  uint64_t* va = at<uint64_t>(m, ps.vals_a);
+  uint64_t* vb = at<uint64_t>(m, ps.vals_b);
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets) + 32;
+  uint64_t* flags = at<uint64_t>(m, ps.run_start);
+  uint64_t* pos = at<uint64_t>(m, ps.row_pos);
+  uint64_t* count = at<uint64_t>(m, off_count);
+  const uint64_t* cat_off = at<uint64_t>(m, off_catoff);
+  const SegPlan& s = plan.s;
+  if ((rc = cu(launch_count_prefix(at<MatDesc>(m, off_mats), 1, at<uint64_t>(m, off_catoff),
+                                   at<uint64_t>(m, off_lens), at<uint64_t>(m, off_total), st), "count")) ||
+      (rc = cu(launch_zero(m + ps.lb, (size_t)sp.ntiles * 8, st), "zero")) ||
+      (rc = cu(launch_zero(m + ps.lb2, (size_t)sp.ntiles * 8, st), "zero")) ||
+      (rc = cu(launch_zero(m + ps.col_hist, kColPasses * kRadix * 4, st), "zero")) ||
+      (rc = cu(launch_gather(plan.g, at<MatDesc>(m, off_mats), cat_off, ka, va, nullptr, at<uint64_t>(m, ps.st0),
+                             tickets, st), "gather")) ||
+      (rc = cu(launch_nonzero_flags(s, va, flags, c->d_err, st), "flags")) ||
+      (rc = cu(launch_scan_u64(s, flags, pos, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st),
+               "scan")) ||
+      (rc = cu(launch_scatter_nonzero(s, ka, va, pos, kb, vb, count, st), "scatter")) ||
+      // the statistics scan reuses this look-back array and ticket
+      (rc = cu(launch_zero(m + ps.lb2, (size_t)sp.ntiles * 8, st), "zero")) ||
+      (rc = cu(launch_zero(tickets + kPasses + 1, 4, st), "zero")))
+    return bail(rc);
+  SegPlan s2 = s;
+  s2.len = count;
+  if ((rc = links_to_block(c, m, ps, s2, kb, vb, plan.blk, st))) return bail(rc);
+  *out = plan.blk;
+  return ANS_OK;
+}
+
+// Sum of k matrices, each with sign +1 or -1 (signs null: all +1), into a
+// new matrix *out (the body of ans_sum_windows and ans_combine).
+int combine_matrices(ans_ctx* c, const ans_matrix* const* mats, const int* signs, size_t k, ans_matrix** out,
+                     cudaStream_t st) {
+  if (!c || !out || (k && !mats)) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  std::vector<uint64_t> caps;
+  std::vector<MatDesc> md;
+  uint64_t total_cap = 0;
+  bool any_neg = false;
+  for (size_t i = 0; i < k; ++i) {
+    const ans_matrix* x = mats[i];
+    if (!x) return fail(ANS_ERR_INVALID_ARG, "NULL matrix");
+    const Block* b = x->blk;
+    if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
+    const uint64_t bs = b->base[x->seg];
+    const bool neg = signs && signs[i] < 0;
+    any_neg = any_neg || neg;
+    md.push_back({b->row_ids + bs, b->row_ptr + bs + x->seg, b->col_ids + bs, b->vals + bs, b->hdr + 2 * x->seg,
+                  neg ? 1ull : 0ull});
+    // An input that has already been computed contributes its actual link
+    // count to the output's capacity; one still running contributes its bound.
+    uint64_t cap = b->cap[x->seg];
+    if (cudaEventQuery(b->done) == cudaSuccess) {
+      ANS_TRY(block_fill_cache(const_cast<Block*>(b)));
+      cap = std::min<uint64_t>(cap, b->h_hdr[2 * (size_t)x->seg + 1]);
+    } else {
+      cudaGetLastError();
+    }
+    caps.push_back(cap);
+    total_cap += cap;
+    ANS_CUDA(cudaStreamWaitEvent(st, b->done, 0));
+  }
+  if (total_cap > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a time sum is limited to 2^31 - 1 links");
+  Block* sblk = nullptr;
+  if (k == 0 || total_cap == 0) {
+    ANS_TRY(make_block(c, 0, 1, {0}, {0}, st, &sblk));
+    ANS_CUDA(cudaMemsetAsync(sblk->row_ptr, 0, 8, st));
+    ANS_CUDA(cudaMemsetAsync(sblk->hdr, 0, 16, st));
+    ANS_CUDA(cudaMemsetAsync(sblk->q, 0, sizeof(ans_quantities), st));
+    ANS_CUDA(cudaMemsetAsync(sblk->status, 0, 4, st));
+  } else {
+    HostPlan sp;
+    sp.build(std::vector<uint64_t>{total_cap}, nullptr);
+    HostPlan gp;
+    gp.build(caps, nullptr);
+    Layout L;
+    PipeScratch ps;
+    ps.reserve(L, sp.pad, 1, std::max(sp.ntiles, gp.ntiles), true);
+    const size_t off_mats = L.add(k * sizeof(MatDesc));
+    const size_t off_gplan = L.add(4 * align_up((k + 1) * 8));
+    const size_t off_splan = L.add(4 * kAlign);
+    const size_t off_catoff = L.add((k + 1) * 8);
+    const size_t off_lens = L.add(k * 8);
+    const size_t off_total = L.add(8);
+    ANS_TRY(ensure_scratch(c, L.size, st));
+    char* m = (char*)c->scratch;
+    UploadSet us;
+    us.add(m + off_mats, md.data(), k * sizeof(MatDesc));
+    SumPlan sump;
+    ANS_TRY(sum_prepare(c, m, (uint32_t)k, caps, off_gplan, off_splan, off_lens, off_total, us, st, &sump));
+    int rc = us.flush(c, st);
+    if (rc) {
+      block_discard(sump.blk, st);
+      return rc;
+    }
+    rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, &sump, off_catoff, off_lens, off_total, st);
+    if (rc) {
+      block_discard(sump.blk, st);
+      return rc;
+    }
+    sblk = sump.blk;
+    if (any_neg) {  // cancelled links are stored as zeros: compact them away
+      Block* clean = nullptr;
+      rc = drop_zeros(c, sblk, total_cap, st, &clean);
+      block_discard(sblk, st);
+      if (rc) return rc;
+      sblk = clean;
+    }
+    rc = capture_err(c, sblk->status, st);
+    if (rc == ANS_OK) rc = reset_err(c, st);
+    if (rc) {
+      block_discard(sblk, st);
+      return rc;
+    }
+  }
+  for (size_t i = 0; i < k; ++i) ANS_TRY(note_read(mats[i]->blk, st));
+  ANS_CUDA(cudaEventRecord(sblk->done, st));
+  sblk->refs = 1;
+  *out = new ans_matrix{sblk, 0};
+  return ANS_OK;
+}
+
 }  // namespace
 
 // =========================================================================
@@ -1474,85 +1661,15 @@ int ans_batch_submit_windows(ans_ctx* c, const uint32_t* const* srcs, const uint
 }
 
 int ans_sum_windows(ans_ctx* c, const ans_matrix* const* mats, size_t k, ans_matrix** out, void* stream) {
-  if (!c || !out || (k && !mats)) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
-  *out = nullptr;
-  cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> g(c->mu);
-  DeviceGuard dg(c->device);
-  std::vector<uint64_t> caps;
-  std::vector<MatDesc> md;
-  uint64_t total_cap = 0;
-  for (size_t i = 0; i < k; ++i) {
-    const ans_matrix* x = mats[i];
-    if (!x) return fail(ANS_ERR_INVALID_ARG, "NULL matrix");
-    const Block* b = x->blk;
-    if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
-    const uint64_t bs = b->base[x->seg];
-    md.push_back({b->row_ids + bs, b->row_ptr + bs + x->seg, b->col_ids + bs, b->vals + bs, b->hdr + 2 * x->seg});
-    // An input that has already been computed contributes its actual link
-    // count to the output's capacity; one still running contributes its bound.
-    uint64_t cap = b->cap[x->seg];
-    if (cudaEventQuery(b->done) == cudaSuccess) {
-      ANS_TRY(block_fill_cache(const_cast<Block*>(b)));
-      cap = std::min<uint64_t>(cap, b->h_hdr[2 * (size_t)x->seg + 1]);
-    } else {
-      cudaGetLastError();
-    }
-    caps.push_back(cap);
-    total_cap += cap;
-    ANS_CUDA(cudaStreamWaitEvent(st, b->done, 0));
-  }
-  if (total_cap > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a time sum is limited to 2^31 - 1 links");
-  Block* sblk = nullptr;
-  if (k == 0 || total_cap == 0) {
-    ANS_TRY(make_block(c, 0, 1, {0}, {0}, st, &sblk));
-    ANS_CUDA(cudaMemsetAsync(sblk->row_ptr, 0, 8, st));
-    ANS_CUDA(cudaMemsetAsync(sblk->hdr, 0, 16, st));
-    ANS_CUDA(cudaMemsetAsync(sblk->q, 0, sizeof(ans_quantities), st));
-    ANS_CUDA(cudaMemsetAsync(sblk->status, 0, 4, st));
-  } else {
-    HostPlan sp;
-    sp.build(std::vector<uint64_t>{total_cap}, nullptr);
-    HostPlan gp;
-    gp.build(caps, nullptr);
-    Layout L;
-    PipeScratch ps;
-    ps.reserve(L, sp.pad, 1, std::max(sp.ntiles, gp.ntiles), true);
-    const size_t off_mats = L.add(k * sizeof(MatDesc));
-    const size_t off_gplan = L.add(4 * align_up((k + 1) * 8));
-    const size_t off_splan = L.add(4 * kAlign);
-    const size_t off_catoff = L.add((k + 1) * 8);
-    const size_t off_lens = L.add(k * 8);
-    const size_t off_total = L.add(8);
-    ANS_TRY(ensure_scratch(c, L.size, st));
-    char* m = (char*)c->scratch;
-    UploadSet us;
-    us.add(m + off_mats, md.data(), k * sizeof(MatDesc));
-    SumPlan sump;
-    ANS_TRY(sum_prepare(c, m, (uint32_t)k, caps, off_gplan, off_splan, off_lens, off_total, us, st, &sump));
-    int rc = us.flush(c, st);
-    if (rc) {
-      block_discard(sump.blk, st);
-      return rc;
-    }
-    rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), (uint32_t)k, &sump, off_catoff, off_lens, off_total, st);
-    if (rc) {
-      block_discard(sump.blk, st);
-      return rc;
-    }
-    sblk = sump.blk;
-    rc = capture_err(c, sblk->status, st);
-    if (rc == ANS_OK) rc = reset_err(c, st);
-    if (rc) {
-      block_discard(sblk, st);
-      return rc;
-    }
-  }
-  for (size_t i = 0; i < k; ++i) ANS_TRY(note_read(mats[i]->blk, st));
-  ANS_CUDA(cudaEventRecord(sblk->done, st));
-  sblk->refs = 1;
-  *out = new ans_matrix{sblk, 0};
-  return ANS_OK;
+  return combine_matrices(c, mats, nullptr, k, out, (cudaStream_t)stream);
+}
+
+int ans_combine(ans_ctx* c, const ans_matrix* const* mats, const int* signs, size_t k, ans_matrix** out,
+                void* stream) {
+  if (k && !signs) return fail(ANS_ERR_INVALID_ARG, "NULL signs");
+  for (size_t i = 0; i < k; ++i)
+    if (signs[i] != 1 && signs[i] != -1) return fail(ANS_ERR_INVALID_ARG, "signs must be +1 or -1");
+  return combine_matrices(c, mats, signs, k, out, (cudaStream_t)stream);
 }
 
 int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out, void* stream) {
@@ -1659,7 +1776,7 @@ int ans_matrix_view(const ans_matrix* x, uint64_t* nrows, uint64_t* nnz, const u
   if (!x) return fail(ANS_ERR_INVALID_ARG, "NULL matrix");
   Block* b = x->blk;
   ANS_TRY(block_fill_cache(b));
-  if (b->h_status) return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(b->h_status) + ")");
+  ANS_TRY(block_status(b));
   const uint64_t bs = b->base[x->seg];
   if (nrows) *nrows = b->h_hdr[2 * x->seg];
   if (nnz) *nnz = b->h_hdr[2 * x->seg + 1];
@@ -1674,7 +1791,7 @@ int ans_matrix_quantities(const ans_matrix* x, ans_quantities* out) {
   if (!x || !out) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
   Block* b = x->blk;
   ANS_TRY(block_fill_cache(b));
-  if (b->h_status) return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(b->h_status) + ")");
+  ANS_TRY(block_status(b));
   *out = b->h_q[x->seg];
   return ANS_OK;
 }

@@ -39,6 +39,7 @@ constexpr uint32_t kSpinLimit = 1u << 20;      // polls (about 1 s) before a wai
 enum ErrBits : uint32_t {
   kErrLookback = 1u,   // a look-back wait hit kSpinLimit
   kErrHashFull = 2u,   // a hash probe sequence found no free slot
+  kErrNegative = 4u,   // a signed combination left a negative count
 };
 
 // How a onesweep pass is launched (chosen per context by the autotuner):
@@ -125,6 +126,7 @@ struct MatDesc {
   const uint32_t* col_ids;
   const uint64_t* vals;
   const uint64_t* hdr;  // {nrows, nnz}
+  uint64_t neg = 0;     // 1: the matrix enters a combination with sign -1 (values negated mod 2^64)
 };
 
 // Record `msg` as the calling thread's ans_last_error() text; returns code.
@@ -196,10 +198,19 @@ cudaError_t launch_merge(const uint64_t* cat_off, uint32_t k, uint64_t total_cap
                          const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st);
 
 // ---- launchers (ans_stats.cu) --------------------------------------------
+// Signed combinations: flags[u] = (vals[u] != 0) over the single segment of
+// p (a value of 2^61 or more, a negative count, sets kErrNegative), then the
+// nonzero (key, value) pairs moved to kout/vout at their exclusive flag
+// prefix pos[u], their number to *count.
+cudaError_t launch_nonzero_flags(const SegPlan& p, const uint64_t* vals, uint64_t* flags, uint32_t* err,
+                                 cudaStream_t st);
+cudaError_t launch_scatter_nonzero(const SegPlan& p, const uint64_t* kin, const uint64_t* vin, const uint64_t* pos,
+                                   uint64_t* kout, uint64_t* vout, uint64_t* count, cudaStream_t st);
 // Run-length reduce sorted keys into DCSR structure (col_ids, row_ids,
 // row_ptr) plus run/row start positions; writes hdr.
 cudaError_t launch_rle(const StatsArgs& a, cudaStream_t st);
-// Exclusive prefix of uint64 values per segment (len + 1 entries at base+s).
+// Exclusive prefix of uint64 values per segment (len + 1 entries at base+s),
+// mod 2^62.
 cudaError_t launch_scan_u64(const SegPlan& p, const uint64_t* in, uint64_t* out,
                             uint64_t* lookback, uint32_t* ticket, uint32_t* err, cudaStream_t st);
 // Values, row statistics, link maximum, and the destination digit histograms

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* _
       }
       key = ((uint64_t)s_ri[lo] << 32) | m.col_ids[tl.start + i];
       keys[o + i] = key;
-      vals[o + i] = m.vals[tl.start + i];
+      vals[o + i] = m.neg ? 0ull - m.vals[tl.start + i] : m.vals[tl.start + i];
     }
     if (sum_hist) hist_add(h, key, valid, vmask);
   }

@@ -142,6 +142,10 @@ __global__ void __launch_bounds__(kThreads) k_rle(StatsArgs a) {
   }
 }
 
+// Prefixes are kept mod 2^62 (the width of a look-back status value), and
+// every difference of two of them is reduced mod 2^62: exact for any sum of
+// counts below 2^62, and for signed combinations whose results are
+// nonnegative and below 2^61.
 __global__ void __launch_bounds__(kThreads) k_scan_u64(SegPlan p, const uint64_t* __restrict__ in,
                                                        uint64_t* __restrict__ out, uint64_t* lookback_st,
                                                        uint32_t* ticket, uint32_t* err) {
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_u64(SegPlan p, const uint64_t
     }
     if (lane == 0) {
       s_excl = excl;
-      if (tl.start + tl.count == tl.len) out[bs + tl.len] = excl + tot;
+      if (tl.start + tl.count == tl.len) out[bs + tl.len] = (excl + tot) & kValMask;
     }
   }
   __syncthreads();
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_u64(SegPlan p, const uint64_t
 #pragma unroll
   for (int i = 0; i < kPerThread; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
-    if (idx < tl.count) out[bs + tl.start + idx] = off + ex[i];
+    if (idx < tl.count) out[bs + tl.start + idx] = (off + ex[i]) & kValMask;
   }
 }
 
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
     if (kMode == kModeMatrix) {
       v = a.vals[tl.base + u];
     } else {
-      v = P(a.run_start[bs + u + 1]) - P(a.run_start[bs + u]);
+      v = (P(a.run_start[bs + u + 1]) - P(a.run_start[bs + u])) & kValMask;
       a.vals[tl.base + u] = v;
       if (a.vals32) a.vals32[tl.base + u] = (uint32_t)v;
     }
@@ -248,7 +252,8 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
   for (uint64_t r = tl.start + threadIdx.x; r < r_end; r += kThreads) {
     const uint64_t p0 = a.row_ptr[bs + r], p1 = a.row_ptr[bs + r + 1];
     const uint64_t fan = p1 - p0;
-    const uint64_t rs = kMode == kModeMatrix ? P(p1) - P(p0) : P(a.row_pos[bs + r + 1]) - P(a.row_pos[bs + r]);
+    const uint64_t rs = (kMode == kModeMatrix ? P(p1) - P(p0) : P(a.row_pos[bs + r + 1]) - P(a.row_pos[bs + r])) &
+                        kValMask;
     mfan = fan > mfan ? fan : mfan;
     mrow = rs > mrow ? rs : mrow;
   }
@@ -561,7 +566,49 @@ __global__ void k_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* __res
   if (f) atomicOr(bad, f);
 }
 
+__global__ void k_nonzero_flags(SegPlan p, const uint64_t* __restrict__ vals, uint64_t* __restrict__ flags,
+                                uint32_t* err) {
+  const uint64_t n = p.len[0];
+  uint32_t bad = 0;
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = vals[p.base[0] + u];
+    flags[p.base[0] + u] = v != 0 ? 1ull : 0ull;
+    if (v >> 61) bad = 1;  // prefixes run mod 2^62: a negative count lands at or above 2^61
+  }
+  if (bad) atomicOr(err, (uint32_t)kErrNegative);
+}
+
+__global__ void k_scatter_nonzero(SegPlan p, const uint64_t* __restrict__ kin, const uint64_t* __restrict__ vin,
+                                  const uint64_t* __restrict__ pos, uint64_t* __restrict__ kout,
+                                  uint64_t* __restrict__ vout, uint64_t* count) {
+  const uint64_t n = p.len[0];
+  const uint64_t b = p.base[0];  // pos is an exclusive prefix at base + seg (seg 0)
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = pos[b + n];
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = vin[b + u];
+    if (v != 0) {
+      const uint64_t o = pos[b + u];
+      kout[b + o] = kin[b + u];
+      vout[b + o] = v;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_nonzero_flags(const SegPlan& p, const uint64_t* vals, uint64_t* flags, uint32_t* err,
+                                 cudaStream_t st) {
+  const unsigned blocks = p.ntiles ? (p.ntiles * 16u > 4096u ? 4096u : p.ntiles * 16u) : 1u;
+  k_nonzero_flags<<<blocks, 512, 0, st>>>(p, vals, flags, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_nonzero(const SegPlan& p, const uint64_t* kin, const uint64_t* vin, const uint64_t* pos,
+                                   uint64_t* kout, uint64_t* vout, uint64_t* count, cudaStream_t st) {
+  const unsigned blocks = p.ntiles ? (p.ntiles * 16u > 4096u ? 4096u : p.ntiles * 16u) : 1u;
+  k_scatter_nonzero<<<blocks, 512, 0, st>>>(p, kin, vin, pos, kout, vout, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* row_ids, const uint64_t* row_ptr,
                               const uint32_t* col_ids, const uint64_t* vals, uint32_t* bad, cudaStream_t st) {

@@ -511,3 +511,36 @@ def test_batch_of_scattered_windows(ans, ctx, synth, where):
         mats[i].free()
     assert_dcsr_equal(summ.to_numpy(), exp_sum, "sum")
     summ.free()
+
+
+def test_signed_combination_subtracts_exactly(ans, ctx, synth):
+    """A sliding-sum update: (A + B + C) - B = A + C exactly, with the links
+    only B had dropped rather than stored as zeros; all-positive signs equal
+    ans_sum_windows; a count driven negative is reported."""
+    w = synth.generate(2, nwin=3, first_window=300)
+    ms = [ctx.build_window(dev(w.window(i)[0]), dev(w.window(i)[1]), int(w.offsets[i + 1] - w.offsets[i]))
+          for i in range(3)]
+    exp = [oracle.traffic_matrix(*w.window(i)) for i in range(3)]
+    total = ctx.combine(ms, [1, 1, 1])
+    assert_dcsr_equal(total.to_numpy(), oracle.sum_matrices(exp), "sum")
+    same = ctx.sum_windows(ms)
+    assert_dcsr_equal(same.to_numpy(), oracle.sum_matrices(exp), "sum_windows")
+    slid = ctx.combine([total, ms[1]], [1, -1])
+    want = oracle.sum_matrices([exp[0], exp[2]])
+    assert_dcsr_equal(slid.to_numpy(), want, "after subtraction")
+    assert slid.quantities() == oracle.network_quantities(want)
+    assert ctx.network_quantities(slid) == oracle.network_quantities(want)
+    # everything leaves: the empty matrix
+    gone = ctx.combine([slid, ms[0], ms[2]], [1, -1, -1])
+    assert gone.view()[:2] == (0, 0)
+    assert gone.quantities() == dict.fromkeys(oracle.QUANTITY_NAMES, 0)
+    # more taken out than was in
+    bad = ctx.combine([ms[0], ms[1]], [1, -1])
+    with pytest.raises(ans.AnsError) as ei:
+        bad.quantities()
+    assert ei.value.code == ans.ERR_INVALID_ARG
+    for m in ms + [total, same, slid, gone, bad]:
+        m.free()
+    with pytest.raises(ans.AnsError) as ei:
+        ctx.combine([ctx.build_window(dev([1]), dev([2]), 1)], [0])
+    assert ei.value.code == ans.ERR_INVALID_ARG
