@@ -17,8 +17,13 @@ they are staged into a slot's pinned buffer and copied.
 
 Running time sums (Table I: A_t summed over t) are kept resident on the
 device per tumbling bucket of the arrival clock (``bucket_seconds``, e.g. one
-minute and one hour).  A worker thread owns them: each bucket holds a few
-partial sums of geometrically growing size, and a completed batch's sum is
+minute and one hour), and optionally as sliding sums (``sliding``: horizon
+and step in seconds): the sum over the newest horizon/step sub-buckets, kept
+exact by adding each completed sub-bucket and subtracting the ones that leave
+the horizon (``ans_combine``).  ``checkpoint()`` / ``restore()`` save and
+reload every resident sum as DCSR arrays (``ans_matrix_import``).  A worker
+thread owns them: each bucket holds a few partial sums of geometrically
+growing size, and a completed batch's sum is
 merged (``ans_sum_windows``) with the newest partial while they are of similar
 size, so the resident set stays small and each link is re-merged O(log n)
 times.  The worker waits for each merge before the next one, so every output
@@ -76,15 +81,21 @@ class ServeStats:
 
 
 class SumKeeper:
-    """Resident tumbling time sums, maintained by a worker thread."""
+    """Resident time sums, maintained by a worker thread: tumbling buckets
+    per level, and sliding sums over the newest n sub-buckets of a level
+    (``sliding``: {level: n}), kept exact by subtracting the sub-buckets that
+    leave the horizon (``ans_combine``)."""
 
-    def __init__(self, device: int, budget_bytes: int):
+    def __init__(self, device: int, budget_bytes: int, sliding=None):
         import torch
         self.torch = torch
         self.device = device
         self.ctx = ans.Context(device, budget_bytes=budget_bytes)
         self.stream = torch.cuda.Stream(device=device)
         self.buckets = {}      # (level, index) -> [(nnz, Matrix)], newest last
+        # sliding level -> {"n": sub-buckets per horizon, "cur": newest sub-bucket,
+        # "base": sum of the horizon's complete sub-buckets [cur - n + 1, cur - 1]}
+        self.slide = {lv: {"n": int(n), "cur": None, "base": None} for lv, n in (sliding or {}).items()}
         self.lock = threading.Lock()
         self.q = _queue.Queue()
         self.error = None
@@ -118,7 +129,7 @@ class SumKeeper:
                     handles = [mat] + [mat.retain() for _ in keys[1:]]
                     for level, (idx, h) in enumerate(zip(keys, handles)):
                         groups.setdefault((level, idx), []).append(h)
-                for key, mats in groups.items():
+                for key, mats in sorted(groups.items()):
                     if len(mats) > 1:
                         merged = self.ctx.sum_windows(mats, stream=self.stream)
                         for m in mats:
@@ -126,6 +137,8 @@ class SumKeeper:
                         self.stream.synchronize()
                         mats = [merged]
                     self._insert(key, mats[0])
+                    if key[0] in self.slide:
+                        self._advance(key[0], key[1])
             except Exception as e:  # surfaced by drain()
                 self.error = e
             finally:
@@ -146,6 +159,117 @@ class SumKeeper:
                 self.stream.synchronize()
                 parts[-2:] = [(merged.nnz, merged)]
 
+    def _merged(self, key):
+        """The bucket's partials merged into one matrix (kept as its only partial)."""
+        parts = self.buckets.get(key)
+        if not parts:
+            return None
+        if len(parts) > 1:
+            mats = [m for _, m in parts]
+            merged = self.ctx.sum_windows(mats, stream=self.stream)
+            for m in mats:
+                m.free()
+            self.stream.synchronize()
+            parts[:] = [(merged.nnz, merged)]
+        return parts[0][1]
+
+    def _advance(self, level, idx):
+        """Sub-bucket idx of a sliding level received data: once it is newer
+        than the current one, fold the completed sub-buckets into the base and
+        take out the ones that left the horizon."""
+        st = self.slide[level]
+        with self.lock:
+            if st["cur"] is None:
+                st["cur"] = idx
+                return
+            if idx <= st["cur"]:
+                return
+            n, cur = st["n"], st["cur"]
+            lo_new = idx - n + 1  # oldest sub-bucket of the new horizon
+            mats, signs = [], []
+            for j in range(max(cur, lo_new), idx):  # completed and still inside
+                m = self._merged((level, j))
+                if m is not None:
+                    mats.append(m)
+                    signs.append(1)
+            for j in range(cur - n + 1, min(cur, lo_new)):  # in the base, now outside
+                m = self._merged((level, j))
+                if m is not None:
+                    mats.append(m)
+                    signs.append(-1)
+            if mats:
+                if st["base"] is not None:
+                    mats.insert(0, st["base"])
+                    signs.insert(0, 1)
+                new_base = self.ctx.combine(mats, signs, stream=self.stream)
+                self.stream.synchronize()
+                if st["base"] is not None:
+                    st["base"].free()
+                st["base"] = new_base
+            for j in [k[1] for k in list(self.buckets) if k[0] == level and k[1] < lo_new]:
+                for _, m in self.buckets.pop((level, j)):  # sub-buckets that left: no longer needed
+                    m.free()
+            st["cur"] = idx
+
+    def sliding_sum(self, level):
+        """Sum of the windows in the newest n sub-buckets of a sliding level
+        (None if it has none)."""
+        self.drain()
+        st = self.slide[level]
+        with self.lock:
+            if st["cur"] is None:
+                return None
+            cur = self._merged((level, st["cur"]))
+            mats = [m for m in (st["base"], cur) if m is not None]
+            if len(mats) == 1:
+                return mats[0].retain()
+            out = self.ctx.sum_windows(mats, stream=self.stream)
+            self.stream.synchronize()
+            return out
+
+    def checkpoint(self, path):
+        """Save every resident sum (bucket sums, sliding bases and their
+        state) to `path` (.npz) as DCSR arrays."""
+        import json
+        self.drain()
+        arrays, meta = {}, {"buckets": [], "slide": {}}
+        with self.lock:
+            for i, key in enumerate(sorted(self.buckets)):
+                m = self._merged(key)
+                for name, a in zip(("row_ids", "row_ptr", "col_ids", "vals"), m.to_numpy()):
+                    arrays[f"b{i}_{name}"] = a
+                meta["buckets"].append([int(key[0]), int(key[1])])
+            for lv, st in self.slide.items():
+                meta["slide"][str(lv)] = {"n": st["n"], "cur": st["cur"], "base": st["base"] is not None}
+                if st["base"] is not None:
+                    for name, a in zip(("row_ids", "row_ptr", "col_ids", "vals"), st["base"].to_numpy()):
+                        arrays[f"s{lv}_{name}"] = a
+        np.savez(path, meta=np.frombuffer(json.dumps(meta).encode(), dtype=np.uint8), **arrays)
+
+    def restore(self, path):
+        """Replace the resident sums by the ones saved by checkpoint()."""
+        import json
+        self.drain()
+        z = np.load(path)
+        meta = json.loads(bytes(z["meta"]).decode())
+        with self.lock:
+            for parts in self.buckets.values():
+                for _, m in parts:
+                    m.free()
+            self.buckets = {}
+            for i, (lv, idx) in enumerate(meta["buckets"]):
+                m = self.ctx.import_matrix(*(z[f"b{i}_{n}"] for n in ("row_ids", "row_ptr", "col_ids", "vals")))
+                self.buckets[(lv, idx)] = [(m.nnz, m)]
+            for lv_s, st in meta["slide"].items():
+                lv = int(lv_s)
+                old = self.slide.get(lv, {}).get("base")
+                if old is not None:
+                    old.free()
+                base = None
+                if st["base"]:
+                    base = self.ctx.import_matrix(*(z[f"s{lv}_{n}"] for n in ("row_ids", "row_ptr", "col_ids", "vals")))
+                self.slide[lv] = {"n": st["n"], "cur": st["cur"], "base": base}
+
     def drain(self):
         self.q.join()
         if self.error is not None:
@@ -154,17 +278,7 @@ class SumKeeper:
     def bucket_sum(self, key):
         self.drain()
         with self.lock:
-            parts = self.buckets.get(key)
-            if not parts:
-                return None
-            mats = [m for _, m in parts]
-            merged = self.ctx.sum_windows(mats, stream=self.stream) if len(mats) > 1 else mats[0]
-            if len(mats) > 1:
-                for m in mats:
-                    m.free()
-            self.stream.synchronize()
-            parts[:] = [(merged.nnz, merged)]
-            return merged
+            return self._merged(key)
 
     def memory(self) -> int:
         return self.ctx.memory()[0]
@@ -176,19 +290,28 @@ class SumKeeper:
             for _, m in parts:
                 m.free()
         self.buckets = {}
+        for st in self.slide.values():
+            if st["base"] is not None:
+                st["base"].free()
+                st["base"] = None
         self.ctx.close()
 
 
 class Server:
     def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int = 64 << 30,
                  max_batch_windows: int = 256, max_batch_packets: int = 1 << 24,
-                 bucket_seconds=(60.0, 3600.0), keep_sums: bool = True, zero_copy: bool = True):
+                 bucket_seconds=(60.0, 3600.0), keep_sums: bool = True, zero_copy: bool = True,
+                 sliding=()):
         import torch
         self.torch = torch
         self.device = device
         self.max_batch_windows = max_batch_windows
         self.max_batch_packets = max_batch_packets
         self.bucket_seconds = tuple(bucket_seconds)
+        # sliding horizons (seconds, step): each adds a level of tumbling
+        # sub-buckets of `step` seconds, summed over the newest horizon/step
+        self.sliding = tuple((float(h), float(g)) for h, g in sliding)
+        self.level_seconds = self.bucket_seconds + tuple(g for _, g in self.sliding)
         self.keep_sums = keep_sums
         self.zero_copy = zero_copy
         self.budget = budget_bytes
@@ -206,11 +329,26 @@ class Server:
                 "q_host": torch.empty((max_batch_windows, 9), dtype=torch.int64).pin_memory(),
                 "inflight": None,
             })
-        self.sums = SumKeeper(device, budget_bytes) if keep_sums else None
+        nb = len(self.bucket_seconds)
+        slide = {nb + i: max(1, int(round(h / g))) for i, (h, g) in enumerate(self.sliding)}
+        self.sums = SumKeeper(device, budget_bytes, slide) if keep_sums else None
 
     def live_bytes(self) -> int:
         """Device bytes held by all of the server's contexts."""
         return sum(s["ctx"].memory()[0] for s in self.slots) + (self.sums.memory() if self.sums else 0)
+
+    def sliding_sum(self, i: int = 0):
+        """The time sum of every served window that arrived in the newest
+        horizon/step sub-buckets of sliding horizon i (None if none)."""
+        return self.sums.sliding_sum(len(self.bucket_seconds) + i) if self.sums else None
+
+    def checkpoint(self, path):
+        """Save the resident sums (tumbling buckets, sliding bases) to a file."""
+        self.sums.checkpoint(path)
+
+    def restore(self, path):
+        """Load resident sums saved by checkpoint() (replacing the current ones)."""
+        self.sums.restore(path)
 
     def bucket_sum(self, level: int, idx: int):
         """One matrix: the time sum of every served window whose arrival falls
@@ -243,7 +381,7 @@ class Server:
         t0 = time.perf_counter()
 
         def bucket_ids(k):
-            return tuple(int(arrivals[k] // w) for w in self.bucket_seconds)
+            return tuple(int(arrivals[k] // w) for w in self.level_seconds)
 
         def complete(slot):
             nonlocal packets

@@ -92,3 +92,55 @@ def test_small_budget_stalls_admission_but_stays_exact():
             assert dict(zip(oracle.QUANTITY_NAMES, (int(v) for v in stats.quantities[k]))) == exp
     finally:
         srv.close()
+
+
+def test_sliding_sum_and_checkpoint_restore(tmp_path):
+    """A 40 ms sliding sum in 10 ms steps equals the oracle's sum of the
+    windows whose step lies in the newest four steps (the older ones were
+    added and later subtracted); the resident sums survive a checkpoint and a
+    restore into a fresh server bit for bit."""
+    from paper_2510_14050_gb300 import serve, synth
+    pool = 16
+    src = serve.pool_source(pool, seed=11)
+    n = 60
+    arrivals = np.sort(synth.arrivals(500.0, n, seed=13))  # about 0.12 s of arrivals
+    order = (np.arange(n) * 3) % pool
+    step, horizon = 0.01, 0.04
+    kw = dict(device=0, slots=2, budget_bytes=48 << 30, max_batch_windows=5, max_batch_packets=1 << 21,
+              bucket_seconds=(0.05,), sliding=((horizon, step),))
+    srv = serve.Server(**kw)
+    try:
+        stats = srv.serve(src, arrivals, order)
+        assert stats.batches >= 4
+        sub = (arrivals // step).astype(int)
+        last = sub.max()
+        ks = np.nonzero(sub > last - int(round(horizon / step)))[0]
+        mats = []
+        for k in ks:
+            w = int(order[k])
+            a, b = int(src.offsets[w]), int(src.offsets[w + 1])
+            mats.append(oracle.traffic_matrix(src.src[a:b], src.dst[a:b]))
+        exp = oracle.sum_matrices(mats)
+        got = srv.sliding_sum(0)
+        for x, y in zip(got.to_numpy(), exp):
+            assert np.array_equal(x, y)
+        assert got.quantities() == oracle.network_quantities(exp)
+        got.free()
+        ids = (arrivals // 0.05).astype(int)
+        before = {int(i): [a.copy() for a in srv.bucket_sum(0, int(i)).to_numpy()] for i in np.unique(ids)}
+        path = tmp_path / "sums.npz"
+        srv.checkpoint(str(path))
+    finally:
+        srv.close()
+    again = serve.Server(**kw)
+    try:
+        again.restore(str(path))
+        for i, arrays in before.items():
+            for x, y in zip(again.bucket_sum(0, i).to_numpy(), arrays):
+                assert np.array_equal(x, y)
+        got = again.sliding_sum(0)
+        for x, y in zip(got.to_numpy(), exp):
+            assert np.array_equal(x, y)
+        got.free()
+    finally:
+        again.close()
