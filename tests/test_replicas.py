@@ -62,3 +62,50 @@ def test_single_process_helpers():
     assert replicas.job_rate(400.0, 2.0) == 200.0
     assert replicas.sum_over_ranks(3.0) == 3.0
     assert replicas.first_window(0, 64) == 0 and replicas.first_window(3, 64) == 192
+
+
+def _exchange_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2510_14050_gb300 import replicas, synth
+        w = synth.generate(5, nwin=3, first_window=replicas.first_window(rank, 3))
+        partial = oracle.sum_matrices([oracle.traffic_matrix(*w.window(i)) for i in range(w.nwin)])
+        parts = replicas.partition_links(*partial, world)
+        pieces = replicas.exchange_links(parts, dist)
+        owned = oracle.sum_matrices([oracle.DCSR(*replicas.keys_to_dcsr(k, v)) for k, v in pieces])
+        out[rank] = tuple(a.tolist() for a in owned)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_exchange_their_time_sums():
+    """The one exchange step of a multi-rank time sum: links go to the owner
+    of their row; the owners' matrices are the row partition of the global
+    sum (checked against the oracle's sum of both ranks' windows)."""
+    import oracle
+    from paper_2510_14050_gb300 import replicas, synth
+    world = 2
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_exchange_main, args=(world, port, out), nprocs=world, join=True)
+        res = {r: tuple(np.asarray(a) for a in out[r]) for r in range(world)}
+    mats = []
+    for r in range(world):
+        w = synth.generate(5, nwin=3, first_window=replicas.first_window(r, 3))
+        mats += [oracle.traffic_matrix(*w.window(i)) for i in range(w.nwin)]
+    exp = oracle.sum_matrices(mats)
+    own = replicas.row_owner(exp.row_ids, world)
+    for r in range(world):
+        rows, rp, cols, vals = res[r]
+        assert np.all(replicas.row_owner(rows, world) == r)
+        assert np.array_equal(rows, exp.row_ids[own == r])
+    # the union of the partitions is the global sum
+    keys = np.concatenate([replicas.partition_links(*[np.asarray(a) for a in res[r]], 1)[0][0] for r in range(world)])
+    vals = np.concatenate([res[r][3] for r in range(world)])
+    order = np.argsort(keys, kind="stable")
+    got = oracle.DCSR(*replicas.keys_to_dcsr(keys[order], vals[order]))
+    for x, y in zip(got, exp):
+        assert np.array_equal(np.asarray(x, dtype=np.uint64), np.asarray(y, dtype=np.uint64))
