@@ -252,8 +252,11 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * heavily.  Setting agg_path 0 waits for the device and releases the tables.  graph: 1 = a batch's launch sequence is recorded into a CUDA
  * graph and replayed through a cached executable graph of the same shape
  * (updated in place with the call's pointers), 0 = launched directly; per-
- * kernel profiling always launches directly.  Results never depend on the
- * configuration. */
+ * kernel profiling always launches directly.  col_hash: 1 = each window's
+ * column statistics are first counted in a shared-memory hash of its
+ * destinations (one CTA per window; up to 12288 distinct destinations), and
+ * only windows with more take the column sort; 0 = the column sort for every
+ * window.  Results never depend on the configuration. */
 typedef struct {
     uint32_t key_threads, key_rank, key_blocks;
     uint32_t kv_threads, kv_rank, kv_blocks;
@@ -262,11 +265,12 @@ typedef struct {
     uint32_t sum_path;
     uint32_t agg_path;
     uint32_t graph;
+    uint32_t col_hash;
 } ans_tuning;
 
 /* Read / set a context's configuration (default: 512 threads, rank 0, one
  * block; win_path 1, win_threads 1024, win_rank 0; sum_path 0; agg_path 0;
- * graph 1).
+ * graph 1; col_hash 1).
  * ans_set_tuning fails with ANS_ERR_INVALID_ARG on values other than the
  * ones listed above. */
 int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);

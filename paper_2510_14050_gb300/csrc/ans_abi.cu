@@ -144,6 +144,9 @@ struct ans_ctx {
   // their own arena, left empty by every call that used them (hash_dirty
   // marks one that may not have been).
   int agg_path = 0;
+  // Window column statistics: 1 = a shared-memory hash of destinations per
+  // window first (windows that fit skip the column sort), 0 = sort only.
+  int col_hash = 1;
   int pageable = -1;  // does the device read pageable host memory (-1: not asked yet)
   // Batches replay their launch sequence as a CUDA graph (graph = 1): it is
   // captured on `cap` each call and applied to a cached executable graph of
@@ -866,7 +869,7 @@ int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n
 std::string launch_sig(uint32_t flags, bool any_tiles, bool any_small, bool any_big, int rounds, const ans_ctx* c) {
   std::string k = std::to_string(flags) + "/" + std::to_string(any_tiles) + std::to_string(any_small) +
                   std::to_string(any_big) + "/" + std::to_string(rounds) + "/" + std::to_string(c->win_path) +
-                  std::to_string(c->sum_path) + std::to_string(c->agg_path);
+                  std::to_string(c->sum_path) + std::to_string(c->agg_path) + std::to_string(c->col_hash);
   for (const SortCfg* f : {&c->cfg_keys, &c->cfg_kv, &c->cfg_col, &c->cfg_win})
     k += "/" + std::to_string(f->threads) + std::to_string(f->rank) + std::to_string(f->blocks);
   return k;
@@ -1213,6 +1216,11 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       if ((rc = cu(timed(c, "empty_fixup", ls, [&] { return launch_empty_fixup(a, ls); }), "empty"))) return rc;
       if ((rc = cu(timed(c, "rle", ls, [&] { return launch_rle(a, ls); }), "rle"))) return rc;
       if ((rc = cu(timed(c, "finish", ls, [&] { return launch_finish(a, ls); }), "finish"))) return rc;
+      if (c->col_hash &&
+          (rc = cu(timed(c, "colhash", ls, [&] {
+                     return launch_colhash(pw, a.ulen, sb.col_ids, a.vals32, sb.q, ls);
+                   }), "colhash")))
+        return rc;
       if ((rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls, true))) return rc;
     }
 
@@ -1898,6 +1906,7 @@ int ans_get_tuning(ans_ctx* c, ans_tuning* out) {
   out->sum_path = (uint32_t)c->sum_path;
   out->agg_path = (uint32_t)c->agg_path;
   out->graph = (uint32_t)c->graph;
+  out->col_hash = (uint32_t)c->col_hash;
   return ANS_OK;
 }
 
@@ -1914,12 +1923,14 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
   if (t->agg_path > 1) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0 or 1");
   if (t->graph > 1) return fail(ANS_ERR_INVALID_ARG, "graph must be 0 or 1");
+  if (t->col_hash > 1) return fail(ANS_ERR_INVALID_ARG, "col_hash must be 0 or 1");
   std::lock_guard<std::mutex> g(c->mu);
   c->win_path = (int)t->win_path;
   c->cfg_win = SortCfg{(int)t->win_threads, (int)t->win_rank, 1};
   c->sum_path = (int)t->sum_path;
   c->agg_path = (int)t->agg_path;
   c->graph = (int)t->graph;
+  c->col_hash = (int)t->col_hash;
   if (c->agg_path == 0 && c->hash_mem) {  // the hash tables are no longer needed
     DeviceGuard dg(c->device);
     ANS_CUDA(cudaDeviceSynchronize());
@@ -2098,6 +2109,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   res.sum_path = (uint32_t)sum_path;
   res.agg_path = (uint32_t)agg_path;
   res.graph = (uint32_t)c->graph;
+  res.col_hash = (uint32_t)c->col_hash;
   ANS_TRY(ans_set_tuning(c, &res));
   if (chosen) *chosen = res;
   return ANS_OK;

@@ -226,6 +226,12 @@ cudaError_t launch_colstat32(const SegPlan& p, const uint32_t* keys, const uint3
 // Canonical-DCSR check of an imported matrix; ORs failure bits into *bad.
 cudaError_t launch_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* row_ids, const uint64_t* row_ptr,
                               const uint32_t* col_ids, const uint64_t* vals, uint32_t* bad, cudaStream_t st);
+// Window column statistics from a shared-memory hash of destinations, one
+// CTA per window of p (links: col_ids / vals32 at base[s], ulen[s] of them);
+// a window whose distinct destinations fit gets its three column quantities
+// in q and ulen[s] = 0 (the column sort then skips it).
+cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
+                           ans_quantities* q, cudaStream_t st);
 // Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.

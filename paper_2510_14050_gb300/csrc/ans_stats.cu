@@ -594,7 +594,137 @@ __global__ void k_scatter_nonzero(SegPlan p, const uint64_t* __restrict__ kin, c
   }
 }
 
+// ---- window column statistics by a shared-memory hash of destinations -----
+//
+// One CTA per window counts, per distinct destination, its links (fan-in)
+// and their packets (destination packets) in a shared-memory open-addressing
+// table, then reduces the table to the three column quantities (Table I;
+// Sec. IV-C).  This replaces the four column-sort passes for every window
+// whose distinct destinations fit the table: once the table passes three
+// quarters full the CTA gives up and leaves the window to the sort; a window
+// it finished gets ulen = 0, so the column sort and its run reduction skip it.
+
+constexpr int kColHashThreads = 1024;
+constexpr uint32_t kColHashSlots = 1u << 14;                 // 16384
+constexpr uint32_t kColHashMaxFill = kColHashSlots / 4 * 3;  // give up above this
+constexpr size_t kColHashSmem = (size_t)kColHashSlots * 12;  // key, links, packets (uint32 each)
+constexpr uint32_t kColEmpty = 0xFFFFFFFFu;                  // empty slot (that destination is counted apart)
+
+// Finalizer of MurmurHash3 (Appleby): a bijective 32-bit mix.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__global__ void __launch_bounds__(kColHashThreads, 1) k_colhash(SegPlan p, uint64_t* __restrict__ ulen,
+                                                                 const uint32_t* __restrict__ col_ids,
+                                                                 const uint32_t* __restrict__ vals32,
+                                                                 ans_quantities* __restrict__ q) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* t_key = sm;
+  uint32_t* t_cnt = sm + kColHashSlots;
+  uint32_t* t_sum = sm + 2 * kColHashSlots;
+  __shared__ uint32_t s_fill, s_over, s_spec_cnt, s_spec_sum;
+  __shared__ unsigned long long s_red[3][kColHashThreads / 32];
+  const uint32_t s = blockIdx.x;
+  if (s >= p.nseg) return;
+  const uint64_t n = ulen[s];
+  const uint64_t b = p.base[s];
+  for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
+    t_key[i] = kColEmpty;
+    t_cnt[i] = 0;
+    t_sum[i] = 0;
+  }
+  if (threadIdx.x == 0) s_fill = s_over = s_spec_cnt = s_spec_sum = 0;
+  __syncthreads();
+  for (uint64_t u = threadIdx.x; u < n; u += kColHashThreads) {
+    if (*(volatile uint32_t*)&s_over) break;
+    const uint32_t d = col_ids[b + u];
+    const uint32_t v = vals32[b + u];
+    if (d == kColEmpty) {
+      atomicAdd(&s_spec_cnt, 1u);
+      atomicAdd(&s_spec_sum, v);
+      continue;
+    }
+    uint32_t h = fmix32(d) & (kColHashSlots - 1);
+    for (uint32_t probe = 0; probe < kColHashSlots; ++probe) {
+      uint32_t cur = *(volatile uint32_t*)&t_key[h];
+      if (cur == kColEmpty) {
+        cur = atomicCAS(&t_key[h], kColEmpty, d);
+        if (cur == kColEmpty) {
+          cur = d;
+          if (atomicAdd(&s_fill, 1u) + 1 > kColHashMaxFill) s_over = 1;
+        }
+      }
+      if (cur == d) {
+        atomicAdd(&t_cnt[h], 1u);
+        atomicAdd(&t_sum[h], v);
+        break;
+      }
+      h = (h + 1) & (kColHashSlots - 1);
+    }
+  }
+  __syncthreads();
+  if (s_over) return;  // the column sort takes this window
+  unsigned long long c = 0, mcnt = 0, msum = 0;
+  for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
+    if (t_key[i] != kColEmpty) {
+      ++c;
+      mcnt = t_cnt[i] > mcnt ? t_cnt[i] : mcnt;
+      msum = t_sum[i] > msum ? t_sum[i] : msum;
+    }
+  }
+  c = warp_sum(c);
+  mcnt = warp_max(mcnt);
+  msum = warp_max(msum);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_red[0][warp] = c;
+    s_red[1][warp] = mcnt;
+    s_red[2][warp] = msum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c = 0;
+    mcnt = msum = 0;
+    for (int w = 0; w < kColHashThreads / 32; ++w) {
+      c += s_red[0][w];
+      mcnt = s_red[1][w] > mcnt ? s_red[1][w] : mcnt;
+      msum = s_red[2][w] > msum ? s_red[2][w] : msum;
+    }
+    if (s_spec_cnt) {
+      ++c;
+      mcnt = s_spec_cnt > mcnt ? s_spec_cnt : mcnt;
+      msum = s_spec_sum > msum ? s_spec_sum : msum;
+    }
+    q[s].unique_destinations = c;
+    q[s].max_destination_fanin = mcnt;
+    q[s].max_destination_packets = msum;
+    ulen[s] = 0;  // done: the column sort skips this window
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
+                           ans_quantities* q, cudaStream_t st) {
+  if (p.nseg == 0) return cudaSuccess;
+  static unsigned long long configured = 0;  // one bit per device ordinal
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !((configured >> dev) & 1ull)) {
+    e = cudaFuncSetAttribute(k_colhash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColHashSmem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) configured |= 1ull << dev;
+  }
+  k_colhash<<<p.nseg, kColHashThreads, kColHashSmem, st>>>(p, ulen, col_ids, vals32, q);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_nonzero_flags(const SegPlan& p, const uint64_t* vals, uint64_t* flags, uint32_t* err,
                                  cudaStream_t st) {

@@ -544,3 +544,28 @@ def test_signed_combination_subtracts_exactly(ans, ctx, synth):
     with pytest.raises(ans.AnsError) as ei:
         ctx.combine([ctx.build_window(dev([1]), dev([2]), 1)], [0])
     assert ei.value.code == ans.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("col_hash", [0, 1])
+def test_column_statistics_by_hash_or_sort(ans, synth, col_hash):
+    """Window column statistics from the shared-memory destination hash (and
+    the sort for windows whose destinations overflow it) equal the oracle:
+    few and many distinct destinations, the all-ones destination, fan-in
+    concentrated on one destination, and more destinations than the table
+    holds."""
+    rng = np.random.default_rng(5)
+    sizes = [0, 1, 5000, 131072, 30000, 70000]
+    w = synth.generate(5, sizes=sizes, first_window=123)
+    src, dst = w.src.copy(), w.dst.copy()
+    a, b = int(w.offsets[4]), int(w.offsets[5])
+    dst[a:b:3] = 0xFFFFFFFF  # the empty-slot marker as a real destination, heavily
+    a, b = int(w.offsets[5]), int(w.offsets[6])
+    dst[a:b] = rng.integers(0, 1 << 32, b - a, dtype=np.uint64).astype(np.uint32)  # > 12288 destinations
+    from paper_2510_14050_gb300 import synth as sy
+    w2 = sy.Windows(src, dst, w.offsets)
+    c = ans.Context(0)
+    try:
+        c.set_tuning(col_hash=col_hash)
+        check_batch(ans, c, w2)
+    finally:
+        c.close()
