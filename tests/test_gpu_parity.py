@@ -569,3 +569,45 @@ def test_column_statistics_by_hash_or_sort(ans, synth, col_hash):
         check_batch(ans, c, w2)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("cfg", [3, 4])
+def test_full_size_batches_sampled(ans, synth, cfg):
+    """The mixed 1024-window workload and the 2^30-packet workload at full
+    size, in the bench's configuration (autotuned paths): sampled windows
+    against the oracle, and properties every result must have at any size
+    -- the time sum holds every packet, no more links than the windows
+    together, at least as many rows as any window, canonical DCSR order."""
+    import oracle as orc
+    nwin = {3: 1024, 4: 8192}[cfg]
+    w = synth.generate(cfg, nwin=nwin)
+    c = ans.Context(0)
+    try:
+        src, dst = dev(w.src), dev(w.dst)
+        c.autotune(src, dst, w.offsets)
+        out = torch.zeros((w.nwin, 9), dtype=torch.int64, device="cuda")
+        mats, summ, tk = c.batch_submit(src, dst, w.offsets, ans.BATCH_SUM, out=out)
+        c.wait(tk)
+        q = ans.quantities_from_tensor(out)
+        rng = np.random.default_rng(cfg)
+        for i in sorted(set(rng.integers(0, w.nwin, 6).tolist()) | {0, w.nwin - 1}):
+            assert q[i] == orc.window_quantities(*w.window(i)), f"window {i}"
+        sq = summ.quantities()
+        assert sq["valid_packets"] == w.total == sum(x["valid_packets"] for x in q)
+        assert sq["unique_links"] <= sum(x["unique_links"] for x in q)
+        assert sq["unique_sources"] >= max(x["unique_sources"] for x in q)
+        assert sq["unique_destinations"] >= max(x["unique_destinations"] for x in q)
+        assert sq["max_link_packets"] >= max(x["max_link_packets"] for x in q)
+        assert sq["max_source_packets"] >= max(x["max_source_packets"] for x in q)
+        r, p, col, v = summ.to_numpy()
+        assert len(r) == sq["unique_sources"] and len(col) == sq["unique_links"]
+        assert np.all(np.diff(r.astype(np.int64)) > 0) and p[0] == 0 and p[-1] == len(col)
+        assert np.all(np.diff(p.astype(np.int64)) > 0) and np.all(v > 0) and int(v.sum()) == w.total
+        starts = np.zeros(len(col), bool)
+        starts[p[:-1].astype(np.int64)] = True
+        ok = np.diff(col.astype(np.int64)) > 0
+        assert np.all(ok | starts[1:])  # columns ascend within every row
+        assert int(np.diff(p.astype(np.int64)).max()) == sq["max_source_fanout"]
+        summ.free()
+    finally:
+        c.close()
