@@ -213,6 +213,12 @@ __global__ void __launch_bounds__(kT, kMinB)
       if (valid && lane == __ffs(peers) - 1) tab[d] = (uint64_t)(old + __popc(peers)) << 32;
       __syncwarp();
       r[i] = old + __popc(peers & lanemask_lt());
+    } else if (pass == 0) {
+      // The first pass needs no stability (any order of equal digits is a
+      // valid start for the stable passes after it): one shared-memory
+      // atomic per key gives each its slot among the warp's equal digits.
+      const uint32_t d = (uint32_t)(k[i] >> shift) & 0xffu;
+      r[i] = valid ? atomicAdd(&wc[d], 1u) : 0u;
     } else {
       const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & 0xffu : (uint32_t)kRadix;
       const uint32_t peers = digit_peers<kRank>(d, valid);
