@@ -734,10 +734,12 @@ int sum_prepare(ans_ctx* c, char* m, uint32_t k, const std::vector<uint64_t>& ca
 // caller at `m` / `ps` (which must provide vals buffers).  Only queues work
 // on `st` (it may be capturing); on failure the caller discards plan->blk.
 int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s, const uint64_t* fk,
-                   const uint64_t* fv, Block* blk, cudaStream_t st);
+                   const uint64_t* fv, Block* blk, cudaStream_t st, bool narrow = false);
 
+// narrow: every count of the sum is known to stay below 2^32 (the column
+// pass then carries 32-bit counts).
 int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
-               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st) {
+               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st, bool narrow = false) {
   Block* blk = plan->blk;
   const HostPlan& sp = plan->sp;
   const SegPlan& g = plan->g;
@@ -788,7 +790,7 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
     rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
     if (rc != ANS_OK) return rc;
   }
-  return links_to_block(c, m, ps, s, fk, fv, blk, st);
+  return links_to_block(c, m, ps, s, fk, fv, blk, st, narrow);
 }
 
 // From sorted (key, value) links (equal keys adjacent) of the single segment
@@ -796,7 +798,7 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
 // prefix differences, row statistics and the column pass (the time sum's
 // statistics half).  Only queues work on `st`.
 int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s, const uint64_t* fk,
-                   const uint64_t* fv, Block* blk, cudaStream_t st) {
+                   const uint64_t* fv, Block* blk, cudaStream_t st, bool narrow) {
   uint32_t* tickets = at<uint32_t>(m, ps.tickets) + 32;
   auto fail_blk = [&](cudaError_t e, const char* what) {
     return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -827,10 +829,11 @@ int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s,
   a.col_tickets = col_tickets;
   a.err = c->d_err;
   a.mode = kModeSum;
+  if (narrow) a.vals32 = (uint32_t*)at<uint64_t>(m, ps.cv_b);
   if ((e = launch_zero(blk->q, sizeof(ans_quantities), st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = timed(c, "rle", st, [&] { return launch_rle(a, st); })) != cudaSuccess) return fail_blk(e, "rle");
   if ((e = timed(c, "finish", st, [&] { return launch_finish(a, st); })) != cudaSuccess) return fail_blk(e, "finish");
-  return column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st);
+  return column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st, narrow);
 }
 
 // Snapshot the device error word into `dst` (device); reset_err clears it.
@@ -1231,7 +1234,8 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         if ((rc = cu(launch_zero(sblk->hdr, 16, ls), "memset"))) return rc;
         if ((rc = cu(launch_zero(sblk->q, sizeof(ans_quantities), ls), "memset"))) return rc;
       } else {
-        rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, ls);
+        rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, ls,
+                        total < (1ull << 32));  // a sum of window counts stays below the batch's packets
         if (rc) return rc;
       }
     }
