@@ -270,7 +270,7 @@ def test_autotune_picks_valid_configuration(ans, synth):
     c = ans.Context(0)
     try:
         t = c.autotune(dev(w.src), dev(w.dst), w.offsets)
-        assert t["key_threads"] in (512, 1024) and t["col_rank"] in (0, 1)
+        assert t["key_threads"] in (512, 1024) and t["col_rank"] in (0, 1, 2) and t["key_rank"] in (0, 1, 2)
         assert c.get_tuning() == t
         check_batch(ans, c, w)
         with pytest.raises(ans.AnsError) as ei:
@@ -571,6 +571,30 @@ def test_column_statistics_by_hash_or_sort(ans, synth, col_hash):
         c.close()
 
 
+def test_sum_column_statistics_across_calls(ans, synth):
+    """One context sums batches that grow (its scratch is replaced), shrink,
+    repeat, include the all-ones destination and a destination that takes
+    most of the links, with the window column hash switched off and on
+    again; every sum's quantities equal the oracle's."""
+    rng = np.random.default_rng(11)
+    c = ans.Context(0)
+    try:
+        for i, (nwin, col_hash) in enumerate([(3, 1), (40, 1), (2, 1), (2, 1), (9, 0), (9, 1)]):
+            w = synth.generate(5, nwin=nwin, first_window=10 * i)
+            dst = w.dst.copy()
+            if i == 2:
+                dst[::5] = 0xFFFFFFFF
+            if i == 3:
+                dst[rng.random(len(dst)) < 0.7] = 77
+            c.set_tuning(col_hash=col_hash)
+            _, summ, _ = run_batch(ans, c, synth.Windows(w.src, dst, w.offsets), ans.BATCH_SUM)
+            exp = oracle.batch(w.src, dst, w.offsets, want_sum=True)[2]
+            assert summ.quantities() == oracle.network_quantities(exp), f"call {i}"
+            summ.free()
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("cfg", [3, 4])
 def test_full_size_batches_sampled(ans, synth, cfg):
     """The mixed 1024-window workload and the 2^30-packet workload at full
@@ -608,6 +632,11 @@ def test_full_size_batches_sampled(ans, synth, cfg):
         ok = np.diff(col.astype(np.int64)) > 0
         assert np.all(ok | starts[1:])  # columns ascend within every row
         assert int(np.diff(p.astype(np.int64)).max()) == sq["max_source_fanout"]
+        if cfg == 3:  # the column quantities of the sum, from its own stored links
+            cols, inv, fan = np.unique(col, return_inverse=True, return_counts=True)
+            assert sq["unique_destinations"] == len(cols)
+            assert sq["max_destination_fanin"] == int(fan.max())
+            assert sq["max_destination_packets"] == int(np.bincount(inv, weights=v.astype(np.float64)).max())
         summ.free()
     finally:
         c.close()
