@@ -628,8 +628,8 @@ struct PipeScratch {
     vals_a = with_vals ? L.add(pad * 8) : 0;
     vals_b = with_vals ? L.add(pad * 8) : 0;
     seg_hist = L.add((size_t)nseg * kPasses * kRadix * 4);
-    st0 = L.add((size_t)ntiles * kRadix * 8);
-    st1 = L.add((size_t)ntiles * kRadix * 8);
+    st0 = L.add((size_t)ntiles * 2 * kRadix * 8);  // key passes may run two sub-tiles per tile
+    st1 = L.add((size_t)ntiles * 2 * kRadix * 8);
     lb = L.add((size_t)ntiles * 8);
     lb2 = L.add((size_t)ntiles * 8);
     tickets = L.add(kTicketBlocks * 32 * 4);
@@ -1189,7 +1189,8 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         const SegPlan pb = wl.dp_big.bind(m, hp_big);
         const size_t nb = big_ids.size();
         if ((rc = cu(launch_zero(seg_hist, nb * kPasses * kRadix * 4, ls), "memset hist"))) return rc;
-        if ((rc = cu(timed(c, "pack_hist", ls, [&] { return launch_pack_hist(pb, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, ls); }), "pack")))
+        if ((rc = cu(timed(c, "pack_hist", ls, [&] { return launch_pack_hist(pb, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, ls,
+                                                                                         key_subtiles(c->cfg_keys)); }), "pack")))
           return rc;
         if ((rc = sort_segments(c, pb, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
                                 at<uint64_t>(m, ps.st1), tickets, ls)))
@@ -1919,9 +1920,12 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   auto ok = [](uint32_t th, uint32_t rk, uint32_t bl) {
     return (th == 512 || th == 1024) && rk <= 2 && (bl == 1 || (bl == 2 && th == 512));
   };
-  if (!ok(t->key_threads, t->key_rank, t->key_blocks) || !ok(t->kv_threads, t->kv_rank, t->kv_blocks) ||
+  const bool key_sub = t->key_threads == 256 && t->key_rank <= 2 && t->key_blocks == 4;
+  if (!(key_sub || ok(t->key_threads, t->key_rank, t->key_blocks)) || !ok(t->kv_threads, t->kv_rank, t->kv_blocks) ||
       !ok(t->col_threads, t->col_rank, t->col_blocks))
-    return fail(ANS_ERR_INVALID_ARG, "threads must be 512 or 1024, rank 0, 1 or 2, blocks 1 (or 2 with 512 threads)");
+    return fail(ANS_ERR_INVALID_ARG,
+                "threads must be 512 or 1024, rank 0, 1 or 2, blocks 1 (or 2 with 512 threads); key passes also "
+                "take 256 threads with blocks 4");
   if (t->win_path > 1 || t->win_rank > 1 || !ok(t->win_threads, t->win_rank, 1))
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
   if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
@@ -1951,10 +1955,12 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
 int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets, size_t nwin,
                  ans_tuning* chosen, void* stream) {
   if (!c || !h_offsets || nwin == 0) return fail(ANS_ERR_INVALID_ARG, "NULL argument or empty batch");
-  constexpr int kVariants = 9;
+  // The last kKeyOnly shapes exist for the 64-bit key passes only.
+  constexpr int kVariants = 12, kKeyOnly = 3;
   const SortCfg variants[kVariants] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankTable, 1},
                                        {512, kRankMatch, 2}, {512, kRankBallot, 2}, {512, kRankTable, 2},
-                                       {1024, kRankMatch, 1}, {1024, kRankBallot, 1}, {1024, kRankTable, 1}};
+                                       {1024, kRankMatch, 1}, {1024, kRankBallot, 1}, {1024, kRankTable, 1},
+                                       {256, kRankMatch, 4}, {256, kRankBallot, 4}, {256, kRankTable, 4}};
   using Prof = std::map<std::string, double>;
   std::vector<ans_matrix*> per(nwin, nullptr);
   auto run_once = [&]() -> int {
@@ -2009,18 +2015,20 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   // Radix-pass launch shapes, per family, on the paths that use them all.
   double t_keys[kVariants], t_kv[kVariants], t_col[kVariants];
   for (int v = 0; v < kVariants; ++v) {
+    const bool key_only = v >= kVariants - kKeyOnly;
     Prof pr;
     bool ran = false;
     ANS_TRY(trial([&] {
-      c->cfg_keys = c->cfg_kv = c->cfg_col = variants[v];
+      c->cfg_keys = c->cfg_kv = c->cfg_col = variants[key_only ? 0 : v];
+      c->cfg_keys = variants[v];
       c->win_path = 1;  // the key passes on every window
       c->sum_path = 1;  // the kv passes on the time sum
       c->agg_path = 0;
     }, &pr, &ran));
     if (!ran) return fail(ANS_ERR_OOM, "autotune: the batch does not fit the device with the default paths");
     t_keys[v] = get(pr, "onesweep") + get(pr, "pack_hist");
-    t_kv[v] = get(pr, "onesweep_sum") + get(pr, "gather");
-    t_col[v] = get(pr, "onesweep_col");
+    t_kv[v] = key_only ? kNever : get(pr, "onesweep_sum") + get(pr, "gather");
+    t_col[v] = key_only ? kNever : get(pr, "onesweep_col");
   }
   auto best = [&](const double* t) {
     int b = 0;

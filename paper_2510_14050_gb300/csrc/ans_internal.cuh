@@ -43,11 +43,13 @@ enum ErrBits : uint32_t {
 };
 
 // How a onesweep pass is launched (chosen per context by the autotuner):
-// threads per 8192-key tile (512 or 1024), how lanes with equal digits are
-// found (one __match_any_sync; eight ballots; or a per-warp shared-memory
-// table where each lane ORs its bit into its digit's entry, which also holds
-// the digit's running count), and whether a 512-thread tile is compiled to
-// leave room for two resident CTAs per SM (64 registers).
+// threads per 8192-key tile (512 or 1024; for the 64-bit key passes also 256,
+// which splits every tile into two 4096-key sub-tiles with one CTA each and
+// four resident CTAs per SM), how lanes with equal digits are found (one
+// __match_any_sync; eight ballots; or a per-warp shared-memory table where
+// each lane ORs its bit into its digit's entry, which also holds the digit's
+// running count), and whether a 512-thread tile is compiled to leave room for
+// two resident CTAs per SM (64 registers).
 enum RankMode : int { kRankMatch = 0, kRankBallot = 1, kRankTable = 2 };
 struct SortCfg {
   int threads = 512;
@@ -134,10 +136,13 @@ int set_last_error(int code, const std::string& msg);
 
 // ---- launchers (ans_sort.cu) ---------------------------------------------
 // Pack (src, dst) into keys src << 32 | dst, build per-segment digit
-// histograms of all passes, zero the pass-0 status words and the tickets.
+// histograms of all passes, zero the pass-0 status words (sub * kRadix per
+// tile, for key passes over `sub` sub-tiles per tile) and the tickets.
 cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32_t* dst,
                              uint64_t* keys, uint32_t* seg_hist, uint64_t* status0,
-                             uint32_t* tickets, cudaStream_t st);
+                             uint32_t* tickets, cudaStream_t st, uint32_t sub = 1);
+// Sub-tiles per tile of a key-pass configuration.
+inline uint32_t key_subtiles(const SortCfg& cfg) { return cfg.threads == 256 ? 2u : 1u; }
 // One onesweep digit pass (stable), optionally carrying uint64 values.
 cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
                                                         uint64_t* __restrict__ keys,
                                                         uint32_t* __restrict__ seg_hist,
                                                         uint64_t* __restrict__ status0,
-                                                        uint32_t* __restrict__ tickets) {
+                                                        uint32_t* __restrict__ tickets, uint32_t sub) {
   __shared__ uint32_t hc[kHistCopies][kPasses * kRadix];
   uint32_t* h = hc[0];
   __shared__ Tile s_tile;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_hist(SegPlan p, const uint32_
   const Tile tl = block_tile(p, t, &s_tile);
   for (int i = threadIdx.x; i < kHistCopies * kPasses * kRadix; i += kThreads) (&hc[0][0])[i] = 0;
   if (t == 0 && threadIdx.x < 32) tickets[threadIdx.x] = 0;
-  if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  for (uint32_t i = threadIdx.x; i < sub * kRadix; i += kThreads) status0[(uint64_t)t * sub * kRadix + i] = 0;
   __syncthreads();
   if (tl.count == 0) return;
 
@@ -135,29 +135,34 @@ constexpr size_t warp_counter_bytes() {
   return kRank == kRankTable ? (size_t)kRadix * 8 : (size_t)(kRadix + 1) * 4;
 }
 
-template <typename K, typename V, int kT, int kRank>
+template <typename K, typename V, int kT, int kRank, int kSub>
 constexpr size_t onesweep_smem_bytes() {
-  return (size_t)kTile * sizeof(K) + (std::is_same<V, NoVal>::value ? 0 : (size_t)kTile * sizeof(V)) +
+  return (size_t)(kTile / kSub) * sizeof(K) +
+         (std::is_same<V, NoVal>::value ? 0 : (size_t)(kTile / kSub) * sizeof(V)) +
          (size_t)(kT / 32) * warp_counter_bytes<kRank>();
 }
 
 // One stable digit pass over keys of type K (8 passes for 64-bit keys, 4 for
 // 32-bit keys; seg_hist holds sizeof(K) histograms per segment), optionally
-// carrying values of type V.  kT threads share the 8192-key tile (kTile / kT
-// keys each); kRank selects how lanes with equal digits find each other.
-template <typename K, typename V, int kT, int kRank, int kMinB>
+// carrying values of type V.  Each 8192-key tile of the plan is split into
+// kSub sub-tiles, one CTA each (look-back runs over sub-tiles: status word
+// u * kRadix + d belongs to sub-tile u = kSub * tile + half); kT threads
+// share a sub-tile (kTile / kSub / kT keys each); kRank selects how lanes
+// with equal digits find each other.
+template <typename K, typename V, int kT, int kRank, int kMinB, int kSub>
 __global__ void __launch_bounds__(kT, kMinB)
     k_onesweep(SegPlan p, int pass, const K* __restrict__ kin, K* __restrict__ kout,
                const V* __restrict__ vin, V* __restrict__ vout, const uint32_t* __restrict__ seg_hist,
                uint64_t* st_cur, uint64_t* __restrict__ st_next, uint32_t* ticket, uint32_t* err) {
   constexpr bool kVals = !std::is_same<V, NoVal>::value;
   constexpr int kNumPasses = (int)sizeof(K);
-  constexpr int kP = kTile / kT;  // keys per thread
-  constexpr int kW = kT / 32;     // warps
+  constexpr uint32_t kTT = kTile / kSub;  // keys per CTA
+  constexpr int kP = kTT / kT;            // keys per thread
+  constexpr int kW = kT / 32;             // warps
   extern __shared__ __align__(16) uint8_t smem[];
   K* s_keys = reinterpret_cast<K*>(smem);
-  V* s_vals = reinterpret_cast<V*>(smem + (size_t)kTile * sizeof(K));
-  uint8_t* s_cnt = smem + (size_t)kTile * sizeof(K) + (kVals ? (size_t)kTile * sizeof(V) : 0);
+  V* s_vals = reinterpret_cast<V*>(smem + (size_t)kTT * sizeof(K));
+  uint8_t* s_cnt = smem + (size_t)kTT * sizeof(K) + (kVals ? (size_t)kTT * sizeof(V) : 0);
   uint32_t* s_wc = reinterpret_cast<uint32_t*>(s_cnt);   // [kW][kRadix+1] (match / ballot ranking)
   uint64_t* s_tab = reinterpret_cast<uint64_t*>(s_cnt);  // [kW][kRadix]   (table ranking)
   __shared__ uint64_t s_gofs[kRadix];
@@ -166,9 +171,15 @@ __global__ void __launch_bounds__(kT, kMinB)
   __shared__ uint32_t s_ticket;
   __shared__ Tile s_tile;
 
-  const uint32_t t = block_ticket(ticket, &s_ticket);
-  const Tile tl = block_tile(p, t, &s_tile);
-  if (threadIdx.x < kRadix) st_next[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  const uint32_t u = block_ticket(ticket, &s_ticket);  // sub-tile
+  const uint32_t t = u / kSub, half = u % kSub;
+  Tile tl = block_tile(p, t, &s_tile);
+  if (threadIdx.x < kRadix) st_next[(uint64_t)u * kRadix + threadIdx.x] = 0;
+  if constexpr (kSub > 1) {
+    const uint32_t off = half * kTT;
+    tl.count = tl.count > off ? (uint32_t)umin64(tl.count - off, kTT) : 0u;
+    tl.start += off;
+  }
   if (tl.count == 0) return;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -252,12 +263,12 @@ __global__ void __launch_bounds__(kT, kMinB)
         cnt += c;
       }
     }
-    uint64_t* my = st_cur + (uint64_t)t * kRadix + d;
-    if (tl.j == 0) {
+    uint64_t* my = st_cur + (uint64_t)u * kRadix + d;
+    if (tl.j == 0 && half == 0) {
       st_relaxed(my, kFlagPre | cnt);
     } else {
       st_relaxed(my, kFlagAgg | cnt);
-      excl = lookback(st_cur + d, kRadix, t - tl.j, t, err);
+      excl = lookback(st_cur + d, kRadix, kSub * (t - tl.j), u, err);
       st_relaxed(my, kFlagPre | (excl + cnt));
     }
   }
@@ -410,26 +421,26 @@ __global__ void __launch_bounds__(1024) k_count_prefix(const MatDesc* __restrict
 }
 
 // Dynamic shared memory is configured once per kernel instance and device.
-template <typename K, typename V, int kT, int kRank, int kMinB>
+template <typename K, typename V, int kT, int kRank, int kMinB, int kSub>
 cudaError_t configure_onesweep_variant() {
   static unsigned long long done = 0;  // one bit per device ordinal
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_onesweep<K, V, kT, kRank, kMinB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<K, V, kT, kRank>());
+  e = cudaFuncSetAttribute(k_onesweep<K, V, kT, kRank, kMinB, kSub>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem_bytes<K, V, kT, kRank, kSub>());
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
   return e;
 }
 
-template <typename K, typename V, int kT, int kRank, int kMinB>
+template <typename K, typename V, int kT, int kRank, int kMinB, int kSub = 1>
 cudaError_t run_onesweep_variant(const SegPlan& p, int pass, const K* kin, K* kout, const V* vin, V* vout,
                                  const uint32_t* seg_hist, uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
                                  uint32_t* err, cudaStream_t st) {
-  cudaError_t e = configure_onesweep_variant<K, V, kT, kRank, kMinB>();
+  cudaError_t e = configure_onesweep_variant<K, V, kT, kRank, kMinB, kSub>();
   if (e != cudaSuccess) return e;
-  k_onesweep<K, V, kT, kRank, kMinB><<<p.ntiles, kT, onesweep_smem_bytes<K, V, kT, kRank>(), st>>>(
+  k_onesweep<K, V, kT, kRank, kMinB, kSub><<<kSub * p.ntiles, kT, onesweep_smem_bytes<K, V, kT, kRank, kSub>(), st>>>(
       p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err);
   return cudaGetLastError();
 }
@@ -442,6 +453,18 @@ cudaError_t run_onesweep(const SegPlan& p, int pass, const K* kin, K* kout, cons
 #define ANS_OS(T, R, B)                                                                                        \
   return run_onesweep_variant<K, V, T, R, B>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, \
                                              err, st)
+  if constexpr (std::is_same<K, uint64_t>::value && std::is_same<V, NoVal>::value) {
+    if (cfg.threads == 256) {  // two 4096-key sub-tiles per tile, four CTAs per SM
+      if (cfg.rank == kRankBallot)
+        return run_onesweep_variant<K, V, 256, kRankBallot, 4, 2>(p, pass, kin, kout, vin, vout, seg_hist, st_cur,
+                                                                  st_next, ticket, err, st);
+      if (cfg.rank == kRankTable)
+        return run_onesweep_variant<K, V, 256, kRankTable, 4, 2>(p, pass, kin, kout, vin, vout, seg_hist, st_cur,
+                                                                 st_next, ticket, err, st);
+      return run_onesweep_variant<K, V, 256, kRankMatch, 4, 2>(p, pass, kin, kout, vin, vout, seg_hist, st_cur,
+                                                               st_next, ticket, err, st);
+    }
+  }
   if (cfg.threads == 1024) {
     if (cfg.rank == kRankBallot) ANS_OS(1024, kRankBallot, 1);
     if (cfg.rank == kRankTable) ANS_OS(1024, kRankTable, 1);
@@ -462,9 +485,9 @@ cudaError_t run_onesweep(const SegPlan& p, int pass, const K* kin, K* kout, cons
 
 cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32_t* dst,
                              uint64_t* keys, uint32_t* seg_hist, uint64_t* status0, uint32_t* tickets,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint32_t sub) {
   if (p.ntiles == 0) return cudaSuccess;
-  k_pack_hist<<<p.ntiles, kThreads, 0, st>>>(p, src, dst, keys, seg_hist, status0, tickets);
+  k_pack_hist<<<p.ntiles, kThreads, 0, st>>>(p, src, dst, keys, seg_hist, status0, tickets, sub);
   return cudaGetLastError();
 }
 

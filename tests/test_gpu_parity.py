@@ -265,12 +265,35 @@ def test_every_sort_configuration_is_exact(ans, synth, threads, rank, blocks):
         c.close()
 
 
+@pytest.mark.parametrize("rank", [0, 1, 2])
+def test_key_passes_over_subtiles_are_exact(ans, synth, rank):
+    """Key passes that split every tile into two 4096-key sub-tiles give the
+    same results: windows ending inside either half of a tile, exactly at
+    the half, one key past it, empty and single-packet windows, and the
+    one-window path."""
+    h = KT // 2
+    w = synth.generate(5, sizes=[KT * 3 + 17, 0, h, h + 1, h - 1, 1, 2 * KT, KT + h, 40000])
+    c = ans.Context(0)
+    try:
+        c.set_tuning(key_threads=256, key_rank=rank, key_blocks=4, win_path=1)
+        assert c.get_tuning()["key_threads"] == 256
+        check_batch(ans, c, w)
+        check_window(c, *w.window(8), "one window").free()
+        for bad in ({"key_threads": 256, "key_blocks": 2}, {"kv_threads": 256, "kv_blocks": 4},
+                    {"col_threads": 256, "col_blocks": 4}):
+            with pytest.raises(ans.AnsError) as ei:
+                c.set_tuning(**bad)
+            assert ei.value.code == ans.ERR_INVALID_ARG
+    finally:
+        c.close()
+
+
 def test_autotune_picks_valid_configuration(ans, synth):
     w = synth.generate(2, nwin=4)
     c = ans.Context(0)
     try:
         t = c.autotune(dev(w.src), dev(w.dst), w.offsets)
-        assert t["key_threads"] in (512, 1024) and t["col_rank"] in (0, 1, 2) and t["key_rank"] in (0, 1, 2)
+        assert t["key_threads"] in (256, 512, 1024) and t["col_rank"] in (0, 1, 2) and t["key_rank"] in (0, 1, 2)
         assert c.get_tuning() == t
         check_batch(ans, c, w)
         with pytest.raises(ans.AnsError) as ei:
