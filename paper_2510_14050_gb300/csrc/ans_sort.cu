@@ -302,11 +302,22 @@ __global__ void __launch_bounds__(kT, kMinB)
 }
 
 // Last row r of matrix m with row_ptr[r] <= u.
-__device__ __forceinline__ uint64_t row_of(const MatDesc& m, uint64_t nrows, uint64_t u) {
-  uint64_t lo = 0, hi = nrows;
+// The row holding stored link u: the last r < nrows with row_ptr[r] <= u,
+// found by one warp (all 32 lanes call it; every lane gets the result).
+// Each step tests 32 evenly spaced candidates of the remaining range at once
+// (the test is monotone: true up to the answer), so a range of 2^k rows
+// needs about k / 5 dependent loads.
+__device__ __forceinline__ uint64_t row_of_warp(const MatDesc& m, uint64_t nrows, uint64_t u) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint64_t lo = 0, hi = nrows;  // row_ptr[lo] <= u; the answer lies in [lo, hi)
   while (hi - lo > 1) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if (m.row_ptr[mid] <= u) lo = mid; else hi = mid;
+    const uint64_t c = lo + ((hi - lo) * (lane + 1)) / 33;  // lo <= c < hi, nondecreasing in lane
+    const uint32_t le = __ballot_sync(0xffffffffu, m.row_ptr[c] <= u);
+    const int nt = __popc(le);  // the lanes testing true are a prefix
+    const uint64_t c_last = __shfl_sync(0xffffffffu, c, nt > 0 ? nt - 1 : 0);
+    const uint64_t c_first = __shfl_sync(0xffffffffu, c, nt < 32 ? nt : 31);
+    if (nt > 0) lo = c_last;
+    if (nt < 32) hi = c_first;
   }
   return lo;
 }
@@ -340,13 +351,14 @@ __global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* _
   if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
   if (tl.count == 0) return;
   const MatDesc m = mats[tl.seg];
-  if (threadIdx.x == 0) {
-    const uint64_t nrows = m.hdr[0];
-    const uint64_t r0 = row_of(m, nrows, tl.start);
-    const uint64_t r1 = row_of(m, nrows, tl.start + tl.count - 1);
-    s_r0 = r0;
-    s_nr = (uint32_t)(r1 - r0 + 1);
+  __shared__ uint64_t s_r1;
+  if (threadIdx.x < 64) {  // warp 0: the tile's first row, warp 1: its last
+    const uint64_t r = row_of_warp(m, m.hdr[0], threadIdx.x < 32 ? tl.start : tl.start + tl.count - 1);
+    if (threadIdx.x == 0) s_r0 = r;
+    if (threadIdx.x == 32) s_r1 = r;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) s_nr = (uint32_t)(s_r1 - s_r0 + 1);
   __syncthreads();
   const uint64_t r0 = s_r0;
   const uint32_t nr = s_nr;

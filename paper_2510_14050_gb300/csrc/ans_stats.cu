@@ -708,6 +708,174 @@ __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash(SegPlan p, uint6
   }
 }
 
+// The same statistics with one cluster of C CTAs per window (launched with
+// clusters along x; cluster c takes window c; C a power of two): CTA r
+// counts links [r, r + 1) * ceil(n / C) of the window in its own table;
+// then, in log2(C) rounds, CTA r pulls the table of CTA r + 2^k (for r a
+// multiple of 2^(k+1)) over distributed shared memory and adds it into its
+// own, so CTA 0 ends with the window's table and reduces it.  A table that
+// passes kColHashMaxFill -- its own links, or a pulled table -- marks its CTA
+// overflowing, and the mark travels with the pulls: the window gives up
+// (ulen kept) exactly when it has more distinct destinations than that.
+// Every CTA of a cluster passes the same cluster barriers.
+__global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_cl(SegPlan p, uint64_t* __restrict__ ulen,
+                                                                    const uint32_t* __restrict__ col_ids,
+                                                                    const uint32_t* __restrict__ vals32,
+                                                                    ans_quantities* __restrict__ q) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* t_key = sm;
+  uint32_t* t_cnt = sm + kColHashSlots;
+  uint32_t* t_sum = sm + 2 * kColHashSlots;
+  __shared__ uint32_t s_fill, s_over, s_spec_cnt, s_spec_sum;
+  __shared__ unsigned long long s_red[3][kColHashThreads / 32];
+  const uint32_t me = cta_rank(), nc = cluster_nctarank();
+  const uint32_t s = cluster_id();
+  const uint64_t n = s < p.nseg ? ulen[s] : 0;
+  const uint64_t b = s < p.nseg ? p.base[s] : 0;
+  for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
+    t_key[i] = kColEmpty;
+    t_cnt[i] = 0;
+    t_sum[i] = 0;
+  }
+  if (threadIdx.x == 0) s_fill = s_over = s_spec_cnt = s_spec_sum = 0;
+  __syncthreads();
+  // Adds (d, c links, v packets) to this CTA's table.
+  auto insert = [&](uint32_t d, uint32_t c, uint32_t v) {
+    uint32_t h = fmix32(d) & (kColHashSlots - 1);
+    for (uint32_t probe = 0; probe < kColHashSlots; ++probe) {
+      uint32_t cur = *(volatile uint32_t*)&t_key[h];
+      if (cur == kColEmpty) {
+        cur = atomicCAS(&t_key[h], kColEmpty, d);
+        if (cur == kColEmpty) {
+          cur = d;
+          if (atomicAdd(&s_fill, 1u) + 1 > kColHashMaxFill) s_over = 1;
+        }
+      }
+      if (cur == d) {
+        atomicAdd(&t_cnt[h], c);
+        atomicAdd(&t_sum[h], v);
+        return;
+      }
+      h = (h + 1) & (kColHashSlots - 1);
+    }
+  };
+  const uint64_t chunk = (n + nc - 1) / nc;
+  const uint64_t lo = umin64((uint64_t)me * chunk, n), hi = umin64(lo + chunk, n);
+  for (uint64_t u = lo + threadIdx.x; u < hi; u += kColHashThreads) {
+    if (*(volatile uint32_t*)&s_over) break;
+    const uint32_t d = col_ids[b + u];
+    const uint32_t v = vals32[b + u];
+    if (d == kColEmpty) {
+      atomicAdd(&s_spec_cnt, 1u);
+      atomicAdd(&s_spec_sum, v);
+      continue;
+    }
+    insert(d, 1u, v);
+  }
+  cluster_sync();  // every local table is complete
+  for (uint32_t step = 1; step < nc; step <<= 1) {
+    if ((me & (2 * step - 1)) == 0 && me + step < nc) {
+      const uint32_t r = me + step;
+      const uint32_t key_r = map_rank(smem_addr(t_key), r), cnt_r = map_rank(smem_addr(t_cnt), r),
+                     sum_r = map_rank(smem_addr(t_sum), r);
+      if (ld_cluster(map_rank(smem_addr(&s_over), r)) != 0) {
+        if (threadIdx.x == 0) s_over = 1;
+      } else {
+        constexpr int kU = 4;  // slots read per round trip
+        for (uint32_t i0 = threadIdx.x; i0 < kColHashSlots; i0 += kU * kColHashThreads) {
+          if (*(volatile uint32_t*)&s_over) break;
+          uint32_t d[kU];
+#pragma unroll
+          for (int j = 0; j < kU; ++j) d[j] = ld_cluster(key_r + 4 * (i0 + j * kColHashThreads));
+#pragma unroll
+          for (int j = 0; j < kU; ++j) {
+            if (d[j] == kColEmpty) continue;
+            const uint32_t i = i0 + j * kColHashThreads;
+            insert(d[j], ld_cluster(cnt_r + 4 * i), ld_cluster(sum_r + 4 * i));
+          }
+        }
+        if (threadIdx.x == 0) {
+          s_spec_cnt += ld_cluster(map_rank(smem_addr(&s_spec_cnt), r));
+          s_spec_sum += ld_cluster(map_rank(smem_addr(&s_spec_sum), r));
+        }
+      }
+    }
+    cluster_sync();  // this round's pulls are done: their sources are read no more
+  }
+  if (me != 0 || s_over || s >= p.nseg) return;  // an overflowing window is left to the column sort
+  unsigned long long c = 0, mcnt = 0, msum = 0;
+  for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
+    if (t_key[i] != kColEmpty) {
+      ++c;
+      mcnt = t_cnt[i] > mcnt ? t_cnt[i] : mcnt;
+      msum = t_sum[i] > msum ? t_sum[i] : msum;
+    }
+  }
+  c = warp_sum(c);
+  mcnt = warp_max(mcnt);
+  msum = warp_max(msum);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_red[0][warp] = c;
+    s_red[1][warp] = mcnt;
+    s_red[2][warp] = msum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c = 0;
+    mcnt = msum = 0;
+    for (int w = 0; w < kColHashThreads / 32; ++w) {
+      c += s_red[0][w];
+      mcnt = s_red[1][w] > mcnt ? s_red[1][w] : mcnt;
+      msum = s_red[2][w] > msum ? s_red[2][w] : msum;
+    }
+    if (s_spec_cnt) {
+      ++c;
+      mcnt = s_spec_cnt > mcnt ? s_spec_cnt : mcnt;
+      msum = s_spec_sum > msum ? s_spec_sum : msum;
+    }
+    q[s].unique_destinations = c;
+    q[s].max_destination_fanin = mcnt;
+    q[s].max_destination_packets = msum;
+    ulen[s] = 0;  // done: the column sort skips this window
+  }
+}
+
+// CTAs per window for the cluster form (1 = the one-CTA kernel): enough to
+// cover the SMs with the batch's windows, if the device hosts such clusters.
+uint32_t colhash_cluster_size(uint32_t nseg) {
+  static int ok[4][64];  // per size index and device: 0 unknown, 1 yes, 2 no
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 1;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  for (uint32_t c = 8, k = 3; c >= 2; c >>= 1, --k) {
+    if ((uint64_t)nseg * c > (uint64_t)sms) continue;
+    if (ok[k][dev] == 0) {
+      cudaLaunchConfig_t lc = {};
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = c;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      lc.attrs = &attr;
+      lc.numAttrs = 1;
+      lc.gridDim = dim3(c, 1, 1);
+      lc.blockDim = dim3(kColHashThreads, 1, 1);
+      lc.dynamicSmemBytes = kColHashSmem;
+      int n = 0;
+      ok[k][dev] = cudaFuncSetAttribute(k_colhash_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kColHashSmem) == cudaSuccess &&
+                           cudaOccupancyMaxActiveClusters(&n, k_colhash_cl, &lc) == cudaSuccess && n > 0
+                       ? 1
+                       : 2;
+      cudaGetLastError();
+    }
+    if (ok[k][dev] == 1) return c;
+  }
+  return 1;
+}
+
 }  // namespace
 
 cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
@@ -721,6 +889,22 @@ cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col
     e = cudaFuncSetAttribute(k_colhash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColHashSmem);
     if (e != cudaSuccess) return e;
     if (dev < 64) configured |= 1ull << dev;
+  }
+  const uint32_t c = colhash_cluster_size(p.nseg);
+  if (c > 1) {
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    lc.gridDim = dim3(p.nseg * c, 1, 1);
+    lc.blockDim = dim3(kColHashThreads, 1, 1);
+    lc.dynamicSmemBytes = kColHashSmem;
+    lc.stream = st;
+    return cudaLaunchKernelEx(&lc, k_colhash_cl, p, ulen, col_ids, vals32, q);
   }
   k_colhash<<<p.nseg, kColHashThreads, kColHashSmem, st>>>(p, ulen, col_ids, vals32, q);
   return cudaGetLastError();

@@ -594,6 +594,46 @@ def test_column_statistics_by_hash_or_sort(ans, synth, col_hash):
         c.close()
 
 
+@pytest.mark.parametrize("nwin", [1, 3, 20, 40, 80])
+def test_column_hash_over_clusters(ans, nwin):
+    """Window column statistics when several CTAs share a window's hash (as
+    many as the batch leaves SMs for: 8, 4, 2 or 1 per window): windows with
+    exactly the table's limit of distinct destinations (12288), one more,
+    more in total than the limit while every CTA's share stays below it, the
+    all-ones destination, few destinations, and empty and one-packet
+    windows, all equal to the oracle."""
+    from paper_2510_14050_gb300 import synth as sy
+    rng = np.random.default_rng(nwin)
+    wins = []
+    for i in range(nwin):
+        kind = i % 7
+        if kind == 0:
+            d = np.repeat(rng.permutation(1 << 20)[:12288].astype(np.uint32), 3)
+        elif kind == 1:
+            d = np.repeat(rng.permutation(1 << 20)[:12289].astype(np.uint32), 2)
+        elif kind == 2:
+            d = rng.permutation(1 << 20)[:20000].astype(np.uint32)
+        elif kind == 3:
+            d = rng.integers(0, 50, 30000).astype(np.uint32)
+            d[::4] = 0xFFFFFFFF
+        elif kind == 4:
+            d = np.zeros(0, np.uint32)
+        elif kind == 5:
+            d = np.array([7], np.uint32)
+        else:
+            d = rng.integers(0, 5000, 60000).astype(np.uint32)
+        rng.shuffle(d)
+        wins.append((rng.integers(0, 1 << 12, len(d)).astype(np.uint32), d))
+    offsets = np.zeros(nwin + 1, np.uint64)
+    offsets[1:] = np.cumsum([len(d) for _, d in wins])
+    w = sy.Windows(np.concatenate([s_ for s_, _ in wins]), np.concatenate([d for _, d in wins]), offsets)
+    c = ans.Context(0)
+    try:
+        check_batch(ans, c, w, check_sum=nwin <= 20)
+    finally:
+        c.close()
+
+
 def test_sum_column_statistics_across_calls(ans, synth):
     """One context sums batches that grow (its scratch is replaced), shrink,
     repeat, include the all-ones destination and a destination that takes
