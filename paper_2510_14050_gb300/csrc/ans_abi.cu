@@ -155,6 +155,10 @@ struct ans_ctx {
   int graph = 1;
   cudaStream_t cap = nullptr;
   std::map<std::string, cudaGraphExec_t> graphs;
+  // A batch's time sum orders its links (gather, merge rounds) on `side`,
+  // beside the window column pass on the main stream: fork and join events.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* hash_mem = nullptr;
   size_t hash_slots = 0;
   bool hash_dirty = false;
@@ -736,11 +740,15 @@ int sum_prepare(ans_ctx* c, char* m, uint32_t k, const std::vector<uint64_t>& ca
 int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s, const uint64_t* fk,
                    const uint64_t* fv, Block* blk, cudaStream_t st, bool narrow = false);
 
-// narrow: every count of the sum is known to stay below 2^32 (the column
-// pass then carries 32-bit counts).
-int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
-               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st, bool narrow = false) {
-  Block* blk = plan->blk;
+// First half of the time sum: the input links gathered and ordered (merge
+// rounds, or the kv passes with sum_path 1), left in (*fk, *fv).  Touches
+// only the sum's own scratch (keys and values ping-pong, run offsets, the
+// look-back words lb / lb2, the digit histograms, the tickets at 32..63) --
+// with sum_path 0 none of what a window column pass uses, so it may run
+// beside one (col_hist is cleared by the second half).  Only queues work.
+int sum_order(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
+              size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st, const uint64_t** fk_out,
+              const uint64_t** fv_out) {
   const HostPlan& sp = plan->sp;
   const SegPlan& g = plan->g;
   const SegPlan& s = plan->s;
@@ -763,16 +771,14 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
   if ((e = launch_zero(seg_hist, kPasses * kRadix * 4, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = launch_zero(m + ps.lb, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = launch_zero(m + ps.lb2, (size_t)sp.ntiles * 8, st)) != cudaSuccess) return fail_blk(e, "memset");
-  if ((e = launch_zero(m + ps.col_hist, kColPasses * kRadix * 4, st)) != cudaSuccess)
-    return fail_blk(e, "memset");
-  // gather (with the radix path: also the sum segment's histograms) zeroes
-  // the sort's first status words (the gather plan has at least as many
-  // tiles as the sum plan) and tickets
+  // gather zeroes the tickets and, for the radix path, builds the sum
+  // segment's histograms and zeroes the sort's first status words (the
+  // gather plan has at least as many tiles as the sum plan)
   const bool merge = c->sum_path == 0;
   const uint64_t* cat_off = at<uint64_t>(m, off_catoff);
   if ((e = timed(c, "gather", st, [&] {
-         return launch_gather(g, d_mats, cat_off, ka, va, merge ? nullptr : seg_hist, at<uint64_t>(m, ps.st0),
-                              tickets, st);
+         return launch_gather(g, d_mats, cat_off, ka, va, merge ? nullptr : seg_hist,
+                              merge ? nullptr : at<uint64_t>(m, ps.st0), tickets, st);
        })) != cudaSuccess)
     return fail_blk(e, "gather");
   uint64_t *fk = ka, *fv = va;  // the sorted links
@@ -790,7 +796,18 @@ int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats
     rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
     if (rc != ANS_OK) return rc;
   }
-  return links_to_block(c, m, ps, s, fk, fv, blk, st, narrow);
+  *fk_out = fk;
+  *fv_out = fv;
+  return ANS_OK;
+}
+
+// narrow: every count of the sum is known to stay below 2^32 (the column
+// pass then carries 32-bit counts).
+int sum_launch(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
+               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st, bool narrow = false) {
+  const uint64_t *fk = nullptr, *fv = nullptr;
+  ANS_TRY(sum_order(c, m, ps, d_mats, k, plan, off_catoff, off_lens, off_total, st, &fk, &fv));
+  return links_to_block(c, m, ps, plan->s, fk, fv, plan->blk, st, narrow);
 }
 
 // From sorted (key, value) links (equal keys adjacent) of the single segment
@@ -804,6 +821,8 @@ int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s,
     return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
   cudaError_t e;
+  if ((e = launch_zero(m + ps.col_hist, kColPasses * kRadix * 4, st)) != cudaSuccess)
+    return fail_blk(e, "memset");
   uint64_t* pre = at<uint64_t>(m, ps.pre);
   if ((e = timed(c, "scan_u64", st, [&] { return launch_scan_u64(s, fv, pre, at<uint64_t>(m, ps.lb2), tickets + kPasses + 1, c->d_err, st); })) !=
       cudaSuccess)
@@ -882,6 +901,9 @@ std::string launch_sig(uint32_t flags, bool any_tiles, bool any_small, bool any_
 // context's graph cache.
 template <typename F>
 int run_launches(ans_ctx* c, cudaStream_t st, const std::string& key, F&& fn) {
+  if (!c->side) ANS_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  if (!c->ev_fork) ANS_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  if (!c->ev_join) ANS_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   if (!c->graph || c->prof.on) return fn(st);
   if (!c->cap) ANS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   ANS_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -1126,6 +1148,10 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   // CUDA graph.  Host-side state is only read here.
   auto launch_all = [&](cudaStream_t ls) -> int {
     int rc = ANS_OK;
+    // With merge rounds, the sum's first half runs on the side stream from
+    // the end of the window statistics, beside the window column pass.
+    bool forked = false;
+    const uint64_t *sfk = nullptr, *sfv = nullptr;
     uint64_t* ka = at<uint64_t>(m, ps.keys_a);
     uint64_t* kb = at<uint64_t>(m, ps.keys_b);
     uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
@@ -1220,12 +1246,25 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       if ((rc = cu(timed(c, "empty_fixup", ls, [&] { return launch_empty_fixup(a, ls); }), "empty"))) return rc;
       if ((rc = cu(timed(c, "rle", ls, [&] { return launch_rle(a, ls); }), "rle"))) return rc;
       if ((rc = cu(timed(c, "finish", ls, [&] { return launch_finish(a, ls); }), "finish"))) return rc;
-      if (c->col_hash &&
-          (rc = cu(timed(c, "colhash", ls, [&] {
-                     return launch_colhash(pw, a.ulen, sb.col_ids, a.vals32, sb.q, ls);
-                   }), "colhash")))
-        return rc;
-      if ((rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls, true))) return rc;
+      if (want_sum && c->sum_path == 0) {
+        if ((rc = cu(cudaEventRecord(c->ev_fork, ls), "event")) ||
+            (rc = cu(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "event")))
+          return rc;
+        forked = true;
+        rc = sum_order(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, c->side,
+                       &sfk, &sfv);
+        const cudaError_t ej = cudaEventRecord(c->ev_join, c->side);
+        if (rc == ANS_OK) rc = cu(ej, "event");
+      }
+      if (rc == ANS_OK && c->col_hash)
+        rc = cu(timed(c, "colhash", ls, [&] { return launch_colhash(pw, a.ulen, sb.col_ids, a.vals32, sb.q, ls); }),
+                "colhash");
+      if (rc == ANS_OK) rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls, true);
+      if (forked) {  // join (also after a failure, so that a capture ends joined)
+        const cudaError_t ew = cudaStreamWaitEvent(ls, c->ev_join, 0);
+        if (rc == ANS_OK) rc = cu(ew, "event");
+      }
+      if (rc) return rc;
     }
 
     if (want_sum) {
@@ -1234,9 +1273,11 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         if ((rc = cu(launch_zero(sblk->row_ptr, 8, ls), "memset"))) return rc;
         if ((rc = cu(launch_zero(sblk->hdr, 16, ls), "memset"))) return rc;
         if ((rc = cu(launch_zero(sblk->q, sizeof(ans_quantities), ls), "memset"))) return rc;
+      } else if (forked) {  // a sum of window counts stays below the batch's packets
+        if ((rc = links_to_block(c, m, ps, sump.s, sfk, sfv, sump.blk, ls, total < (1ull << 32)))) return rc;
       } else {
         rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, ls,
-                        total < (1ull << 32));  // a sum of window counts stays below the batch's packets
+                        total < (1ull << 32));
         if (rc) return rc;
       }
     }
@@ -1384,7 +1425,6 @@ int drop_zeros(ans_ctx* c, Block* blk, uint64_t cap, cudaStream_t st, Block** ou
                                    at<uint64_t>(m, off_lens), at<uint64_t>(m, off_total), st), "count")) ||
       (rc = cu(launch_zero(m + ps.lb, (size_t)sp.ntiles * 8, st), "zero")) ||
       (rc = cu(launch_zero(m + ps.lb2, (size_t)sp.ntiles * 8, st), "zero")) ||
-      (rc = cu(launch_zero(m + ps.col_hist, kColPasses * kRadix * 4, st), "zero")) ||
       (rc = cu(launch_gather(plan.g, at<MatDesc>(m, off_mats), cat_off, ka, va, nullptr, at<uint64_t>(m, ps.st0),
                              tickets, st), "gather")) ||
       (rc = cu(launch_nonzero_flags(s, va, flags, c->d_err, st), "flags")) ||
@@ -1593,6 +1633,11 @@ int ans_ctx_destroy(ans_ctx* c) {
     c->graphs.clear();
     if (c->cap) cudaStreamDestroy(c->cap);
     c->cap = nullptr;
+    if (c->side) cudaStreamDestroy(c->side);
+    c->side = nullptr;
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->ev_fork = c->ev_join = nullptr;
     for (auto& kv : c->prof.pending) {
       cudaEventDestroy(kv.a);
       cudaEventDestroy(kv.b);

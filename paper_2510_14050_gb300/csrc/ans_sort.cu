@@ -329,8 +329,9 @@ constexpr size_t kGatherSmem = 2 * (size_t)(kTile + 1) * sizeof(uint32_t);
 // unless sum_hist is null, accumulates the digit histograms of the single
 // time-sum segment.  The rows
 // that cover the tile (at most one per link) are staged in shared memory, so
-// each link finds its row by a binary search there.  Also zeroes the sum
-// sort's first status words and tickets (k_hist's other duties).
+// each link finds its row by a binary search there.  Also zeroes the tickets
+// and, unless status0 is null, the sum sort's first status words (k_hist's
+// other duties).
 __global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* __restrict__ mats,
                                                      const uint64_t* __restrict__ cat_off,
                                                      uint64_t* __restrict__ keys, uint64_t* __restrict__ vals,
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(SegPlan p, const MatDesc* _
   const Tile tl = block_tile(p, t, &s_tile);
   for (int i = threadIdx.x; i < kPasses * kRadix; i += kThreads) h[i] = 0;
   if (t == 0 && threadIdx.x < 32) tickets[threadIdx.x] = 0;
-  if (threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  if (status0 && threadIdx.x < kRadix) status0[(uint64_t)t * kRadix + threadIdx.x] = 0;
   if (tl.count == 0) return;
   const MatDesc m = mats[tl.seg];
   __shared__ uint64_t s_r1;
