@@ -745,10 +745,15 @@ int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s,
 // only the sum's own scratch (keys and values ping-pong, run offsets, the
 // look-back words lb / lb2, the digit histograms, the tickets at 32..63) --
 // with sum_path 0 none of what a window column pass uses, so it may run
-// beside one (col_hist is cleared by the second half).  Only queues work.
+// beside one (col_hist is cleared by the second half).  in_keys / in_vals /
+// run_base (merge rounds only): the input links already lie as sorted runs
+// at run_base[m] (the window statistics wrote their keys beside the stored
+// values), so the gather is skipped and the first round reads them in
+// place.  Only queues work.
 int sum_order(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats, uint32_t k, SumPlan* plan,
               size_t off_catoff, size_t off_lens, size_t off_total, cudaStream_t st, const uint64_t** fk_out,
-              const uint64_t** fv_out) {
+              const uint64_t** fv_out, const uint64_t* run_base = nullptr, const uint64_t* in_keys = nullptr,
+              const uint64_t* in_vals = nullptr) {
   const HostPlan& sp = plan->sp;
   const SegPlan& g = plan->g;
   const SegPlan& s = plan->s;
@@ -776,21 +781,35 @@ int sum_order(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats,
   // gather plan has at least as many tiles as the sum plan)
   const bool merge = c->sum_path == 0;
   const uint64_t* cat_off = at<uint64_t>(m, off_catoff);
-  if ((e = timed(c, "gather", st, [&] {
-         return launch_gather(g, d_mats, cat_off, ka, va, merge ? nullptr : seg_hist,
-                              merge ? nullptr : at<uint64_t>(m, ps.st0), tickets, st);
-       })) != cudaSuccess)
+  const bool in_place = merge && run_base;
+  if (in_place) {
+    if ((e = launch_zero(tickets, 32 * 4, st)) != cudaSuccess) return fail_blk(e, "memset");
+  } else if ((e = timed(c, "gather", st, [&] {
+                return launch_gather(g, d_mats, cat_off, ka, va, merge ? nullptr : seg_hist,
+                                     merge ? nullptr : at<uint64_t>(m, ps.st0), tickets, st);
+              })) != cudaSuccess) {
     return fail_blk(e, "gather");
-  uint64_t *fk = ka, *fv = va;  // the sorted links
+  }
+  const uint64_t *fk = ka, *fv = va;  // the sorted links
   if (merge) {
-    uint64_t *ok = kb, *ov = vb;
+    const uint64_t* rb = in_place ? run_base : nullptr;
+    if (in_place) {
+      fk = in_keys;
+      fv = in_vals;
+    }
+    uint64_t *ok = in_place ? ka : kb, *ov = in_place ? va : vb;
     for (int round = 0; (1ull << round) < k; ++round) {
       if ((e = timed(c, "merge", st, [&] {
-             return launch_merge(cat_off, k, sp.pad, round, fk, fv, ok, ov, st);
+             return launch_merge(cat_off, rb, k, sp.pad, round, fk, fv, ok, ov, st);
            })) != cudaSuccess)
         return fail_blk(e, "merge");
-      std::swap(fk, ok);
-      std::swap(fv, ov);
+      // the next round reads what this one wrote and writes the other pair
+      // (never the window values the first round may have read in place)
+      uint64_t *nk = ok == ka ? kb : ka, *nv = ov == va ? vb : va;
+      fk = ok;
+      fv = ov;
+      ok = nk;
+      ov = nv;
     }
   } else {
     rc = sort_segments(c, s, ka, kb, va, vb, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1), tickets, st);
@@ -1243,6 +1262,11 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       a.col_tickets = tickets + 2 * 32;
       a.err = c->d_err;
       a.mode = mode;
+      // With merge rounds, the run reduction also writes each link's key
+      // beside its stored value (keys_b at the window's padded base): the
+      // windows' links are then the time sum's sorted input runs in place.
+      const bool in_place = want_sum && c->sum_path == 0;
+      if (in_place) a.sum_keys = kb;
       if ((rc = cu(timed(c, "empty_fixup", ls, [&] { return launch_empty_fixup(a, ls); }), "empty"))) return rc;
       if ((rc = cu(timed(c, "rle", ls, [&] { return launch_rle(a, ls); }), "rle"))) return rc;
       if ((rc = cu(timed(c, "finish", ls, [&] { return launch_finish(a, ls); }), "finish"))) return rc;
@@ -1252,7 +1276,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
           return rc;
         forked = true;
         rc = sum_order(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, c->side,
-                       &sfk, &sfv);
+                       &sfk, &sfv, p.base, kb, sb.vals);
         const cudaError_t ej = cudaEventRecord(c->ev_join, c->side);
         if (rc == ANS_OK) rc = cu(ej, "event");
       }

@@ -90,6 +90,10 @@ struct StatsArgs {
   uint64_t* col_st0 = nullptr;    // first column pass's status words (zeroed here)
   uint32_t* col_tickets = nullptr;  // the column passes' tickets (zeroed here)
   uint32_t* err = nullptr;
+  // Optional (window mode): each link's key (src << 32 | dst) also written
+  // at base[s] + u, beside its column id -- with the link values this is the
+  // time sum's input run of the window, read in place by the merge.
+  uint64_t* sum_keys = nullptr;
   int mode = 0;
 };
 
@@ -196,11 +200,15 @@ cudaError_t launch_hash_compact(const SegPlan& pc, const HashTabs& h, uint64_t* 
 
 // ---- launchers (ans_merge.cu) --------------------------------------------
 // One round of pairwise merges of sorted (key, value) runs: runs of 2^round
-// matrices of the concatenation described by cat_off (k + 1 starts on the
-// device) are merged pairwise from kin/vin into kout/vout at the same
-// offsets.  total_cap bounds cat_off[k] (it sizes the grid).
-cudaError_t launch_merge(const uint64_t* cat_off, uint32_t k, uint64_t total_cap, int round, const uint64_t* kin,
-                         const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st);
+// matrices of the concatenation described by cat_off (k + 1 dense starts on
+// the device) are merged pairwise from kin/vin into kout/vout.  Matrix m's
+// items sit at run_base[m] (device, k entries, nondecreasing, with room for
+// each matrix's items before the next one's base; null: at cat_off[m]); a
+// merged run is written from the base of its first matrix, so the last
+// round leaves all items dense from run_base[0] = 0.  total_cap bounds
+// cat_off[k] (it sizes the grid).
+cudaError_t launch_merge(const uint64_t* cat_off, const uint64_t* run_base, uint32_t k, uint64_t total_cap, int round,
+                         const uint64_t* kin, const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st);
 
 // ---- launchers (ans_stats.cu) --------------------------------------------
 // Signed combinations: flags[u] = (vals[u] != 0) over the single segment of

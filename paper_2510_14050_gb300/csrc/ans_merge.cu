@@ -46,9 +46,12 @@ __device__ __forceinline__ uint64_t co_rank_warp(const uint64_t* A, uint64_t na,
 
 constexpr size_t kMergeSmem = (size_t)kMergeTile * 8 * 2;  // the two slices, keys and values
 
-// cat_off: k + 1 run starts of round 0 (cat_off[k] = total).  Round `round`
-// merges pairs of runs of 2^round matrices each.
-__global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t* __restrict__ cat_off, uint32_t k, int round,
+// cat_off: k + 1 dense run starts of round 0 (cat_off[k] = total); run_base
+// (null: cat_off) where each matrix's items sit.  Round `round` merges pairs
+// of runs of 2^round matrices each; CTAs cover spans of dense output
+// positions.
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t* __restrict__ cat_off,
+                                                         const uint64_t* __restrict__ run_base, uint32_t k, int round,
                                                          const uint64_t* __restrict__ kin,
                                                          const uint64_t* __restrict__ vin, uint64_t* __restrict__ kout,
                                                          uint64_t* __restrict__ vout) {
@@ -76,8 +79,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t* __restr
     if (b_end <= o0) continue;
     const uint64_t na = b_beg - a_beg, nb = b_end - b_beg;
     const uint64_t x0 = (o0 > a_beg ? o0 : a_beg) - a_beg, x1 = umin64(o1, b_end) - a_beg;
-    const uint64_t* A = kin + a_beg;
-    const uint64_t* B = kin + b_beg;
+    // where the two runs and the merged run sit (a missing B run is empty)
+    const uint64_t pa = run_base ? run_base[j * 2 * width] : a_beg;
+    const uint64_t pb = run_base ? (nb ? run_base[j * 2 * width + width] : pa) : b_beg;
+    const uint64_t* A = kin + pa;
+    const uint64_t* B = kin + pb;
     if (threadIdx.x < 64) {
       const uint64_t c = co_rank_warp(A, na, B, nb, threadIdx.x < 32 ? x0 : x1);
       if ((threadIdx.x & 31) == 0) s_cut[threadIdx.x >> 5] = c;
@@ -88,15 +94,15 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t* __restr
     const uint32_t ca = (uint32_t)(a1 - a0), cb = (uint32_t)(b1 - b0);  // ca + cb = x1 - x0 <= kMergeTile
     for (uint32_t i = threadIdx.x; i < ca; i += kMergeThreads) {
       s_k[i] = A[a0 + i];
-      s_v[i] = vin[a_beg + a0 + i];
+      s_v[i] = vin[pa + a0 + i];
     }
     for (uint32_t i = threadIdx.x; i < cb; i += kMergeThreads) {
       s_k[ca + i] = B[b0 + i];
-      s_v[ca + i] = vin[b_beg + b0 + i];
+      s_v[ca + i] = vin[pb + b0 + i];
     }
     __syncthreads();
-    uint64_t* ko = kout + a_beg + x0;
-    uint64_t* vo = vout + a_beg + x0;
+    uint64_t* ko = kout + pa + x0;
+    uint64_t* vo = vout + pa + x0;
     for (uint32_t i = threadIdx.x; i < ca + cb; i += kMergeThreads) {
       const uint64_t key = s_k[i];
       uint32_t pos;
@@ -124,8 +130,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t* __restr
 
 }  // namespace
 
-cudaError_t launch_merge(const uint64_t* cat_off, uint32_t k, uint64_t total_cap, int round, const uint64_t* kin,
-                         const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st) {
+cudaError_t launch_merge(const uint64_t* cat_off, const uint64_t* run_base, uint32_t k, uint64_t total_cap, int round,
+                         const uint64_t* kin, const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st) {
   const uint64_t blocks = (total_cap + kMergeTile - 1) / kMergeTile;
   if (blocks == 0) return cudaSuccess;
   static unsigned long long configured = 0;  // one bit per device ordinal
@@ -137,7 +143,7 @@ cudaError_t launch_merge(const uint64_t* cat_off, uint32_t k, uint64_t total_cap
     if (e != cudaSuccess) return e;
     if (dev < 64) configured |= 1ull << dev;
   }
-  k_merge<<<(unsigned)blocks, kMergeThreads, kMergeSmem, st>>>(cat_off, k, round, kin, vin, kout, vout);
+  k_merge<<<(unsigned)blocks, kMergeThreads, kMergeSmem, st>>>(cat_off, run_base, k, round, kin, vin, kout, vout);
   return cudaGetLastError();
 }
 

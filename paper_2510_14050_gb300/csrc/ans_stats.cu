@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_rle(StatsArgs a) {
     if ((hb[i] >> lane) & 1u) {
       const uint64_t u = uh + __popc(hb[i] & lt);
       a.col_ids[tl.base + u] = (uint32_t)k[i];
+      if (a.sum_keys) a.sum_keys[tl.base + u] = k[i];
       if (a.run_start) a.run_start[bs + u] = tl.start + idx;
       if ((rb[i] >> lane) & 1u) {
         const uint64_t r = ur + __popc(rb[i] & lt);
