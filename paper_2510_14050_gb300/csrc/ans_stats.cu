@@ -27,7 +27,7 @@ namespace {
 
 constexpr uint64_t kLow31 = (1ull << 31) - 1;
 
-__global__ void __launch_bounds__(kThreads) k_rle(StatsArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_rle(StatsArgs a) {
   __shared__ uint32_t s_ticket;
   __shared__ Tile s_tile;
   __shared__ uint32_t s_wh[kWarps], s_wr[kWarps];
