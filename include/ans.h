@@ -284,9 +284,10 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
  * keeps, per family, the configuration with the least total pass time; it
  * then times the on-chip window sort (win_path 0, three cluster
  * configurations) and keeps it if the batch's windows sort faster that way
- * than by the best key passes plus their histogram sweep, likewise picks the
- * faster sum_path, and finally the agg_path with the smaller total kernel
- * time of the whole batch.  An optional path whose trial cannot get its
+ * than by the best key passes plus their histogram sweep, and finally picks
+ * sum_path, then agg_path, by the batch's device time as submitted (one
+ * CUDA graph with its concurrent branches, between CUDA events on
+ * `stream`, the host's planning included).  An optional path whose trial cannot get its
  * device memory (ANS_ERR_OOM / ANS_ERR_BUDGET) is skipped; the call fails
  * with ANS_ERR_OOM only if the default paths do not fit.  The choice is applied to the context and returned in *chosen (optional).  The
  * call blocks until the runs have finished; it leaves per-kernel profiling

@@ -2045,9 +2045,13 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     return ANS_OK;
   };
   // One trial: apply `set` to the context, run the batch once untimed (module
-  // load, shared-memory carve-out), then twice with per-kernel timing; the
-  // kernel totals go to *out.  A trial that cannot get its memory (a path the
-  // device cannot hold for this batch) reports false instead of failing.
+  // load, shared-memory carve-out), then twice with per-kernel timing (the
+  // kernel totals go to *out) and twice as the production path runs it (one
+  // graph with its concurrent branches, no per-kernel events): the least
+  // device time of those two, between CUDA events on `stream`, goes to
+  // (*out)[kWall].  A trial that cannot get its memory (a path the device
+  // cannot hold for this batch) reports false instead of failing.
+  const std::string kWall = "(batch)";
   auto trial = [&](auto&& set, Prof* out, bool* ran) -> int {
     {
       std::lock_guard<std::mutex> g(c->mu);
@@ -2059,22 +2063,49 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       ANS_TRY(ans_profile_enable(c, 1));
       for (int rep = 0; rep < 2 && rc == ANS_OK; ++rep) rc = run_once();
     }
-    std::lock_guard<std::mutex> g(c->mu);
-    DeviceGuard dg(c->device);
-    prof_collect(c);
-    out->clear();
-    for (const auto& kv : c->prof.acc) (*out)[kv.first] = kv.second.first;
-    c->prof.acc.clear();
-    c->prof.on = false;
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      DeviceGuard dg(c->device);
+      prof_collect(c);
+      out->clear();
+      for (const auto& kv : c->prof.acc) (*out)[kv.first] = kv.second.first;
+      c->prof.acc.clear();
+      c->prof.on = false;
+    }
+    double wall = 1e300;
+    if (rc == ANS_OK) {
+      DeviceGuard dg(c->device);
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(ANS_ERR_CUDA, "cudaEventCreate failed");
+      }
+      for (int rep = 0; rep < 2 && rc == ANS_OK; ++rep) {
+        cudaEventRecord(e0, (cudaStream_t)stream);
+        ans_matrix* sum = nullptr;
+        rc = ans_batch_submit(c, d_src, d_dst, h_offsets, nwin, ANS_BATCH_MATRICES | ANS_BATCH_SUM, nullptr,
+                              per.data(), &sum, nullptr, stream);
+        cudaEventRecord(e1, (cudaStream_t)stream);
+        if (rc == ANS_OK) {
+          float ms = 0;
+          if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+            wall = std::min(wall, (double)ms);
+          for (auto& m : per) {
+            ans_matrix_free(m);
+            m = nullptr;
+          }
+          ans_matrix_free(sum);
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    (*out)[kWall] = wall;
     if (rc == ANS_ERR_OOM || rc == ANS_ERR_BUDGET) return ANS_OK;
     if (rc == ANS_OK) *ran = true;
     return rc;
   };
-  auto total = [](const Prof& p) {
-    double t = 0;
-    for (const auto& kv : p) t += kv.second;
-    return t;
-  };
+
   auto get = [](const Prof& p, const char* k) {
     auto it = p.find(k);
     return it == p.end() ? 0.0 : it->second;
@@ -2138,26 +2169,30 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     }
   }
 
-  // Time sums: pairwise merges against the kv passes (each with its gather).
-  int sum_path = 1;
+  // Time sums (pairwise merges, whose ordering runs beside the window column
+  // pass, against the kv passes) and then window aggregation (hash counting
+  // against sorting every packet): each by the batch's device time as the
+  // production path runs it, everything else as chosen.
+  int sum_path = 0;
   {
-    Prof pr;
-    bool ran = false;
-    ANS_TRY(trial([&] {
-      base();
-      c->win_path = win_path;
-      c->cfg_win = win_cfg;
-      c->sum_path = 0;
-      c->agg_path = 0;
-    }, &pr, &ran));
-    if (ran && get(pr, "merge") + get(pr, "gather") < t_kv[bv_i]) sum_path = 0;
+    double wall[2] = {kNever, kNever};
+    for (int sp = 0; sp < 2; ++sp) {
+      Prof pr;
+      bool ran = false;
+      ANS_TRY(trial([&] {
+        base();
+        c->win_path = win_path;
+        c->cfg_win = win_cfg;
+        c->sum_path = sp;
+        c->agg_path = 0;
+      }, &pr, &ran));
+      if (ran) wall[sp] = pr[kWall];
+    }
+    sum_path = wall[1] < wall[0] ? 1 : 0;
   }
-
-  // Window aggregation: hash counting against sorting every packet, by the
-  // whole batch's kernel time with everything else as chosen.
   int agg_path = 0;
   {
-    double tot[2] = {kNever, kNever};
+    double wall[2] = {kNever, kNever};
     for (int a = 0; a < 2; ++a) {
       Prof pr;
       bool ran = false;
@@ -2168,9 +2203,9 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
         c->sum_path = sum_path;
         c->agg_path = a;
       }, &pr, &ran));
-      if (ran) tot[a] = total(pr);
+      if (ran) wall[a] = pr[kWall];
     }
-    agg_path = tot[1] < tot[0] ? 1 : 0;
+    agg_path = wall[1] < wall[0] ? 1 : 0;
   }
 
   ans_tuning res{};
