@@ -237,8 +237,10 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * 1 = eight ballots per key, 2 = a per-warp shared-memory table (each lane
  * ORs its bit into its digit's entry, which also carries the digit's count).  *_blocks: CTAs per SM the kernel is compiled
  * for, 1, or 2 (512 threads only: registers capped at 64).  The key passes
- * also take key_threads 256 with key_blocks 4: every 8192-key tile is split
- * into two 4096-key sub-tiles, one CTA each, four CTAs resident per SM.
+ * and the column passes also take 256 threads with blocks 4: every 8192-key
+ * tile is split into two 4096-key sub-tiles, one CTA each, four CTAs
+ * resident per SM (column passes carrying 64-bit counts then run the
+ * 512-thread shape).
  * win_path: how window keys are sorted, 0 = on chip, one 8-CTA thread-block
  * cluster per window of at most 2^17 packets sorting it in distributed shared
  * memory (larger windows, and every window when the device cannot host such

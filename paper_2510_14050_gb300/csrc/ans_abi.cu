@@ -1989,12 +1989,13 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   auto ok = [](uint32_t th, uint32_t rk, uint32_t bl) {
     return (th == 512 || th == 1024) && rk <= 2 && (bl == 1 || (bl == 2 && th == 512));
   };
-  const bool key_sub = t->key_threads == 256 && t->key_rank <= 2 && t->key_blocks == 4;
-  if (!(key_sub || ok(t->key_threads, t->key_rank, t->key_blocks)) || !ok(t->kv_threads, t->kv_rank, t->kv_blocks) ||
-      !ok(t->col_threads, t->col_rank, t->col_blocks))
+  auto sub = [](uint32_t th, uint32_t rk, uint32_t bl) { return th == 256 && rk <= 2 && bl == 4; };
+  if (!(sub(t->key_threads, t->key_rank, t->key_blocks) || ok(t->key_threads, t->key_rank, t->key_blocks)) ||
+      !ok(t->kv_threads, t->kv_rank, t->kv_blocks) ||
+      !(sub(t->col_threads, t->col_rank, t->col_blocks) || ok(t->col_threads, t->col_rank, t->col_blocks)))
     return fail(ANS_ERR_INVALID_ARG,
-                "threads must be 512 or 1024, rank 0, 1 or 2, blocks 1 (or 2 with 512 threads); key passes also "
-                "take 256 threads with blocks 4");
+                "threads must be 512 or 1024, rank 0, 1 or 2, blocks 1 (or 2 with 512 threads); key and column "
+                "passes also take 256 threads with blocks 4");
   if (t->win_path > 1 || t->win_rank > 1 || !ok(t->win_threads, t->win_rank, 1))
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
   if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
@@ -2024,7 +2025,8 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
 int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets, size_t nwin,
                  ans_tuning* chosen, void* stream) {
   if (!c || !h_offsets || nwin == 0) return fail(ANS_ERR_INVALID_ARG, "NULL argument or empty batch");
-  // The last kKeyOnly shapes exist for the 64-bit key passes only.
+  // The last kKeyOnly shapes exist for the key and column passes only (not
+  // for the kv passes).
   constexpr int kVariants = 12, kKeyOnly = 3;
   const SortCfg variants[kVariants] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankTable, 1},
                                        {512, kRankMatch, 2}, {512, kRankBallot, 2}, {512, kRankTable, 2},
@@ -2120,7 +2122,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     bool ran = false;
     ANS_TRY(trial([&] {
       c->cfg_keys = c->cfg_kv = c->cfg_col = variants[key_only ? 0 : v];
-      c->cfg_keys = variants[v];
+      c->cfg_keys = c->cfg_col = variants[v];
       c->win_path = 1;  // the key passes on every window
       c->sum_path = 1;  // the kv passes on the time sum
       c->agg_path = 0;
@@ -2128,7 +2130,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     if (!ran) return fail(ANS_ERR_OOM, "autotune: the batch does not fit the device with the default paths");
     t_keys[v] = get(pr, "onesweep") + get(pr, "pack_hist");
     t_kv[v] = key_only ? kNever : get(pr, "onesweep_sum") + get(pr, "gather");
-    t_col[v] = key_only ? kNever : get(pr, "onesweep_col");
+    t_col[v] = get(pr, "onesweep_col");
   }
   auto best = [&](const double* t) {
     int b = 0;

@@ -43,9 +43,9 @@ enum ErrBits : uint32_t {
 };
 
 // How a onesweep pass is launched (chosen per context by the autotuner):
-// threads per 8192-key tile (512 or 1024; for the 64-bit key passes also 256,
-// which splits every tile into two 4096-key sub-tiles with one CTA each and
-// four resident CTAs per SM), how lanes with equal digits are found (one
+// threads per 8192-key tile (512 or 1024; for the 64-bit key passes and the
+// column passes with 32-bit counts also 256, which splits every tile into
+// two 4096-key sub-tiles with one CTA each and four resident CTAs per SM), how lanes with equal digits are found (one
 // __match_any_sync; eight ballots; or a per-warp shared-memory table where
 // each lane ORs its bit into its digit's entry, which also holds the digit's
 // running count), and whether a 512-thread tile is compiled to leave room for

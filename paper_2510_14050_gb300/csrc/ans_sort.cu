@@ -466,7 +466,8 @@ cudaError_t run_onesweep(const SegPlan& p, int pass, const K* kin, K* kout, cons
 #define ANS_OS(T, R, B)                                                                                        \
   return run_onesweep_variant<K, V, T, R, B>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, \
                                              err, st)
-  if constexpr (std::is_same<K, uint64_t>::value && std::is_same<V, NoVal>::value) {
+  if constexpr ((std::is_same<K, uint64_t>::value && std::is_same<V, NoVal>::value) ||
+                (std::is_same<K, uint32_t>::value && std::is_same<V, uint32_t>::value)) {
     if (cfg.threads == 256) {  // two 4096-key sub-tiles per tile, four CTAs per SM
       if (cfg.rank == kRankBallot)
         return run_onesweep_variant<K, V, 256, kRankBallot, 4, 2>(p, pass, kin, kout, vin, vout, seg_hist, st_cur,

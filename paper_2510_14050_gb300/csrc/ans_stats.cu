@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
   // Prepare the column sort: its first-pass status words, its tickets and
   // the number of links per segment.
   if (t == 0 && threadIdx.x < 32) a.col_tickets[threadIdx.x] = 0;
-  if (threadIdx.x < kRadix) a.col_st0[(uint64_t)t * kRadix + threadIdx.x] = 0;
+  // (two sub-tiles' worth per tile: the column passes may run sub-tiles)
+  for (uint32_t i = threadIdx.x; i < 2 * kRadix; i += kThreads) a.col_st0[(uint64_t)t * 2 * kRadix + i] = 0;
   if (tl.j == 0 && threadIdx.x == 0) a.ulen[s] = nnz;
   __syncthreads();
 

@@ -267,20 +267,27 @@ def test_every_sort_configuration_is_exact(ans, synth, threads, rank, blocks):
 
 @pytest.mark.parametrize("rank", [0, 1, 2])
 def test_key_passes_over_subtiles_are_exact(ans, synth, rank):
-    """Key passes that split every tile into two 4096-key sub-tiles give the
-    same results: windows ending inside either half of a tile, exactly at
-    the half, one key past it, empty and single-packet windows, and the
-    one-window path."""
+    """Key and column passes that split every tile into two 4096-key
+    sub-tiles give the same results: windows ending inside either half of a
+    tile, exactly at the half, one key past it, empty and single-packet
+    windows, windows the column hash leaves to the column sort, the time sum,
+    and the one-window path."""
     h = KT // 2
     w = synth.generate(5, sizes=[KT * 3 + 17, 0, h, h + 1, h - 1, 1, 2 * KT, KT + h, 40000])
+    src, dst = w.src.copy(), w.dst.copy()
+    a, b = int(w.offsets[8]), int(w.offsets[9])
+    dst[a:b] = np.random.default_rng(rank).integers(0, 1 << 32, b - a, dtype=np.uint64).astype(np.uint32)
+    from paper_2510_14050_gb300 import synth as sy
+    w = sy.Windows(src, dst, w.offsets)
     c = ans.Context(0)
     try:
-        c.set_tuning(key_threads=256, key_rank=rank, key_blocks=4, win_path=1)
-        assert c.get_tuning()["key_threads"] == 256
+        c.set_tuning(key_threads=256, key_rank=rank, key_blocks=4, col_threads=256, col_rank=rank, col_blocks=4,
+                     win_path=1)
+        assert c.get_tuning()["key_threads"] == 256 and c.get_tuning()["col_threads"] == 256
         check_batch(ans, c, w)
         check_window(c, *w.window(8), "one window").free()
         for bad in ({"key_threads": 256, "key_blocks": 2}, {"kv_threads": 256, "kv_blocks": 4},
-                    {"col_threads": 256, "col_blocks": 4}):
+                    {"col_threads": 256, "col_blocks": 2}):
             with pytest.raises(ans.AnsError) as ei:
                 c.set_tuning(**bad)
             assert ei.value.code == ans.ERR_INVALID_ARG
