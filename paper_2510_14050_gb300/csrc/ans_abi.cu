@@ -1309,7 +1309,10 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   };
   int rounds = 0;
   while ((1ull << rounds) < nseg) ++rounds;
-  const std::string sig = launch_sig(flags, hp.ntiles > 0, !small_ids.empty(), !big_ids.empty(), rounds, c);
+  // the column hash's cluster shape changes with the window count: a cached
+  // graph must not be updated to another one
+  const std::string sig = launch_sig(flags, hp.ntiles > 0, !small_ids.empty(), !big_ids.empty(), rounds, c) + "/h" +
+                          std::to_string(c->col_hash && nseg ? colhash_ctas(nseg) : 0u);
   if ((rc = run_launches(c, st, sig, launch_all))) return bail(rc);
   if (sump.blk) {  // the time sum's block is filled
     sblk = sump.blk;

@@ -239,6 +239,9 @@ cudaError_t launch_colstat32(const SegPlan& p, const uint32_t* keys, const uint3
 // Canonical-DCSR check of an imported matrix; ORs failure bits into *bad.
 cudaError_t launch_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* row_ids, const uint64_t* row_ptr,
                               const uint32_t* col_ids, const uint64_t* vals, uint32_t* bad, cudaStream_t st);
+// CTAs per window launch_colhash uses for a batch of nseg windows (its
+// launch shape: part of the key of a cached batch graph).
+uint32_t colhash_ctas(uint32_t nseg);
 // Window column statistics from a shared-memory hash of destinations, one
 // CTA per window of p (links: col_ids / vals32 at base[s], ulen[s] of them);
 // a window whose distinct destinations fit gets its three column quantities

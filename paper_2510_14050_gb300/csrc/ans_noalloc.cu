@@ -44,9 +44,11 @@ constexpr size_t oPlan = 0;                                        // in_off, le
 constexpr size_t oKeysA = al(oPlan + 64);
 constexpr size_t oKeysB = al(oKeysA + kNoAllocMaxPackets * 8);
 constexpr size_t oHist = al(oKeysB + kNoAllocMaxPackets * 8);
+// look-back status words: two sub-tiles' worth per tile (k_finish clears
+// that many for the column passes)
 constexpr size_t oSt0 = al(oHist + (size_t)kPasses * kRadix * 4);
-constexpr size_t oSt1 = al(oSt0 + (size_t)kNoAllocTiles * kRadix * 8);
-constexpr size_t oLb = al(oSt1 + (size_t)kNoAllocTiles * kRadix * 8);
+constexpr size_t oSt1 = al(oSt0 + (size_t)kNoAllocTiles * 2 * kRadix * 8);
+constexpr size_t oLb = al(oSt1 + (size_t)kNoAllocTiles * 2 * kRadix * 8);
 constexpr size_t oTickets = al(oLb + (size_t)kNoAllocTiles * 8);
 constexpr size_t oRunStart = al(oTickets + 128 * 4);
 constexpr size_t oRowPos = al(oRunStart + (kNoAllocMaxPackets + 1) * 8);

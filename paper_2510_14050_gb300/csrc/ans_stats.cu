@@ -732,6 +732,10 @@ __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_cl(SegPlan p, ui
   __shared__ unsigned long long s_red[3][kColHashThreads / 32];
   const uint32_t me = cta_rank(), nc = cluster_nctarank();
   const uint32_t s = cluster_id();
+  // A launch whose grid is not one cluster per window (the same for every
+  // CTA, so all leave before any cluster barrier) counts nothing: its
+  // windows keep their ulen and the column sort takes them.
+  if (gridDim.x != p.nseg * nc || gridDim.y != 1 || gridDim.z != 1) return;
   const uint64_t n = s < p.nseg ? ulen[s] : 0;
   const uint64_t b = s < p.nseg ? p.base[s] : 0;
   for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
@@ -879,6 +883,8 @@ uint32_t colhash_cluster_size(uint32_t nseg) {
 }
 
 }  // namespace
+
+uint32_t colhash_ctas(uint32_t nseg) { return nseg ? colhash_cluster_size(nseg) : 1u; }
 
 cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
                            ans_quantities* q, cudaStream_t st) {

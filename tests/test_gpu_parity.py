@@ -641,6 +641,25 @@ def test_column_hash_over_clusters(ans, nwin):
         c.close()
 
 
+def test_graph_cache_follows_column_hash_shape(ans, synth):
+    """Batches whose window counts give the same merge depth but a different
+    column-hash cluster shape (19 windows: 8 CTAs per window; 20 or 21: 4;
+    38: 4; 39: 2) follow one another on one context, replayed as graphs;
+    every result equals the oracle."""
+    c = ans.Context(0)
+    try:
+        for i, nwin in enumerate([19, 20, 19, 21, 38, 39, 38]):
+            w = synth.generate(5, sizes=synth.window_sizes(5, nwin, first_window=100 * i) // 16 + 1,
+                               first_window=100 * i)
+            _, summ, quants = run_batch(ans, c, w, ans.BATCH_SUM)
+            _, exp_q, exp_sum = oracle.batch(w.src, w.dst, w.offsets, want_sum=True)
+            assert quants == exp_q, f"batch {i} ({nwin} windows)"
+            assert summ.quantities() == oracle.network_quantities(exp_sum), f"batch {i} sum"
+            summ.free()
+    finally:
+        c.close()
+
+
 def test_sum_column_statistics_across_calls(ans, synth):
     """One context sums batches that grow (its scratch is replaced), shrink,
     repeat, include the all-ones destination and a destination that takes
