@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_u64(SegPlan p, const uint64_t
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_finish(StatsArgs a) {
   __shared__ Tile s_tile;
   __shared__ uint64_t s_red[3][kWarps];
   __shared__ uint32_t s_h[kColPasses * kRadix];
@@ -236,19 +236,50 @@ __global__ void __launch_bounds__(kThreads) k_finish(StatsArgs a) {
 
   uint64_t mlink = 0, mfan = 0, mrow = 0;
   const uint64_t u_end = umin64(tl.start + kTile, nnz);
-  for (uint64_t u = tl.start + threadIdx.x; u < u_end; u += kThreads) {
-    uint64_t v;
-    if (kMode == kModeMatrix) {
-      v = a.vals[tl.base + u];
-    } else {
-      v = (P(a.run_start[bs + u + 1]) - P(a.run_start[bs + u])) & kValMask;
-      a.vals[tl.base + u] = v;
-      if (a.vals32) a.vals32[tl.base + u] = (uint32_t)v;
-    }
-    mlink = v > mlink ? v : mlink;
-    const uint32_t dst = a.col_ids[tl.base + u];
+  // kU links per thread and step, their loads issued before any use (the
+  // loads of one link depend on one another, the links do not).
+  constexpr int kU = 4;
+  for (uint64_t u0 = tl.start + threadIdx.x; u0 < u_end; u0 += (uint64_t)kU * kThreads) {
+    uint64_t x0[kU], x1[kU];
+    uint32_t dst[kU];
 #pragma unroll
-    for (int p = 0; p < kColPasses; ++p) atomicAdd(&s_h[p * kRadix + ((dst >> (p * kRadixBits)) & 0xffu)], 1u);
+    for (int j = 0; j < kU; ++j) {
+      const uint64_t u = u0 + (uint64_t)j * kThreads;
+      x0[j] = x1[j] = 0;
+      dst[j] = 0;
+      if (u < u_end) {
+        if (kMode == kModeMatrix) {
+          x0[j] = a.vals[tl.base + u];
+        } else {
+          x0[j] = a.run_start[bs + u];
+          x1[j] = a.run_start[bs + u + 1];
+        }
+        dst[j] = a.col_ids[tl.base + u];
+      }
+    }
+    if (kMode != kModeMatrix && a.pre) {
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        if (u0 + (uint64_t)j * kThreads < u_end) {
+          x0[j] = a.pre[bs + x0[j]];
+          x1[j] = a.pre[bs + x1[j]];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const uint64_t u = u0 + (uint64_t)j * kThreads;
+      if (u >= u_end) continue;
+      const uint64_t v = kMode == kModeMatrix ? x0[j] : (x1[j] - x0[j]) & kValMask;
+      if (kMode != kModeMatrix) {
+        a.vals[tl.base + u] = v;
+        if (a.vals32) a.vals32[tl.base + u] = (uint32_t)v;
+      }
+      mlink = v > mlink ? v : mlink;
+#pragma unroll
+      for (int p = 0; p < kColPasses; ++p)
+        atomicAdd(&s_h[p * kRadix + ((dst[j] >> (p * kRadixBits)) & 0xffu)], 1u);
+    }
   }
   const uint64_t r_end = umin64(tl.start + kTile, nrows);
   for (uint64_t r = tl.start + threadIdx.x; r < r_end; r += kThreads) {
