@@ -18,6 +18,11 @@
 //    fan-in and its value sum the destination's packets (Table I, Sec. IV-C).
 //    Runs inside a tile are reduced in place; runs that cross tiles are
 //    completed from per-tile boundary records.
+//  * k_colhash / k_colhash_cl: the same three column quantities of a window
+//    from a shared-memory hash of its destinations (one CTA per window, or a
+//    thread-block cluster per window whose CTAs merge their tables over
+//    distributed shared memory); windows with more distinct destinations than
+//    the table takes are left to the column sort.
 // Maxima are combined with 64-bit atomicMax; every value is an exact integer.
 #include "ans_internal.cuh"
 
@@ -742,7 +747,7 @@ __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash(SegPlan p, uint6
 }
 
 // The same statistics with one cluster of C CTAs per window (launched with
-// clusters along x; cluster c takes window c; C a power of two): CTA r
+// clusters along x; cluster i takes window i; C a power of two): CTA r
 // counts links [r, r + 1) * ceil(n / C) of the window in its own table;
 // then, in log2(C) rounds, CTA r pulls the table of CTA r + 2^k (for r a
 // multiple of 2^(k+1)) over distributed shared memory and adds it into its
