@@ -334,7 +334,7 @@ def main():
         for part in args.tuning.split(";"):
             fam, vals = part.split("=")
             fam = fam.strip()
-            if fam.endswith("_path") or fam == "col_hash":  # e.g. agg_path=1; graph_path=0 sets graph
+            if fam.endswith("_path") or fam in ("col_hash", "merge_tile"):  # e.g. agg_path=1; graph_path=0 sets graph
                 kw["graph" if fam == "graph_path" else fam] = int(vals)
                 continue
             for field, v in zip(("threads", "rank", "blocks"), vals.split(",")):

@@ -260,7 +260,9 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * column statistics are first counted in a shared-memory hash of its
  * destinations (one CTA per window; up to 12288 distinct destinations), and
  * only windows with more take the column sort; 0 = the column sort for every
- * window.  Results never depend on the configuration. */
+ * window.  merge_tile: output positions per CTA of the time sum's merge
+ * rounds, 4096 or 2048 (more resident CTAs per SM, twice the merge-path
+ * searches).  Results never depend on the configuration. */
 typedef struct {
     uint32_t key_threads, key_rank, key_blocks;
     uint32_t kv_threads, kv_rank, kv_blocks;
@@ -270,11 +272,12 @@ typedef struct {
     uint32_t agg_path;
     uint32_t graph;
     uint32_t col_hash;
+    uint32_t merge_tile;
 } ans_tuning;
 
 /* Read / set a context's configuration (default: 512 threads, rank 0, one
  * block; win_path 1, win_threads 1024, win_rank 0; sum_path 0; agg_path 0;
- * graph 1; col_hash 1).
+ * graph 1; col_hash 1; merge_tile 4096).
  * ans_set_tuning fails with ANS_ERR_INVALID_ARG on values other than the
  * ones listed above. */
 int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);
@@ -287,7 +290,8 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
  * then times the on-chip window sort (win_path 0, three cluster
  * configurations) and keeps it if the batch's windows sort faster that way
  * than by the best key passes plus their histogram sweep, and finally picks
- * sum_path, then agg_path, by the batch's device time as submitted (one
+ * sum_path, merge_tile (with merge rounds), then agg_path, by the batch's
+ * device time as submitted (one
  * CUDA graph with its concurrent branches, between CUDA events on
  * `stream`, the host's planning included).  An optional path whose trial cannot get its
  * device memory (ANS_ERR_OOM / ANS_ERR_BUDGET) is skipped; the call fails

@@ -60,7 +60,7 @@ class Tuning(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in ("key_threads", "key_rank", "key_blocks", "kv_threads", "kv_rank",
                                             "kv_blocks", "col_threads", "col_rank", "col_blocks",
                                             "win_path", "win_threads", "win_rank", "sum_path",
-                                            "agg_path", "graph", "col_hash")]
+                                            "agg_path", "graph", "col_hash", "merge_tile")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

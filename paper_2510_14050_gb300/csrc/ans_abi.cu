@@ -139,6 +139,7 @@ struct ans_ctx {
   // Time sum: 0 = merge the matrices' sorted links pairwise, 1 = radix-sort
   // the gathered links (kv passes).
   int sum_path = 0;
+  int merge_tile = 4096;  // merge rounds: output positions per CTA (4096 or 2048)
   // Window aggregation: 0 = sort every packet's key, 1 = count links in
   // per-window hash tables and sort the distinct links.  The tables live in
   // their own arena, left empty by every call that used them (hash_dirty
@@ -800,7 +801,7 @@ int sum_order(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats,
     uint64_t *ok = in_place ? ka : kb, *ov = in_place ? va : vb;
     for (int round = 0; (1ull << round) < k; ++round) {
       if ((e = timed(c, "merge", st, [&] {
-             return launch_merge(cat_off, rb, k, sp.pad, round, fk, fv, ok, ov, st);
+             return launch_merge(cat_off, rb, k, sp.pad, round, fk, fv, ok, ov, c->merge_tile, st);
            })) != cudaSuccess)
         return fail_blk(e, "merge");
       // the next round reads what this one wrote and writes the other pair
@@ -910,7 +911,8 @@ int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n
 std::string launch_sig(uint32_t flags, bool any_tiles, bool any_small, bool any_big, int rounds, const ans_ctx* c) {
   std::string k = std::to_string(flags) + "/" + std::to_string(any_tiles) + std::to_string(any_small) +
                   std::to_string(any_big) + "/" + std::to_string(rounds) + "/" + std::to_string(c->win_path) +
-                  std::to_string(c->sum_path) + std::to_string(c->agg_path) + std::to_string(c->col_hash);
+                  std::to_string(c->sum_path) + std::to_string(c->agg_path) + std::to_string(c->col_hash) + "/" +
+                  std::to_string(c->merge_tile);
   for (const SortCfg* f : {&c->cfg_keys, &c->cfg_kv, &c->cfg_col, &c->cfg_win})
     k += "/" + std::to_string(f->threads) + std::to_string(f->rank) + std::to_string(f->blocks);
   return k;
@@ -1984,6 +1986,7 @@ int ans_get_tuning(ans_ctx* c, ans_tuning* out) {
   out->agg_path = (uint32_t)c->agg_path;
   out->graph = (uint32_t)c->graph;
   out->col_hash = (uint32_t)c->col_hash;
+  out->merge_tile = (uint32_t)c->merge_tile;
   return ANS_OK;
 }
 
@@ -2005,6 +2008,7 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   if (t->agg_path > 1) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0 or 1");
   if (t->graph > 1) return fail(ANS_ERR_INVALID_ARG, "graph must be 0 or 1");
   if (t->col_hash > 1) return fail(ANS_ERR_INVALID_ARG, "col_hash must be 0 or 1");
+  if (t->merge_tile != 2048 && t->merge_tile != 4096) return fail(ANS_ERR_INVALID_ARG, "merge_tile must be 2048 or 4096");
   std::lock_guard<std::mutex> g(c->mu);
   c->win_path = (int)t->win_path;
   c->cfg_win = SortCfg{(int)t->win_threads, (int)t->win_rank, 1};
@@ -2012,6 +2016,7 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   c->agg_path = (int)t->agg_path;
   c->graph = (int)t->graph;
   c->col_hash = (int)t->col_hash;
+  c->merge_tile = (int)t->merge_tile;
   if (c->agg_path == 0 && c->hash_mem) {  // the hash tables are no longer needed
     DeviceGuard dg(c->device);
     ANS_CUDA(cudaDeviceSynchronize());
@@ -2195,6 +2200,28 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     }
     sum_path = wall[1] < wall[0] ? 1 : 0;
   }
+  // Merge rounds: 4096 or 2048 output positions per CTA (the smaller tile
+  // fits more CTAs per SM; the larger needs fewer merge-path searches).
+  int merge_tile = 4096;
+  if (sum_path == 0) {
+    double wall[2] = {kNever, kNever};
+    const int tiles[2] = {4096, 2048};
+    for (int i = 0; i < 2; ++i) {
+      Prof pr;
+      bool ran = false;
+      ANS_TRY(trial([&] {
+        base();
+        c->win_path = win_path;
+        c->cfg_win = win_cfg;
+        c->sum_path = 0;
+        c->merge_tile = tiles[i];
+        c->agg_path = 0;
+      }, &pr, &ran));
+      if (ran) wall[i] = pr[kWall];
+    }
+    merge_tile = wall[1] < wall[0] ? 2048 : 4096;
+    c->merge_tile = merge_tile;
+  }
   int agg_path = 0;
   {
     double wall[2] = {kNever, kNever};
@@ -2231,6 +2258,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   res.agg_path = (uint32_t)agg_path;
   res.graph = (uint32_t)c->graph;
   res.col_hash = (uint32_t)c->col_hash;
+  res.merge_tile = (uint32_t)merge_tile;
   ANS_TRY(ans_set_tuning(c, &res));
   if (chosen) *chosen = res;
   return ANS_OK;

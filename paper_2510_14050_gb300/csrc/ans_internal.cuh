@@ -207,8 +207,10 @@ cudaError_t launch_hash_compact(const SegPlan& pc, const HashTabs& h, uint64_t* 
 // merged run is written from the base of its first matrix, so the last
 // round leaves all items dense from run_base[0] = 0.  total_cap bounds
 // cat_off[k] (it sizes the grid).
+// `tile`: output positions per CTA, 4096 or 2048.
 cudaError_t launch_merge(const uint64_t* cat_off, const uint64_t* run_base, uint32_t k, uint64_t total_cap, int round,
-                         const uint64_t* kin, const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st);
+                         const uint64_t* kin, const uint64_t* vin, uint64_t* kout, uint64_t* vout, int tile,
+                         cudaStream_t st);
 
 // ---- launchers (ans_stats.cu) --------------------------------------------
 // Signed combinations: flags[u] = (vals[u] != 0) over the single segment of

@@ -21,7 +21,6 @@ namespace ans {
 namespace {
 
 constexpr int kMergeThreads = 512;
-constexpr int kMergeTile = 4096;  // output positions per CTA
 
 // Number of items of A among the first x items of merge(A, B), A first on
 // equal keys, found by one warp: each step tests 32 evenly spaced candidates
@@ -44,12 +43,18 @@ __device__ __forceinline__ uint64_t co_rank_warp(const uint64_t* A, uint64_t na,
   return lo;
 }
 
-constexpr size_t kMergeSmem = (size_t)kMergeTile * 8 * 2;  // the two slices, keys and values
+// kMergeTile output positions per CTA (4096, or 2048 for more resident CTAs
+// per SM: the shared memory holds the two slices, keys and values).
+template <int kMergeTile>
+constexpr size_t merge_smem() {
+  return (size_t)kMergeTile * 8 * 2;
+}
 
 // cat_off: k + 1 dense run starts of round 0 (cat_off[k] = total); run_base
 // (null: cat_off) where each matrix's items sit.  Round `round` merges pairs
 // of runs of 2^round matrices each; CTAs cover spans of dense output
 // positions.
+template <int kMergeTile>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t* __restrict__ cat_off,
                                                          const uint64_t* __restrict__ run_base, uint32_t k, int round,
                                                          const uint64_t* __restrict__ kin,
@@ -128,10 +133,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint64_t* __restr
   }
 }
 
-}  // namespace
-
-cudaError_t launch_merge(const uint64_t* cat_off, const uint64_t* run_base, uint32_t k, uint64_t total_cap, int round,
-                         const uint64_t* kin, const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st) {
+template <int kMergeTile>
+cudaError_t run_merge(const uint64_t* cat_off, const uint64_t* run_base, uint32_t k, uint64_t total_cap, int round,
+                      const uint64_t* kin, const uint64_t* vin, uint64_t* kout, uint64_t* vout, cudaStream_t st) {
   const uint64_t blocks = (total_cap + kMergeTile - 1) / kMergeTile;
   if (blocks == 0) return cudaSuccess;
   static unsigned long long configured = 0;  // one bit per device ordinal
@@ -139,12 +143,23 @@ cudaError_t launch_merge(const uint64_t* cat_off, const uint64_t* run_base, uint
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 64 || !((configured >> dev) & 1ull)) {
-    e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMergeSmem);
+    e = cudaFuncSetAttribute(k_merge<kMergeTile>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)merge_smem<kMergeTile>());
     if (e != cudaSuccess) return e;
     if (dev < 64) configured |= 1ull << dev;
   }
-  k_merge<<<(unsigned)blocks, kMergeThreads, kMergeSmem, st>>>(cat_off, run_base, k, round, kin, vin, kout, vout);
+  k_merge<kMergeTile><<<(unsigned)blocks, kMergeThreads, merge_smem<kMergeTile>(), st>>>(cat_off, run_base, k, round,
+                                                                                       kin, vin, kout, vout);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_merge(const uint64_t* cat_off, const uint64_t* run_base, uint32_t k, uint64_t total_cap, int round,
+                         const uint64_t* kin, const uint64_t* vin, uint64_t* kout, uint64_t* vout, int tile,
+                         cudaStream_t st) {
+  if (tile == 2048) return run_merge<2048>(cat_off, run_base, k, total_cap, round, kin, vin, kout, vout, st);
+  return run_merge<4096>(cat_off, run_base, k, total_cap, round, kin, vin, kout, vout, st);
 }
 
 }  // namespace ans

@@ -347,17 +347,20 @@ def test_window_sort_degenerate_windows(ans, n, path):
         c.close()
 
 
-@pytest.mark.parametrize("sum_path", [0, 1])
+@pytest.mark.parametrize("sum_path,merge_tile", [(0, 4096), (0, 2048), (1, 4096)])
 @pytest.mark.parametrize("nwin", [1, 2, 3, 5, 8, 13])
-def test_time_sum_paths_are_exact(ans, synth, sum_path, nwin):
-    """Time sums by pairwise merges (0) and by radix passes (1), for window
-    counts that leave odd runs and empty windows at every merge round."""
+def test_time_sum_paths_are_exact(ans, synth, sum_path, merge_tile, nwin):
+    """Time sums by pairwise merges (0, with either merge tile) and by radix
+    passes (1), for window counts that leave odd runs and empty windows at
+    every merge round."""
     sizes = [(i * 7919) % 30000 if i % 4 != 2 else 0 for i in range(nwin)]
     sizes[0] = max(sizes[0], 3)
     w = synth.generate(5, sizes=sizes, first_window=nwin)
     c = ans.Context(0)
     try:
-        c.set_tuning(sum_path=sum_path)
+        c.set_tuning(sum_path=sum_path, merge_tile=merge_tile)
+        with pytest.raises(ans.AnsError):
+            c.set_tuning(merge_tile=1024)
         mats, summ, _ = check_batch(ans, c, w)
         # sums of sums and of matrices in another order
         exp = oracle.sum_matrices([oracle.traffic_matrix(*w.window(i)) for i in range(nwin)])
