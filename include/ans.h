@@ -24,6 +24,10 @@
  *     are stream-ordered and asynchronous unless a comment says otherwise.
  *     Calls that share one context must be ordered (one stream, or the caller
  *     orders them): the context's scratch memory is reused from call to call.
+ *     A batch may run part of its work on a second stream of the context
+ *     (the time sum's merge rounds beside the window column pass); that work
+ *     is forked from and joined back into `stream`, so completion on
+ *     `stream` covers it.
  *   - Matrices are owned by the caller once returned and released with
  *     ans_matrix_free().  A matrix keeps its memory alive independently of
  *     the context's scratch.
