@@ -2,23 +2,25 @@
 """Throughput of the batched anonymized-network-sensing path on GB300.
 
 One step = one pass of the whole hot path over one batch of synthetic
-windows: pack + sort + run-length reduction to per-window DCSR matrices, the
-nine quantities of every window, and the time sum of all windows of the batch
-(its DCSR and quantities).  The default workload is the 64-window batch
-(64 x 2^17 packets, src Zipf(1.1)/2^20, dst Zipf(1.3)/2^22, 5% bursts).
+windows: pack + sort + run-length reduction of every window, the nine
+quantities of every window, and the time sum of all windows of the batch
+(its DCSR and quantities).  The default workload is the 2^30-packet
+aggregate: 8192 windows of 2^17 packets, src and dst Zipf(1.05) over the full
+2^32 address space, per-window quantities plus the single summed matrix.
+The 64-window workload (--config 2) also returns every window's DCSR.
 
 Prints ONE JSON line (rank 0).  Fields beyond the base contract:
-  per_window   the same work as 64 separate ans_build_window calls + one
-               ans_sum_windows (the plain one-window-per-launch method)
-  roofline     dominant kernel: algorithmic bytes per launch / mean launch
-               time against the measured HBM copy bandwidth.  The timed
-               region runs the production path (every batch replayed as a
-               CUDA graph); the launch times come from a second timed pass
-               over the same steps with CUDA events around every library
-               kernel on its launching stream (kernel_timing)
-  path_roofline  the whole step's algorithmic bytes / step time
-  cpu_baseline the CPU oracle timed on this host on a bounded sample
-
+  roofline       the whole step's algorithmic bytes (read every packet pair
+                 once, write the quantities, write the DCSR that is returned)
+                 over the step time, against the measured HBM copy bandwidth;
+                 extra passes of the method are not credited
+  kernel_roofline  the dominant kernel: its own algorithmic bytes per launch
+                 (e.g. 16 B per key per digit pass) over its mean launch time
+  per_window     the plain method: one ans_build_window per window + one
+                 ans_sum_windows
+  cpu_baseline   the CPU oracle on this host: every core (a process per core,
+                 windows split between them) on a bounded sample, and one
+                 core
 `--impl reference` times the CPU oracle instead (the reference arm).
 Multi-GPU (torchrun): independent replicas, one batch of distinct windows per
 rank, barrier + max-over-ranks timing, weak scaling.
@@ -26,12 +28,15 @@ rank, barrier + max-over-ranks timing, weak scaling.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
+from pathlib import Path
 
 import numpy as np
 
@@ -39,39 +44,52 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "packets/s (batched hot path: per-window DCSR + 9 quantities + time sum)"
+METRIC = "packets/s (batched hot path: per-window quantities + time-summed DCSR)"
 UNIT = "packets/s"
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
 FALLBACK_HBM_GBS = 6800.0
 
 WORKLOADS = {
-    1: "1 window x 2^17 packets; src, dst Zipf(1.2)/2^16; DCSR + 9 quantities (the plain single-window case)",
+    1: "1 window x 2^17 packets; src, dst Zipf(1.2)/2^16; DCSR + 9 quantities + its time sum",
     2: "64 windows x 2^17 packets (8.4M pairs); src Zipf(1.1)/2^20, dst Zipf(1.3)/2^22, 5% bursts of 2..100; "
        "per-window DCSR + 9 quantities + 64-window time sum",
     3: "1024 windows, P loguniform [2^10, 2^20]; heavy hitter 10%, scanners, rest Zipf(1.1)/2^24; "
-       "per-window DCSR + 9 quantities + time sum",
-    4: "2^13 windows x 2^17 (2^30 pairs); src, dst Zipf(1.05) over 2^32; per-window DCSR + quantities + time sum",
+       "per-window 9 quantities + time-summed DCSR",
+    4: "2^13 windows x 2^17 (2^30 pairs, 8 GiB); src, dst Zipf(1.05) over 2^32; per-window 9 quantities + "
+       "one time-summed DCSR",
 }
+DEFAULT_CONFIG = 4
 DEFAULT_NWIN = {1: 1, 2: 64, 3: 1024, 4: 8192}
+# Per-window DCSR matrices are returned on the small workloads; on the large
+# ones the step returns the windows' quantities and the summed matrix.
+WANT_MATRICES = {1: True, 2: True, 3: False, 4: False}
+# Windows of the oracle's bounded samples: all cores (a process per core) and
+# the reference arm's per-step sample.
+ORACLE_SAMPLE = {1: 1, 2: 64, 3: 192, 4: 512}
+REFERENCE_SAMPLE = {1: 1, 2: 64, 3: 96, 4: 256}
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_onesweep launch
-# (64-bit link keys, first digit pass) on the 64-window batch, cold cache; set
-# to None whenever that kernel changes until it is captured again.
-ONESWEEP_NCU_TRAFFIC = 92343552  # 69165056 + 23178496 B, pass 0, cold cache
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum summed over
+# every kernel of one step) per packet, from a capture of a smaller case of
+# the same workload, valid only for the library sources and launch
+# configuration it was taken with (else the bench reports null).
+NCU_TRAFFIC = {}
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS))
+    ap.add_argument("--config", type=int, default=DEFAULT_CONFIG, choices=sorted(WORKLOADS))
     ap.add_argument("--nwin", type=int, default=None, help="override the number of windows per step")
     ap.add_argument("--impl", default="ans", choices=["ans", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-per-window", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-kernel-timing", action="store_true")
+    ap.add_argument("--matrices", type=int, default=None, choices=[0, 1],
+                    help="return per-window DCSR matrices (default: 1 on configs 1-2, 0 on 3-4)")
     ap.add_argument("--tuning", default=None,
                     help="fix launch shapes and paths instead of autotuning, e.g. key=512,0,2;kv=512,0,1;agg_path=1")
     ap.add_argument("--no-serve", action="store_true")
@@ -83,7 +101,7 @@ def parse_args():
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
     ap.add_argument("--serve-sweep", action="store_true",
                     help="only serving: every rate of 1e3..1e5 windows/s x budgets 32/64/128 GiB, one line each")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -99,6 +117,42 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def host_cpu():
+    """(logical cores this process may use, CPU model name)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return cores, model or "unknown"
+
+
+def library_fingerprint() -> str:
+    """Hash of the CUDA library's sources (kernels, launchers, header)."""
+    h = hashlib.sha256()
+    csrc = Path(ROOT) / "paper_2510_14050_gb300" / "csrc"
+    for p in sorted(csrc.glob("ans_*.cu")) + sorted(csrc.glob("*.cuh")) + [Path(ROOT) / "include" / "ans.h"]:
+        h.update(p.name.encode())
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -149,22 +203,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(sizes, quants, sum_q):
-    """Sec. 8(d) bytes of one step: read pairs, write DCSR + quantities per
-    window, write the time-summed DCSR + quantities."""
+def algorithmic_bytes(sizes, quants, sum_q, with_matrices: bool):
+    """Bytes the method must move in one step: every packet pair read once
+    (8 B), the nine quantities written (72 B per window), each returned DCSR
+    written once (12 B per link: column id + count; 12 B per row: row id +
+    row pointer; 8 B for the closing row pointer).  Extra passes of the
+    method are not credited."""
     b = 0
     for p, q in zip(sizes, quants):
-        b += 8 * int(p) + 12 * q["unique_links"] + 12 * q["unique_sources"] + 8 + 72
+        b += 8 * int(p) + 72
+        if with_matrices:
+            b += 12 * q["unique_links"] + 12 * q["unique_sources"] + 8
     if sum_q is not None:
         b += 12 * sum_q["unique_links"] + 12 * sum_q["unique_sources"] + 8 + 72
     return b
 
 
-def kernel_bytes_per_step(name, sizes, quants, sum_q, tuning):
-    """Algorithmic bytes one step's launches of kernel family `name` move
-    (reads + writes each item needs once per pass; DESIGN lists the rules).
-    P = packets (split by window-sort path), U/R = links/rows of the windows,
-    Us/Rs = links/rows of the time sum."""
+def kernel_bytes_per_step(name, sizes, quants, sum_q, tuning, with_matrices):
+    """Algorithmic bytes one step's launches of kernel family `name` move:
+    reads + writes each item needs once per pass.  P = packets (split by
+    window-sort path), U/R = links/rows of the windows, Us/Rs = links/rows of
+    the time sum."""
     cluster_max = 1 << 17
     on_chip = bool(tuning) and tuning.get("win_path") == 0
     p_cl = sum(int(p) for p in sizes if on_chip and p <= cluster_max)
@@ -184,14 +243,126 @@ def kernel_bytes_per_step(name, sizes, quants, sum_q, tuning):
         "onesweep_hash": 8 * 32 * u,                   # 8 passes over (key, count)
         "rle": 8 * p_all + 12 * u + 20 * r + 8 * u + 12 * us + 20 * rs,
         "finish": 32 * u + 32 * r + 28 * us + 32 * rs,
-        "onesweep_col": 4 * 16 * u + 4 * 24 * us,      # (dst, u32 count) / (dst, u64 count)
-        "colstat": 8 * u + 12 * us,
+        "onesweep_col": 4 * 16 * u + 4 * 16 * us,      # (dst, u32 count) per digit pass
+        "colhash": 8 * u,
+        "colstat": 8 * u + 8 * us,
         "gather": 28 * u,                              # link + its row in, (key, count) out
         "merge": rounds * 32 * u,                      # each round: read both runs, write the merge
         "onesweep_sum": 8 * 32 * u,                    # 8 passes over (key, count)
-        "scan_u64": 16 * u,
+        "scan_u64": 16 * us,
     }
     return rules.get(name)
+
+
+# ---- the CPU oracle, for the baseline and the reference arm -----------------
+# A process per core; the windows of the sample are split between them in
+# contiguous ranges.  Each process builds its windows' matrices and
+# quantities and the time sum of its range; the parent adds the ranges' sums
+# (the time sum is associative: Table I's A_t added link by link).
+
+def _oracle_range(args):
+    path_src, path_dst, offsets, lo, hi = args
+    import oracle
+    src = np.load(path_src, mmap_mode="r")
+    dst = np.load(path_dst, mmap_mode="r")
+    mats = []
+    for i in range(lo, hi):
+        a, b = int(offsets[i]), int(offsets[i + 1])
+        m = oracle.traffic_matrix(np.asarray(src[a:b]), np.asarray(dst[a:b]))
+        oracle.network_quantities(m)
+        mats.append(m)
+    return tuple(oracle.sum_matrices(mats))
+
+
+def _oracle_warm(_):
+    import oracle  # noqa: F401  (the import is the warm-up)
+    time.sleep(0.2)
+    return os.getpid()
+
+
+class OraclePool:
+    """The oracle over a sample of windows on every host core."""
+
+    def __init__(self, w, cores: int):
+        import multiprocessing as mp
+        self.w = w
+        self.cores = max(1, cores)
+        self.dir = tempfile.TemporaryDirectory(prefix="ans_oracle_")
+        self.paths = (os.path.join(self.dir.name, "src.npy"), os.path.join(self.dir.name, "dst.npy"))
+        np.save(self.paths[0], w.src)
+        np.save(self.paths[1], w.dst)
+        # spawn: the parent holds a CUDA context, which a forked child must not inherit
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_warm, range(self.cores), chunksize=1)  # every worker up, numpy imported
+
+    def run(self):
+        """One pass over the sample; returns (packets, seconds)."""
+        import oracle
+        n = self.w.nwin
+        cuts = np.linspace(0, n, min(self.cores, n) + 1).astype(int)
+        jobs = [(*self.paths, self.w.offsets, int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        t0 = time.perf_counter()
+        parts = [oracle.DCSR(*p) for p in self.pool.map(_oracle_range, jobs, chunksize=1)]
+        oracle.network_quantities(oracle.sum_matrices(parts))
+        return self.w.total, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.dir.cleanup()
+
+
+def time_oracle_one_core(w, budget_s=5.0):
+    """The oracle over windows of `w` on one core until ~budget_s has elapsed
+    (at least one window) plus their time sum; (packets/s, windows, s)."""
+    import oracle
+    t0 = time.perf_counter()
+    mats, pk, n = [], 0, 0
+    for i in range(w.nwin):
+        s, d = w.window(i)
+        m = oracle.traffic_matrix(s, d)
+        oracle.network_quantities(m)
+        mats.append(m)
+        pk += len(s)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    oracle.network_quantities(oracle.sum_matrices(mats))
+    dt = time.perf_counter() - t0
+    return pk / dt, n, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2510_14050_gb300 import synth
+    nwin = args.nwin or DEFAULT_NWIN[args.config]
+    sample = max(1, min(nwin, REFERENCE_SAMPLE[args.config]))
+    w = synth.generate(args.config, nwin=sample)
+    cores, model = host_cpu()
+    pool = OraclePool(w, cores)
+    try:
+        for _ in range(args.warmup):
+            pool.run()
+        total_s = 0.0
+        for _ in range(args.steps):
+            _, dt = pool.run()
+            total_s += dt
+    finally:
+        pool.close()
+    value = w.total * args.steps / total_s
+    sample_desc = (f"first {sample} of {nwin} windows ({w.total} packets) + their time sum per step; "
+                   f"numpy oracle, a process per core over windows ({cores} cores, {model})")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc,
+                         "cpu_model": model},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_serving(local, rate, n, budget_gib, pool=None, seed=0):
@@ -216,59 +387,21 @@ def run_serving(local, rate, n, budget_gib, pool=None, seed=0):
     return out, pool
 
 
-def oracle_step(w):
-    import oracle
-    oracle.batch(w.src, w.dst, w.offsets, want_sum=True)
+def parse_tuning(text: str) -> dict:
+    kw = {}
+    for part in text.split(";"):
+        fam, vals = part.split("=")
+        fam = fam.strip()
+        if fam.endswith("_path") or fam in ("col_hash", "merge_tile"):  # e.g. agg_path=1; graph_path=0 sets graph
+            kw["graph" if fam == "graph_path" else fam] = int(vals)
+            continue
+        for field, v in zip(("threads", "rank", "blocks"), vals.split(",")):
+            kw[f"{fam}_{field}"] = int(v)
+    return kw
 
 
-def time_oracle(w, budget_s=12.0):
-    """Run the oracle over windows of `w` until ~budget_s has elapsed (at
-    least one window); return (packets/s, windows used)."""
-    import oracle
-    t0 = time.perf_counter()
-    mats, pk, n = [], 0, 0
-    for i in range(w.nwin):
-        s, d = w.window(i)
-        m = oracle.traffic_matrix(s, d)
-        oracle.network_quantities(m)
-        mats.append(m)
-        pk += len(s)
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    oracle.network_quantities(oracle.sum_matrices(mats))
-    dt = time.perf_counter() - t0
-    return pk / dt, n, dt
-
-
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    from paper_2510_14050_gb300 import synth
-    nwin = args.nwin or DEFAULT_NWIN[args.config]
-    sample = max(1, min(nwin, 8))
-    w = synth.generate(args.config, nwin=sample)
-    for _ in range(args.warmup):
-        oracle_step(w.subset(0, 1))
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(w)
-    dt = time.perf_counter() - t0
-    value = w.total * args.steps / dt
-    sample_desc = f"first {sample} of {nwin} windows ({w.total} packets) + their time sum, per step"
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.config], "sample": sample_desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-
-
-def main():
-    args = parse_args()
+def main(argv=None):
+    args = parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -303,13 +436,16 @@ def main():
 
     cfg = args.config
     nwin = args.nwin or DEFAULT_NWIN[cfg]
+    with_mats = bool(WANT_MATRICES[cfg] if args.matrices is None else args.matrices)
+    flags = ans.BATCH_SUM | (ans.BATCH_MATRICES if with_mats else 0)
+    t_gen = time.perf_counter()
     w = synth.generate(cfg, nwin=nwin, first_window=replicas.first_window(rank, nwin))
+    t_gen = time.perf_counter() - t_gen
     total = w.total
     sizes = np.diff(w.offsets)
 
     ctx = ans.Context(local)
     stream = torch.cuda.current_stream()
-    tuning = None
     src_h = torch.from_numpy(w.src.view(np.int32)).pin_memory()
     dst_h = torch.from_numpy(w.dst.view(np.int32)).pin_memory()
     src_d = src_h.cuda()
@@ -317,7 +453,6 @@ def main():
     q_dev = torch.zeros((nwin, 9), dtype=torch.int64, device="cuda")
     q_host = torch.zeros((nwin, 9), dtype=torch.int64).pin_memory()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    flags = ans.BATCH_MATRICES | ans.BATCH_SUM
 
     def step(s, d):
         mats, summ, _ = ctx.batch_submit(s, d, w.offsets, flags, out=q_dev, want_ticket=False)
@@ -325,24 +460,18 @@ def main():
 
     def release(res):
         mats, summ = res
-        for m in mats:
+        for m in mats or ():
             m.free()
         summ.free()
 
+    tuning = None
+    t_tune = time.perf_counter()
     if args.tuning:
-        kw = {}
-        for part in args.tuning.split(";"):
-            fam, vals = part.split("=")
-            fam = fam.strip()
-            if fam.endswith("_path") or fam in ("col_hash", "merge_tile"):  # e.g. agg_path=1; graph_path=0 sets graph
-                kw["graph" if fam == "graph_path" else fam] = int(vals)
-                continue
-            for field, v in zip(("threads", "rank", "blocks"), vals.split(",")):
-                kw[f"{fam}_{field}"] = int(v)
-        ctx.set_tuning(**kw)
+        ctx.set_tuning(**parse_tuning(args.tuning))
         tuning = ctx.get_tuning()
     elif not args.no_autotune:
         tuning = ctx.autotune(src_d, dst_d, w.offsets)
+    t_tune = time.perf_counter() - t_tune
     for _ in range(max(args.warmup, 0)):
         res = step(src_d, dst_d)
         torch.cuda.synchronize()
@@ -354,64 +483,79 @@ def main():
     torch.cuda.synchronize()
     sum_q = res[1].quantities()
     release(res)
-    alg_bytes = algorithmic_bytes(sizes, quants, sum_q)
+    alg_bytes = algorithmic_bytes(sizes, quants, sum_q, with_mats)
 
     # ---- timed region: device-resident inputs, the production path (each
-    # batch's launch sequence replayed as a CUDA graph), no per-kernel events
+    # batch's launch sequence replayed as a CUDA graph), no per-kernel events.
+    # A step's results are released after its end event has been recorded
+    # (the release waits for the step, outside the step's own event pair).
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
 
-    def timed_steps(per_kernel: bool):
+    def timed_steps(fn, k, per_kernel=False, after=None):
         ctx.profile(per_kernel)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        keep = []
-        for i in range(args.steps):
+        ms = []
+        prev = None
+        for i in range(k):
             flush.fill_(i & 0xFF)
-            evs[i][0].record(stream)
-            keep.append(step(src_d, dst_d))
-            evs[i][1].record(stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            if after is not None:
+                after()
+            b.record(stream)
+            if prev is not None:
+                release(prev[0])
+                ms.append(prev[1].elapsed_time(prev[2]))
+            prev = (r, a, b)
         barrier()
+        release(prev[0])
+        ms.append(prev[1].elapsed_time(prev[2]))
         prof = ctx.profile_read() if per_kernel else {}
         ctx.profile(False)
-        ms = [a.elapsed_time(b) for a, b in evs]
-        for r in keep:
-            release(r)
         return ms, prof
 
-    step_ms, _ = timed_steps(False)
+    step_ms, _ = timed_steps(lambda: step(src_d, dst_d), args.steps)
     # ---- kernel timing pass: the same steps again, every library kernel
     # bracketed by CUDA events on the stream it is launched on (per-kernel
     # events launch the sequence directly instead of as a graph)
-    prof_step_ms, prof = timed_steps(True)
+    prof, prof_step_ms = {}, []
+    if not args.no_kernel_timing:
+        prof_step_ms, prof = timed_steps(lambda: step(src_d, dst_d), args.steps, per_kernel=True)
     clk = clocks.stop()
     t_ms = max_over_ranks(sum(step_ms))
     job_total = replicas.sum_over_ranks(total, dist, "cuda")  # packets of one step, all ranks
     value = replicas.job_rate(job_total * args.steps, t_ms / 1e3)
 
-    # ---- dominant kernel and roofline
+    # ---- roofline: the whole path (bytes the method must move), and the dominant kernel
     peak, peak_kind = hbm_peak()
+    path_gbs = alg_bytes * args.steps / (t_ms / 1e3) / 1e9
+    fp = library_fingerprint()
+    traffic = None
+    rec = NCU_TRAFFIC.get(cfg)
+    if rec and rec.get("library") == fp and rec.get("tuning") == tuning and rec.get("matrices") == with_mats:
+        traffic = int(rec["bytes_per_packet"] * total)
+    roof = {"bound": "hbm", "achieved": round(path_gbs, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(path_gbs / peak, 5), "traffic": traffic, "scope": "whole step (every kernel)",
+            "bytes_per_step": alg_bytes, "ms_per_step": round(t_ms / args.steps, 4),
+            "bytes_rule": "8 B per packet + 72 B per window" + (" + 12 B per window link and row + 8" if with_mats
+                                                               else "") + " + 12 B per summed link and row + 80",
+            "peak_kind": f"of {peak_kind}", "library": fp}
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     launches = sum(n for n, _ in prof.values())
-    roof = None
+    kroof = None
     if dom is not None:
         name, (n_l, ms_l) = dom
         mean_ms = ms_l / n_l
-        per_step = kernel_bytes_per_step(name, sizes, quants, sum_q, tuning)
-        per_launch = int(per_step / (n_l / args.steps)) if per_step is not None else alg_bytes
-        unit_desc = {"onesweep": "16 B per packet per digit pass",
-                     "merge": "32 B per window link per merge round",
-                     "onesweep_sum": "32 B per window link per digit pass",
-                     "onesweep_col": "16 B per window link (u32 count) / 24 B per time-sum link per digit pass",
-                     "cluster_sort": "16 B per packet"}.get(name, "per-kernel algorithmic bytes" if per_step
-                                                            else "whole-step algorithmic bytes")
-        ach = per_launch / (mean_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": ONESWEEP_NCU_TRAFFIC if name == "onesweep" else None,
-                "kernel": name, "mean_launch_ms": round(mean_ms, 5), "bytes_per_launch": per_launch,
-                "bytes_rule": unit_desc, "peak_kind": f"of {peak_kind}"}
-    path_gbs = alg_bytes * args.steps / (t_ms / 1e3) / 1e9
+        per_step = kernel_bytes_per_step(name, sizes, quants, sum_q, tuning, with_mats)
+        if per_step is not None:
+            per_launch = int(per_step / (n_l / args.steps))
+            ach = per_launch / (mean_ms / 1e3) / 1e9
+            kroof = {"kernel": name, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "mean_launch_ms": round(mean_ms, 5),
+                     "bytes_per_launch": per_launch, "peak_kind": f"of {peak_kind}",
+                     "bytes_rule": "reads + writes each item needs once per launch of this kernel"}
     kernel_share = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4) for k, v in prof.items()}
 
     # ---- end to end through the C ABI with host buffers
@@ -419,32 +563,26 @@ def main():
     if not args.no_e2e:
         src_e = torch.empty_like(src_d)
         dst_e = torch.empty_like(dst_d)
-        for _ in range(2):
+
+        def e2e_step():
             src_e.copy_(src_h, non_blocking=True)
             dst_e.copy_(dst_h, non_blocking=True)
-            r = step(src_e, dst_e)
+            return step(src_e, dst_e)
+
+        def d2h():
             q_host.copy_(q_dev, non_blocking=True)
+
+        for _ in range(2):
+            r = e2e_step()
+            d2h()
             torch.cuda.synchronize()
             release(r)
         barrier()
-        evs2 = []
-        keep = []
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            src_e.copy_(src_h, non_blocking=True)
-            dst_e.copy_(dst_h, non_blocking=True)
-            keep.append(step(src_e, dst_e))
-            q_host.copy_(q_dev, non_blocking=True)
-            b.record(stream)
-            evs2.append((a, b))
-        barrier()
-        e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs2))
-        for r in keep:
-            release(r)
-        e2e = {"value": replicas.job_rate(job_total * args.steps, e2e_ms / 1e3), "unit": UNIT,
+        e2e_ms, _ = timed_steps(e2e_step, args.steps, after=d2h)
+        e2e_t = max_over_ranks(sum(e2e_ms))
+        e2e = {"value": replicas.job_rate(job_total * args.steps, e2e_t / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 72 * nwin}
+        del src_e, dst_e
 
         # The same through ans_batch_submit_windows: the batch kernels read
         # every window's pairs in place from the pinned host arrays (the
@@ -457,24 +595,13 @@ def main():
 
         for _ in range(2):
             r = zc_step()
-            q_host.copy_(q_dev, non_blocking=True)
+            d2h()
             torch.cuda.synchronize()
             release(r)
         barrier()
-        evs4, keep = [], []
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            keep.append(zc_step())
-            q_host.copy_(q_dev, non_blocking=True)
-            b.record(stream)
-            evs4.append((a, b))
-        barrier()
-        zc_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs4))
-        for r in keep:
-            release(r)
-        e2e["zero_copy"] = {"value": replicas.job_rate(job_total * args.steps, zc_ms / 1e3), "unit": UNIT,
+        zc_ms, _ = timed_steps(zc_step, args.steps, after=d2h)
+        zc_t = max_over_ranks(sum(zc_ms))
+        e2e["zero_copy"] = {"value": replicas.job_rate(job_total * args.steps, zc_t / 1e3), "unit": UNIT,
                             "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 72 * nwin,
                             "how": "ans_batch_submit_windows: the kernels read each window's pairs in place "
                                    "from pinned host memory"}
@@ -494,27 +621,30 @@ def main():
         release(pw_step())
         torch.cuda.synchronize()
         barrier()
-        evs3, keep = [], []
-        for i in range(k2):
-            flush.fill_(i & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            keep.append(pw_step())
-            b.record(stream)
-            evs3.append((a, b))
-        barrier()
-        pw_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs3))
-        for r in keep:
-            release(r)
-        per_window = {"value": replicas.job_rate(job_total * k2, pw_ms / 1e3), "unit": UNIT, "steps": k2,
-                      "ms_per_step": pw_ms / k2, "launches": f"{nwin} x ans_build_window + ans_sum_windows"}
+        pw_ms, _ = timed_steps(pw_step, k2)
+        pw_t = max_over_ranks(sum(pw_ms))
+        per_window = {"value": replicas.job_rate(job_total * k2, pw_t / 1e3), "unit": UNIT, "steps": k2,
+                      "ms_per_step": pw_t / k2, "launches": f"{nwin} x ans_build_window + ans_sum_windows"}
+    ctx.close()
+    del src_d, dst_d, flush
 
-    # ---- CPU oracle baseline (rank 0, N=1 only)
+    # ---- CPU oracle baseline (rank 0, N=1 only): all cores and one core
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, n_used, dt = time_oracle(w)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_used} of {nwin} windows + their time sum ({dt:.1f} s, numpy, 1 thread)"}
+        cores, model = host_cpu()
+        ns = max(1, min(nwin, ORACLE_SAMPLE[cfg]))
+        sample = w.subset(0, ns)
+        pool = OraclePool(sample, cores)
+        try:
+            pk, dt = pool.run()
+        finally:
+            pool.close()
+        v1, n1, dt1 = time_oracle_one_core(w)
+        cpu = {"value": pk / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+               "sample": f"first {ns} of {nwin} windows ({pk} packets) + their time sum, {dt:.1f} s; numpy "
+                         f"oracle, a process per core over windows, the ranges' sums added",
+               "one_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {n1} of {nwin} windows + their time sum ({dt1:.1f} s)"}}
 
     serving = None
     if rank == 0 and not args.no_serve:
@@ -539,22 +669,25 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[cfg], "windows": nwin, "packets_per_step": total,
+            "config": {"workload": WORKLOADS[cfg], "config": cfg, "windows": nwin, "packets_per_step": total,
+                       "per_window_matrices": with_mats,
                        "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
-            "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "path_roofline": {"achieved": round(path_gbs, 1), "peak": peak, "unit": "GB/s",
-                              "frac": round(path_gbs / peak, 4), "bytes_per_step": alg_bytes},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "kernel_roofline": kroof,
             "per_window": per_window,
             "batched_over_per_window": (value / per_window["value"]) if per_window else None,
             "kernel_time_share": kernel_share,
             "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
             "kernel_timing": {"how": "a second pass of the same steps with CUDA events around every library "
                                      "kernel on its launching stream (launched directly, not as a graph)",
-                              "ms_per_step": round(max_over_ranks(sum(prof_step_ms)) / args.steps, 4)},
+                              "ms_per_step": round(max_over_ranks(sum(prof_step_ms)) / args.steps, 4)
+                              if prof_step_ms else None},
+            "time_sum": {"unique_links": sum_q["unique_links"], "unique_sources": sum_q["unique_sources"],
+                         "unique_destinations": sum_q["unique_destinations"],
+                         "window_links": sum(q["unique_links"] for q in quants)},
             "tuning": tuning, "serving": serving, "out_of_core": out_of_core, "clocks": clk, "cpu_baseline": cpu,
+            "setup_s": {"generate": round(t_gen, 2), "autotune": round(t_tune, 2)},
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -179,6 +179,26 @@ int ans_batch_submit_windows(ans_ctx* ctx, const uint32_t* const* srcs, const ui
  * ANS_ERR_INVALID_ARG (unknown ticket). */
 int ans_wait(ans_ctx* ctx, ans_ticket ticket, uint64_t timeout_ns);
 
+/* Poll limit of the context's bounded device waits (the decoupled look-back
+ * of the radix passes, run reductions and scans waits for the tile before it
+ * to publish; after `polls` polls with back-off the wait gives up, sets the
+ * context's error word and returns, and the batch reports ANS_ERR_INTERNAL).
+ * polls == 0 restores the default of 2^20 polls (about one second); at most
+ * 2^24.  Waits for the device before it changes the limit, which applies to
+ * work queued afterwards.  Not in the paper: failure detection of this
+ * implementation.  Errors: ANS_ERR_INVALID_ARG, ANS_ERR_CUDA. */
+int ans_set_wait_limit(ans_ctx* ctx, uint32_t polls);
+
+/* Health check of the bounded waits (not in the paper): runs, on `stream`,
+ * one look-back wait of each form for a predecessor tile that never
+ * publishes, so each can only end by giving up at the context's poll limit.
+ * The expiry is reported exactly as inside a batch: ans_wait(*ticket) and
+ * ans_matrix_view / ans_matrix_quantities of *out (an empty matrix, optional)
+ * return ANS_ERR_INTERNAL, and the context stays usable for later calls.
+ * ticket and out may be NULL.  Errors: ANS_ERR_INVALID_ARG, ANS_ERR_OOM,
+ * ANS_ERR_BUDGET, ANS_ERR_CUDA. */
+int ans_probe_wait_expiry(ans_ctx* ctx, ans_matrix** out, ans_ticket* ticket, void* stream);
+
 /* Host-side view of a matrix: counts and device pointers to its arrays
  * (row_ids[nrows], row_ptr[nrows + 1], col_ids[nnz], vals[nnz]).  Blocks
  * until the matrix has been computed.  Any output pointer may be NULL. */

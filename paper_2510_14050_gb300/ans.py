@@ -46,7 +46,12 @@ EXPORTS = (
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
     "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
     "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import", "ans_batch_submit_windows", "ans_combine",
+    "ans_set_wait_limit", "ans_probe_wait_expiry",
 )
+
+# The allocator hook types of ans_ctx_create.
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 
 class Quantities(C.Structure):
@@ -113,6 +118,8 @@ def load(path: str | os.PathLike | None = None):
         "ans_combine": ([_vp, P(_vp), P(C.c_int), C.c_size_t, P(_vp), _vp], C.c_int),
         "ans_batch_submit_windows": ([_vp, P(_vp), P(_vp), P(_u64), C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp),
                                       P(_u64), _vp], C.c_int),
+        "ans_set_wait_limit": ([_vp, C.c_uint32], C.c_int),
+        "ans_probe_wait_expiry": ([_vp, P(_vp), P(_u64), _vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -235,13 +242,53 @@ class Matrix:
             pass
 
 
-class Context:
-    """One ans_ctx: a device, an allocator, a memory budget and scratch."""
+class TorchAllocator:
+    """Device-memory hooks for ans_ctx_create backed by torch's caching
+    allocator (stream-ordered: each block is tied to the stream the library
+    names).  ``fail_after`` (tests) makes allocation number ``fail_after``
+    and later return NULL until it is reset to None."""
 
-    def __init__(self, device: int = 0, budget_bytes: int = 0):
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.calls = 0
+        self.fail_after = None
+        self.live = {}
+
+        def _alloc(nbytes, stream, user):
+            import torch
+            self.calls += 1
+            if self.fail_after is not None and self.calls >= self.fail_after:
+                return None
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+            except Exception:
+                return None
+            self.live[ptr] = int(nbytes)
+            return ptr
+
+        def _free(ptr, stream, user):
+            import torch
+            if ptr:
+                self.live.pop(ptr, None)
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
+
+
+class Context:
+    """One ans_ctx: a device, an allocator, a memory budget and scratch.
+
+    ``allocator``: optional object with ``alloc_fn`` / ``free_fn`` ctypes hooks
+    (e.g. TorchAllocator); it must outlive every matrix of the context."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, allocator=None):
         self._lib = load()
         h = _vp()
-        _check(self._lib.ans_ctx_create(C.byref(h), int(device), int(budget_bytes), None, None, None), "ctx_create")
+        self._allocator = allocator  # the hooks must stay alive with the context
+        fa = C.cast(allocator.alloc_fn, _vp) if allocator is not None else None
+        ff = C.cast(allocator.free_fn, _vp) if allocator is not None else None
+        _check(self._lib.ans_ctx_create(C.byref(h), int(device), int(budget_bytes), fa, ff, None), "ctx_create")
         self._h = h
         self.device = device
 
@@ -432,6 +479,24 @@ class Context:
                                       offs.ctypes.data_as(C.POINTER(_u64)), len(offs) - 1, C.byref(t),
                                       _vp(_stream(stream))), "autotune", self._h)
         return t.as_dict()
+
+    def set_wait_limit(self, polls: int = 0):
+        """Poll limit of the bounded device waits (0: the default, ~1 s)."""
+        _check(self._lib.ans_set_wait_limit(self._h, int(polls)), "set_wait_limit", self._h)
+
+    def probe_wait_expiry(self, want_matrix: bool = True, stream=None):
+        """Run one device wait that can only end at the poll limit; returns
+        (empty matrix or None, ticket).  ans_wait on the ticket and the
+        matrix's view then report ERR_INTERNAL."""
+        m = _vp()
+        tk = _u64()
+        _check(self._lib.ans_probe_wait_expiry(self._h, C.byref(m) if want_matrix else None, C.byref(tk),
+                                               _vp(_stream(stream))), "probe_wait_expiry", self._h)
+        return (Matrix(m.value) if want_matrix else None), int(tk.value)
+
+    def wait_status(self, ticket: int, timeout_s: float = 60.0) -> int:
+        """ans_wait's status code (no exception)."""
+        return int(self._lib.ans_wait(self._h, int(ticket), int(timeout_s * 1e9)))
 
     def wait(self, ticket: int, timeout_s: float = 60.0):
         _check(self._lib.ans_wait(self._h, int(ticket), int(timeout_s * 1e9)), "wait", self._h)

@@ -1858,6 +1858,58 @@ int ans_wait(ans_ctx* c, ans_ticket t, uint64_t timeout_ns) {
   return ANS_OK;
 }
 
+int ans_set_wait_limit(ans_ctx* c, uint32_t polls) {
+  if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
+  if (polls > kSpinLimitMax) return fail(ANS_ERR_INVALID_ARG, "the poll limit is at most 2^24");
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  // the limit is read by kernels: change it only with nothing in flight
+  ANS_CUDA(cudaDeviceSynchronize());
+  ANS_CUDA(cudaMemcpy(c->d_err + 1, &polls, 4, cudaMemcpyHostToDevice));
+  return ANS_OK;
+}
+
+int ans_probe_wait_expiry(ans_ctx* c, ans_matrix** out, ans_ticket* ticket, void* stream) {
+  if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
+  if (out) *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  // two status words beside the error word: tile 0 of the probed chain never
+  // publishes, so tile 1's wait can only end at the poll limit
+  uint64_t* words = (uint64_t*)((char*)c->small_mem + 64);
+  ANS_CUDA(cudaMemsetAsync(words, 0, 16, st));
+  ANS_CUDA(launch_wait_probe(words, c->d_err, st));
+  Block* b = nullptr;
+  if (out) {
+    ANS_TRY(make_block(c, 0, 1, {0}, {0}, st, &b));
+    auto cu = [&](cudaError_t e, const char* what) -> int {
+      if (e == cudaSuccess) return ANS_OK;
+      block_discard(b, st);
+      return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    int rc;
+    if ((rc = cu(cudaMemsetAsync(b->row_ptr, 0, 8, st), "memset")) || (rc = cu(cudaMemsetAsync(b->hdr, 0, 16, st), "memset")) ||
+        (rc = cu(cudaMemsetAsync(b->q, 0, sizeof(ans_quantities), st), "memset")) ||
+        (rc = cu(cudaMemcpyAsync(b->status, c->d_err, 4, cudaMemcpyDeviceToDevice, st), "copy")))
+      return rc;
+  }
+  if (ticket) {
+    const int rc = new_ticket(c, st, ticket);
+    if (rc) {
+      block_discard(b, st);
+      return rc;
+    }
+  }
+  ANS_TRY(reset_err(c, st));
+  if (b) {
+    ANS_CUDA(cudaEventRecord(b->done, st));
+    b->refs = 1;
+    *out = new ans_matrix{b, 0};
+  }
+  return ANS_OK;
+}
+
 int ans_matrix_view(const ans_matrix* x, uint64_t* nrows, uint64_t* nnz, const uint32_t** row_ids,
                     const uint64_t** row_ptr, const uint32_t** col_ids, const uint64_t** vals) {
   if (!x) return fail(ANS_ERR_INVALID_ARG, "NULL matrix");

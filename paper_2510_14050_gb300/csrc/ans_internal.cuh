@@ -34,10 +34,14 @@ constexpr uint32_t kClusterWindowMax = 1u << 17;  // largest window sorted on ch
 constexpr uint64_t kFlagAgg = 1ull << 62;      // tile aggregate available
 constexpr uint64_t kFlagPre = 2ull << 62;      // inclusive prefix available
 constexpr uint64_t kValMask = (1ull << 62) - 1;
-constexpr uint32_t kSpinLimit = 1u << 20;      // polls (about 1 s) before a wait gives up
+constexpr uint32_t kSpinLimit = 1u << 20;      // default polls (about 1 s) before a wait gives up
+constexpr uint32_t kSpinLimitMax = 1u << 24;   // largest settable poll limit (about 16 s)
 
+// Every kernel that waits receives `err`, the device error word of its
+// context: err[0] collects ErrBits, err[1] holds the context's poll limit for
+// bounded waits (0 = kSpinLimit).
 enum ErrBits : uint32_t {
-  kErrLookback = 1u,   // a look-back wait hit kSpinLimit
+  kErrLookback = 1u,   // a look-back wait hit its poll limit
   kErrHashFull = 2u,   // a hash probe sequence found no free slot
   kErrNegative = 4u,   // a signed combination left a negative count
 };
@@ -146,7 +150,7 @@ cudaError_t launch_pack_hist(const SegPlan& p, const uint32_t* src, const uint32
                              uint64_t* keys, uint32_t* seg_hist, uint64_t* status0,
                              uint32_t* tickets, cudaStream_t st, uint32_t sub = 1);
 // Sub-tiles per tile of a key-pass configuration.
-inline uint32_t key_subtiles(const SortCfg& cfg) { return cfg.threads == 256 ? 2u : 1u; }
+constexpr uint32_t key_subtiles(const SortCfg& cfg) { return cfg.threads == 256 ? 2u : 1u; }
 // One onesweep digit pass (stable), optionally carrying uint64 values.
 cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
@@ -250,6 +254,12 @@ uint32_t colhash_ctas(uint32_t nseg);
 // in q and ulen[s] = 0 (the column sort then skips it).
 cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
                            ans_quantities* q, cudaStream_t st);
+// One bounded look-back wait (both forms: the single-thread walk of the
+// radix passes and the warp walk of the run reductions and scans) for the
+// predecessor of tile 1 of a chain whose tile 0 never publishes (st: two
+// words, zero on entry).  Each wait gives up after the context's poll limit
+// and sets kErrLookback in err[0].
+cudaError_t launch_wait_probe(const uint64_t* st, uint32_t* err, cudaStream_t stream);
 // Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.
@@ -357,16 +367,24 @@ __device__ __forceinline__ T warp_sum(T v) {
 // `first` is the first tile of the segment, `t` this tile (t > first).
 // Returns the exclusive prefix; on timeout flags kErrLookback and returns the
 // partial sum (never larger than the true prefix, so indexes stay in range).
+// Poll limit of the bounded waits of the context whose error word is `err`.
+__device__ __forceinline__ uint32_t wait_limit(const uint32_t* err) {
+  const uint32_t l = err[1];
+  return l ? l : kSpinLimit;
+}
+
 __device__ __forceinline__ uint64_t lookback(const uint64_t* st, uint32_t stride, uint32_t first,
                                              uint32_t t, uint32_t* err) {
   uint64_t excl = 0;
   uint32_t q = t - 1;
   uint32_t spins = 0;
+  uint32_t limit = 0;  // read at the first wait only
   while (true) {
     uint64_t v = ld_relaxed(st + (uint64_t)q * stride);
     uint64_t f = v & ~kValMask;
     if (f == 0) {
-      if (++spins > kSpinLimit) {
+      if (spins == 0) limit = wait_limit(err);
+      if (++spins > limit) {
         atomicOr(err, (uint32_t)kErrLookback);
         break;
       }
@@ -391,6 +409,7 @@ __device__ __forceinline__ uint64_t warp_lookback(const uint64_t* st, uint32_t s
   uint64_t excl = 0;
   uint32_t q = t - 1;  // newest tile not yet added; q >= first
   uint32_t spins = 0;
+  uint32_t limit = 0;  // read at the first wait only
   while (true) {
     const uint64_t v = lane <= q - first ? ld_relaxed(st + (uint64_t)(q - lane) * stride) : kFlagPre;
     const uint64_t f = v & ~kValMask;
@@ -399,7 +418,8 @@ __device__ __forceinline__ uint64_t warp_lookback(const uint64_t* st, uint32_t s
     const int p = pre ? __ffs(pre) - 1 : 32;              // nearest tile with its prefix
     const uint32_t upto = p == 32 ? 0xffffffffu : (2u << p) - 1u;  // lanes 0..p
     if (none & upto) {                                     // a nearer tile is not ready
-      if (++spins > kSpinLimit) {
+      if (spins == 0) limit = wait_limit(err);
+      if (++spins > limit) {
         if (lane == 0) atomicOr(err, (uint32_t)kErrLookback);
         return excl;
       }

@@ -21,7 +21,10 @@
 //    threads without ordering) race and give wrong results;
 //  * the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress with that device current); make that first call
-//    before any stream capture begins.
+//    before any stream capture begins.  The address is kept for the life of
+//    the process, so the entry point must not be used after a
+//    cudaDeviceReset() of that device (the array's old address would be
+//    stale).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,6 +39,13 @@ namespace {
 
 constexpr uint64_t kNoAllocMaxPackets = 1ull << 16;
 constexpr uint32_t kNoAllocTiles = (uint32_t)(kNoAllocMaxPackets / kTile);
+// The buffers below are sized for kNoAllocMaxPackets items, which must cover
+// the padded index space (whole tiles) of the largest window.
+static_assert(kNoAllocMaxPackets % kTile == 0, "the packet limit must be a whole number of tiles");
+// The key passes run with the default launch shape; its sub-tiles' status
+// words must fit the two per tile reserved at oSt0 / oSt1.
+constexpr SortCfg kNoAllocSort{};
+static_assert(key_subtiles(kNoAllocSort) <= 2, "status words hold at most two sub-tiles per tile");
 constexpr size_t kAl = 256;
 constexpr size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
@@ -129,7 +139,7 @@ extern "C" int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32
   };
   int rc;
   if ((rc = cu(cudaMemsetAsync(q, 0, sizeof(ans_quantities), st), "memset"))) return rc;
-  if ((rc = cu(cudaMemsetAsync(err, 0, 4, st), "memset"))) return rc;
+  if ((rc = cu(cudaMemsetAsync(err, 0, 8, st), "memset"))) return rc;  // error bits; default poll limit
   const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
   if (ntiles) {
     if ((rc = cu(cudaMemsetAsync(m + oHist, 0, (size_t)kPasses * kRadix * 4, st), "memset"))) return rc;
@@ -151,11 +161,11 @@ extern "C" int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32
     uint64_t* st1 = reinterpret_cast<uint64_t*>(m + oSt1);
     uint32_t* hist = reinterpret_cast<uint32_t*>(m + oHist);
     uint32_t* tickets = reinterpret_cast<uint32_t*>(m + oTickets);
-    if ((rc = cu(launch_pack_hist(p, d_src, d_dst, ka, hist, st0, tickets, st), "pack"))) return rc;
+    if ((rc = cu(launch_pack_hist(p, d_src, d_dst, ka, hist, st0, tickets, st, key_subtiles(kNoAllocSort)), "pack"))) return rc;
     for (int pass = 0; pass < kPasses; ++pass) {
       const bool even = (pass % 2) == 0;
       if ((rc = cu(launch_onesweep(p, pass, even ? ka : kb, even ? kb : ka, nullptr, nullptr, hist,
-                                   even ? st0 : st1, even ? st1 : st0, tickets + pass, err, SortCfg(), st),
+                                   even ? st0 : st1, even ? st1 : st0, tickets + pass, err, kNoAllocSort, st),
                    "onesweep")))
         return rc;
     }
@@ -193,7 +203,7 @@ extern "C" int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32
       const uint64_t* vin = pass == 0 ? a.vals : (pass % 2 ? cva : cvb);
       if ((rc = cu(launch_onesweep_col(cp, pass, kin, pass % 2 ? ckb : cka, vin, pass % 2 ? cvb : cva, a.col_hist,
                                        pass % 2 ? st1 : st0, pass % 2 ? st0 : st1, a.col_tickets + pass, err,
-                                       SortCfg(), st),
+                                       kNoAllocSort, st),
                    "onesweep_col")))
         return rc;
     }

@@ -565,6 +565,16 @@ __global__ void k_empty_fixup(StatsArgs a) {
   if (a.ulen) a.ulen[s] = 0;
 }
 
+// Warp 0 waits with warp_lookback, thread 32 with lookback, both for tile 0
+// of a chain that nobody publishes; both give up at the poll limit.
+__global__ void k_wait_probe(const uint64_t* st, uint32_t* err) {
+  if (threadIdx.x < 32) {
+    warp_lookback(st, 1, 0, 1, err);
+  } else if (threadIdx.x == 32) {
+    lookback(st, 1, 0, 1, err);
+  }
+}
+
 // Zero `bytes` bytes at p (4-byte aligned): a kernel instead of a memset so
 // that a recorded launch sequence keeps its topology when sizes change.
 __global__ void k_zero(uint32_t* __restrict__ p, size_t words, uint8_t* __restrict__ tail, uint32_t ntail) {
@@ -974,6 +984,11 @@ cudaError_t launch_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* row_
   const uint64_t want = (n + 255) / 256;
   const unsigned blocks = (unsigned)(want > 4096 ? 4096 : want);
   k_check_dcsr<<<blocks, 256, 0, st>>>(nrows, nnz, row_ids, row_ptr, col_ids, vals, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(const uint64_t* st, uint32_t* err, cudaStream_t stream) {
+  k_wait_probe<<<1, 64, 0, stream>>>(st, err);
   return cudaGetLastError();
 }
 
