@@ -142,9 +142,25 @@ int ans_network_quantities(ans_ctx* ctx, const ans_matrix* m, ans_quantities* ou
 
 /* Batched analysis of nwin windows stored back to back (Sec. III-C batching,
  * taken to its limit: every window of the batch in one fixed launch sequence).
- *   d_src, d_dst : device arrays holding h_offsets[nwin] packets.
- *   h_offsets    : HOST array of nwin + 1 nondecreasing offsets, h_offsets[0]
- *                  may be nonzero; window w is [h_offsets[w], h_offsets[w+1]).
+ *   d_src, d_dst : device arrays; window w is packets [d_offsets[w],
+ *                  d_offsets[w+1]) of them.
+ *   d_offsets    : DEVICE array of nwin + 1 nondecreasing uint64 offsets
+ *                  (d_offsets[0] may be nonzero).  The batch is planned on the
+ *                  device (window lengths, tile table, padded starts: one
+ *                  scan kernel at the head of the launch sequence), so the
+ *                  offsets may be written by earlier work on `stream`.
+ *                  With a capacity set (ans_set_batch_capacity) the call
+ *                  never reads the offsets on the host and sizes scratch and
+ *                  grids for that many packets; without one it first copies
+ *                  d_offsets[0] and d_offsets[nwin] to the host (waiting for
+ *                  `stream`).  Offsets that decrease, a window of 2^31 packets
+ *                  or more, or a batch above the capacity are found on the
+ *                  device: every window then comes out empty and ans_wait,
+ *                  ans_matrix_view and ans_matrix_quantities report
+ *                  ANS_ERR_INVALID_ARG.  Per-window matrices of such a batch
+ *                  learn their layout when the batch completes: summing or
+ *                  re-analysing them waits for it.  Every window is sorted by
+ *                  the radix passes (win_path is not consulted).
  *   flags        : ANS_BATCH_* bits.
  *   out          : nwin ans_quantities (host or device memory; pageable host
  *                  memory makes the call blocking).  May be NULL.
@@ -155,8 +171,24 @@ int ans_network_quantities(ans_ctx* ctx, const ans_matrix* m, ans_quantities* ou
  * ans_sum_windows.  Errors: ANS_ERR_INVALID_ARG, ANS_ERR_BUDGET, ANS_ERR_OOM,
  * ANS_ERR_CUDA. */
 int ans_batch_submit(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst,
-                     const uint64_t* h_offsets, size_t nwin, uint32_t flags, ans_quantities* out,
+                     const uint64_t* d_offsets, size_t nwin, uint32_t flags, ans_quantities* out,
                      ans_matrix** per_window, ans_matrix** sum, ans_ticket* ticket, void* stream);
+
+/* The same with the offsets in HOST memory (h_offsets, nwin + 1 entries,
+ * read during the call): the host plans the tiles, sizes everything
+ * exactly, and validates the offsets before any work is queued (bad offsets
+ * fail the call with ANS_ERR_INVALID_ARG). */
+int ans_batch_submit_host(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst,
+                          const uint64_t* h_offsets, size_t nwin, uint32_t flags, ans_quantities* out,
+                          ans_matrix** per_window, ans_matrix** sum, ans_ticket* ticket, void* stream);
+
+/* Capacity, in packets, of batches submitted with device-resident offsets
+ * (ans_batch_submit): scratch, output blocks and grids are sized for it, so
+ * a larger capacity costs memory (about 100 bytes per packet of scratch,
+ * and the per-window and time-sum blocks at 24 bytes per packet each) and
+ * some empty tiles.  0 (the default) sizes each batch by reading its first
+ * and last offset back.  Errors: ANS_ERR_INVALID_ARG. */
+int ans_set_batch_capacity(ans_ctx* ctx, uint64_t max_packets);
 
 /* The same analysis with every window in its own arrays: window w is
  * srcs[w][0..lens[w]) and dsts[w][0..lens[w]), in device memory, in
@@ -166,7 +198,7 @@ int ans_batch_submit(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst,
  * (cudaDevAttrPageableMemoryAccess).  srcs, dsts and lens are host arrays of
  * nwin entries, read during the call; the windows' arrays must stay valid
  * until the batch completes.  Every other argument, result and error as
- * ans_batch_submit; ANS_ERR_INVALID_ARG also for a window the device cannot
+ * ans_batch_submit_host; ANS_ERR_INVALID_ARG also for a window the device cannot
  * read. */
 int ans_batch_submit_windows(ans_ctx* ctx, const uint32_t* const* srcs, const uint32_t* const* dsts,
                              const uint64_t* lens, size_t nwin, uint32_t flags, ans_quantities* out,
@@ -248,7 +280,7 @@ int ans_window_quantities_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
 /* Memory accounting for admission control.  ans_ctx_memory reports the
  * device bytes the context holds now (scratch plus live matrices) and its
  * budget (0 = none).  ans_batch_bytes gives the additional device bytes that
- * ans_batch_submit with these offsets and flags would allocate if called now
+ * ans_batch_submit_host with these offsets and flags would allocate if called now
  * (scratch growth plus output matrices); nothing is allocated. */
 int ans_ctx_memory(ans_ctx* ctx, size_t* live_bytes, size_t* budget_bytes);
 int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32_t flags, size_t* bytes);
@@ -272,7 +304,12 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * win_threads (512 or 1024) and win_rank (0 or 1, as *_rank) configure the
  * cluster kernel.  sum_path: how time sums order the links of their input matrices,
  * 0 = ceil(log2 k) rounds of pairwise merges of the matrices' already sorted
- * links, 1 = the kv_* radix passes over all gathered links.  agg_path: how
+ * links, 1 = the kv_* radix passes over all gathered links, 2 = (a batch's
+ * own time sum, windows stored back to back) every packet of the batch
+ * sorted again as one segment by the key_* passes and reduced like a window
+ * -- the sum of Table I's A_t is the matrix of the concatenated packets;
+ * sums of given matrices, and batches of windows in their own arrays, then
+ * take the kv_* passes.  agg_path: how
  * a window's equal packets are grouped, 0 = sorting every packet's link key,
  * 1 = counting links in a per-window hash table (2^k >= 2 x packets slots of
  * 12 bytes, kept by the context between calls) and sorting only the distinct
@@ -282,9 +319,11 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * (updated in place with the call's pointers), 0 = launched directly; per-
  * kernel profiling always launches directly.  col_hash: 1 = each window's
  * column statistics are first counted in a shared-memory hash of its
- * destinations (one CTA per window; up to 12288 distinct destinations), and
- * only windows with more take the column sort; 0 = the column sort for every
- * window.  merge_tile: output positions per CTA of the time sum's merge
+ * destinations (one CTA, or a cluster, per window; up to 12288 distinct
+ * destinations), then windows with more destinations and at most 2^18 links
+ * in shared-memory hashes of destination partitions (up to 32 CTAs per
+ * window, one partition each), and only windows neither fits take the
+ * column sort; 0 = the column sort for every window.  merge_tile: output positions per CTA of the time sum's merge
  * rounds, 4096 or 2048 (more resident CTAs per SM, twice the merge-path
  * searches).  Results never depend on the configuration. */
 typedef struct {
@@ -307,7 +346,7 @@ typedef struct {
 int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);
 int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
 
-/* Autotuner: runs the caller's representative batch (as ans_batch_submit with
+/* Autotuner: runs the caller's representative batch (as ans_batch_submit_host with
  * per-window matrices and the time sum) once per candidate configuration,
  * three times each, times every radix pass with CUDA events on `stream`, and
  * keeps, per family, the configuration with the least total pass time; it

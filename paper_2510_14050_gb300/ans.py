@@ -46,7 +46,7 @@ EXPORTS = (
     "ans_status_string", "ans_last_error", "ans_profile_enable", "ans_profile_read",
     "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
     "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import", "ans_batch_submit_windows", "ans_combine",
-    "ans_set_wait_limit", "ans_probe_wait_expiry",
+    "ans_set_wait_limit", "ans_probe_wait_expiry", "ans_batch_submit_host", "ans_set_batch_capacity",
 )
 
 # The allocator hook types of ans_ctx_create.
@@ -97,8 +97,11 @@ def load(path: str | os.PathLike | None = None):
         "ans_build_window": ([_vp, _vp, _vp, _u64, P(_vp), _vp], C.c_int),
         "ans_sum_windows": ([_vp, P(_vp), C.c_size_t, P(_vp), _vp], C.c_int),
         "ans_network_quantities": ([_vp, _vp, _vp, _vp], C.c_int),
-        "ans_batch_submit": ([_vp, _vp, _vp, P(_u64), C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp), P(_u64), _vp],
+        "ans_batch_submit": ([_vp, _vp, _vp, _vp, C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp), P(_u64), _vp],
                              C.c_int),
+        "ans_batch_submit_host": ([_vp, _vp, _vp, P(_u64), C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp), P(_u64),
+                                   _vp], C.c_int),
+        "ans_set_batch_capacity": ([_vp, _u64], C.c_int),
         "ans_wait": ([_vp, _u64, _u64], C.c_int),
         "ans_matrix_view": ([_vp, P(_u64), P(_u64), P(_vp), P(_vp), P(_vp), P(_vp)], C.c_int),
         "ans_matrix_quantities": ([_vp, P(Quantities)], C.c_int),
@@ -384,19 +387,32 @@ class Context:
     def batch_submit(self, src, dst, offsets, flags: int = 0, out=None, stream=None, want_ticket: bool = True):
         """Analyse windows [offsets[w], offsets[w+1]) of (src, dst).
 
-        ``offsets``: host array-like of nwin + 1 uint64.  ``out``: optional
-        tensor of nwin x 9 int64 (device or pinned host) receiving the
-        quantities.  Returns (per_window matrices or None, sum or None, ticket)."""
-        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
-        nwin = len(offs) - 1
+        ``offsets``: nwin + 1 uint64 offsets -- a CUDA tensor (int64/uint64,
+        read on the device: ans_batch_submit) or a host array-like
+        (ans_batch_submit_host).  ``out``: optional tensor of nwin x 9 int64
+        (device or pinned host) receiving the quantities.  Returns
+        (per_window matrices or None, sum or None, ticket)."""
+        on_device = hasattr(offsets, "device") and getattr(offsets.device, "type", "") == "cuda"
+        if on_device:
+            if offsets.element_size() != 8 or not offsets.is_contiguous():
+                raise ValueError("device offsets must be a contiguous 64-bit tensor")
+            nwin = offsets.numel() - 1
+        else:
+            offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+            nwin = len(offs) - 1
         per = (_vp * max(nwin, 1))() if flags & BATCH_MATRICES else None
         sm = _vp() if flags & BATCH_SUM else None
         tk = _u64() if want_ticket else None
         outp = _vp(out.data_ptr()) if out is not None else None
-        _check(self._lib.ans_batch_submit(
-            self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)), offs.ctypes.data_as(C.POINTER(_u64)), nwin,
-            int(flags), outp, per, C.byref(sm) if sm is not None else None,
-            C.byref(tk) if tk is not None else None, _vp(_stream(stream))), "batch_submit", self._h)
+        tail = (nwin, int(flags), outp, per, C.byref(sm) if sm is not None else None,
+                C.byref(tk) if tk is not None else None, _vp(_stream(stream)))
+        if on_device:
+            _check(self._lib.ans_batch_submit(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)),
+                                              _vp(offsets.data_ptr()), *tail), "batch_submit", self._h)
+        else:
+            _check(self._lib.ans_batch_submit_host(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)),
+                                                   offs.ctypes.data_as(C.POINTER(_u64)), *tail),
+                   "batch_submit_host", self._h)
         mats = [Matrix(per[i]) for i in range(nwin)] if per is not None else None
         summ = Matrix(sm.value) if sm is not None else None
         return mats, summ, (int(tk.value) if tk is not None else None)
@@ -479,6 +495,11 @@ class Context:
                                       offs.ctypes.data_as(C.POINTER(_u64)), len(offs) - 1, C.byref(t),
                                       _vp(_stream(stream))), "autotune", self._h)
         return t.as_dict()
+
+    def set_batch_capacity(self, max_packets: int = 0):
+        """Packets a batch with device-resident offsets may hold (0: each such
+        batch reads its first and last offset back to size itself)."""
+        _check(self._lib.ans_set_batch_capacity(self._h, int(max_packets)), "set_batch_capacity", self._h)
 
     def set_wait_limit(self, polls: int = 0):
         """Poll limit of the bounded device waits (0: the default, ~1 s)."""

@@ -149,6 +149,9 @@ struct ans_ctx {
   // window first (windows that fit skip the column sort), 0 = sort only.
   int col_hash = 1;
   int pageable = -1;  // does the device read pageable host memory (-1: not asked yet)
+  // Packets a batch with device-resident offsets may hold (0: the call reads
+  // the first and last offset back to size its scratch).
+  uint64_t batch_cap = 0;
   // Batches replay their launch sequence as a CUDA graph (graph = 1): it is
   // captured on `cap` each call and applied to a cached executable graph of
   // the same shape by cudaGraphExecUpdate (re-instantiated if the topology
@@ -253,6 +256,11 @@ struct Block {
   uint64_t* hdr = nullptr;
   ans_quantities* q = nullptr;
   uint32_t* status = nullptr;  // device error word captured at completion
+  // A block of a batch planned on the device: the padded starts live in
+  // d_base until the block completes; base and cap (then the exact link
+  // counts) are filled by block_fill_cache.
+  bool dev_plan = false;
+  uint64_t* d_base = nullptr;
   cudaEvent_t done = nullptr;
   std::atomic<int> refs{0};
   std::mutex mu;
@@ -390,8 +398,8 @@ struct UploadSet {
 
 // Device layout of a block holding nseg matrices over `pad` padded items.
 struct BlockLayout {
-  size_t col_ids, vals, row_ids, row_ptr, hdr, q, status, total;
-  BlockLayout(uint64_t pad, uint32_t nseg) {
+  size_t col_ids, vals, row_ids, row_ptr, hdr, q, status, base = 0, total;
+  BlockLayout(uint64_t pad, uint32_t nseg, bool dev_base = false) {
     Layout L;
     col_ids = L.add(pad * 4);
     vals = L.add(pad * 8);
@@ -400,13 +408,16 @@ struct BlockLayout {
     hdr = L.add((size_t)nseg * 16);
     q = L.add((size_t)nseg * sizeof(ans_quantities));
     status = L.add(8);
+    if (dev_base) base = L.add((size_t)nseg * 8);
     total = L.size;
   }
 };
 
+// dev_base: the segments' padded starts are computed on the device (base
+// and cap stay empty until the block completes).
 int make_block(ans_ctx* c, uint64_t pad, uint32_t nseg, std::vector<uint64_t> base, std::vector<uint64_t> cap,
-               cudaStream_t st, Block** out) {
-  BlockLayout bl(pad, nseg);
+               cudaStream_t st, Block** out, bool dev_base = false) {
+  BlockLayout bl(pad, nseg, dev_base);
   void* mem = nullptr;
   ANS_TRY(dev_alloc(c, bl.total, st, &mem));
   Block* b = new Block();
@@ -424,6 +435,10 @@ int make_block(ans_ctx* c, uint64_t pad, uint32_t nseg, std::vector<uint64_t> ba
   b->hdr = (uint64_t*)(m + bl.hdr);
   b->q = (ans_quantities*)(m + bl.q);
   b->status = (uint32_t*)(m + bl.status);
+  if (dev_base) {
+    b->dev_plan = true;
+    b->d_base = (uint64_t*)(m + bl.base);
+  }
   cudaError_t e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     dev_free(c, mem, bl.total, st);
@@ -508,17 +523,32 @@ int block_fill_cache(Block* b) {
   ANS_CUDA(cudaMemcpy(b->h_hdr.data(), b->hdr, b->h_hdr.size() * 8, cudaMemcpyDeviceToHost));
   ANS_CUDA(cudaMemcpy(b->h_q.data(), b->q, b->h_q.size() * sizeof(ans_quantities), cudaMemcpyDeviceToHost));
   ANS_CUDA(cudaMemcpy(&b->h_status, b->status, 4, cudaMemcpyDeviceToHost));
+  if (b->dev_plan) {
+    b->base.resize(b->nseg);
+    ANS_CUDA(cudaMemcpy(b->base.data(), b->d_base, (size_t)b->nseg * 8, cudaMemcpyDeviceToHost));
+    b->cap.resize(b->nseg);
+    for (uint32_t s = 0; s < b->nseg; ++s) b->cap[s] = b->h_hdr[2 * (size_t)s + 1];
+  }
   b->cached = true;
   return ANS_OK;
 }
 
-// The device-side outcome recorded with a block's results.
-int block_status(const Block* b) {
-  if (!b->h_status) return ANS_OK;
-  if (b->h_status == kErrNegative)
-    return fail(ANS_ERR_INVALID_ARG, "a signed combination left a negative count");
-  return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(b->h_status) + ")");
+// A block's host-side padded starts and link bounds (a block planned on the
+// device learns them when it completes: this waits for it).
+int block_plan(Block* b) { return b->dev_plan ? block_fill_cache(b) : ANS_OK; }
+
+// The status code of a device error word.
+int status_of_err(uint32_t err) {
+  if (!err) return ANS_OK;
+  if (err == kErrNegative) return fail(ANS_ERR_INVALID_ARG, "a signed combination left a negative count");
+  if (err & kErrPlan)
+    return fail(ANS_ERR_INVALID_ARG, "device batch offsets decrease, hold a window of 2^31 packets or more, "
+                                     "or exceed the batch capacity");
+  return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(err) + ")");
 }
+
+// The device-side outcome recorded with a block's results.
+int block_status(const Block* b) { return status_of_err(b->h_status); }
 
 // Everything the statistics phases of one segment set need.
 struct StatsBufs {
@@ -711,19 +741,28 @@ struct SumPlan {
   Block* blk = nullptr;
 };
 
+// caps: a bound on each input matrix's links.  dev_gather (optional): a
+// device-resident plan whose segment s covers at least caps[s] items, used
+// as the gather plan instead of one built from caps (a batch planned on the
+// device: its window plan; caps then holds only the total).
 int sum_prepare(ans_ctx* c, char* m, uint32_t k, const std::vector<uint64_t>& caps, size_t off_gplan,
-                size_t off_splan, size_t off_lens, size_t off_total, UploadSet& us, cudaStream_t st, SumPlan* out) {
-  out->gp.build(caps, nullptr);
+                size_t off_splan, size_t off_lens, size_t off_total, UploadSet& us, cudaStream_t st, SumPlan* out,
+                const SegPlan* dev_gather = nullptr) {
   uint64_t total_cap = 0;
   for (uint64_t x : caps) total_cap += x;
   out->sp.build(std::vector<uint64_t>{total_cap}, nullptr);
   ANS_TRY(make_block(c, out->sp.pad, 1, std::vector<uint64_t>{0}, std::vector<uint64_t>{total_cap}, st, &out->blk));
-  DevPlan gdp{off_gplan, off_gplan + align_up(k * 8), off_gplan + 2 * align_up(k * 8),
-              off_gplan + 3 * align_up(k * 8)};
-  us.add(m + gdp.in_off, out->gp.in_off.data(), k * 8);
-  us.add(m + gdp.base, out->gp.base.data(), k * 8);
-  us.add(m + gdp.first_tile, out->gp.first_tile.data(), (k + 1) * 4);
-  out->g = gdp.bind(m, out->gp);
+  if (dev_gather) {
+    out->g = *dev_gather;
+  } else {
+    out->gp.build(caps, nullptr);
+    DevPlan gdp{off_gplan, off_gplan + align_up(k * 8), off_gplan + 2 * align_up(k * 8),
+                off_gplan + 3 * align_up(k * 8)};
+    us.add(m + gdp.in_off, out->gp.in_off.data(), k * 8);
+    us.add(m + gdp.base, out->gp.base.data(), k * 8);
+    us.add(m + gdp.first_tile, out->gp.first_tile.data(), (k + 1) * 4);
+    out->g = gdp.bind(m, out->gp);
+  }
   out->g.len = at<uint64_t>(m, off_lens);
   DevPlan sdp{off_splan, off_splan + kAlign, off_splan + 2 * kAlign, off_splan + 3 * kAlign};
   us.add(m + sdp.in_off, out->sp.in_off.data(), 8);
@@ -875,6 +914,60 @@ int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s,
   return column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st, narrow);
 }
 
+// Time sum of a batch from its packets (sum_path 2): every packet of the
+// batch, as the one segment of `pk`, is packed and sorted again, and the
+// sorted keys are reduced like a window (counts = run lengths) into `blk`,
+// with the sum's row and column statistics.  Runs after the window
+// statistics, whose key buffers, status words and tickets it reuses.  Only
+// queues work on `st`.
+int sum_packets(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& pk, const uint32_t* d_src,
+                const uint32_t* d_dst, Block* blk, cudaStream_t st, bool narrow) {
+  uint64_t* ka = at<uint64_t>(m, ps.keys_a);
+  uint64_t* kb = at<uint64_t>(m, ps.keys_b);
+  uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets);
+  auto cu = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return ANS_OK;
+    return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  int rc;
+  if ((rc = cu(launch_zero(seg_hist, kPasses * kRadix * 4, st), "memset")) ||
+      (rc = cu(launch_zero(m + ps.lb, (size_t)pk.ntiles * 8, st), "memset")) ||
+      (rc = cu(launch_zero(m + ps.col_hist, kColPasses * kRadix * 4, st), "memset")) ||
+      (rc = cu(launch_zero(blk->q, sizeof(ans_quantities), st), "memset")))
+    return rc;
+  if ((rc = cu(timed(c, "pack_hist_sum", st, [&] {
+                 return launch_pack_hist(pk, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st,
+                                         key_subtiles(c->cfg_keys));
+               }), "pack")))
+    return rc;
+  ANS_TRY(sort_segments(c, pk, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1),
+                        tickets, st, "onesweep_pk"));
+  StatsArgs a;
+  a.plan = pk;
+  a.hdr = blk->hdr;
+  a.q = blk->q;
+  a.keys = ka;
+  a.col_ids = blk->col_ids;
+  a.vals = blk->vals;
+  a.row_ids = blk->row_ids;
+  a.row_ptr = blk->row_ptr;
+  a.run_start = at<uint64_t>(m, ps.run_start);
+  a.row_pos = at<uint64_t>(m, ps.row_pos);
+  if (narrow) a.vals32 = (uint32_t*)at<uint64_t>(m, ps.cv_b);
+  a.lookback = at<uint64_t>(m, ps.lb);
+  a.ticket = tickets + kPasses;  // zeroed by the pack kernel
+  a.col_hist = at<uint32_t>(m, ps.col_hist);
+  a.ulen = at<uint64_t>(m, ps.ulen);
+  a.col_st0 = at<uint64_t>(m, ps.st0);
+  a.col_tickets = tickets + 3 * 32;
+  a.err = c->d_err;
+  a.mode = kModeWindow;
+  if ((rc = cu(timed(c, "rle", st, [&] { return launch_rle(a, st); }), "rle"))) return rc;
+  if ((rc = cu(timed(c, "finish", st, [&] { return launch_finish(a, st); }), "finish"))) return rc;
+  return column_pass(c, pk, a.ulen, blk->col_ids, blk->vals, ps, m, a.col_tickets, blk->q, st, narrow);
+}
+
 // Snapshot the device error word into `dst` (device); reset_err clears it.
 int capture_err(ans_ctx* c, uint32_t* dst_dev, cudaStream_t st) {
   ANS_CUDA(cudaMemcpyAsync(dst_dev, c->d_err, 4, cudaMemcpyDeviceToDevice, st));
@@ -983,7 +1076,9 @@ void plan_tables(const std::vector<uint64_t>& lens, std::vector<uint32_t>* lg, H
 struct WinLayout {
   DevPlan dp, dp_big;  // every window; the windows sorted by onesweep passes
   size_t off_small = 0;  // ids of the windows sorted on chip
+  size_t off_colacc = 0; // per-window accumulators of the partitioned column hash
   DevPlan dp_tab;        // hash path: the windows' tables as segments
+  DevPlan dp_pk;         // sum_path 2: all packets of the batch as one segment
   size_t off_tlg = 0, off_special = 0, off_hulen = 0, off_nclaim = 0, off_claims = 0;
   PipeScratch ps;
   size_t s_col = 0, s_vals = 0, s_row = 0, s_rp = 0, s_hdr = 0, s_q = 0;
@@ -995,6 +1090,8 @@ struct WinLayout {
     dp.reserve(L, nseg, addrs);
     dp_big.reserve(L, nseg, addrs);
     off_small = L.add((size_t)nseg * 4);
+    off_colacc = L.add((size_t)nseg * sizeof(ColPartAcc));
+    dp_pk.reserve(L, 1);
     if (hash) {
       dp_tab.reserve(L, nseg);
       off_tlg = L.add((size_t)nseg * 4);
@@ -1028,24 +1125,42 @@ struct WinLayout {
 int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
                 size_t nwin, uint32_t flags, ans_quantities* out, ans_matrix** per_window, ans_matrix** sum,
                 ans_ticket* ticket, cudaStream_t st, const uint32_t* const* h_srcs = nullptr,
-                const uint32_t* const* h_dsts = nullptr) {
-  std::vector<uint64_t> lens(nwin), offs(nwin);
-  for (size_t w = 0; w < nwin; ++w) {
-    if (h_offsets[w + 1] < h_offsets[w]) return fail(ANS_ERR_INVALID_ARG, "offsets must be nondecreasing");
-    lens[w] = h_offsets[w + 1] - h_offsets[w];
-    if (lens[w] > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a window exceeds 2^31 - 1 packets");
-    offs[w] = h_offsets[w];
-  }
-  const uint64_t total = h_offsets[nwin] - h_offsets[0];
-  if (total && !h_srcs && (!d_src || !d_dst)) return fail(ANS_ERR_INVALID_ARG, "NULL packet arrays");
+                const uint32_t* const* h_dsts = nullptr, const uint64_t* d_offsets = nullptr,
+                uint64_t dev_cap = 0) {
+  // dev: the offsets live on the device and the batch is planned there
+  // (launch_plan); the host sizes everything for dev_cap packets.
+  const bool dev = d_offsets != nullptr;
   if (nwin > 0xFFFFFFF0ull) return fail(ANS_ERR_INVALID_ARG, "too many windows");
+  std::vector<uint64_t> lens(nwin), offs(nwin);
+  uint64_t total = dev_cap;
+  if (!dev) {
+    for (size_t w = 0; w < nwin; ++w) {
+      if (h_offsets[w + 1] < h_offsets[w]) return fail(ANS_ERR_INVALID_ARG, "offsets must be nondecreasing");
+      lens[w] = h_offsets[w + 1] - h_offsets[w];
+      if (lens[w] > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a window exceeds 2^31 - 1 packets");
+      offs[w] = h_offsets[w];
+    }
+    total = h_offsets[nwin] - h_offsets[0];
+  }
+  if (total && !h_srcs && (!d_src || !d_dst)) return fail(ANS_ERR_INVALID_ARG, "NULL packet arrays");
   const bool want_mats = (flags & ANS_BATCH_MATRICES) != 0;
   const bool want_sum = (flags & ANS_BATCH_SUM) != 0;
   if (want_sum && total > kMaxWindow) return fail(ANS_ERR_INVALID_ARG, "a time sum is limited to 2^31 - 1 links");
   const uint32_t nseg = (uint32_t)nwin;
 
   HostPlan hp;
-  hp.build(lens, &offs);
+  if (dev) {  // a bound: every window may add up to one tile of padding
+    const uint64_t nt = nseg ? tiles_for(total) + nseg : 0;
+    if (nt > 0xFFFFFFF0ull) return fail(ANS_ERR_INVALID_ARG, "batch capacity too large");
+    hp.in_off.assign(nseg, 0);
+    hp.len.assign(nseg, 0);
+    hp.base.assign(nseg, 0);
+    hp.first_tile.assign(nseg + 1, 0);
+    hp.ntiles = (uint32_t)nt;
+    hp.pad = nt * kTile;
+  } else {
+    hp.build(lens, &offs);
+  }
   if ((uint64_t)hp.ntiles * kTile != hp.pad) return fail(ANS_ERR_INTERNAL, "plan");
   if (h_srcs) {  // every window's own arrays
     hp.src_at.resize(nwin);
@@ -1060,19 +1175,24 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   std::vector<uint32_t> small_ids, big_ids;
   const int win_path = c->win_path;  // the caller holds c->mu
   const SortCfg cfg_win = c->cfg_win;
-  const bool on_chip = win_path == 0 && cluster_sort_clusters(c->device) > 0;
+  const bool on_chip = !dev && win_path == 0 && cluster_sort_clusters(c->device) > 0;
   for (uint32_t s = 0; s < nseg; ++s) {
     if (on_chip && lens[s] <= kClusterWindowMax) small_ids.push_back(s);
     else big_ids.push_back(s);
   }
   HostPlan hp_big;
-  hp_big.subset(hp, big_ids);
+  if (dev) hp_big = hp;  // planned on the device: the onesweep passes take every window
+  else hp_big.subset(hp, big_ids);
   // Hash path: one table per window of 2^lg >= 2 * packets slots (at least
   // one tile; none for an empty window), as segments of the table arena.
   const bool hash = c->agg_path == 1 && nseg > 0;
   HostPlan hp_tab;
   std::vector<uint32_t> tab_lg;
-  if (hash) plan_tables(lens, &tab_lg, &hp_tab);
+  if (hash && dev) {  // a bound: 2^lg < max(2^13 + 1, 4 * packets)
+    hp_tab.pad = (uint64_t)nseg * (1ull << 13) + 4 * total;
+  } else if (hash) {
+    plan_tables(lens, &tab_lg, &hp_tab);
+  }
 
   // ---- scratch layout
   WinLayout wl;
@@ -1090,8 +1210,12 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
 
   Block* blk = nullptr;
   if (want_mats && nseg > 0) {
-    std::vector<uint64_t> caps(lens);
-    ANS_TRY(make_block(c, hp.pad, nseg, hp.base, caps, st, &blk));
+    if (dev) {
+      ANS_TRY(make_block(c, hp.pad, nseg, {}, {}, st, &blk, true));
+    } else {
+      std::vector<uint64_t> caps(lens);
+      ANS_TRY(make_block(c, hp.pad, nseg, hp.base, caps, st, &blk));
+    }
   }
   StatsBufs sb;
   if (blk) {
@@ -1113,7 +1237,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   // block; every small array goes to the device in one staged upload.
   int rc = ANS_OK;
   UploadSet us;
-  if (nseg) {
+  if (nseg && !dev) {
     us.add(m + dp.in_off, hp.in_off.data(), nseg * 8);
     us.add(m + dp.len, hp.len.data(), nseg * 8);
     us.add(m + dp.base, hp.base.data(), nseg * 8);
@@ -1124,11 +1248,26 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     }
   }
   if (!small_ids.empty()) us.add(m + wl.off_small, small_ids.data(), small_ids.size() * 4);
-  if (hash) {
+  // sum_path 2: all packets of the batch as one segment (device-planned
+  // batches: its offset and length come from the planner, the tile count is
+  // the capacity's)
+  const bool sum_pk = want_sum && nseg && c->sum_path == 2 && !h_srcs;
+  HostPlan hp_pk;
+  if (sum_pk) {
+    std::vector<uint64_t> pk_off{dev ? 0 : h_offsets[0]};
+    hp_pk.build(std::vector<uint64_t>{total}, &pk_off);
+    if (!dev) {
+      us.add(m + wl.dp_pk.in_off, hp_pk.in_off.data(), 8);
+      us.add(m + wl.dp_pk.len, hp_pk.len.data(), 8);
+    }
+    us.add(m + wl.dp_pk.base, hp_pk.base.data(), 8);
+    us.add(m + wl.dp_pk.first_tile, hp_pk.first_tile.data(), 8);
+  }
+  if (hash && !dev) {
     us.add(m + wl.dp_tab.base, hp_tab.base.data(), nseg * 8);
     us.add(m + wl.off_tlg, tab_lg.data(), nseg * 4);
   }
-  if (!hash && !big_ids.empty()) {
+  if (!hash && !big_ids.empty() && !dev) {
     const size_t nb = big_ids.size();
     us.add(m + wl.dp_big.in_off, hp_big.in_off.data(), nb * 8);
     us.add(m + wl.dp_big.len, hp_big.len.data(), nb * 8);
@@ -1139,8 +1278,13 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       us.add(m + wl.dp_big.dst_at, hp_big.dst_at.data(), nb * 8);
     }
   }
+  const SegPlan p = dp.bind(m, hp);
   std::vector<MatDesc> md;
-  if (want_sum && nseg) {
+  if (want_sum && nseg && dev) {  // descriptors written by the device planner; the window plan gathers
+    if ((rc = sum_prepare(c, m, nseg, std::vector<uint64_t>{total}, off_gplan, off_splan, off_lens, off_total, us,
+                          st, &sump, &p)))
+      return bail(rc);
+  } else if (want_sum && nseg) {
     md.resize(nseg);
     for (uint32_t s = 0; s < nseg; ++s) {
       md[s].row_ids = sb.row_ids + hp.base[s];
@@ -1154,7 +1298,6 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       return bail(rc);
   }
   if ((rc = us.flush(c, st))) return bail(rc);
-  const SegPlan p = dp.bind(m, hp);
 
   auto cu = [&](cudaError_t e, const char* what) -> int {
     if (e == cudaSuccess) return ANS_OK;
@@ -1177,6 +1320,33 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     uint64_t* kb = at<uint64_t>(m, ps.keys_b);
     uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
     uint32_t* tickets = at<uint32_t>(m, ps.tickets);
+    if (nseg && dev) {  // the plan of the batch, from the device-resident offsets
+      DevPlanOut o;
+      o.in_off = at<uint64_t>(m, dp.in_off);
+      o.len = at<uint64_t>(m, dp.len);
+      o.base = at<uint64_t>(m, dp.base);
+      o.first_tile = at<uint32_t>(m, dp.first_tile);
+      if (hash) {
+        o.tab_lg = at<uint32_t>(m, wl.off_tlg);
+        o.tab_base = at<uint64_t>(m, wl.dp_tab.base);
+      }
+      if (blk) o.blk_base = blk->d_base;
+      if (sum_pk) {
+        o.pk_in_off = at<uint64_t>(m, wl.dp_pk.in_off);
+        o.pk_len = at<uint64_t>(m, wl.dp_pk.len);
+      }
+      if (want_sum) {
+        o.md = at<MatDesc>(m, off_mats);
+        o.row_ids = sb.row_ids;
+        o.row_ptr = sb.row_ptr;
+        o.col_ids = sb.col_ids;
+        o.vals = sb.vals;
+        o.hdr = sb.hdr;
+      }
+      if ((rc = cu(timed(c, "plan", ls, [&] { return launch_plan(d_offsets, nseg, total, o, c->d_err, ls); }),
+                   "plan")))
+        return rc;
+    }
     if (nseg) {
       if ((rc = cu(launch_zero(sb.q, (size_t)nseg * sizeof(ans_quantities), ls), "memset q"))) return rc;
       if ((rc = cu(launch_zero(m + ps.lb, (size_t)hp.ntiles * 8, ls), "memset lb"))) return rc;
@@ -1233,7 +1403,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
           return rc;
       }
       if (!hash && !big_ids.empty()) {
-        const SegPlan pb = wl.dp_big.bind(m, hp_big);
+        const SegPlan pb = dev ? p : wl.dp_big.bind(m, hp_big);
         const size_t nb = big_ids.size();
         if ((rc = cu(launch_zero(seg_hist, nb * kPasses * kRadix * 4, ls), "memset hist"))) return rc;
         if ((rc = cu(timed(c, "pack_hist", ls, [&] { return launch_pack_hist(pb, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, ls,
@@ -1285,6 +1455,14 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       if (rc == ANS_OK && c->col_hash)
         rc = cu(timed(c, "colhash", ls, [&] { return launch_colhash(pw, a.ulen, sb.col_ids, a.vals32, sb.q, ls); }),
                 "colhash");
+      if (rc == ANS_OK && c->col_hash) {  // windows with more destinations than one table holds
+        ColPartAcc* acc = at<ColPartAcc>(m, wl.off_colacc);
+        rc = cu(launch_zero(acc, (size_t)nseg * sizeof(ColPartAcc), ls), "memset");
+        if (rc == ANS_OK)
+          rc = cu(timed(c, "colhash_part", ls,
+                        [&] { return launch_colhash_part(pw, a.ulen, sb.col_ids, a.vals32, acc, sb.q, ls); }),
+                  "colhash part");
+      }
       if (rc == ANS_OK) rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls, true);
       if (forked) {  // join (also after a failure, so that a capture ends joined)
         const cudaError_t ew = cudaStreamWaitEvent(ls, c->ev_join, 0);
@@ -1301,6 +1479,9 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         if ((rc = cu(launch_zero(sblk->q, sizeof(ans_quantities), ls), "memset"))) return rc;
       } else if (forked) {  // a sum of window counts stays below the batch's packets
         if ((rc = links_to_block(c, m, ps, sump.s, sfk, sfv, sump.blk, ls, total < (1ull << 32)))) return rc;
+      } else if (sum_pk) {
+        if ((rc = sum_packets(c, m, ps, wl.dp_pk.bind(m, hp_pk), d_src, d_dst, sump.blk, ls, total < (1ull << 32))))
+          return rc;
       } else {
         rc = sum_launch(c, m, ps, at<MatDesc>(m, off_mats), nseg, &sump, off_catoff, off_lens, off_total, ls,
                         total < (1ull << 32));
@@ -1314,7 +1495,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   // the column hash's cluster shape changes with the window count: a cached
   // graph must not be updated to another one
   const std::string sig = launch_sig(flags, hp.ntiles > 0, !small_ids.empty(), !big_ids.empty(), rounds, c) + "/h" +
-                          std::to_string(c->col_hash && nseg ? colhash_ctas(nseg) : 0u);
+                          std::to_string(c->col_hash && nseg ? colhash_ctas(nseg) : 0u) + (dev ? "/d" : "");
   if ((rc = run_launches(c, st, sig, launch_all))) return bail(rc);
   if (sump.blk) {  // the time sum's block is filled
     sblk = sump.blk;
@@ -1488,6 +1669,7 @@ int combine_matrices(ans_ctx* c, const ans_matrix* const* mats, const int* signs
     if (!x) return fail(ANS_ERR_INVALID_ARG, "NULL matrix");
     const Block* b = x->blk;
     if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
+    ANS_TRY(block_plan(const_cast<Block*>(b)));
     const uint64_t bs = b->base[x->seg];
     const bool neg = signs && signs[i] < 0;
     any_neg = any_neg || neg;
@@ -1693,9 +1875,33 @@ int ans_build_window(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, u
                      (cudaStream_t)stream);
 }
 
-int ans_batch_submit(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
+int ans_batch_submit(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* d_offsets,
                      size_t nwin, uint32_t flags, ans_quantities* out, ans_matrix** per_window, ans_matrix** sum,
                      ans_ticket* ticket, void* stream) {
+  if (!c || !d_offsets) return fail(ANS_ERR_INVALID_ARG, "NULL context or offsets");
+  if (flags & ~(ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC))
+    return fail(ANS_ERR_INVALID_ARG, "unknown flag");
+  if ((flags & ANS_BATCH_MATRICES) && !per_window) return fail(ANS_ERR_INVALID_ARG, "per_window is NULL");
+  if ((flags & ANS_BATCH_SUM) && !sum) return fail(ANS_ERR_INVALID_ARG, "sum is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  uint64_t cap = c->batch_cap;
+  if (cap == 0 && nwin > 0) {  // no capacity set: size the batch by its first and last offsets
+    uint64_t ends[2] = {0, 0};
+    ANS_CUDA(cudaMemcpyAsync(&ends[0], d_offsets, 8, cudaMemcpyDeviceToHost, st));
+    ANS_CUDA(cudaMemcpyAsync(&ends[1], d_offsets + nwin, 8, cudaMemcpyDeviceToHost, st));
+    ANS_CUDA(cudaStreamSynchronize(st));
+    if (ends[1] < ends[0]) return fail(ANS_ERR_INVALID_ARG, "offsets must be nondecreasing");
+    cap = ends[1] - ends[0];
+  }
+  return run_windows(c, d_src, d_dst, nullptr, nwin, flags, out, per_window, sum, ticket, st, nullptr, nullptr,
+                     d_offsets, cap);
+}
+
+int ans_batch_submit_host(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
+                          size_t nwin, uint32_t flags, ans_quantities* out, ans_matrix** per_window, ans_matrix** sum,
+                          ans_ticket* ticket, void* stream) {
   if (!c || !h_offsets) return fail(ANS_ERR_INVALID_ARG, "NULL context or offsets");
   if (flags & ~(ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC))
     return fail(ANS_ERR_INVALID_ARG, "unknown flag");
@@ -1704,6 +1910,15 @@ int ans_batch_submit(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, c
   std::lock_guard<std::mutex> g(c->mu);
   DeviceGuard dg(c->device);
   return run_windows(c, d_src, d_dst, h_offsets, nwin, flags, out, per_window, sum, ticket, (cudaStream_t)stream);
+}
+
+int ans_set_batch_capacity(ans_ctx* c, uint64_t max_packets) {
+  if (!c) return fail(ANS_ERR_INVALID_ARG, "NULL context");
+  if (max_packets > ((uint64_t)0xFFFFFFF0ull - (1ull << 20)) * kTile)
+    return fail(ANS_ERR_INVALID_ARG, "batch capacity too large");
+  std::lock_guard<std::mutex> g(c->mu);
+  c->batch_cap = max_packets;
+  return ANS_OK;
 }
 
 int ans_batch_submit_windows(ans_ctx* c, const uint32_t* const* srcs, const uint32_t* const* dsts,
@@ -1766,6 +1981,7 @@ int ans_network_quantities(ans_ctx* c, const ans_matrix* x, ans_quantities* out,
   DeviceGuard dg(c->device);
   const Block* b = x->blk;
   if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
+  ANS_TRY(block_plan(const_cast<Block*>(b)));
   ANS_CUDA(cudaStreamWaitEvent(st, b->done, 0));
   ANS_TRY(matrix_stats(c, b, x->seg, out, st));
   ANS_CUDA(cudaMemsetAsync(c->d_err, 0, 4, st));
@@ -1854,8 +2070,7 @@ int ans_wait(ans_ctx* c, ans_ticket t, uint64_t timeout_ns) {
     cudaEventDestroy(ev);
     c->tickets.erase(t);
   }
-  if (err) return fail(ANS_ERR_INTERNAL, "device check failed (code " + std::to_string(err) + ")");
-  return ANS_OK;
+  return status_of_err(err);
 }
 
 int ans_set_wait_limit(ans_ctx* c, uint32_t polls) {
@@ -2056,7 +2271,7 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
                 "passes also take 256 threads with blocks 4");
   if (t->win_path > 1 || t->win_rank > 1 || !ok(t->win_threads, t->win_rank, 1))
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
-  if (t->sum_path > 1) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0 or 1");
+  if (t->sum_path > 2) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0, 1 or 2");
   if (t->agg_path > 1) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0 or 1");
   if (t->graph > 1) return fail(ANS_ERR_INVALID_ARG, "graph must be 0 or 1");
   if (t->col_hash > 1) return fail(ANS_ERR_INVALID_ARG, "col_hash must be 0 or 1");
@@ -2096,8 +2311,9 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   std::vector<ans_matrix*> per(nwin, nullptr);
   auto run_once = [&]() -> int {
     ans_matrix* sum = nullptr;
-    int rc = ans_batch_submit(c, d_src, d_dst, h_offsets, nwin, ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC,
-                              nullptr, per.data(), &sum, nullptr, stream);
+    int rc = ans_batch_submit_host(c, d_src, d_dst, h_offsets, nwin,
+                                   ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC, nullptr, per.data(), &sum,
+                                   nullptr, stream);
     if (rc != ANS_OK) return rc;
     for (auto& m : per) {
       ans_matrix_free(m);
@@ -2145,8 +2361,8 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       for (int rep = 0; rep < 2 && rc == ANS_OK; ++rep) {
         cudaEventRecord(e0, (cudaStream_t)stream);
         ans_matrix* sum = nullptr;
-        rc = ans_batch_submit(c, d_src, d_dst, h_offsets, nwin, ANS_BATCH_MATRICES | ANS_BATCH_SUM, nullptr,
-                              per.data(), &sum, nullptr, stream);
+        rc = ans_batch_submit_host(c, d_src, d_dst, h_offsets, nwin, ANS_BATCH_MATRICES | ANS_BATCH_SUM, nullptr,
+                                   per.data(), &sum, nullptr, stream);
         cudaEventRecord(e1, (cudaStream_t)stream);
         if (rc == ANS_OK) {
           float ms = 0;
@@ -2237,8 +2453,8 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   // production path runs it, everything else as chosen.
   int sum_path = 0;
   {
-    double wall[2] = {kNever, kNever};
-    for (int sp = 0; sp < 2; ++sp) {
+    double wall[3] = {kNever, kNever, kNever};
+    for (int sp = 0; sp < 3; ++sp) {
       Prof pr;
       bool ran = false;
       ANS_TRY(trial([&] {
@@ -2250,7 +2466,8 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       }, &pr, &ran));
       if (ran) wall[sp] = pr[kWall];
     }
-    sum_path = wall[1] < wall[0] ? 1 : 0;
+    for (int sp = 1; sp < 3; ++sp)
+      if (wall[sp] < wall[sum_path]) sum_path = sp;
   }
   // Merge rounds: 4096 or 2048 output positions per CTA (the smaller tile
   // fits more CTAs per SM; the larger needs fewer merge-path searches).

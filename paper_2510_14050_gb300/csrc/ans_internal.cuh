@@ -44,7 +44,9 @@ enum ErrBits : uint32_t {
   kErrLookback = 1u,   // a look-back wait hit its poll limit
   kErrHashFull = 2u,   // a hash probe sequence found no free slot
   kErrNegative = 4u,   // a signed combination left a negative count
+  kErrPlan = 8u,       // device-resident batch offsets were invalid or above the capacity
 };
+constexpr uint64_t kMaxWindowItems = (1ull << 31) - 1;  // packets of one window, links of one time sum
 
 // How a onesweep pass is launched (chosen per context by the autotuner):
 // threads per 8192-key tile (512 or 1024; for the 64-bit key passes and the
@@ -138,6 +140,38 @@ struct MatDesc {
   const uint64_t* hdr;  // {nrows, nnz}
   uint64_t neg = 0;     // 1: the matrix enters a combination with sign -1 (values negated mod 2^64)
 };
+
+// Outputs of the device-side batch planner (launch_plan): the window plan
+// (in_off, len, base: nseg entries; first_tile: nseg + 1), optionally the
+// hash path's table plan (tab_lg, tab_base), a copy of the padded starts in
+// the per-window matrix block (blk_base), the offset and length of all the
+// batch's packets as one segment (pk_in_off, pk_len), and the time sum's matrix
+// descriptors (md) over the statistics arrays row_ids / row_ptr / col_ids /
+// vals / hdr.  Null pointers are skipped.
+struct DevPlanOut {
+  uint64_t* in_off = nullptr;
+  uint64_t* len = nullptr;
+  uint64_t* base = nullptr;
+  uint32_t* first_tile = nullptr;
+  uint32_t* tab_lg = nullptr;
+  uint64_t* tab_base = nullptr;
+  uint64_t* blk_base = nullptr;
+  uint64_t* pk_in_off = nullptr;  // the batch's packets as one segment: its offset and length
+  uint64_t* pk_len = nullptr;
+  MatDesc* md = nullptr;
+  const uint32_t* row_ids = nullptr;
+  const uint64_t* row_ptr = nullptr;
+  const uint32_t* col_ids = nullptr;
+  const uint64_t* vals = nullptr;
+  const uint64_t* hdr = nullptr;
+};
+
+// ---- launcher (ans_plan.cu) ------------------------------------------------
+// Plan the nseg windows [d_offsets[s], d_offsets[s+1]) on the device (one
+// CTA; nseg > 0).  Invalid offsets, or more than `cap` packets in all, give
+// every window length 0 and set kErrPlan in err[0].
+cudaError_t launch_plan(const uint64_t* d_offsets, uint32_t nseg, uint64_t cap, const DevPlanOut& o, uint32_t* err,
+                        cudaStream_t st);
 
 // Record `msg` as the calling thread's ans_last_error() text; returns code.
 int set_last_error(int code, const std::string& msg);
@@ -260,6 +294,17 @@ cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col
 // words, zero on entry).  Each wait gives up after the context's poll limit
 // and sets kErrLookback in err[0].
 cudaError_t launch_wait_probe(const uint64_t* st, uint32_t* err, cudaStream_t stream);
+// Per-window accumulator of the partitioned column hash (zeroed before it).
+struct ColPartAcc {
+  unsigned long long count, max_fanin, max_packets;
+  uint32_t fail, done;
+};
+// Window column statistics of the windows launch_colhash left (ulen[s] > 0)
+// with between 2 and 32 x 8192 links: their destinations split by a hash
+// between several CTAs, one shared-memory table each; windows whose
+// partitions all fit get their three column quantities and ulen[s] = 0.
+cudaError_t launch_colhash_part(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
+                                ColPartAcc* acc, ans_quantities* q, cudaStream_t st);
 // Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.

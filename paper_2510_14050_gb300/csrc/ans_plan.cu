@@ -1,0 +1,122 @@
+// Device-side planning of a batch whose window offsets live in device
+// memory (Sec. III-C batching with the offsets produced on the GPU).
+//
+// The host knows only the number of windows and a capacity (an upper bound
+// on the batch's packets); it sizes scratch and grids for that bound.  This
+// kernel turns the offsets into the plan every other kernel reads -- each
+// window's input offset, length, padded start and first tile (an exclusive
+// scan of the windows' tile counts), the hash path's per-window table sizes
+// and offsets, and the time sum's matrix descriptors -- so that nothing
+// returns to the host.  Tiles past the plan's last one find no items and
+// leave at once.  Offsets that decrease, a window of 2^31 packets or more,
+// or a batch above the capacity make every window empty and set kErrPlan in
+// the context's error word; the batch then reports ANS_ERR_INVALID_ARG.
+#include "ans_internal.cuh"
+
+namespace ans {
+
+namespace {
+
+constexpr int kPlanThreads = 1024;
+
+__device__ __forceinline__ uint32_t table_lg(uint64_t len) {
+  uint32_t l = 13;  // at least one tile of slots
+  while ((1ull << l) < 2 * len) ++l;
+  return l;
+}
+
+// Block-wide exclusive scan of one uint64 per thread; returns the exclusive
+// prefix and writes the block total to *total.
+__device__ __forceinline__ uint64_t scan_excl_u64(uint64_t v, uint64_t* tmp, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[warp] = x;
+  __syncthreads();
+  uint64_t off = 0, tot = 0;
+  for (int w = 0; w < kPlanThreads / 32; ++w) {
+    const uint64_t s = tmp[w];
+    off += w < warp ? s : 0ull;
+    tot += s;
+  }
+  *total = tot;
+  __syncthreads();
+  return off + x - v;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan(const uint64_t* __restrict__ off, uint32_t nseg, uint64_t cap,
+                                                       DevPlanOut o, uint32_t* err) {
+  __shared__ uint64_t s_tmp[kPlanThreads / 32];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  // validate: nondecreasing, every window below 2^31 packets, total within the capacity
+  int bad = 0;
+  for (uint32_t s = threadIdx.x; s < nseg; s += kPlanThreads) {
+    const uint64_t a = off[s], b = off[s + 1];
+    if (b < a || b - a > kMaxWindowItems) bad = 1;
+  }
+  if (threadIdx.x == 0 && off[nseg] >= off[0] && off[nseg] - off[0] > cap) bad = 1;
+  if (bad) s_bad = 1;
+  __syncthreads();
+  const bool ok = s_bad == 0;
+  if (!ok && threadIdx.x == 0) atomicOr(err, (uint32_t)kErrPlan);
+
+  uint64_t tile_carry = 0, slot_carry = 0;
+  for (uint32_t c0 = 0; c0 < nseg; c0 += kPlanThreads) {
+    const uint32_t s = c0 + threadIdx.x;
+    const bool in = s < nseg;
+    const uint64_t len = in && ok ? off[s + 1] - off[s] : 0ull;
+    const uint64_t tiles = (len + kTile - 1) / kTile;
+    const uint64_t slots = len ? (1ull << table_lg(len)) : 0ull;
+    uint64_t ttot, stot;
+    const uint64_t tex = scan_excl_u64(tiles, s_tmp, &ttot);
+    const uint64_t sex = scan_excl_u64(slots, s_tmp, &stot);
+    if (in) {
+      const uint64_t ft = tile_carry + tex;
+      const uint64_t base = ft * kTile;
+      o.in_off[s] = ok ? off[s] : 0ull;
+      o.len[s] = len;
+      o.base[s] = base;
+      o.first_tile[s] = (uint32_t)ft;
+      if (o.blk_base) o.blk_base[s] = base;
+      if (o.tab_lg) {
+        o.tab_lg[s] = table_lg(len);
+        o.tab_base[s] = slot_carry + sex;
+      }
+      if (o.md) {
+        MatDesc d;
+        d.row_ids = o.row_ids + base;
+        d.row_ptr = o.row_ptr + base + s;
+        d.col_ids = o.col_ids + base;
+        d.vals = o.vals + base;
+        d.hdr = o.hdr + 2 * (uint64_t)s;
+        d.neg = 0;
+        o.md[s] = d;
+      }
+    }
+    tile_carry += ttot;
+    slot_carry += stot;
+  }
+  if (threadIdx.x == 0) {
+    o.first_tile[nseg] = (uint32_t)tile_carry;
+    if (o.pk_in_off) {
+      o.pk_in_off[0] = ok ? off[0] : 0ull;
+      o.pk_len[0] = ok ? off[nseg] - off[0] : 0ull;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const uint64_t* d_offsets, uint32_t nseg, uint64_t cap, const DevPlanOut& o, uint32_t* err,
+                        cudaStream_t st) {
+  k_plan<<<1, kPlanThreads, 0, st>>>(d_offsets, nseg, cap, o, err);
+  return cudaGetLastError();
+}
+
+}  // namespace ans

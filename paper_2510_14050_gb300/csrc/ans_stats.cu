@@ -893,6 +893,139 @@ __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_cl(SegPlan p, ui
   }
 }
 
+// Windows with more destinations than one table holds: the destinations
+// are split between up to kColParts CTAs by a hash (CTA r of window s takes
+// the destinations whose partition is r), each counting its share of the
+// window's links in its own shared-memory table -- every CTA reads all the
+// window's links (from L2 after the first) and keeps only its own.  A
+// window of n links gets ceil(n / kColPartLinks) partitions (n bounds its
+// distinct destinations).  Partial results meet in a per-window accumulator;
+// the last CTA of a window to finish writes the window's three quantities
+// and marks it done (ulen = 0) -- unless some partition overflowed its
+// table, in which case the window is left, untouched, to the column sort.
+constexpr uint32_t kColParts = 32;
+constexpr uint32_t kColPartLinks = 8192;
+
+// Finalizer-derived partition of a destination: the high bits of its mix
+// (the table slot uses the low bits), scaled to [0, parts).
+__device__ __forceinline__ uint32_t col_part(uint32_t d, uint32_t parts) {
+  return (uint32_t)(((uint64_t)(fmix32(d) >> 14) * parts) >> 18);
+}
+
+__global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_part(SegPlan p, uint64_t* __restrict__ ulen,
+                                                                      const uint32_t* __restrict__ col_ids,
+                                                                      const uint32_t* __restrict__ vals32,
+                                                                      ColPartAcc* __restrict__ acc,
+                                                                      ans_quantities* __restrict__ q) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* t_key = sm;
+  uint32_t* t_cnt = sm + kColHashSlots;
+  uint32_t* t_sum = sm + 2 * kColHashSlots;
+  __shared__ uint32_t s_fill, s_over, s_spec_cnt, s_spec_sum, s_last;
+  __shared__ unsigned long long s_red[3][kColHashThreads / 32];
+  const uint32_t s = blockIdx.x / kColParts, r = blockIdx.x % kColParts;
+  if (s >= p.nseg) return;
+  const uint64_t n = ulen[s];
+  if (n == 0) return;  // empty, or finished by the one-table hash
+  const uint64_t parts64 = (n + kColPartLinks - 1) / kColPartLinks;
+  if (parts64 < 2 || parts64 > kColParts) return;  // the one-table hash's case, or too many for this kernel
+  const uint32_t parts = (uint32_t)parts64;
+  if (r >= parts) return;
+  const uint64_t b = p.base[s];
+  for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
+    t_key[i] = kColEmpty;
+    t_cnt[i] = 0;
+    t_sum[i] = 0;
+  }
+  if (threadIdx.x == 0) s_fill = s_over = s_spec_cnt = s_spec_sum = 0;
+  __syncthreads();
+  for (uint64_t u = threadIdx.x; u < n; u += kColHashThreads) {
+    if (*(volatile uint32_t*)&s_over) break;
+    const uint32_t d = col_ids[b + u];
+    if (col_part(d, parts) != r) continue;
+    const uint32_t v = vals32[b + u];
+    if (d == kColEmpty) {
+      atomicAdd(&s_spec_cnt, 1u);
+      atomicAdd(&s_spec_sum, v);
+      continue;
+    }
+    uint32_t h = fmix32(d) & (kColHashSlots - 1);
+    for (uint32_t probe = 0; probe < kColHashSlots; ++probe) {
+      uint32_t cur = *(volatile uint32_t*)&t_key[h];
+      if (cur == kColEmpty) {
+        cur = atomicCAS(&t_key[h], kColEmpty, d);
+        if (cur == kColEmpty) {
+          cur = d;
+          if (atomicAdd(&s_fill, 1u) + 1 > kColHashMaxFill) s_over = 1;
+        }
+      }
+      if (cur == d) {
+        atomicAdd(&t_cnt[h], 1u);
+        atomicAdd(&t_sum[h], v);
+        break;
+      }
+      h = (h + 1) & (kColHashSlots - 1);
+    }
+  }
+  __syncthreads();
+  ColPartAcc* a = acc + s;
+  if (!s_over) {
+    unsigned long long c = 0, mcnt = 0, msum = 0;
+    for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
+      if (t_key[i] != kColEmpty) {
+        ++c;
+        mcnt = t_cnt[i] > mcnt ? t_cnt[i] : mcnt;
+        msum = t_sum[i] > msum ? t_sum[i] : msum;
+      }
+    }
+    c = warp_sum(c);
+    mcnt = warp_max(mcnt);
+    msum = warp_max(msum);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      s_red[0][warp] = c;
+      s_red[1][warp] = mcnt;
+      s_red[2][warp] = msum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      c = 0;
+      mcnt = msum = 0;
+      for (int w = 0; w < kColHashThreads / 32; ++w) {
+        c += s_red[0][w];
+        mcnt = s_red[1][w] > mcnt ? s_red[1][w] : mcnt;
+        msum = s_red[2][w] > msum ? s_red[2][w] : msum;
+      }
+      if (s_spec_cnt) {
+        ++c;
+        mcnt = s_spec_cnt > mcnt ? s_spec_cnt : mcnt;
+        msum = s_spec_sum > msum ? s_spec_sum : msum;
+      }
+      if (c) atomicAdd(&a->count, c);
+      if (mcnt) atomicMax(&a->max_fanin, mcnt);
+      if (msum) atomicMax(&a->max_packets, msum);
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(&a->fail, 1u);
+  }
+  // The last partition of the window to arrive publishes the result.
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a->done, 1u) == parts - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_last) {
+    __threadfence();
+    const volatile ColPartAcc* va = a;
+    if (va->fail == 0) {
+      q[s].unique_destinations = va->count;
+      q[s].max_destination_fanin = va->max_fanin;
+      q[s].max_destination_packets = va->max_packets;
+      ulen[s] = 0;  // done: the column sort skips this window
+    }
+  }
+}
+
 // CTAs per window for the cluster form (1 = the one-CTA kernel): enough to
 // cover the SMs with the batch's windows, if the device hosts such clusters.
 uint32_t colhash_cluster_size(uint32_t nseg) {
@@ -961,6 +1094,22 @@ cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col
     return cudaLaunchKernelEx(&lc, k_colhash_cl, p, ulen, col_ids, vals32, q);
   }
   k_colhash<<<p.nseg, kColHashThreads, kColHashSmem, st>>>(p, ulen, col_ids, vals32, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colhash_part(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
+                                ColPartAcc* acc, ans_quantities* q, cudaStream_t st) {
+  if (p.nseg == 0) return cudaSuccess;
+  static unsigned long long configured = 0;  // one bit per device ordinal
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !((configured >> dev) & 1ull)) {
+    e = cudaFuncSetAttribute(k_colhash_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColHashSmem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) configured |= 1ull << dev;
+  }
+  k_colhash_part<<<p.nseg * kColParts, kColHashThreads, kColHashSmem, st>>>(p, ulen, col_ids, vals32, acc, q);
   return cudaGetLastError();
 }
 

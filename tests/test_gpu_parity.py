@@ -347,11 +347,12 @@ def test_window_sort_degenerate_windows(ans, n, path):
         c.close()
 
 
-@pytest.mark.parametrize("sum_path,merge_tile", [(0, 4096), (0, 2048), (1, 4096)])
+@pytest.mark.parametrize("sum_path,merge_tile", [(0, 4096), (0, 2048), (1, 4096), (2, 4096)])
 @pytest.mark.parametrize("nwin", [1, 2, 3, 5, 8, 13])
 def test_time_sum_paths_are_exact(ans, synth, sum_path, merge_tile, nwin):
-    """Time sums by pairwise merges (0, with either merge tile) and by radix
-    passes (1), for window counts that leave odd runs and empty windows at
+    """Time sums by pairwise merges (0, with either merge tile), by radix
+    passes over the windows' links (1) and by sorting the batch's packets
+    again (2), for window counts that leave odd runs and empty windows at
     every merge round."""
     sizes = [(i * 7919) % 30000 if i % 4 != 2 else 0 for i in range(nwin)]
     sizes[0] = max(sizes[0], 3)
@@ -644,6 +645,57 @@ def test_column_hash_over_clusters(ans, nwin):
         c.close()
 
 
+def _fmix32(h):
+    """MurmurHash3's 32-bit finalizer (Appleby), vectorised."""
+    h = np.asarray(h, dtype=np.uint64)
+    m = np.uint64(0xFFFFFFFF)
+    h ^= h >> np.uint64(16)
+    h = (h * np.uint64(0x85EBCA6B)) & m
+    h ^= h >> np.uint64(13)
+    h = (h * np.uint64(0xC2B2AE35)) & m
+    h ^= h >> np.uint64(16)
+    return h
+
+
+@pytest.mark.parametrize("col_hash", [1, 0])
+def test_column_hash_over_destination_partitions(ans, col_hash):
+    """Windows with more distinct destinations than one shared-memory table
+    holds: split into 2..32 destination partitions (8192 links each) by the
+    partitioned hash, with the boundaries of its range (2^18 links, one more),
+    windows whose links hit few destinations, the all-ones destination among
+    many, and a window whose destinations all fall in one partition (it
+    overflows its table and is left to the column sort) -- all equal to the
+    oracle, whichever path each window takes."""
+    from paper_2510_14050_gb300 import synth as sy
+    rng = np.random.default_rng(17)
+    wins = []
+    for n in (8193, 16384, 16385, 60000, 150000, 1 << 18, (1 << 18) + 1):
+        d = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        if n == 60000:
+            d[::5] = 0xFFFFFFFF
+        wins.append((rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32), d))
+    # few destinations behind many links: the one-table hash finishes it
+    wins.append((rng.integers(0, 1 << 32, 100000, dtype=np.uint64).astype(np.uint32),
+                 rng.integers(0, 3000, 100000).astype(np.uint32)))
+    # 16000 distinct destinations, all in partition 0 of 2: that table overflows
+    cand = rng.integers(0, 1 << 32, 200000, dtype=np.uint64).astype(np.uint32)
+    part = ((_fmix32(cand) >> np.uint64(14)) * np.uint64(2)) >> np.uint64(18)
+    d = np.unique(cand[part == 0])[:16000]
+    assert len(d) == 16000
+    wins.append((rng.integers(0, 1 << 32, len(d), dtype=np.uint64).astype(np.uint32), rng.permutation(d)))
+    offsets = np.zeros(len(wins) + 1, np.uint64)
+    offsets[1:] = np.cumsum([len(x) for x, _ in wins])
+    w = sy.Windows(np.concatenate([x for x, _ in wins]), np.concatenate([y for _, y in wins]), offsets)
+    c = ans.Context(0)
+    try:
+        c.set_tuning(col_hash=col_hash)
+        check_batch(ans, c, w, check_sum=False)
+        _, _, quants = run_batch(ans, c, w, 0)  # quantities only: the DCSR arrays stay in scratch
+        assert quants == [oracle.window_quantities(*w.window(i)) for i in range(w.nwin)]
+    finally:
+        c.close()
+
+
 def test_graph_cache_follows_column_hash_shape(ans, synth):
     """Batches whose window counts give the same merge depth but a different
     column-hash cluster shape (19 windows: 8 CTAs per window; 20 or 21: 4;
@@ -683,52 +735,5 @@ def test_sum_column_statistics_across_calls(ans, synth):
             exp = oracle.batch(w.src, dst, w.offsets, want_sum=True)[2]
             assert summ.quantities() == oracle.network_quantities(exp), f"call {i}"
             summ.free()
-    finally:
-        c.close()
-
-
-@pytest.mark.parametrize("cfg", [3, 4])
-def test_full_size_batches_sampled(ans, synth, cfg):
-    """The mixed 1024-window workload and the 2^30-packet workload at full
-    size, in the bench's configuration (autotuned paths): sampled windows
-    against the oracle, and properties every result must have at any size
-    -- the time sum holds every packet, no more links than the windows
-    together, at least as many rows as any window, canonical DCSR order."""
-    import oracle as orc
-    nwin = {3: 1024, 4: 8192}[cfg]
-    w = synth.generate(cfg, nwin=nwin)
-    c = ans.Context(0)
-    try:
-        src, dst = dev(w.src), dev(w.dst)
-        c.autotune(src, dst, w.offsets)
-        out = torch.zeros((w.nwin, 9), dtype=torch.int64, device="cuda")
-        mats, summ, tk = c.batch_submit(src, dst, w.offsets, ans.BATCH_SUM, out=out)
-        c.wait(tk)
-        q = ans.quantities_from_tensor(out)
-        rng = np.random.default_rng(cfg)
-        for i in sorted(set(rng.integers(0, w.nwin, 6).tolist()) | {0, w.nwin - 1}):
-            assert q[i] == orc.window_quantities(*w.window(i)), f"window {i}"
-        sq = summ.quantities()
-        assert sq["valid_packets"] == w.total == sum(x["valid_packets"] for x in q)
-        assert sq["unique_links"] <= sum(x["unique_links"] for x in q)
-        assert sq["unique_sources"] >= max(x["unique_sources"] for x in q)
-        assert sq["unique_destinations"] >= max(x["unique_destinations"] for x in q)
-        assert sq["max_link_packets"] >= max(x["max_link_packets"] for x in q)
-        assert sq["max_source_packets"] >= max(x["max_source_packets"] for x in q)
-        r, p, col, v = summ.to_numpy()
-        assert len(r) == sq["unique_sources"] and len(col) == sq["unique_links"]
-        assert np.all(np.diff(r.astype(np.int64)) > 0) and p[0] == 0 and p[-1] == len(col)
-        assert np.all(np.diff(p.astype(np.int64)) > 0) and np.all(v > 0) and int(v.sum()) == w.total
-        starts = np.zeros(len(col), bool)
-        starts[p[:-1].astype(np.int64)] = True
-        ok = np.diff(col.astype(np.int64)) > 0
-        assert np.all(ok | starts[1:])  # columns ascend within every row
-        assert int(np.diff(p.astype(np.int64)).max()) == sq["max_source_fanout"]
-        if cfg == 3:  # the column quantities of the sum, from its own stored links
-            cols, inv, fan = np.unique(col, return_inverse=True, return_counts=True)
-            assert sq["unique_destinations"] == len(cols)
-            assert sq["max_destination_fanin"] == int(fan.max())
-            assert sq["max_destination_packets"] == int(np.bincount(inv, weights=v.astype(np.float64)).max())
-        summ.free()
     finally:
         c.close()
