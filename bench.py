@@ -470,7 +470,7 @@ def main(argv=None):
         ctx.set_tuning(**parse_tuning(args.tuning))
         tuning = ctx.get_tuning()
     elif not args.no_autotune:
-        tuning = ctx.autotune(src_d, dst_d, w.offsets)
+        tuning = ctx.autotune(src_d, dst_d, w.offsets, flags=flags)
     t_tune = time.perf_counter() - t_tune
     for _ in range(max(args.warmup, 0)):
         res = step(src_d, dst_d)

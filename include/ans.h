@@ -314,7 +314,13 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * 1 = counting links in a per-window hash table (2^k >= 2 x packets slots of
  * 12 bytes, kept by the context between calls) and sorting only the distinct
  * links with their counts (kv_* passes); worth it when windows repeat links
- * heavily.  Setting agg_path 0 waits for the device and releases the tables.  graph: 1 = a batch's launch sequence is recorded into a CUDA
+ * heavily; 2 = for batches that return no per-window matrix (and whose time
+ * sum, if any, takes sum_path 2): every quantity of a window by counting in
+ * shared-memory hash tables -- its packets grouped by link hash into
+ * partitions of ~4096, one table of 8192 links per partition, then its
+ * distinct links grouped by source and by destination, one table of 16384
+ * keys per partition -- with no sort; a window whose table overflows, or of
+ * more than 2^18 packets, is sorted instead (other batches sort as agg_path 0).  Setting agg_path 0 waits for the device and releases the tables.  graph: 1 = a batch's launch sequence is recorded into a CUDA
  * graph and replayed through a cached executable graph of the same shape
  * (updated in place with the call's pointers), 0 = launched directly; per-
  * kernel profiling always launches directly.  col_hash: 1 = each window's
@@ -346,23 +352,26 @@ typedef struct {
 int ans_get_tuning(ans_ctx* ctx, ans_tuning* out);
 int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
 
-/* Autotuner: runs the caller's representative batch (as ans_batch_submit_host with
- * per-window matrices and the time sum) once per candidate configuration,
- * three times each, times every radix pass with CUDA events on `stream`, and
- * keeps, per family, the configuration with the least total pass time; it
- * then times the on-chip window sort (win_path 0, three cluster
- * configurations) and keeps it if the batch's windows sort faster that way
- * than by the best key passes plus their histogram sweep, and finally picks
- * sum_path, merge_tile (with merge rounds), then agg_path, by the batch's
- * device time as submitted (one
- * CUDA graph with its concurrent branches, between CUDA events on
- * `stream`, the host's planning included).  An optional path whose trial cannot get its
+/* Autotuner: runs the caller's representative batch once per candidate
+ * configuration, three times each, times every radix pass with CUDA events on
+ * `stream` (these runs return per-window matrices and the time sum, so that
+ * every pass family runs), and keeps, per family, the configuration with the
+ * least total pass time; it then times the on-chip window sort (win_path 0,
+ * three cluster configurations) and keeps it if the batch's windows sort
+ * faster that way than by the best key passes plus their histogram sweep, and
+ * finally picks sum_path, merge_tile (with merge rounds), then agg_path (2
+ * only without ANS_BATCH_MATRICES in `flags`, together with sum_path 2 when
+ * the batch has a time sum) by the batch's device time as submitted with
+ * `flags` (ANS_BATCH_* bits of the batches the context will run; one CUDA
+ * graph with its concurrent branches, between CUDA events on `stream`, the
+ * host's planning included).  An optional path whose trial cannot get its
  * device memory (ANS_ERR_OOM / ANS_ERR_BUDGET) is skipped; the call fails
- * with ANS_ERR_OOM only if the default paths do not fit.  The choice is applied to the context and returned in *chosen (optional).  The
- * call blocks until the runs have finished; it leaves per-kernel profiling
+ * with ANS_ERR_OOM only if the default paths do not fit.  The choice is
+ * applied to the context and returned in *chosen (optional).  The call
+ * blocks until the runs have finished; it leaves per-kernel profiling
  * disabled and its data cleared. */
 int ans_autotune(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
-                 size_t nwin, ans_tuning* chosen, void* stream);
+                 size_t nwin, uint32_t flags, ans_tuning* chosen, void* stream);
 
 /* Diagnostics: per-kernel timing.  While enabled, every kernel launch of the
  * context is bracketed by CUDA events on its launching stream (the paper

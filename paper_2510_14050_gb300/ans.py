@@ -114,7 +114,7 @@ def load(path: str | os.PathLike | None = None):
         "ans_window_quantities_noalloc": ([_vp, _vp, _u64, _vp, _vp, _vp], C.c_int),
         "ans_get_tuning": ([_vp, P(Tuning)], C.c_int),
         "ans_set_tuning": ([_vp, P(Tuning)], C.c_int),
-        "ans_autotune": ([_vp, _vp, _vp, P(_u64), C.c_size_t, P(Tuning), _vp], C.c_int),
+        "ans_autotune": ([_vp, _vp, _vp, P(_u64), C.c_size_t, C.c_uint32, P(Tuning), _vp], C.c_int),
         "ans_ctx_memory": ([_vp, P(C.c_size_t), P(C.c_size_t)], C.c_int),
         "ans_batch_bytes": ([_vp, P(_u64), C.c_size_t, C.c_uint32, P(C.c_size_t)], C.c_int),
         "ans_matrix_import": ([_vp, _u64, _u64, _vp, _vp, _vp, _vp, P(_vp), _vp], C.c_int),
@@ -486,13 +486,13 @@ class Context:
         t = Tuning(**{**self.get_tuning(), **kw})
         _check(self._lib.ans_set_tuning(self._h, C.byref(t)), "set_tuning", self._h)
 
-    def autotune(self, src, dst, offsets, stream=None) -> dict:
-        """Time the candidate radix-pass configurations on this batch and keep
-        the fastest per pass family; returns the chosen configuration."""
+    def autotune(self, src, dst, offsets, stream=None, flags: int = BATCH_MATRICES | BATCH_SUM) -> dict:
+        """Time the candidate radix-pass configurations and paths on this
+        batch, as submitted with ``flags``; returns the chosen configuration."""
         offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
         t = Tuning()
         _check(self._lib.ans_autotune(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)),
-                                      offs.ctypes.data_as(C.POINTER(_u64)), len(offs) - 1, C.byref(t),
+                                      offs.ctypes.data_as(C.POINTER(_u64)), len(offs) - 1, int(flags), C.byref(t),
                                       _vp(_stream(stream))), "autotune", self._h)
         return t.as_dict()
 

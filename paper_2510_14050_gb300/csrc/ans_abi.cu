@@ -1077,6 +1077,9 @@ struct WinLayout {
   DevPlan dp, dp_big;  // every window; the windows sorted by onesweep passes
   size_t off_small = 0;  // ids of the windows sorted on chip
   size_t off_colacc = 0; // per-window accumulators of the partitioned column hash
+  size_t off_colpart = 0; // its partition starts per window
+  size_t off_tileseg = 0; // the window plan's segment of every tile
+  size_t off_hqwin = 0, off_lstart = 0, off_kstart = 0, off_sortlen = 0;  // hashed window statistics
   DevPlan dp_tab;        // hash path: the windows' tables as segments
   DevPlan dp_pk;         // sum_path 2: all packets of the batch as one segment
   size_t off_tlg = 0, off_special = 0, off_hulen = 0, off_nclaim = 0, off_claims = 0;
@@ -1091,6 +1094,12 @@ struct WinLayout {
     dp_big.reserve(L, nseg, addrs);
     off_small = L.add((size_t)nseg * 4);
     off_colacc = L.add((size_t)nseg * sizeof(ColPartAcc));
+    off_colpart = L.add((size_t)nseg * 33 * 4);
+    off_tileseg = L.add((size_t)hp.ntiles * 4);
+    off_hqwin = L.add((size_t)nseg * sizeof(HqWin));
+    off_lstart = L.add((size_t)nseg * 65 * 4);
+    off_kstart = L.add((size_t)nseg * 33 * 4);
+    off_sortlen = L.add((size_t)nseg * 8);
     dp_pk.reserve(L, 1);
     if (hash) {
       dp_tab.reserve(L, nseg);
@@ -1175,7 +1184,10 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   std::vector<uint32_t> small_ids, big_ids;
   const int win_path = c->win_path;  // the caller holds c->mu
   const SortCfg cfg_win = c->cfg_win;
-  const bool on_chip = !dev && win_path == 0 && cluster_sort_clusters(c->device) > 0;
+  // (hashed window statistics, agg_path 2, sort only the windows the hash
+  // gives up on: those take the key passes)
+  const bool on_chip = !dev && win_path == 0 && !(c->agg_path == 2 && !want_mats) &&
+                       cluster_sort_clusters(c->device) > 0;
   for (uint32_t s = 0; s < nseg; ++s) {
     if (on_chip && lens[s] <= kClusterWindowMax) small_ids.push_back(s);
     else big_ids.push_back(s);
@@ -1252,6 +1264,9 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   // batches: its offset and length come from the planner, the tile count is
   // the capacity's)
   const bool sum_pk = want_sum && nseg && c->sum_path == 2 && !h_srcs;
+  // agg_path 2: the windows' quantities by on-chip hashing, when no window
+  // DCSR is returned and the time sum (if any) comes from the packets
+  const bool hq = c->agg_path == 2 && nseg && !want_mats && (!want_sum || sum_pk);
   HostPlan hp_pk;
   if (sum_pk) {
     std::vector<uint64_t> pk_off{dev ? 0 : h_offsets[0]};
@@ -1278,7 +1293,8 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       us.add(m + wl.dp_big.dst_at, hp_big.dst_at.data(), nb * 8);
     }
   }
-  const SegPlan p = dp.bind(m, hp);
+  SegPlan p = dp.bind(m, hp);
+  if (nseg > 1) p.tile_seg = at<uint32_t>(m, wl.off_tileseg);  // filled at the head of the launch sequence
   std::vector<MatDesc> md;
   if (want_sum && nseg && dev) {  // descriptors written by the device planner; the window plan gathers
     if ((rc = sum_prepare(c, m, nseg, std::vector<uint64_t>{total}, off_gplan, off_splan, off_lens, off_total, us,
@@ -1347,12 +1363,35 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
                    "plan")))
         return rc;
     }
+    if (p.tile_seg && (rc = cu(launch_tile_seg(p, at<uint32_t>(m, wl.off_tileseg), ls), "tile segments")))
+      return rc;
     if (nseg) {
       if ((rc = cu(launch_zero(sb.q, (size_t)nseg * sizeof(ans_quantities), ls), "memset q"))) return rc;
       if ((rc = cu(launch_zero(m + ps.lb, (size_t)hp.ntiles * 8, ls), "memset lb"))) return rc;
       if ((rc = cu(launch_zero(m + ps.col_hist, (size_t)nseg * kColPasses * kRadix * 4, ls), "memset")))
         return rc;
-      SegPlan pw = p;  // the plan of the statistics phases
+      // The window plan of the sort path: with hashed statistics, the windows
+      // the hash finished get length 0 there (only failed windows are sorted).
+      SegPlan pwin = p;
+      if (hq) {
+        HqBufs hb;
+        hb.keys = kb;
+        hb.lsrc = at<uint32_t>(m, ps.ck_a);
+        hb.ldst = at<uint32_t>(m, ps.ck_b);
+        hb.lcnt = (uint32_t*)at<uint64_t>(m, ps.cv_a);
+        hb.pkey = (uint32_t*)at<uint64_t>(m, ps.cv_b);
+        hb.pval = hb.pkey + hp.pad;
+        hb.lstart = at<uint32_t>(m, wl.off_lstart);
+        hb.kstart = at<uint32_t>(m, wl.off_kstart);
+        hb.win = at<HqWin>(m, wl.off_hqwin);
+        hb.sort_len = at<uint64_t>(m, wl.off_sortlen);
+        if ((rc = cu(launch_zero(hb.win, (size_t)nseg * sizeof(HqWin), ls), "memset"))) return rc;
+        if ((rc = cu(timed(c, "hash_stats", ls, [&] { return launch_hq_stats(p, d_src, d_dst, hb, ls); }),
+                     "hash statistics")))
+          return rc;
+        pwin.len = hb.sort_len;
+      }
+      SegPlan pw = pwin;  // the plan of the statistics phases
       int mode = kModeWindow;
       uint64_t* pre = nullptr;
       if (hash) {
@@ -1397,13 +1436,13 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       if (!hash && !small_ids.empty()) {
         const uint32_t* ids = small_ids.size() == nseg ? nullptr : at<uint32_t>(m, wl.off_small);
         if ((rc = cu(timed(c, "cluster_sort", ls, [&] {
-                       return launch_cluster_sort(p, ids, (uint32_t)small_ids.size(), d_src, d_dst, ka, tickets,
+                       return launch_cluster_sort(pwin, ids, (uint32_t)small_ids.size(), d_src, d_dst, ka, tickets,
                                                   cfg_win, ls);
                      }), "cluster sort")))
           return rc;
       }
       if (!hash && !big_ids.empty()) {
-        const SegPlan pb = dev ? p : wl.dp_big.bind(m, hp_big);
+        const SegPlan pb = dev || big_ids.size() == nseg ? pwin : wl.dp_big.bind(m, hp_big);
         const size_t nb = big_ids.size();
         if ((rc = cu(launch_zero(seg_hist, nb * kPasses * kRadix * 4, ls), "memset hist"))) return rc;
         if ((rc = cu(timed(c, "pack_hist", ls, [&] { return launch_pack_hist(pb, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, ls,
@@ -1460,10 +1499,16 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         rc = cu(launch_zero(acc, (size_t)nseg * sizeof(ColPartAcc), ls), "memset");
         if (rc == ANS_OK)
           rc = cu(timed(c, "colhash_part", ls,
-                        [&] { return launch_colhash_part(pw, a.ulen, sb.col_ids, a.vals32, acc, sb.q, ls); }),
+                        [&] {  // links regrouped into the column sort's buffers, which it overwrites later
+                          return launch_colhash_part(pw, a.ulen, sb.col_ids, a.vals32, at<uint32_t>(m, ps.ck_a),
+                                                     (uint32_t*)at<uint64_t>(m, ps.cv_a),
+                                                     at<uint32_t>(m, wl.off_colpart), acc, sb.q, ls);
+                        }),
                   "colhash part");
       }
       if (rc == ANS_OK) rc = column_pass(c, pw, a.ulen, sb.col_ids, sb.vals, ps, m, a.col_tickets, sb.q, ls, true);
+      if (rc == ANS_OK && hq)  // the hashed windows' quantities over the (empty) sorted results
+        rc = cu(launch_hq_write(p, at<HqWin>(m, wl.off_hqwin), sb.q, ls), "hash statistics");
       if (forked) {  // join (also after a failure, so that a capture ends joined)
         const cudaError_t ew = cudaStreamWaitEvent(ls, c->ev_join, 0);
         if (rc == ANS_OK) rc = cu(ew, "event");
@@ -2272,7 +2317,7 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   if (t->win_path > 1 || t->win_rank > 1 || !ok(t->win_threads, t->win_rank, 1))
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
   if (t->sum_path > 2) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0, 1 or 2");
-  if (t->agg_path > 1) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0 or 1");
+  if (t->agg_path > 2) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0, 1 or 2");
   if (t->graph > 1) return fail(ANS_ERR_INVALID_ARG, "graph must be 0 or 1");
   if (t->col_hash > 1) return fail(ANS_ERR_INVALID_ARG, "col_hash must be 0 or 1");
   if (t->merge_tile != 2048 && t->merge_tile != 4096) return fail(ANS_ERR_INVALID_ARG, "merge_tile must be 2048 or 4096");
@@ -2284,7 +2329,7 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   c->graph = (int)t->graph;
   c->col_hash = (int)t->col_hash;
   c->merge_tile = (int)t->merge_tile;
-  if (c->agg_path == 0 && c->hash_mem) {  // the hash tables are no longer needed
+  if (c->agg_path != 1 && c->hash_mem) {  // the hash tables are no longer needed
     DeviceGuard dg(c->device);
     ANS_CUDA(cudaDeviceSynchronize());
     dev_free(c, c->hash_mem, c->hash_slots * 12, c->aux);
@@ -2298,8 +2343,10 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
 }
 
 int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets, size_t nwin,
-                 ans_tuning* chosen, void* stream) {
+                 uint32_t flags, ans_tuning* chosen, void* stream) {
   if (!c || !h_offsets || nwin == 0) return fail(ANS_ERR_INVALID_ARG, "NULL argument or empty batch");
+  if (flags & ~(ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC)) return fail(ANS_ERR_INVALID_ARG, "unknown flag");
+  flags &= ANS_BATCH_MATRICES | ANS_BATCH_SUM;
   // The last kKeyOnly shapes exist for the key and column passes only (not
   // for the kv passes).
   constexpr int kVariants = 12, kKeyOnly = 3;
@@ -2309,11 +2356,13 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
                                        {256, kRankMatch, 4}, {256, kRankBallot, 4}, {256, kRankTable, 4}};
   using Prof = std::map<std::string, double>;
   std::vector<ans_matrix*> per(nwin, nullptr);
+  // The radix-pass shapes are timed with per-window matrices and the time
+  // sum (every pass family runs); the paths by the caller's own flags.
+  uint32_t run_flags = ANS_BATCH_MATRICES | ANS_BATCH_SUM;
   auto run_once = [&]() -> int {
     ans_matrix* sum = nullptr;
-    int rc = ans_batch_submit_host(c, d_src, d_dst, h_offsets, nwin,
-                                   ANS_BATCH_MATRICES | ANS_BATCH_SUM | ANS_BATCH_SYNC, nullptr, per.data(), &sum,
-                                   nullptr, stream);
+    int rc = ans_batch_submit_host(c, d_src, d_dst, h_offsets, nwin, run_flags | ANS_BATCH_SYNC, nullptr,
+                                   per.data(), &sum, nullptr, stream);
     if (rc != ANS_OK) return rc;
     for (auto& m : per) {
       ans_matrix_free(m);
@@ -2361,8 +2410,8 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       for (int rep = 0; rep < 2 && rc == ANS_OK; ++rep) {
         cudaEventRecord(e0, (cudaStream_t)stream);
         ans_matrix* sum = nullptr;
-        rc = ans_batch_submit_host(c, d_src, d_dst, h_offsets, nwin, ANS_BATCH_MATRICES | ANS_BATCH_SUM, nullptr,
-                                   per.data(), &sum, nullptr, stream);
+        rc = ans_batch_submit_host(c, d_src, d_dst, h_offsets, nwin, run_flags, nullptr, per.data(), &sum, nullptr,
+                                   stream);
         cudaEventRecord(e1, (cudaStream_t)stream);
         if (rc == ANS_OK) {
           float ms = 0;
@@ -2448,9 +2497,12 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   }
 
   // Time sums (pairwise merges, whose ordering runs beside the window column
-  // pass, against the kv passes) and then window aggregation (hash counting
-  // against sorting every packet): each by the batch's device time as the
-  // production path runs it, everything else as chosen.
+  // pass, against the kv passes and the packet re-sort) and then window
+  // aggregation (sorting every packet, hash counting of links, or -- without
+  // per-window matrices -- every quantity by on-chip hashing): each by the
+  // batch's device time as the production path runs it with the caller's
+  // flags, everything else as chosen.
+  run_flags = flags;
   int sum_path = 0;
   {
     double wall[3] = {kNever, kNever, kNever};
@@ -2493,20 +2545,25 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   }
   int agg_path = 0;
   {
-    double wall[2] = {kNever, kNever};
-    for (int a = 0; a < 2; ++a) {
+    // hashed statistics need no window DCSR, and a time sum from the packets
+    const bool hq_ok = !(flags & ANS_BATCH_MATRICES);
+    const int sum_for[3] = {sum_path, sum_path, (flags & ANS_BATCH_SUM) ? 2 : sum_path};
+    double wall[3] = {kNever, kNever, kNever};
+    for (int a = 0; a < (hq_ok ? 3 : 2); ++a) {
       Prof pr;
       bool ran = false;
       ANS_TRY(trial([&] {
         base();
         c->win_path = win_path;
         c->cfg_win = win_cfg;
-        c->sum_path = sum_path;
+        c->sum_path = sum_for[a];
         c->agg_path = a;
       }, &pr, &ran));
       if (ran) wall[a] = pr[kWall];
     }
-    agg_path = wall[1] < wall[0] ? 1 : 0;
+    for (int a = 1; a < 3; ++a)
+      if (wall[a] < wall[agg_path]) agg_path = a;
+    sum_path = sum_for[agg_path];
   }
 
   ans_tuning res{};

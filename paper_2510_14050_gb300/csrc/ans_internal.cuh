@@ -71,6 +71,9 @@ struct SegPlan {
   const uint64_t* len = nullptr;        // items in the segment (may be computed on the device)
   const uint64_t* base = nullptr;       // padded start, a multiple of kTile
   const uint32_t* first_tile = nullptr; // nseg + 1 entries
+  // Optional: the segment of every tile (ntiles entries, launch_tile_seg),
+  // which saves each tile a binary search over first_tile.
+  const uint32_t* tile_seg = nullptr;
   uint32_t nseg = 0;
   uint32_t ntiles = 0;
 };
@@ -165,6 +168,43 @@ struct DevPlanOut {
   const uint64_t* vals = nullptr;
   const uint64_t* hdr = nullptr;
 };
+
+// ---- window quantities by on-chip hashing (ans_winhash.cu) -----------------
+constexpr uint32_t kHqMaxPackets = 1u << 18;  // larger windows are sorted
+// Per-window accumulator of the hashed statistics (zeroed before the batch):
+// the link stage's distinct links and largest count, then per stage (0 =
+// sources, 1 = destinations) the distinct keys, the largest number of links
+// of a key (fan-out / fan-in) and the largest packet count of a key; fail =
+// some table overflowed (the window is sorted instead); nlinks = the
+// window's distinct links appended so far.
+struct HqWin {
+  unsigned long long links, max_link;
+  unsigned long long keys[2], max_links[2], max_packets[2];
+  uint32_t fail, nlinks;
+};
+// Device buffers of the hashed statistics (keys: packets regrouped by link
+// partition, at each window's padded base; lsrc / ldst / lcnt: the windows'
+// distinct links; pkey / pval: links regrouped by key partition; lstart /
+// kstart: partition starts, 65 / 33 per window; sort_len: the plan lengths
+// the sort path then uses).
+struct HqBufs {
+  uint64_t* keys = nullptr;
+  uint32_t* lsrc = nullptr;
+  uint32_t* ldst = nullptr;
+  uint32_t* lcnt = nullptr;
+  uint32_t* pkey = nullptr;
+  uint32_t* pval = nullptr;
+  uint32_t* lstart = nullptr;
+  uint32_t* kstart = nullptr;
+  HqWin* win = nullptr;
+  uint64_t* sort_len = nullptr;
+};
+// The hashed statistics of every window of p (win zeroed by the caller),
+// ending with sort_len; the quantities are written by launch_hq_write once
+// the sort path has run over sort_len.
+cudaError_t launch_hq_stats(const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HqBufs& b,
+                            cudaStream_t st);
+cudaError_t launch_hq_write(const SegPlan& p, const HqWin* win, ans_quantities* q, cudaStream_t st);
 
 // ---- launcher (ans_plan.cu) ------------------------------------------------
 // Plan the nseg windows [d_offsets[s], d_offsets[s+1]) on the device (one
@@ -300,11 +340,17 @@ struct ColPartAcc {
   uint32_t fail, done;
 };
 // Window column statistics of the windows launch_colhash left (ulen[s] > 0)
-// with between 2 and 32 x 8192 links: their destinations split by a hash
-// between several CTAs, one shared-memory table each; windows whose
-// partitions all fit get their three column quantities and ulen[s] = 0.
+// with more than 8192 and at most 32 x 8192 links: their destinations split
+// by a hash into partitions (the links regrouped by partition into
+// pkeys/pvals at the window's base, partition starts in bstart[s][0..33)),
+// one CTA and shared-memory table per partition; windows whose partitions
+// all fit get their three column quantities and ulen[s] = 0.
 cudaError_t launch_colhash_part(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
-                                ColPartAcc* acc, ans_quantities* q, cudaStream_t st);
+                                uint32_t* pkeys, uint32_t* pvals, uint32_t* bstart, ColPartAcc* acc, ans_quantities* q,
+                                cudaStream_t st);
+// tile_seg[t] = the segment of tile t of `p` (its first_tile searched once
+// per tile), for SegPlan::tile_seg.
+cudaError_t launch_tile_seg(const SegPlan& p, uint32_t* tile_seg, cudaStream_t st);
 // Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.
@@ -334,6 +380,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // Segment of a tile: the last s with first_tile[s] <= t (empty segments are
 // skipped because their first_tile equals the next one's).
 __device__ __forceinline__ uint32_t find_seg(const SegPlan& p, uint32_t t) {
+  if (p.tile_seg) return p.tile_seg[t];
   uint32_t lo = 0, hi = p.nseg;  // first_tile[lo] <= t < first_tile[hi]
   while (hi - lo > 1) {
     uint32_t mid = (lo + hi) >> 1;
@@ -536,6 +583,25 @@ __device__ __forceinline__ uint32_t scan256_excl(uint32_t v, uint32_t* tmp, uint
     tot += s;
   }
   if (total) *total = tot;
+  __syncthreads();
+  return off + x - v;
+}
+
+// The same over uint64 (two 32-bit counts packed in one word are scanned
+// together as long as neither half's total overflows).  `tmp` needs 8 words.
+__device__ __forceinline__ uint64_t scan256_excl64(uint64_t v, uint64_t* tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (warp < 8 && lane == 31) tmp[warp] = x;
+  __syncthreads();
+  uint64_t off = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) off += (w < warp) ? tmp[w] : 0ull;
   __syncthreads();
   return off + x - v;
 }

@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kT, kMinB)
   uint64_t* s_tab = reinterpret_cast<uint64_t*>(s_cnt);  // [kW][kRadix]   (table ranking)
   __shared__ uint64_t s_gofs[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
-  __shared__ uint32_t s_tmp[8];
+  __shared__ uint32_t s_hv[kRadix];
+  __shared__ uint64_t s_tmp[8];
   __shared__ uint32_t s_ticket;
   __shared__ Tile s_tile;
 
@@ -181,6 +182,14 @@ __global__ void __launch_bounds__(kT, kMinB)
     tl.start += off;
   }
   if (tl.count == 0) return;
+  // the segment's count of this pass's digit: copied to shared memory
+  // asynchronously now, read after ranking (no register held meanwhile)
+  if (threadIdx.x < kRadix) {
+    const uint32_t* src = seg_hist + ((size_t)tl.seg * kNumPasses + pass) * kRadix + threadIdx.x;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;" ::"r"(smem_addr(&s_hv[threadIdx.x])),
+                 "l"(src)
+                 : "memory");
+  }
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int shift = pass * kRadixBits;
@@ -272,9 +281,15 @@ __global__ void __launch_bounds__(kT, kMinB)
       st_relaxed(my, kFlagPre | (excl + cnt));
     }
   }
-  const uint32_t dstart = scan256_excl(d < kRadix ? cnt : 0u, s_tmp, nullptr);
-  const uint32_t hv = d < kRadix ? seg_hist[((size_t)tl.seg * kNumPasses + pass) * kRadix + d] : 0u;
-  const uint32_t bstart = scan256_excl(hv, s_tmp, nullptr);
+  // one scan for both: the digit's start in this tile (low half) and in the
+  // segment (high half; the segment holds fewer than 2^31 keys)
+  uint32_t hv = 0;
+  if (d < kRadix) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    hv = s_hv[d];  // this thread's own copy
+  }
+  const uint64_t both = scan256_excl64(((uint64_t)hv << 32) | (d < kRadix ? cnt : 0u), s_tmp);
+  const uint32_t dstart = (uint32_t)both, bstart = (uint32_t)(both >> 32);
   if (d < kRadix) {
     s_dstart[d] = dstart;
     s_gofs[d] = tl.base + bstart + excl - dstart;  // + position in the sorted tile
@@ -293,11 +308,21 @@ __global__ void __launch_bounds__(kT, kMinB)
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < tl.count; i += kT) {
-    const K key = s_keys[i];
-    const uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
-    kout[o] = key;
-    if constexpr (kVals) vout[o] = s_vals[i];
+  if (tl.count == kTT) {  // a full tile: a fixed trip count the compiler unrolls
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < kTT; i += kT) {
+      const K key = s_keys[i];
+      const uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
+      kout[o] = key;
+      if constexpr (kVals) vout[o] = s_vals[i];
+    }
+  } else {
+    for (uint32_t i = threadIdx.x; i < tl.count; i += kT) {
+      const K key = s_keys[i];
+      const uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
+      kout[o] = key;
+      if constexpr (kVals) vout[o] = s_vals[i];
+    }
   }
 }
 

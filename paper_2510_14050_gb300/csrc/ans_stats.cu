@@ -565,6 +565,12 @@ __global__ void k_empty_fixup(StatsArgs a) {
   if (a.ulen) a.ulen[s] = 0;
 }
 
+__global__ void k_tile_seg(SegPlan p, uint32_t* __restrict__ out) {
+  p.tile_seg = nullptr;  // search first_tile
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < p.ntiles; t += gridDim.x * blockDim.x)
+    out[t] = find_seg(p, t);
+}
+
 // Warp 0 waits with warp_lookback, thread 32 with lookback, both for tile 0
 // of a chain that nobody publishes; both give up at the poll limit.
 __global__ void k_wait_probe(const uint64_t* st, uint32_t* err) {
@@ -894,17 +900,20 @@ __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_cl(SegPlan p, ui
 }
 
 // Windows with more destinations than one table holds: the destinations
-// are split between up to kColParts CTAs by a hash (CTA r of window s takes
-// the destinations whose partition is r), each counting its share of the
-// window's links in its own shared-memory table -- every CTA reads all the
-// window's links (from L2 after the first) and keeps only its own.  A
-// window of n links gets ceil(n / kColPartLinks) partitions (n bounds its
-// distinct destinations).  Partial results meet in a per-window accumulator;
-// the last CTA of a window to finish writes the window's three quantities
-// and marks it done (ulen = 0) -- unless some partition overflowed its
-// table, in which case the window is left, untouched, to the column sort.
+// are split between up to kColParts partitions by a hash, and each
+// partition's links are counted by its own CTA in its own shared-memory
+// table.  A window of n links gets ceil(n / kColPartLinks) partitions (n
+// bounds its distinct destinations).  First one CTA per window groups the
+// window's links by partition (a counting pass and a scatter pass, both
+// warp-aggregated); then CTA r of the window counts partition r's links.
+// Partial results meet in a per-window accumulator; the last CTA of a
+// window to finish writes the window's three quantities and marks it done
+// (ulen = 0) -- unless some partition overflowed its table, in which case
+// the window is left, untouched, to the column sort.
 constexpr uint32_t kColParts = 32;
 constexpr uint32_t kColPartLinks = 8192;
+constexpr int kSplitThreads = 1024;
+constexpr int kSplitUnroll = 4;
 
 // Finalizer-derived partition of a destination: the high bits of its mix
 // (the table slot uses the low bits), scaled to [0, parts).
@@ -912,9 +921,96 @@ __device__ __forceinline__ uint32_t col_part(uint32_t d, uint32_t parts) {
   return (uint32_t)(((uint64_t)(fmix32(d) >> 14) * parts) >> 18);
 }
 
+// Partitions of a window of n links, or 0 if the partitioned hash does not
+// take it (empty, finished, within one table, or too large).
+__device__ __forceinline__ uint32_t col_parts_of(uint64_t n) {
+  const uint64_t parts = (n + kColPartLinks - 1) / kColPartLinks;
+  return parts >= 2 && parts <= kColParts ? (uint32_t)parts : 0u;
+}
+
+// One CTA per window: the window's (destination, count) links regrouped by
+// partition into okeys/ovals at the window's base; the partition starts in
+// bstart[s][0..parts].
+__global__ void __launch_bounds__(kSplitThreads, 2) k_colpart_split(SegPlan p, const uint64_t* __restrict__ ulen,
+                                                                    const uint32_t* __restrict__ col_ids,
+                                                                    const uint32_t* __restrict__ vals32,
+                                                                    uint32_t* __restrict__ okeys,
+                                                                    uint32_t* __restrict__ ovals,
+                                                                    uint32_t* __restrict__ bstart) {
+  __shared__ uint32_t s_cnt[kColParts], s_cur[kColParts];
+  const uint32_t s = blockIdx.x;
+  if (s >= p.nseg) return;
+  const uint64_t n = ulen[s];
+  const uint32_t parts = col_parts_of(n);
+  if (!parts) return;
+  const uint64_t b = p.base[s];
+  const uint32_t* ci = col_ids + b;
+  const uint32_t* vi = vals32 + b;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < kColParts) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  // pass 1: links per partition
+  for (uint64_t w0 = threadIdx.x & ~31u; w0 < n; w0 += (uint64_t)kSplitUnroll * kSplitThreads) {
+    const uint64_t u0 = w0 + (threadIdx.x & 31);  // the loop bound is the same for the whole warp
+    uint32_t d[kSplitUnroll];
+#pragma unroll
+    for (int k = 0; k < kSplitUnroll; ++k) {
+      const uint64_t u = u0 + (uint64_t)k * kSplitThreads;
+      d[k] = u < n ? ci[u] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kSplitUnroll; ++k) {
+      const bool valid = u0 + (uint64_t)k * kSplitThreads < n;
+      const uint32_t pt = valid ? col_part(d[k], parts) : kColParts;
+      const uint32_t peers = __match_any_sync(0xffffffffu, pt);
+      if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[pt], __popc(peers));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t r = 0; r < parts; ++r) {
+      s_cur[r] = run;
+      bstart[(uint64_t)s * (kColParts + 1) + r] = run;
+      run += s_cnt[r];
+    }
+    bstart[(uint64_t)s * (kColParts + 1) + parts] = run;
+  }
+  __syncthreads();
+  // pass 2: scatter each link to its partition (order within a partition is free)
+  uint32_t* ko = okeys + b;
+  uint32_t* vo = ovals + b;
+  for (uint64_t w0 = threadIdx.x & ~31u; w0 < n; w0 += (uint64_t)kSplitUnroll * kSplitThreads) {
+    const uint64_t u0 = w0 + (threadIdx.x & 31);  // the loop bound is the same for the whole warp
+    uint32_t d[kSplitUnroll], v[kSplitUnroll];
+#pragma unroll
+    for (int k = 0; k < kSplitUnroll; ++k) {
+      const uint64_t u = u0 + (uint64_t)k * kSplitThreads;
+      d[k] = u < n ? ci[u] : 0u;
+      v[k] = u < n ? vi[u] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kSplitUnroll; ++k) {
+      const bool valid = u0 + (uint64_t)k * kSplitThreads < n;
+      const uint32_t pt = valid ? col_part(d[k], parts) : kColParts;
+      const uint32_t peers = __match_any_sync(0xffffffffu, pt);
+      const int leader = __ffs(peers) - 1;
+      uint32_t pos = 0;
+      if (valid && lane == leader) pos = atomicAdd(&s_cur[pt], __popc(peers));
+      pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lanemask_lt());
+      if (valid) {
+        ko[pos] = d[k];
+        vo[pos] = v[k];
+      }
+    }
+  }
+}
+
+// CTA r of window s counts partition r's links (from k_colpart_split).
 __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_part(SegPlan p, uint64_t* __restrict__ ulen,
-                                                                      const uint32_t* __restrict__ col_ids,
-                                                                      const uint32_t* __restrict__ vals32,
+                                                                      const uint32_t* __restrict__ pkeys,
+                                                                      const uint32_t* __restrict__ pvals,
+                                                                      const uint32_t* __restrict__ bstart,
                                                                       ColPartAcc* __restrict__ acc,
                                                                       ans_quantities* __restrict__ q) {
   extern __shared__ __align__(16) uint32_t sm[];
@@ -925,13 +1021,10 @@ __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_part(SegPlan p, 
   __shared__ unsigned long long s_red[3][kColHashThreads / 32];
   const uint32_t s = blockIdx.x / kColParts, r = blockIdx.x % kColParts;
   if (s >= p.nseg) return;
-  const uint64_t n = ulen[s];
-  if (n == 0) return;  // empty, or finished by the one-table hash
-  const uint64_t parts64 = (n + kColPartLinks - 1) / kColPartLinks;
-  if (parts64 < 2 || parts64 > kColParts) return;  // the one-table hash's case, or too many for this kernel
-  const uint32_t parts = (uint32_t)parts64;
-  if (r >= parts) return;
+  const uint32_t parts = col_parts_of(ulen[s]);
+  if (r >= parts) return;  // also: the window is not taken by the partitioned hash
   const uint64_t b = p.base[s];
+  const uint32_t lo = bstart[(uint64_t)s * (kColParts + 1) + r], hi = bstart[(uint64_t)s * (kColParts + 1) + r + 1];
   for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
     t_key[i] = kColEmpty;
     t_cnt[i] = 0;
@@ -939,11 +1032,10 @@ __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_part(SegPlan p, 
   }
   if (threadIdx.x == 0) s_fill = s_over = s_spec_cnt = s_spec_sum = 0;
   __syncthreads();
-  for (uint64_t u = threadIdx.x; u < n; u += kColHashThreads) {
+  for (uint32_t u = lo + threadIdx.x; u < hi; u += kColHashThreads) {
     if (*(volatile uint32_t*)&s_over) break;
-    const uint32_t d = col_ids[b + u];
-    if (col_part(d, parts) != r) continue;
-    const uint32_t v = vals32[b + u];
+    const uint32_t d = pkeys[b + u];
+    const uint32_t v = pvals[b + u];
     if (d == kColEmpty) {
       atomicAdd(&s_spec_cnt, 1u);
       atomicAdd(&s_spec_sum, v);
@@ -1098,7 +1190,8 @@ cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col
 }
 
 cudaError_t launch_colhash_part(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
-                                ColPartAcc* acc, ans_quantities* q, cudaStream_t st) {
+                                uint32_t* pkeys, uint32_t* pvals, uint32_t* bstart, ColPartAcc* acc, ans_quantities* q,
+                                cudaStream_t st) {
   if (p.nseg == 0) return cudaSuccess;
   static unsigned long long configured = 0;  // one bit per device ordinal
   int dev = 0;
@@ -1109,7 +1202,10 @@ cudaError_t launch_colhash_part(const SegPlan& p, uint64_t* ulen, const uint32_t
     if (e != cudaSuccess) return e;
     if (dev < 64) configured |= 1ull << dev;
   }
-  k_colhash_part<<<p.nseg * kColParts, kColHashThreads, kColHashSmem, st>>>(p, ulen, col_ids, vals32, acc, q);
+  k_colpart_split<<<p.nseg, kSplitThreads, 0, st>>>(p, ulen, col_ids, vals32, pkeys, pvals, bstart);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_colhash_part<<<p.nseg * kColParts, kColHashThreads, kColHashSmem, st>>>(p, ulen, pkeys, pvals, bstart, acc, q);
   return cudaGetLastError();
 }
 
@@ -1133,6 +1229,13 @@ cudaError_t launch_check_dcsr(uint64_t nrows, uint64_t nnz, const uint32_t* row_
   const uint64_t want = (n + 255) / 256;
   const unsigned blocks = (unsigned)(want > 4096 ? 4096 : want);
   k_check_dcsr<<<blocks, 256, 0, st>>>(nrows, nnz, row_ids, row_ptr, col_ids, vals, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_seg(const SegPlan& p, uint32_t* tile_seg, cudaStream_t st) {
+  if (p.ntiles == 0) return cudaSuccess;
+  const uint32_t want = (p.ntiles + 255) / 256;
+  k_tile_seg<<<want < 4096 ? want : 4096, 256, 0, st>>>(p, tile_seg);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,527 @@
+// Window quantities by on-chip hashing, without sorting (aggregation path 2;
+// batches that return no per-window DCSR).
+//
+// The nine quantities of a window (Table I, Sec. IV-C) need three groupings
+// of its packets: by link (unique links, max link packets), by source over
+// the distinct links (unique sources, max source packets, max fan-out) and
+// by destination over the distinct links (unique destinations, max
+// destination packets, max fan-in).  None needs the links in order, so each
+// grouping is done by counting in shared-memory hash tables:
+//  1. one CTA per window regroups its packets by a hash of the link into
+//     ceil(P / 4096) partitions (a counting pass and a scatter pass);
+//  2. one CTA per (window, partition) counts the partition's links in a
+//     table of 8192 link keys, adds the partition's distinct links and its
+//     largest count into the window's accumulator, and appends the distinct
+//     links as (source, destination, count) triples to the window's list;
+//  3. the same two steps over the distinct links keyed by source (partitions
+//     of 8192 links, tables of 16384 sources: links and packets per source),
+//     then keyed by destination.
+// A partition whose table overflows (more distinct keys than it holds at
+// three quarters load), or a window of more than 2^18 packets, marks the
+// window failed; the batch then sorts exactly the failed windows (their
+// plan length is kept, every other window's is set to 0) and the hashed
+// quantities are written over the sorted windows' results only where the
+// window did not fail.
+#include "ans_internal.cuh"
+
+namespace ans {
+
+namespace {
+
+constexpr int kHqThreads = 1024;
+constexpr int kHqUnroll = 4;
+constexpr uint32_t kLinkPartPackets = 4096;                  // packets per link partition (mean)
+constexpr uint32_t kLinkParts = kHqMaxPackets / kLinkPartPackets;  // 64
+constexpr uint32_t kLinkSlots = 8192;                        // link table: uint64 key + uint32 count
+constexpr uint32_t kLinkMaxFill = kLinkSlots / 4 * 3;
+constexpr size_t kLinkSmem = (size_t)kLinkSlots * 12;
+constexpr uint64_t kLinkEmpty = ~0ull;                       // marks an empty slot (that link is counted apart)
+constexpr uint32_t kKeyPartLinks = 8192;                     // links per source / destination partition (mean)
+constexpr uint32_t kKeyParts = kHqMaxPackets / kKeyPartLinks;  // 32
+constexpr uint32_t kKeySlots = 16384;                        // key, links, packets (uint32 each)
+constexpr uint32_t kKeyMaxFill = kKeySlots / 4 * 3;
+constexpr size_t kKeySmem = (size_t)kKeySlots * 12;
+constexpr uint32_t kKeyEmpty = 0xFFFFFFFFu;
+static_assert(kLinkParts * kLinkPartPackets == kHqMaxPackets, "link partitions cover the largest window");
+static_assert(kKeyParts * kKeyPartLinks == kHqMaxPackets, "key partitions cover the largest window's links");
+
+// MurmurHash3's finalizers (Appleby): bijective 64- and 32-bit mixes.
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+__device__ __forceinline__ uint32_t fmix32h(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Partitions: the high bits of the mix, scaled to [0, parts); table slots
+// use the low bits.
+__device__ __forceinline__ uint32_t link_part(uint64_t key, uint32_t parts) {
+  return (uint32_t)(((fmix64(key) >> 40) * parts) >> 24);
+}
+__device__ __forceinline__ uint32_t key_part(uint32_t key, uint32_t parts) {
+  return (uint32_t)(((uint64_t)(fmix32h(key) >> 14) * parts) >> 18);
+}
+
+__device__ __forceinline__ uint32_t ceil_div(uint64_t n, uint32_t d) { return (uint32_t)((n + d - 1) / d); }
+
+// Warp-aggregated slot in a partition: lanes with the same partition share
+// one shared-memory atomic on its cursor.
+__device__ __forceinline__ uint32_t claim_slot(uint32_t* cur, uint32_t pt, bool valid) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t peers = __match_any_sync(0xffffffffu, valid ? pt : 0xFFFFFFFFu);
+  const int leader = __ffs(peers) - 1;
+  uint32_t pos = 0;
+  if (valid && lane == leader) pos = atomicAdd(&cur[pt], __popc(peers));
+  return __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lanemask_lt());
+}
+
+// Step 1: one CTA per window regroups its packets (as link keys) by link
+// partition into keys + base[s]; partition starts in lstart[s][0..parts].
+// A window above kHqMaxPackets is marked failed (it will be sorted).
+__global__ void __launch_bounds__(kHqThreads, 2) k_hq_split(SegPlan p, const uint32_t* __restrict__ src,
+                                                            const uint32_t* __restrict__ dst,
+                                                            uint64_t* __restrict__ keys, uint32_t* __restrict__ lstart,
+                                                            HqWin* __restrict__ win) {
+  __shared__ uint32_t s_cnt[kLinkParts], s_cur[kLinkParts];
+  const uint32_t s = blockIdx.x;
+  if (s >= p.nseg) return;
+  const uint64_t n = p.len[s];
+  if (n == 0) return;
+  if (n > kHqMaxPackets) {
+    if (threadIdx.x == 0) win[s].fail = 1;
+    return;
+  }
+  const uint32_t parts = ceil_div(n, kLinkPartPackets);
+  const uint32_t *ws, *wd;
+  window_inputs(p, s, src, dst, &ws, &wd);
+  if (threadIdx.x < kLinkParts) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t w0 = threadIdx.x & ~31u; w0 < n; w0 += kHqUnroll * kHqThreads) {
+    const uint32_t u0 = w0 + (threadIdx.x & 31);  // the loop bound is the same for the whole warp
+    uint64_t k[kHqUnroll];
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const uint32_t u = u0 + j * kHqThreads;
+      k[j] = u < n ? ((uint64_t)ws[u] << 32) | wd[u] : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const bool valid = u0 + j * kHqThreads < n;
+      const uint32_t pt = valid ? link_part(k[j], parts) : 0u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? pt : 0xFFFFFFFFu);
+      if (valid && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_cnt[pt], __popc(peers));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t r = 0; r < parts; ++r) {
+      s_cur[r] = run;
+      lstart[(uint64_t)s * (kLinkParts + 1) + r] = run;
+      run += s_cnt[r];
+    }
+    lstart[(uint64_t)s * (kLinkParts + 1) + parts] = run;
+  }
+  __syncthreads();
+  uint64_t* out = keys + p.base[s];
+  for (uint32_t w0 = threadIdx.x & ~31u; w0 < n; w0 += kHqUnroll * kHqThreads) {
+    const uint32_t u0 = w0 + (threadIdx.x & 31);  // the loop bound is the same for the whole warp
+    uint64_t k[kHqUnroll];
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const uint32_t u = u0 + j * kHqThreads;
+      k[j] = u < n ? ((uint64_t)ws[u] << 32) | wd[u] : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const bool valid = u0 + j * kHqThreads < n;
+      const uint32_t pt = valid ? link_part(k[j], parts) : 0u;
+      const uint32_t pos = claim_slot(s_cur, pt, valid);
+      if (valid) out[pos] = k[j];
+    }
+  }
+}
+
+// Block reduction of (sum, max) over all threads; thread 0 gets the result.
+__device__ __forceinline__ void block_sum_max(unsigned long long& sum, unsigned long long& mx,
+                                              unsigned long long (*red)[kHqThreads / 32]) {
+  sum = warp_sum(sum);
+  mx = warp_max(mx);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = sum;
+    red[1][warp] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sum = 0;
+    mx = 0;
+    for (int w = 0; w < kHqThreads / 32; ++w) {
+      sum += red[0][w];
+      mx = red[1][w] > mx ? red[1][w] : mx;
+    }
+  }
+}
+
+// Step 2: CTA r of window s counts the links of partition r in a table of
+// kLinkSlots keys; adds its distinct links and its largest link count to the
+// window's accumulator and appends the distinct links as (source,
+// destination, count) at lsrc / ldst / lcnt + base[s] + (the window's running
+// link count).
+__global__ void __launch_bounds__(kHqThreads, 2) k_hq_links(SegPlan p, const uint64_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ lstart,
+                                                            uint32_t* __restrict__ lsrc, uint32_t* __restrict__ ldst,
+                                                            uint32_t* __restrict__ lcnt, HqWin* __restrict__ win) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t* t_key = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* t_cnt = reinterpret_cast<uint32_t*>(smem + (size_t)kLinkSlots * 8);
+  __shared__ uint32_t s_fill, s_over, s_spec, s_off;
+  __shared__ unsigned long long s_red[2][kHqThreads / 32];
+  __shared__ uint32_t s_wcnt[kHqThreads / 32];
+  const uint32_t s = blockIdx.x / kLinkParts, r = blockIdx.x % kLinkParts;
+  if (s >= p.nseg) return;
+  const uint64_t n = p.len[s];
+  if (n == 0 || n > kHqMaxPackets) return;
+  const uint32_t parts = ceil_div(n, kLinkPartPackets);
+  if (r >= parts) return;
+  const uint32_t lo = lstart[(uint64_t)s * (kLinkParts + 1) + r], hi = lstart[(uint64_t)s * (kLinkParts + 1) + r + 1];
+  const uint64_t* in = keys + p.base[s];
+  for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
+    t_key[i] = kLinkEmpty;
+    t_cnt[i] = 0;
+  }
+  if (threadIdx.x == 0) s_fill = s_over = s_spec = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t u0 = lo; u0 < hi; u0 += kHqThreads) {
+    const uint32_t u = u0 + threadIdx.x;
+    const bool valid = u < hi;
+    const uint64_t k = valid ? in[u] : kLinkEmpty;
+    // lanes holding the same link add it once
+    const uint32_t peers = __match_any_sync(0xffffffffu, k);
+    if (!valid || lane != __ffs(peers) - 1) continue;
+    const uint32_t c = __popc(peers);
+    if (k == kLinkEmpty) {
+      atomicAdd(&s_spec, c);
+      continue;
+    }
+    if (*(volatile uint32_t*)&s_over) continue;
+    uint32_t h = (uint32_t)fmix64(k) & (kLinkSlots - 1);
+    for (uint32_t probe = 0; probe < kLinkSlots; ++probe) {
+      unsigned long long cur = *(volatile unsigned long long*)&t_key[h];
+      if (cur == kLinkEmpty) {
+        cur = atomicCAS((unsigned long long*)&t_key[h], (unsigned long long)kLinkEmpty, (unsigned long long)k);
+        if (cur == kLinkEmpty) {
+          cur = k;
+          if (atomicAdd(&s_fill, 1u) + 1 > kLinkMaxFill) s_over = 1;
+        }
+      }
+      if (cur == k) {
+        atomicAdd(&t_cnt[h], c);
+        break;
+      }
+      h = (h + 1) & (kLinkSlots - 1);
+    }
+  }
+  __syncthreads();
+  HqWin* w = win + s;
+  if (s_over) {
+    if (threadIdx.x == 0) atomicOr(&w->fail, 1u);
+    return;
+  }
+  // distinct links of this partition: count, largest count, then append
+  unsigned long long nl = 0, mx = 0;
+  for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
+    if (t_key[i] != kLinkEmpty) {
+      ++nl;
+      mx = t_cnt[i] > mx ? t_cnt[i] : mx;
+    }
+  }
+  // per-thread counts -> exclusive offsets within the CTA (warp scan + warp totals)
+  uint32_t mine = (uint32_t)nl, x = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wcnt[warp] = x;
+  unsigned long long tot = nl, m2 = mx;
+  block_sum_max(tot, m2, s_red);
+  if (threadIdx.x == 0) {
+    const uint32_t spec = s_spec;
+    tot += spec ? 1 : 0;
+    m2 = spec > m2 ? spec : m2;
+    s_off = atomicAdd(&w->nlinks, (uint32_t)tot);
+    if (tot) atomicAdd(&w->links, tot);
+    if (m2) atomicMax(&w->max_link, m2);
+  }
+  __syncthreads();
+  uint32_t woff = 0;
+  for (int v = 0; v < warp; ++v) woff += s_wcnt[v];
+  uint32_t o = s_off + woff + x - mine;
+  const uint64_t b = p.base[s];
+  for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
+    const uint64_t k = t_key[i];
+    if (k != kLinkEmpty) {
+      lsrc[b + o] = (uint32_t)(k >> 32);
+      ldst[b + o] = (uint32_t)k;
+      lcnt[b + o] = t_cnt[i];
+      ++o;
+    }
+  }
+  if (threadIdx.x == 0 && s_spec) {  // the all-ones link, counted apart, goes last
+    const uint32_t last = s_off + (uint32_t)tot - 1;
+    lsrc[b + last] = kKeyEmpty;
+    ldst[b + last] = kKeyEmpty;
+    lcnt[b + last] = s_spec;
+  }
+}
+
+// Step 3a: one CTA per window regroups its distinct links' (key, count) --
+// key = source (stage 0) or destination (stage 1) -- by key partition into
+// pkey / pval + base[s]; partition starts in kstart[s][0..parts].
+__global__ void __launch_bounds__(kHqThreads, 2) k_hq_keysplit(SegPlan p, const uint32_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ cin,
+                                                               uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval,
+                                                               uint32_t* __restrict__ kstart,
+                                                               const HqWin* __restrict__ win) {
+  __shared__ uint32_t s_cnt[kKeyParts], s_cur[kKeyParts];
+  const uint32_t s = blockIdx.x;
+  if (s >= p.nseg) return;
+  const HqWin& w = win[s];
+  const uint32_t n = w.nlinks;
+  if (n == 0 || w.fail) return;
+  const uint32_t parts = ceil_div(n, kKeyPartLinks);
+  const uint64_t b = p.base[s];
+  if (threadIdx.x < kKeyParts) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint32_t w0 = threadIdx.x & ~31u; w0 < n; w0 += kHqUnroll * kHqThreads) {
+    const uint32_t u0 = w0 + (threadIdx.x & 31);  // the loop bound is the same for the whole warp
+    uint32_t k[kHqUnroll];
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const uint32_t u = u0 + j * kHqThreads;
+      k[j] = u < n ? kin[b + u] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const bool valid = u0 + j * kHqThreads < n;
+      const uint32_t pt = valid ? key_part(k[j], parts) : 0u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? pt : 0xFFFFFFFFu);
+      if (valid && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_cnt[pt], __popc(peers));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t r = 0; r < parts; ++r) {
+      s_cur[r] = run;
+      kstart[(uint64_t)s * (kKeyParts + 1) + r] = run;
+      run += s_cnt[r];
+    }
+    kstart[(uint64_t)s * (kKeyParts + 1) + parts] = run;
+  }
+  __syncthreads();
+  for (uint32_t w0 = threadIdx.x & ~31u; w0 < n; w0 += kHqUnroll * kHqThreads) {
+    const uint32_t u0 = w0 + (threadIdx.x & 31);  // the loop bound is the same for the whole warp
+    uint32_t k[kHqUnroll], c[kHqUnroll];
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const uint32_t u = u0 + j * kHqThreads;
+      k[j] = u < n ? kin[b + u] : 0u;
+      c[j] = u < n ? cin[b + u] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kHqUnroll; ++j) {
+      const bool valid = u0 + j * kHqThreads < n;
+      const uint32_t pt = valid ? key_part(k[j], parts) : 0u;
+      const uint32_t pos = claim_slot(s_cur, pt, valid);
+      if (valid) {
+        pkey[b + pos] = k[j];
+        pval[b + pos] = c[j];
+      }
+    }
+  }
+}
+
+// Step 3b: CTA r of window s counts partition r's keys: per key its links
+// (fan-out / fan-in) and packets; the window gets the number of distinct
+// keys, the largest link count and the largest packet count of stage `st`.
+__global__ void __launch_bounds__(kHqThreads, 1) k_hq_keyhash(SegPlan p, const uint32_t* __restrict__ pkey,
+                                                              const uint32_t* __restrict__ pval,
+                                                              const uint32_t* __restrict__ kstart,
+                                                              HqWin* __restrict__ win, int st) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* t_key = sm;
+  uint32_t* t_lnk = sm + kKeySlots;
+  uint32_t* t_pkt = sm + 2 * kKeySlots;
+  __shared__ uint32_t s_fill, s_over, s_spec_l, s_spec_p;
+  __shared__ unsigned long long s_red[3][kHqThreads / 32];
+  const uint32_t s = blockIdx.x / kKeyParts, r = blockIdx.x % kKeyParts;
+  if (s >= p.nseg) return;
+  HqWin* w = win + s;
+  const uint32_t n = w->nlinks;
+  if (n == 0 || w->fail) return;
+  const uint32_t parts = ceil_div(n, kKeyPartLinks);
+  if (r >= parts) return;
+  const uint64_t b = p.base[s];
+  const uint32_t lo = kstart[(uint64_t)s * (kKeyParts + 1) + r], hi = kstart[(uint64_t)s * (kKeyParts + 1) + r + 1];
+  for (uint32_t i = threadIdx.x; i < kKeySlots; i += kHqThreads) {
+    t_key[i] = kKeyEmpty;
+    t_lnk[i] = 0;
+    t_pkt[i] = 0;
+  }
+  if (threadIdx.x == 0) s_fill = s_over = s_spec_l = s_spec_p = 0;
+  __syncthreads();
+  for (uint32_t u = lo + threadIdx.x; u < hi; u += kHqThreads) {
+    if (*(volatile uint32_t*)&s_over) break;
+    const uint32_t k = pkey[b + u];
+    const uint32_t c = pval[b + u];
+    if (k == kKeyEmpty) {
+      atomicAdd(&s_spec_l, 1u);
+      atomicAdd(&s_spec_p, c);
+      continue;
+    }
+    uint32_t h = fmix32h(k) & (kKeySlots - 1);
+    for (uint32_t probe = 0; probe < kKeySlots; ++probe) {
+      uint32_t cur = *(volatile uint32_t*)&t_key[h];
+      if (cur == kKeyEmpty) {
+        cur = atomicCAS(&t_key[h], kKeyEmpty, k);
+        if (cur == kKeyEmpty) {
+          cur = k;
+          if (atomicAdd(&s_fill, 1u) + 1 > kKeyMaxFill) s_over = 1;
+        }
+      }
+      if (cur == k) {
+        atomicAdd(&t_lnk[h], 1u);
+        atomicAdd(&t_pkt[h], c);
+        break;
+      }
+      h = (h + 1) & (kKeySlots - 1);
+    }
+  }
+  __syncthreads();
+  if (s_over) {
+    if (threadIdx.x == 0) atomicOr(&w->fail, 1u);
+    return;
+  }
+  unsigned long long cnt = 0, ml = 0, mp = 0;
+  for (uint32_t i = threadIdx.x; i < kKeySlots; i += kHqThreads) {
+    if (t_key[i] != kKeyEmpty) {
+      ++cnt;
+      ml = t_lnk[i] > ml ? t_lnk[i] : ml;
+      mp = t_pkt[i] > mp ? t_pkt[i] : mp;
+    }
+  }
+  cnt = warp_sum(cnt);
+  ml = warp_max(ml);
+  mp = warp_max(mp);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_red[0][warp] = cnt;
+    s_red[1][warp] = ml;
+    s_red[2][warp] = mp;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cnt = ml = mp = 0;
+    for (int v = 0; v < kHqThreads / 32; ++v) {
+      cnt += s_red[0][v];
+      ml = s_red[1][v] > ml ? s_red[1][v] : ml;
+      mp = s_red[2][v] > mp ? s_red[2][v] : mp;
+    }
+    if (s_spec_l) {
+      ++cnt;
+      ml = s_spec_l > ml ? s_spec_l : ml;
+      mp = s_spec_p > mp ? s_spec_p : mp;
+    }
+    if (cnt) atomicAdd(&w->keys[st], cnt);
+    if (ml) atomicMax(&w->max_links[st], ml);
+    if (mp) atomicMax(&w->max_packets[st], mp);
+  }
+}
+
+// Before the sort: the windows the hash finished get sort length 0 (the
+// sort, run statistics and column pass then leave them empty); the others,
+// failed or too large, keep their length.
+__global__ void k_hq_mask(SegPlan p, const HqWin* __restrict__ win, uint64_t* __restrict__ sort_len) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < p.nseg; s += gridDim.x * blockDim.x) {
+    const uint64_t n = p.len[s];
+    sort_len[s] = (n == 0 || win[s].fail || n > kHqMaxPackets) ? n : 0ull;
+  }
+}
+
+// After the sorted windows' statistics: the hashed windows' nine quantities.
+__global__ void k_hq_write(SegPlan p, const HqWin* __restrict__ win, ans_quantities* __restrict__ q) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < p.nseg; s += gridDim.x * blockDim.x) {
+    const uint64_t n = p.len[s];
+    const HqWin& w = win[s];
+    if (n == 0 || w.fail || n > kHqMaxPackets) continue;
+    ans_quantities r;
+    r.valid_packets = n;
+    r.unique_links = w.links;
+    r.max_link_packets = w.max_link;
+    r.unique_sources = w.keys[0];
+    r.max_source_packets = w.max_packets[0];
+    r.max_source_fanout = w.max_links[0];
+    r.unique_destinations = w.keys[1];
+    r.max_destination_packets = w.max_packets[1];
+    r.max_destination_fanin = w.max_links[1];
+    q[s] = r;
+  }
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* configured) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && ((*configured >> dev) & 1ull)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev < 64) *configured |= 1ull << dev;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_hq_stats(const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HqBufs& b,
+                            cudaStream_t st) {
+  if (p.nseg == 0) return cudaSuccess;
+  static unsigned long long cfg_links = 0, cfg_keys = 0;
+  cudaError_t e;
+  if ((e = set_smem(k_hq_links, kLinkSmem, &cfg_links)) != cudaSuccess) return e;
+  if ((e = set_smem(k_hq_keyhash, kKeySmem, &cfg_keys)) != cudaSuccess) return e;
+  k_hq_split<<<p.nseg, kHqThreads, 0, st>>>(p, src, dst, b.keys, b.lstart, b.win);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_hq_links<<<p.nseg * kLinkParts, kHqThreads, kLinkSmem, st>>>(p, b.keys, b.lstart, b.lsrc, b.ldst, b.lcnt, b.win);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int stage = 0; stage < 2; ++stage) {
+    const uint32_t* kin = stage == 0 ? b.lsrc : b.ldst;
+    k_hq_keysplit<<<p.nseg, kHqThreads, 0, st>>>(p, kin, b.lcnt, b.pkey, b.pval, b.kstart, b.win);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_hq_keyhash<<<p.nseg * kKeyParts, kHqThreads, kKeySmem, st>>>(p, b.pkey, b.pval, b.kstart, b.win, stage);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const uint32_t g = (p.nseg + 255) / 256;
+  k_hq_mask<<<g < 1024 ? g : 1024, 256, 0, st>>>(p, b.win, b.sort_len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hq_write(const SegPlan& p, const HqWin* win, ans_quantities* q, cudaStream_t st) {
+  if (p.nseg == 0) return cudaSuccess;
+  const uint32_t g = (p.nseg + 255) / 256;
+  k_hq_write<<<g < 1024 ? g : 1024, 256, 0, st>>>(p, win, q);
+  return cudaGetLastError();
+}
+
+}  // namespace ans

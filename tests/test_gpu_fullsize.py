@@ -43,7 +43,7 @@ def test_full_size_batch_against_oracle(cfg):
     results = []  # host copies of the GPU time sums
     ctx = ans.Context(0)
     try:
-        tuned = ctx.autotune(src, dst, w.offsets)
+        tuned = ctx.autotune(src, dst, w.offsets, flags=ans.BATCH_SUM)
         _, summ, q = _run(ans, ctx, src, dst, w, ans.BATCH_SUM)
         results.append((f"bench paths (sum_path {tuned['sum_path']})", summ.to_numpy(), summ.quantities()))
         summ.free()
