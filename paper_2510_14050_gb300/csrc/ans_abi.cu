@@ -1098,7 +1098,7 @@ struct WinLayout {
     off_tileseg = L.add((size_t)hp.ntiles * 4);
     off_hqwin = L.add((size_t)nseg * sizeof(HqWin));
     off_lstart = L.add((size_t)nseg * 65 * 4);
-    off_kstart = L.add((size_t)nseg * 33 * 4);
+    off_kstart = L.add((size_t)nseg * 2 * 65 * 4);
     off_sortlen = L.add((size_t)nseg * 8);
     dp_pk.reserve(L, 1);
     if (hash) {
@@ -1379,16 +1379,21 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         hb.lsrc = at<uint32_t>(m, ps.ck_a);
         hb.ldst = at<uint32_t>(m, ps.ck_b);
         hb.lcnt = (uint32_t*)at<uint64_t>(m, ps.cv_a);
-        hb.pkey = (uint32_t*)at<uint64_t>(m, ps.cv_b);
-        hb.pval = hb.pkey + hp.pad;
+        hb.pkey[0] = (uint32_t*)at<uint64_t>(m, ps.cv_b);
+        hb.pval[0] = hb.pkey[0] + hp.pad;
+        hb.pkey[1] = (uint32_t*)ka;  // the window sort's keys: free until the failed windows are sorted
+        hb.pval[1] = hb.pkey[1] + hp.pad;
         hb.lstart = at<uint32_t>(m, wl.off_lstart);
         hb.kstart = at<uint32_t>(m, wl.off_kstart);
         hb.win = at<HqWin>(m, wl.off_hqwin);
         hb.sort_len = at<uint64_t>(m, wl.off_sortlen);
         if ((rc = cu(launch_zero(hb.win, (size_t)nseg * sizeof(HqWin), ls), "memset"))) return rc;
-        if ((rc = cu(timed(c, "hash_stats", ls, [&] { return launch_hq_stats(p, d_src, d_dst, hb, ls); }),
-                     "hash statistics")))
-          return rc;
+        static const char* const kHqNames[5] = {"hq_split", "hq_links", "hq_keysplit", "hq_keyhash", "hq_mask"};
+        for (int stage = 0; stage < 5; ++stage)
+          if ((rc = cu(timed(c, kHqNames[stage], ls,
+                             [&] { return launch_hq_stage(stage, p, d_src, d_dst, hb, ls); }),
+                       "hash statistics")))
+            return rc;
         pwin.len = hb.sort_len;
       }
       SegPlan pw = pwin;  // the plan of the statistics phases

@@ -184,25 +184,28 @@ struct HqWin {
 };
 // Device buffers of the hashed statistics (keys: packets regrouped by link
 // partition, at each window's padded base; lsrc / ldst / lcnt: the windows'
-// distinct links; pkey / pval: links regrouped by key partition; lstart /
-// kstart: partition starts, 65 / 33 per window; sort_len: the plan lengths
-// the sort path then uses).
+// distinct links; pkey[st] / pval[st]: links regrouped by source (st = 0) or
+// destination (1) partition; lstart: 65 link-partition starts per window;
+// kstart: 65 key-partition starts per window and stage, stage 0 first;
+// sort_len: the plan lengths the sort path then uses).
 struct HqBufs {
   uint64_t* keys = nullptr;
   uint32_t* lsrc = nullptr;
   uint32_t* ldst = nullptr;
   uint32_t* lcnt = nullptr;
-  uint32_t* pkey = nullptr;
-  uint32_t* pval = nullptr;
+  uint32_t* pkey[2] = {nullptr, nullptr};
+  uint32_t* pval[2] = {nullptr, nullptr};
   uint32_t* lstart = nullptr;
   uint32_t* kstart = nullptr;
   HqWin* win = nullptr;
   uint64_t* sort_len = nullptr;
 };
-// The hashed statistics of every window of p (win zeroed by the caller),
-// ending with sort_len; the quantities are written by launch_hq_write once
-// the sort path has run over sort_len.
-cudaError_t launch_hq_stats(const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HqBufs& b,
+// The hashed statistics of every window of p (win zeroed by the caller), in
+// five launches, stage 0 .. 4: regroup packets by link partition, count
+// links, regroup the distinct links by source and destination partition,
+// count sources and destinations, set sort_len.  The quantities are written
+// by launch_hq_write once the sort path has run over sort_len.
+cudaError_t launch_hq_stage(int stage, const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HqBufs& b,
                             cudaStream_t st);
 cudaError_t launch_hq_write(const SegPlan& p, const HqWin* win, ans_quantities* q, cudaStream_t st);
 

@@ -36,9 +36,9 @@ constexpr uint32_t kLinkSlots = 8192;                        // link table: uint
 constexpr uint32_t kLinkMaxFill = kLinkSlots / 4 * 3;
 constexpr size_t kLinkSmem = (size_t)kLinkSlots * 12;
 constexpr uint64_t kLinkEmpty = ~0ull;                       // marks an empty slot (that link is counted apart)
-constexpr uint32_t kKeyPartLinks = 8192;                     // links per source / destination partition (mean)
-constexpr uint32_t kKeyParts = kHqMaxPackets / kKeyPartLinks;  // 32
-constexpr uint32_t kKeySlots = 16384;                        // key, links, packets (uint32 each)
+constexpr uint32_t kKeyPartLinks = 4096;                     // links per source / destination partition (mean)
+constexpr uint32_t kKeyParts = kHqMaxPackets / kKeyPartLinks;  // 64
+constexpr uint32_t kKeySlots = 8192;                         // key, links, packets (uint32 each): 96 KB
 constexpr uint32_t kKeyMaxFill = kKeySlots / 4 * 3;
 constexpr size_t kKeySmem = (size_t)kKeySlots * 12;
 constexpr uint32_t kKeyEmpty = 0xFFFFFFFFu;
@@ -207,8 +207,9 @@ __global__ void __launch_bounds__(kHqThreads, 2) k_hq_links(SegPlan p, const uin
     const uint32_t u = u0 + threadIdx.x;
     const bool valid = u < hi;
     const uint64_t k = valid ? in[u] : kLinkEmpty;
-    // lanes holding the same link add it once
-    const uint32_t peers = __match_any_sync(0xffffffffu, k);
+    // lanes holding the same link add it once (lanes past the partition's
+    // end hold a filler equal to the all-ones link: masked out)
+    const uint32_t peers = __match_any_sync(0xffffffffu, k) & __ballot_sync(0xffffffffu, valid);
     if (!valid || lane != __ffs(peers) - 1) continue;
     const uint32_t c = __popc(peers);
     if (k == kLinkEmpty) {
@@ -290,14 +291,15 @@ __global__ void __launch_bounds__(kHqThreads, 2) k_hq_links(SegPlan p, const uin
 // Step 3a: one CTA per window regroups its distinct links' (key, count) --
 // key = source (stage 0) or destination (stage 1) -- by key partition into
 // pkey / pval + base[s]; partition starts in kstart[s][0..parts].
-__global__ void __launch_bounds__(kHqThreads, 2) k_hq_keysplit(SegPlan p, const uint32_t* __restrict__ kin,
-                                                               const uint32_t* __restrict__ cin,
-                                                               uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval,
-                                                               uint32_t* __restrict__ kstart,
-                                                               const HqWin* __restrict__ win) {
+__global__ void __launch_bounds__(kHqThreads, 2) k_hq_keysplit(SegPlan p, HqBufs bufs) {
   __shared__ uint32_t s_cnt[kKeyParts], s_cur[kKeyParts];
-  const uint32_t s = blockIdx.x;
-  if (s >= p.nseg) return;
+  const uint32_t stage = blockIdx.x / p.nseg, s = blockIdx.x % p.nseg;  // both stages in one grid
+  const uint32_t* kin = stage == 0 ? bufs.lsrc : bufs.ldst;
+  const uint32_t* cin = bufs.lcnt;
+  uint32_t* pkey = bufs.pkey[stage];
+  uint32_t* pval = bufs.pval[stage];
+  uint32_t* kstart = bufs.kstart + (size_t)stage * p.nseg * (kKeyParts + 1);
+  const HqWin* win = bufs.win;
   const HqWin& w = win[s];
   const uint32_t n = w.nlinks;
   if (n == 0 || w.fail) return;
@@ -357,19 +359,19 @@ __global__ void __launch_bounds__(kHqThreads, 2) k_hq_keysplit(SegPlan p, const 
 // Step 3b: CTA r of window s counts partition r's keys: per key its links
 // (fan-out / fan-in) and packets; the window gets the number of distinct
 // keys, the largest link count and the largest packet count of stage `st`.
-__global__ void __launch_bounds__(kHqThreads, 1) k_hq_keyhash(SegPlan p, const uint32_t* __restrict__ pkey,
-                                                              const uint32_t* __restrict__ pval,
-                                                              const uint32_t* __restrict__ kstart,
-                                                              HqWin* __restrict__ win, int st) {
+__global__ void __launch_bounds__(kHqThreads, 2) k_hq_keyhash(SegPlan p, HqBufs bufs) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* t_key = sm;
   uint32_t* t_lnk = sm + kKeySlots;
   uint32_t* t_pkt = sm + 2 * kKeySlots;
   __shared__ uint32_t s_fill, s_over, s_spec_l, s_spec_p;
   __shared__ unsigned long long s_red[3][kHqThreads / 32];
-  const uint32_t s = blockIdx.x / kKeyParts, r = blockIdx.x % kKeyParts;
-  if (s >= p.nseg) return;
-  HqWin* w = win + s;
+  const uint32_t st = blockIdx.x / (p.nseg * kKeyParts);  // both stages in one grid
+  const uint32_t s = (blockIdx.x / kKeyParts) % p.nseg, r = blockIdx.x % kKeyParts;
+  const uint32_t* pkey = bufs.pkey[st];
+  const uint32_t* pval = bufs.pval[st];
+  const uint32_t* kstart = bufs.kstart + (size_t)st * p.nseg * (kKeyParts + 1);
+  HqWin* w = bufs.win + s;
   const uint32_t n = w->nlinks;
   if (n == 0 || w->fail) return;
   const uint32_t parts = ceil_div(n, kKeyPartLinks);
@@ -494,26 +496,32 @@ cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* configured) {
 
 }  // namespace
 
-cudaError_t launch_hq_stats(const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HqBufs& b,
+cudaError_t launch_hq_stage(int stage, const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HqBufs& b,
                             cudaStream_t st) {
   if (p.nseg == 0) return cudaSuccess;
   static unsigned long long cfg_links = 0, cfg_keys = 0;
   cudaError_t e;
-  if ((e = set_smem(k_hq_links, kLinkSmem, &cfg_links)) != cudaSuccess) return e;
-  if ((e = set_smem(k_hq_keyhash, kKeySmem, &cfg_keys)) != cudaSuccess) return e;
-  k_hq_split<<<p.nseg, kHqThreads, 0, st>>>(p, src, dst, b.keys, b.lstart, b.win);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_hq_links<<<p.nseg * kLinkParts, kHqThreads, kLinkSmem, st>>>(p, b.keys, b.lstart, b.lsrc, b.ldst, b.lcnt, b.win);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int stage = 0; stage < 2; ++stage) {
-    const uint32_t* kin = stage == 0 ? b.lsrc : b.ldst;
-    k_hq_keysplit<<<p.nseg, kHqThreads, 0, st>>>(p, kin, b.lcnt, b.pkey, b.pval, b.kstart, b.win);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_hq_keyhash<<<p.nseg * kKeyParts, kHqThreads, kKeySmem, st>>>(p, b.pkey, b.pval, b.kstart, b.win, stage);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  switch (stage) {
+    case 0:
+      k_hq_split<<<p.nseg, kHqThreads, 0, st>>>(p, src, dst, b.keys, b.lstart, b.win);
+      break;
+    case 1:
+      if ((e = set_smem(k_hq_links, kLinkSmem, &cfg_links)) != cudaSuccess) return e;
+      k_hq_links<<<p.nseg * kLinkParts, kHqThreads, kLinkSmem, st>>>(p, b.keys, b.lstart, b.lsrc, b.ldst, b.lcnt,
+                                                                   b.win);
+      break;
+    case 2:
+      k_hq_keysplit<<<2 * p.nseg, kHqThreads, 0, st>>>(p, b);
+      break;
+    case 3:
+      if ((e = set_smem(k_hq_keyhash, kKeySmem, &cfg_keys)) != cudaSuccess) return e;
+      k_hq_keyhash<<<2 * p.nseg * kKeyParts, kHqThreads, kKeySmem, st>>>(p, b);
+      break;
+    default: {
+      const uint32_t g = (p.nseg + 255) / 256;
+      k_hq_mask<<<g < 1024 ? g : 1024, 256, 0, st>>>(p, b.win, b.sort_len);
+    }
   }
-  const uint32_t g = (p.nseg + 255) / 256;
-  k_hq_mask<<<g < 1024 ? g : 1024, 256, 0, st>>>(p, b.win, b.sort_len);
   return cudaGetLastError();
 }
 
