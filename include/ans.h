@@ -400,6 +400,19 @@ int ans_matrix_import(ans_ctx* ctx, uint64_t nrows, uint64_t nnz, const uint32_t
                       const uint64_t* row_ptr, const uint32_t* col_ids, const uint64_t* vals,
                       ans_matrix** out, void* stream);
 
+/* Row partition of a matrix for the exchange step of a time sum computed on
+ * several devices (Sec. III-A, Fig. 4: each device's windows summed there,
+ * the global sum owned in row partitions).  Rank o of nparts owns the rows
+ * whose source address i has ((i * 0x9E3779B1 mod 2^32) * nparts) >> 32 == o;
+ * out[o] receives those rows of m with all their links, as a new canonical
+ * DCSR matrix with its quantities (so sum_o out[o] == m, row by row).  Each
+ * piece can then be sent to its owner (its arrays through ans_matrix_view)
+ * and added there to the pieces of the other ranks (ans_matrix_import +
+ * ans_sum_windows).  nparts: 1 .. 64.  Waits for m and for the pieces'
+ * sizes.  Errors: ANS_ERR_INVALID_ARG, ANS_ERR_BUDGET, ANS_ERR_OOM,
+ * ANS_ERR_CUDA; a failed m's status. */
+int ans_matrix_split_rows(ans_ctx* ctx, const ans_matrix* m, uint32_t nparts, ans_matrix** out, void* stream);
+
 /* Static description of a status code. */
 const char* ans_status_string(int status);
 

@@ -47,6 +47,7 @@ EXPORTS = (
     "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
     "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import", "ans_batch_submit_windows", "ans_combine",
     "ans_set_wait_limit", "ans_probe_wait_expiry", "ans_batch_submit_host", "ans_set_batch_capacity",
+    "ans_matrix_split_rows",
 )
 
 # The allocator hook types of ans_ctx_create.
@@ -102,6 +103,7 @@ def load(path: str | os.PathLike | None = None):
         "ans_batch_submit_host": ([_vp, _vp, _vp, P(_u64), C.c_size_t, C.c_uint32, _vp, P(_vp), P(_vp), P(_u64),
                                    _vp], C.c_int),
         "ans_set_batch_capacity": ([_vp, _u64], C.c_int),
+        "ans_matrix_split_rows": ([_vp, _vp, C.c_uint32, P(_vp), _vp], C.c_int),
         "ans_wait": ([_vp, _u64, _u64], C.c_int),
         "ans_matrix_view": ([_vp, P(_u64), P(_u64), P(_vp), P(_vp), P(_vp), P(_vp)], C.c_int),
         "ans_matrix_quantities": ([_vp, P(Quantities)], C.c_int),
@@ -370,6 +372,14 @@ class Context:
         _check(self._lib.ans_sum_windows(self._h, arr, len(mats), C.byref(out), _vp(_stream(stream))),
                "sum_windows", self._h)
         return Matrix(out.value)
+
+    def split_rows(self, m: Matrix, nparts: int, stream=None) -> list:
+        """m's rows split by owner rank (a hash of the source address mod
+        nparts), one new matrix per owner."""
+        arr = (_vp * nparts)()
+        _check(self._lib.ans_matrix_split_rows(self._h, m.handle, int(nparts), arr, _vp(_stream(stream))),
+               "matrix_split_rows", self._h)
+        return [Matrix(arr[i]) for i in range(nparts)]
 
     def network_quantities(self, m: Matrix, out=None, stream=None) -> dict | None:
         """Recompute the nine quantities of ``m`` on the device.  With ``out``

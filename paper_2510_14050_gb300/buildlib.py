@@ -25,7 +25,7 @@ OBJ = PKG / "_build"
 LIBANS = PKG / "libans.so"
 LIBSYNTH = PKG / "libans_synth.so"
 
-CUDA_UNITS = ["ans_abi.cu", "ans_sort.cu", "ans_stats.cu", "ans_cluster.cu", "ans_merge.cu", "ans_hash.cu", "ans_noalloc.cu", "ans_plan.cu", "ans_winhash.cu"]
+CUDA_UNITS = ["ans_abi.cu", "ans_sort.cu", "ans_stats.cu", "ans_cluster.cu", "ans_merge.cu", "ans_hash.cu", "ans_noalloc.cu", "ans_plan.cu", "ans_winhash.cu", "ans_split.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"]

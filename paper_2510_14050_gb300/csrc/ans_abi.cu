@@ -1079,7 +1079,7 @@ struct WinLayout {
   size_t off_colacc = 0; // per-window accumulators of the partitioned column hash
   size_t off_colpart = 0; // its partition starts per window
   size_t off_tileseg = 0; // the window plan's segment of every tile
-  size_t off_hqwin = 0, off_lstart = 0, off_kstart = 0, off_sortlen = 0;  // hashed window statistics
+  size_t off_hqwin = 0, off_lstart = 0, off_kstart = 0, off_sortlen = 0, off_items = 0;  // hashed window statistics
   DevPlan dp_tab;        // hash path: the windows' tables as segments
   DevPlan dp_pk;         // sum_path 2: all packets of the batch as one segment
   size_t off_tlg = 0, off_special = 0, off_hulen = 0, off_nclaim = 0, off_claims = 0;
@@ -1100,6 +1100,7 @@ struct WinLayout {
     off_lstart = L.add((size_t)nseg * 65 * 4);
     off_kstart = L.add((size_t)nseg * 2 * 65 * 4);
     off_sortlen = L.add((size_t)nseg * 8);
+    off_items = L.add(((size_t)2 * nseg + 2) * 4);
     dp_pk.reserve(L, 1);
     if (hash) {
       dp_tab.reserve(L, nseg);
@@ -1387,6 +1388,8 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         hb.kstart = at<uint32_t>(m, wl.off_kstart);
         hb.win = at<HqWin>(m, wl.off_hqwin);
         hb.sort_len = at<uint64_t>(m, wl.off_sortlen);
+        hb.items = at<uint32_t>(m, wl.off_items);
+        hb.counter = hb.items + 2 * (size_t)nseg + 1;
         if ((rc = cu(launch_zero(hb.win, (size_t)nseg * sizeof(HqWin), ls), "memset"))) return rc;
         static const char* const kHqNames[5] = {"hq_split", "hq_links", "hq_keysplit", "hq_keyhash", "hq_mask"};
         for (int stage = 0; stage < 5; ++stage)
@@ -2204,6 +2207,81 @@ int ans_matrix_free(ans_matrix* x) {
   if (!x) return ANS_OK;
   block_release(x->blk);
   delete x;
+  return ANS_OK;
+}
+
+int ans_matrix_split_rows(ans_ctx* c, const ans_matrix* x, uint32_t nparts, ans_matrix** out, void* stream) {
+  if (!c || !x || !out) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  if (nparts < 1 || nparts > kMaxSplitParts) return fail(ANS_ERR_INVALID_ARG, "nparts must be 1 .. 64");
+  for (uint32_t o = 0; o < nparts; ++o) out[o] = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  Block* b = x->blk;
+  if (b->ctx->device != c->device) return fail(ANS_ERR_INVALID_ARG, "matrix on another device");
+  ANS_TRY(block_fill_cache(b));  // the matrix's size (waits for it)
+  ANS_TRY(block_status(b));
+  const uint64_t nrows = b->h_hdr[2 * (size_t)x->seg], nnz = b->h_hdr[2 * (size_t)x->seg + 1];
+  const uint64_t bs = b->base[x->seg];
+  const uint32_t* row_ids = b->row_ids + bs;
+  const uint64_t* row_ptr = b->row_ptr + bs + x->seg;
+  const uint32_t* col_ids = b->col_ids + bs;
+  const uint64_t* vals = b->vals + bs;
+  // scratch: per-tile counts, totals, per-row owner and first link
+  const uint32_t nt = split_row_tiles(nrows);
+  Layout L;
+  const size_t o_trows = L.add((size_t)nt * nparts * 4);
+  const size_t o_tlinks = L.add((size_t)nt * nparts * 8);
+  const size_t o_tot = L.add((size_t)nparts * 16);
+  const size_t o_rown = L.add(nrows * 4);
+  const size_t o_rlink = L.add(nrows * 8);
+  ANS_TRY(ensure_scratch(c, L.size, st));
+  char* m = (char*)c->scratch;
+  uint32_t* trows = at<uint32_t>(m, o_trows);
+  uint64_t* tlinks = at<uint64_t>(m, o_tlinks);
+  uint64_t* tot = at<uint64_t>(m, o_tot);
+  ANS_CUDA(launch_split_count(nrows, row_ids, row_ptr, nparts, trows, tlinks, tot, st));
+  std::vector<uint64_t> h_tot(2 * (size_t)nparts);
+  ANS_CUDA(cudaMemcpyAsync(h_tot.data(), tot, h_tot.size() * 8, cudaMemcpyDeviceToHost, st));
+  ANS_CUDA(cudaStreamSynchronize(st));
+  // one block per owner
+  std::vector<Block*> blks(nparts, nullptr);
+  auto bail = [&](int rc) {
+    for (Block* q : blks) block_discard(q, st);
+    return rc;
+  };
+  SplitOut so{};
+  for (uint32_t o = 0; o < nparts; ++o) {
+    const uint64_t u = h_tot[2 * o + 1];
+    int rc = make_block(c, tiles_for(u) * kTile, 1, {0}, {u}, st, &blks[o]);
+    if (rc) return bail(rc);
+    so.row_ids[o] = blks[o]->row_ids;
+    so.row_ptr[o] = blks[o]->row_ptr;
+    so.col_ids[o] = blks[o]->col_ids;
+    so.vals[o] = blks[o]->vals;
+    so.hdr[o] = blks[o]->hdr;
+  }
+  auto cu = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return ANS_OK;
+    return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  int rc = cu(launch_split_fill(nrows, nnz, row_ids, row_ptr, col_ids, vals, nparts, trows, tlinks, tot,
+                                at<uint32_t>(m, o_rown), at<uint64_t>(m, o_rlink), so, st),
+              "split");
+  if (rc) return bail(rc);
+  for (uint32_t o = 0; o < nparts && rc == ANS_OK; ++o) {
+    if ((rc = cu(cudaMemsetAsync(blks[o]->status, 0, 4, st), "memset")) == ANS_OK &&
+        (rc = matrix_stats(c, blks[o], 0, blks[o]->q, st)) == ANS_OK)
+      rc = capture_err(c, blks[o]->status, st);
+  }
+  if (rc == ANS_OK) rc = reset_err(c, st);
+  if (rc == ANS_OK) rc = note_read(b, st);
+  if (rc) return bail(rc);
+  for (uint32_t o = 0; o < nparts; ++o) {
+    ANS_CUDA(cudaEventRecord(blks[o]->done, st));
+    blks[o]->refs = 1;
+    out[o] = new ans_matrix{blks[o], 0};
+  }
   return ANS_OK;
 }
 

@@ -199,6 +199,8 @@ struct HqBufs {
   uint32_t* kstart = nullptr;
   HqWin* win = nullptr;
   uint64_t* sort_len = nullptr;
+  uint32_t* items = nullptr;    // work-item prefix of the counting steps (2 * nseg + 1)
+  uint32_t* counter = nullptr;  // their queue counter
 };
 // The hashed statistics of every window of p (win zeroed by the caller), in
 // five launches, stage 0 .. 4: regroup packets by link partition, count
@@ -208,6 +210,30 @@ struct HqBufs {
 cudaError_t launch_hq_stage(int stage, const SegPlan& p, const uint32_t* src, const uint32_t* dst, const HqBufs& b,
                             cudaStream_t st);
 cudaError_t launch_hq_write(const SegPlan& p, const HqWin* win, ans_quantities* q, cudaStream_t st);
+
+// ---- row partition across ranks (ans_split.cu) ----------------------------
+constexpr uint32_t kMaxSplitParts = 64;
+// The owners' pieces (device pointers per owner; hdr = {nrows, nnz}).
+struct SplitOut {
+  uint32_t* row_ids[kMaxSplitParts];
+  uint64_t* row_ptr[kMaxSplitParts];
+  uint32_t* col_ids[kMaxSplitParts];
+  uint64_t* vals[kMaxSplitParts];
+  uint64_t* hdr[kMaxSplitParts];
+};
+// Row tiles of a matrix of nrows rows (8192 rows each).
+uint32_t split_row_tiles(uint64_t nrows);
+// Per tile and owner the rows (trows) and links (tlinks) of a DCSR, turned
+// into exclusive offsets over the tiles; totals[2 o] / [2 o + 1] = owner o's
+// rows / links.  trows and tlinks hold split_row_tiles(nrows) * nparts entries.
+cudaError_t launch_split_count(uint64_t nrows, const uint32_t* row_ids, const uint64_t* row_ptr, uint32_t nparts,
+                               uint32_t* trows, uint64_t* tlinks, uint64_t* totals, cudaStream_t st);
+// The owners' pieces written (rows in order, each row's links after its
+// first one); rown / rlink: nrows words of scratch each.
+cudaError_t launch_split_fill(uint64_t nrows, uint64_t nnz, const uint32_t* row_ids, const uint64_t* row_ptr,
+                              const uint32_t* col_ids, const uint64_t* vals, uint32_t nparts, const uint32_t* trows,
+                              const uint64_t* tlinks, const uint64_t* totals, uint32_t* rown, uint64_t* rlink,
+                              const SplitOut& out, cudaStream_t st);
 
 // ---- launcher (ans_plan.cu) ------------------------------------------------
 // Plan the nseg windows [d_offsets[s], d_offsets[s+1]) on the device (one

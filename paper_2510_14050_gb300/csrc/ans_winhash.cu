@@ -173,118 +173,189 @@ __device__ __forceinline__ void block_sum_max(unsigned long long& sum, unsigned 
   }
 }
 
-// Step 2: CTA r of window s counts the links of partition r in a table of
-// kLinkSlots keys; adds its distinct links and its largest link count to the
-// window's accumulator and appends the distinct links as (source,
-// destination, count) at lsrc / ldst / lcnt + base[s] + (the window's running
-// link count).
+// Work items of the counting steps: items[v] = the first item of virtual
+// segment v (an exclusive prefix of per-segment partition counts; the last
+// entry is the total), for kind 0 the windows' link partitions, for kind 1
+// the source partitions of every window followed by the destination ones.
+// One CTA; also zeroes the queue counter the persistent kernels draw from.
+__global__ void __launch_bounds__(kHqThreads) k_hq_items(SegPlan p, const HqWin* __restrict__ win, int kind,
+                                                         uint32_t* __restrict__ items, uint32_t* __restrict__ counter) {
+  __shared__ uint32_t s_tmp[kHqThreads / 32];
+  const uint32_t nv = kind == 0 ? p.nseg : 2 * p.nseg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t carry = 0;
+  for (uint32_t c0 = 0; c0 < nv; c0 += kHqThreads) {
+    const uint32_t v = c0 + threadIdx.x;
+    uint32_t cnt = 0;
+    if (v < nv) {
+      if (kind == 0) {
+        const uint64_t n = p.len[v];
+        cnt = (n == 0 || n > kHqMaxPackets) ? 0u : ceil_div(n, kLinkPartPackets);
+      } else {
+        const HqWin& w = win[v % p.nseg];
+        cnt = (w.nlinks == 0 || w.fail) ? 0u : ceil_div(w.nlinks, kKeyPartLinks);
+      }
+    }
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_tmp[warp] = x;
+    __syncthreads();
+    uint32_t off = 0, tot = 0;
+    for (int w = 0; w < kHqThreads / 32; ++w) {
+      off += w < warp ? s_tmp[w] : 0u;
+      tot += s_tmp[w];
+    }
+    if (v < nv) items[v] = carry + off + x - cnt;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    items[nv] = carry;
+    *counter = 0;
+  }
+}
+
+// The next work item of a persistent CTA (every thread gets it), and its
+// virtual segment: the last v with items[v] <= item.  Returns false when the
+// queue is empty.
+__device__ __forceinline__ bool next_item(uint32_t* counter, const uint32_t* items, uint32_t nv, uint32_t* s_item,
+                                          uint32_t* v_out, uint32_t* r_out) {
+  if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t it = *s_item;
+  __syncthreads();  // everyone has read it before the next draw overwrites it
+  if (it >= items[nv]) return false;
+  uint32_t lo = 0, hi = nv;  // items[lo] <= it < items[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (items[mid] <= it) lo = mid; else hi = mid;
+  }
+  *v_out = lo;
+  *r_out = it - items[lo];
+  return true;
+}
+
+// Step 2 (persistent: each CTA draws (window, link partition) items): the
+// partition's links counted in a table of kLinkSlots keys; the window's
+// accumulator gets the partition's distinct links and largest link count,
+// and the distinct links are appended as (source, destination, count) at
+// lsrc / ldst / lcnt + base[s] + (the window's running link count).
 __global__ void __launch_bounds__(kHqThreads, 2) k_hq_links(SegPlan p, const uint64_t* __restrict__ keys,
                                                             const uint32_t* __restrict__ lstart,
                                                             uint32_t* __restrict__ lsrc, uint32_t* __restrict__ ldst,
-                                                            uint32_t* __restrict__ lcnt, HqWin* __restrict__ win) {
+                                                            uint32_t* __restrict__ lcnt, HqWin* __restrict__ win,
+                                                            const uint32_t* __restrict__ items, uint32_t* counter) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t* t_key = reinterpret_cast<uint64_t*>(smem);
   uint32_t* t_cnt = reinterpret_cast<uint32_t*>(smem + (size_t)kLinkSlots * 8);
-  __shared__ uint32_t s_fill, s_over, s_spec, s_off;
+  __shared__ uint32_t s_fill, s_over, s_spec, s_off, s_item;
   __shared__ unsigned long long s_red[2][kHqThreads / 32];
   __shared__ uint32_t s_wcnt[kHqThreads / 32];
-  const uint32_t s = blockIdx.x / kLinkParts, r = blockIdx.x % kLinkParts;
-  if (s >= p.nseg) return;
-  const uint64_t n = p.len[s];
-  if (n == 0 || n > kHqMaxPackets) return;
-  const uint32_t parts = ceil_div(n, kLinkPartPackets);
-  if (r >= parts) return;
-  const uint32_t lo = lstart[(uint64_t)s * (kLinkParts + 1) + r], hi = lstart[(uint64_t)s * (kLinkParts + 1) + r + 1];
-  const uint64_t* in = keys + p.base[s];
-  for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
-    t_key[i] = kLinkEmpty;
-    t_cnt[i] = 0;
-  }
-  if (threadIdx.x == 0) s_fill = s_over = s_spec = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t u0 = lo; u0 < hi; u0 += kHqThreads) {
-    const uint32_t u = u0 + threadIdx.x;
-    const bool valid = u < hi;
-    const uint64_t k = valid ? in[u] : kLinkEmpty;
-    // lanes holding the same link add it once (lanes past the partition's
-    // end hold a filler equal to the all-ones link: masked out)
-    const uint32_t peers = __match_any_sync(0xffffffffu, k) & __ballot_sync(0xffffffffu, valid);
-    if (!valid || lane != __ffs(peers) - 1) continue;
-    const uint32_t c = __popc(peers);
-    if (k == kLinkEmpty) {
-      atomicAdd(&s_spec, c);
-      continue;
+  uint32_t s, r;
+  while (next_item(counter, items, p.nseg, &s_item, &s, &r)) {
+    const uint32_t lo = lstart[(uint64_t)s * (kLinkParts + 1) + r];
+    const uint32_t hi = lstart[(uint64_t)s * (kLinkParts + 1) + r + 1];
+    const uint64_t* in = keys + p.base[s];
+    for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
+      t_key[i] = kLinkEmpty;
+      t_cnt[i] = 0;
     }
-    if (*(volatile uint32_t*)&s_over) continue;
-    uint32_t h = (uint32_t)fmix64(k) & (kLinkSlots - 1);
-    for (uint32_t probe = 0; probe < kLinkSlots; ++probe) {
-      unsigned long long cur = *(volatile unsigned long long*)&t_key[h];
-      if (cur == kLinkEmpty) {
-        cur = atomicCAS((unsigned long long*)&t_key[h], (unsigned long long)kLinkEmpty, (unsigned long long)k);
+    if (threadIdx.x == 0) s_fill = s_over = s_spec = 0;
+    __syncthreads();
+    for (uint32_t u0 = lo; u0 < hi; u0 += kHqThreads) {  // the same bound for every thread
+      const uint32_t u = u0 + threadIdx.x;
+      const bool valid = u < hi;
+      const uint64_t k = valid ? in[u] : kLinkEmpty;
+      // lanes holding the same link add it once (lanes past the partition's
+      // end hold a filler equal to the all-ones link: masked out)
+      const uint32_t peers = __match_any_sync(0xffffffffu, k) & __ballot_sync(0xffffffffu, valid);
+      if (!valid || lane != __ffs(peers) - 1) continue;
+      const uint32_t c = __popc(peers);
+      if (k == kLinkEmpty) {
+        atomicAdd(&s_spec, c);
+        continue;
+      }
+      if (*(volatile uint32_t*)&s_over) continue;
+      uint32_t h = (uint32_t)fmix64(k) & (kLinkSlots - 1);
+      for (uint32_t probe = 0; probe < kLinkSlots; ++probe) {
+        unsigned long long cur = *(volatile unsigned long long*)&t_key[h];
         if (cur == kLinkEmpty) {
-          cur = k;
-          if (atomicAdd(&s_fill, 1u) + 1 > kLinkMaxFill) s_over = 1;
+          cur = atomicCAS((unsigned long long*)&t_key[h], (unsigned long long)kLinkEmpty, (unsigned long long)k);
+          if (cur == kLinkEmpty) {
+            cur = k;
+            if (atomicAdd(&s_fill, 1u) + 1 > kLinkMaxFill) s_over = 1;
+          }
         }
+        if (cur == k) {
+          atomicAdd(&t_cnt[h], c);
+          break;
+        }
+        h = (h + 1) & (kLinkSlots - 1);
       }
-      if (cur == k) {
-        atomicAdd(&t_cnt[h], c);
-        break;
+    }
+    __syncthreads();
+    HqWin* w = win + s;
+    if (s_over) {  // the window is sorted instead
+      if (threadIdx.x == 0) atomicOr(&w->fail, 1u);
+      continue;    // (uniform: s_over is shared)
+    }
+    // distinct links of this partition: count, largest count, then append
+    // them in rounds of one slot per thread, so that a warp's lanes write
+    // consecutive places (the round's occupied slots compacted by ballot)
+    unsigned long long nl = 0, mx = 0;
+    for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
+      if (t_key[i] != kLinkEmpty) {
+        ++nl;
+        mx = t_cnt[i] > mx ? t_cnt[i] : mx;
       }
-      h = (h + 1) & (kLinkSlots - 1);
     }
-  }
-  __syncthreads();
-  HqWin* w = win + s;
-  if (s_over) {
-    if (threadIdx.x == 0) atomicOr(&w->fail, 1u);
-    return;
-  }
-  // distinct links of this partition: count, largest count, then append
-  unsigned long long nl = 0, mx = 0;
-  for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
-    if (t_key[i] != kLinkEmpty) {
-      ++nl;
-      mx = t_cnt[i] > mx ? t_cnt[i] : mx;
+    unsigned long long tot = nl, m2 = mx;
+    block_sum_max(tot, m2, s_red);
+    if (threadIdx.x == 0) {
+      const uint32_t spec = s_spec;
+      tot += spec ? 1 : 0;
+      m2 = spec > m2 ? spec : m2;
+      s_off = atomicAdd(&w->nlinks, (uint32_t)tot);
+      if (tot) atomicAdd(&w->links, tot);
+      if (m2) atomicMax(&w->max_link, m2);
+      s_fill = (uint32_t)tot;  // (the table is done: reuse the word for the total)
     }
-  }
-  // per-thread counts -> exclusive offsets within the CTA (warp scan + warp totals)
-  uint32_t mine = (uint32_t)nl, x = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_wcnt[warp] = x;
-  unsigned long long tot = nl, m2 = mx;
-  block_sum_max(tot, m2, s_red);
-  if (threadIdx.x == 0) {
-    const uint32_t spec = s_spec;
-    tot += spec ? 1 : 0;
-    m2 = spec > m2 ? spec : m2;
-    s_off = atomicAdd(&w->nlinks, (uint32_t)tot);
-    if (tot) atomicAdd(&w->links, tot);
-    if (m2) atomicMax(&w->max_link, m2);
-  }
-  __syncthreads();
-  uint32_t woff = 0;
-  for (int v = 0; v < warp; ++v) woff += s_wcnt[v];
-  uint32_t o = s_off + woff + x - mine;
-  const uint64_t b = p.base[s];
-  for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
-    const uint64_t k = t_key[i];
-    if (k != kLinkEmpty) {
-      lsrc[b + o] = (uint32_t)(k >> 32);
-      ldst[b + o] = (uint32_t)k;
-      lcnt[b + o] = t_cnt[i];
-      ++o;
+    __syncthreads();
+    const uint64_t b = p.base[s];
+    uint32_t round_off = s_off;
+    for (uint32_t i0 = 0; i0 < kLinkSlots; i0 += kHqThreads) {
+      const uint64_t k = t_key[i0 + threadIdx.x];
+      const bool occ = k != kLinkEmpty;
+      const uint32_t bal = __ballot_sync(0xffffffffu, occ);
+      if (lane == 0) s_wcnt[warp] = __popc(bal);
+      __syncthreads();
+      uint32_t woff = 0, rtot = 0;
+      for (int v = 0; v < kHqThreads / 32; ++v) {
+        const uint32_t c = s_wcnt[v];
+        woff += v < warp ? c : 0u;
+        rtot += c;
+      }
+      if (occ) {
+        const uint32_t o = round_off + woff + __popc(bal & lanemask_lt());
+        lsrc[b + o] = (uint32_t)(k >> 32);
+        ldst[b + o] = (uint32_t)k;
+        lcnt[b + o] = t_cnt[i0 + threadIdx.x];
+      }
+      round_off += rtot;
+      __syncthreads();  // s_wcnt is rewritten by the next round
     }
-  }
-  if (threadIdx.x == 0 && s_spec) {  // the all-ones link, counted apart, goes last
-    const uint32_t last = s_off + (uint32_t)tot - 1;
-    lsrc[b + last] = kKeyEmpty;
-    ldst[b + last] = kKeyEmpty;
-    lcnt[b + last] = s_spec;
+    if (threadIdx.x == 0 && s_spec) {  // the all-ones link, counted apart, goes last
+      const uint32_t last = s_off + s_fill - 1;
+      lsrc[b + last] = kKeyEmpty;
+      ldst[b + last] = kKeyEmpty;
+      lcnt[b + last] = s_spec;
+    }
+    __syncthreads();  // the table is read no more
   }
 }
 
@@ -356,100 +427,101 @@ __global__ void __launch_bounds__(kHqThreads, 2) k_hq_keysplit(SegPlan p, HqBufs
   }
 }
 
-// Step 3b: CTA r of window s counts partition r's keys: per key its links
-// (fan-out / fan-in) and packets; the window gets the number of distinct
-// keys, the largest link count and the largest packet count of stage `st`.
-__global__ void __launch_bounds__(kHqThreads, 2) k_hq_keyhash(SegPlan p, HqBufs bufs) {
+// Step 3b (persistent: each CTA draws (stage, window, key partition)
+// items): the partition's keys counted, per key its links (fan-out /
+// fan-in) and packets; the window gets the number of distinct keys, the
+// largest link count and the largest packet count of the stage.
+__global__ void __launch_bounds__(kHqThreads, 2) k_hq_keyhash(SegPlan p, HqBufs bufs, const uint32_t* __restrict__ items,
+                                                              uint32_t* counter) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* t_key = sm;
   uint32_t* t_lnk = sm + kKeySlots;
   uint32_t* t_pkt = sm + 2 * kKeySlots;
-  __shared__ uint32_t s_fill, s_over, s_spec_l, s_spec_p;
+  __shared__ uint32_t s_fill, s_over, s_spec_l, s_spec_p, s_item;
   __shared__ unsigned long long s_red[3][kHqThreads / 32];
-  const uint32_t st = blockIdx.x / (p.nseg * kKeyParts);  // both stages in one grid
-  const uint32_t s = (blockIdx.x / kKeyParts) % p.nseg, r = blockIdx.x % kKeyParts;
-  const uint32_t* pkey = bufs.pkey[st];
-  const uint32_t* pval = bufs.pval[st];
-  const uint32_t* kstart = bufs.kstart + (size_t)st * p.nseg * (kKeyParts + 1);
-  HqWin* w = bufs.win + s;
-  const uint32_t n = w->nlinks;
-  if (n == 0 || w->fail) return;
-  const uint32_t parts = ceil_div(n, kKeyPartLinks);
-  if (r >= parts) return;
-  const uint64_t b = p.base[s];
-  const uint32_t lo = kstart[(uint64_t)s * (kKeyParts + 1) + r], hi = kstart[(uint64_t)s * (kKeyParts + 1) + r + 1];
-  for (uint32_t i = threadIdx.x; i < kKeySlots; i += kHqThreads) {
-    t_key[i] = kKeyEmpty;
-    t_lnk[i] = 0;
-    t_pkt[i] = 0;
-  }
-  if (threadIdx.x == 0) s_fill = s_over = s_spec_l = s_spec_p = 0;
-  __syncthreads();
-  for (uint32_t u = lo + threadIdx.x; u < hi; u += kHqThreads) {
-    if (*(volatile uint32_t*)&s_over) break;
-    const uint32_t k = pkey[b + u];
-    const uint32_t c = pval[b + u];
-    if (k == kKeyEmpty) {
-      atomicAdd(&s_spec_l, 1u);
-      atomicAdd(&s_spec_p, c);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t v, r;
+  while (next_item(counter, items, 2 * p.nseg, &s_item, &v, &r)) {
+    const uint32_t st = v / p.nseg, s = v % p.nseg;
+    const uint32_t* pkey = bufs.pkey[st];
+    const uint32_t* pval = bufs.pval[st];
+    const uint32_t* kstart = bufs.kstart + (size_t)st * p.nseg * (kKeyParts + 1);
+    HqWin* w = bufs.win + s;
+    const uint64_t b = p.base[s];
+    const uint32_t lo = kstart[(uint64_t)s * (kKeyParts + 1) + r], hi = kstart[(uint64_t)s * (kKeyParts + 1) + r + 1];
+    for (uint32_t i = threadIdx.x; i < kKeySlots; i += kHqThreads) {
+      t_key[i] = kKeyEmpty;
+      t_lnk[i] = 0;
+      t_pkt[i] = 0;
+    }
+    if (threadIdx.x == 0) s_fill = s_over = s_spec_l = s_spec_p = 0;
+    __syncthreads();
+    for (uint32_t u = lo + threadIdx.x; u < hi; u += kHqThreads) {
+      if (*(volatile uint32_t*)&s_over) break;
+      const uint32_t k = pkey[b + u];
+      const uint32_t c = pval[b + u];
+      if (k == kKeyEmpty) {
+        atomicAdd(&s_spec_l, 1u);
+        atomicAdd(&s_spec_p, c);
+        continue;
+      }
+      uint32_t h = fmix32h(k) & (kKeySlots - 1);
+      for (uint32_t probe = 0; probe < kKeySlots; ++probe) {
+        uint32_t cur = *(volatile uint32_t*)&t_key[h];
+        if (cur == kKeyEmpty) {
+          cur = atomicCAS(&t_key[h], kKeyEmpty, k);
+          if (cur == kKeyEmpty) {
+            cur = k;
+            if (atomicAdd(&s_fill, 1u) + 1 > kKeyMaxFill) s_over = 1;
+          }
+        }
+        if (cur == k) {
+          atomicAdd(&t_lnk[h], 1u);
+          atomicAdd(&t_pkt[h], c);
+          break;
+        }
+        h = (h + 1) & (kKeySlots - 1);
+      }
+    }
+    __syncthreads();
+    if (s_over) {  // the window is sorted instead (uniform: s_over is shared)
+      if (threadIdx.x == 0) atomicOr(&w->fail, 1u);
       continue;
     }
-    uint32_t h = fmix32h(k) & (kKeySlots - 1);
-    for (uint32_t probe = 0; probe < kKeySlots; ++probe) {
-      uint32_t cur = *(volatile uint32_t*)&t_key[h];
-      if (cur == kKeyEmpty) {
-        cur = atomicCAS(&t_key[h], kKeyEmpty, k);
-        if (cur == kKeyEmpty) {
-          cur = k;
-          if (atomicAdd(&s_fill, 1u) + 1 > kKeyMaxFill) s_over = 1;
-        }
+    unsigned long long cnt = 0, ml = 0, mp = 0;
+    for (uint32_t i = threadIdx.x; i < kKeySlots; i += kHqThreads) {
+      if (t_key[i] != kKeyEmpty) {
+        ++cnt;
+        ml = t_lnk[i] > ml ? t_lnk[i] : ml;
+        mp = t_pkt[i] > mp ? t_pkt[i] : mp;
       }
-      if (cur == k) {
-        atomicAdd(&t_lnk[h], 1u);
-        atomicAdd(&t_pkt[h], c);
-        break;
+    }
+    cnt = warp_sum(cnt);
+    ml = warp_max(ml);
+    mp = warp_max(mp);
+    if (lane == 0) {
+      s_red[0][warp] = cnt;
+      s_red[1][warp] = ml;
+      s_red[2][warp] = mp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      cnt = ml = mp = 0;
+      for (int q = 0; q < kHqThreads / 32; ++q) {
+        cnt += s_red[0][q];
+        ml = s_red[1][q] > ml ? s_red[1][q] : ml;
+        mp = s_red[2][q] > mp ? s_red[2][q] : mp;
       }
-      h = (h + 1) & (kKeySlots - 1);
+      if (s_spec_l) {
+        ++cnt;
+        ml = s_spec_l > ml ? s_spec_l : ml;
+        mp = s_spec_p > mp ? s_spec_p : mp;
+      }
+      if (cnt) atomicAdd(&w->keys[st], cnt);
+      if (ml) atomicMax(&w->max_links[st], ml);
+      if (mp) atomicMax(&w->max_packets[st], mp);
     }
-  }
-  __syncthreads();
-  if (s_over) {
-    if (threadIdx.x == 0) atomicOr(&w->fail, 1u);
-    return;
-  }
-  unsigned long long cnt = 0, ml = 0, mp = 0;
-  for (uint32_t i = threadIdx.x; i < kKeySlots; i += kHqThreads) {
-    if (t_key[i] != kKeyEmpty) {
-      ++cnt;
-      ml = t_lnk[i] > ml ? t_lnk[i] : ml;
-      mp = t_pkt[i] > mp ? t_pkt[i] : mp;
-    }
-  }
-  cnt = warp_sum(cnt);
-  ml = warp_max(ml);
-  mp = warp_max(mp);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    s_red[0][warp] = cnt;
-    s_red[1][warp] = ml;
-    s_red[2][warp] = mp;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cnt = ml = mp = 0;
-    for (int v = 0; v < kHqThreads / 32; ++v) {
-      cnt += s_red[0][v];
-      ml = s_red[1][v] > ml ? s_red[1][v] : ml;
-      mp = s_red[2][v] > mp ? s_red[2][v] : mp;
-    }
-    if (s_spec_l) {
-      ++cnt;
-      ml = s_spec_l > ml ? s_spec_l : ml;
-      mp = s_spec_p > mp ? s_spec_p : mp;
-    }
-    if (cnt) atomicAdd(&w->keys[st], cnt);
-    if (ml) atomicMax(&w->max_links[st], ml);
-    if (mp) atomicMax(&w->max_packets[st], mp);
+    __syncthreads();  // the table is read no more
   }
 }
 
@@ -483,6 +555,19 @@ __global__ void k_hq_write(SegPlan p, const HqWin* __restrict__ win, ans_quantit
   }
 }
 
+// Persistent CTAs of the counting kernels: two per SM (96 KB of shared
+// memory and 1024 threads each).
+unsigned persistent_ctas() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 2 * 148;
+  if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 2 * 148;
+  }
+  return 2u * (unsigned)sms[dev];
+}
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes, unsigned long long* configured) {
   int dev = 0;
@@ -507,15 +592,19 @@ cudaError_t launch_hq_stage(int stage, const SegPlan& p, const uint32_t* src, co
       break;
     case 1:
       if ((e = set_smem(k_hq_links, kLinkSmem, &cfg_links)) != cudaSuccess) return e;
-      k_hq_links<<<p.nseg * kLinkParts, kHqThreads, kLinkSmem, st>>>(p, b.keys, b.lstart, b.lsrc, b.ldst, b.lcnt,
-                                                                   b.win);
+      k_hq_items<<<1, kHqThreads, 0, st>>>(p, b.win, 0, b.items, b.counter);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      k_hq_links<<<persistent_ctas(), kHqThreads, kLinkSmem, st>>>(p, b.keys, b.lstart, b.lsrc, b.ldst, b.lcnt, b.win,
+                                                                  b.items, b.counter);
       break;
     case 2:
       k_hq_keysplit<<<2 * p.nseg, kHqThreads, 0, st>>>(p, b);
       break;
     case 3:
       if ((e = set_smem(k_hq_keyhash, kKeySmem, &cfg_keys)) != cudaSuccess) return e;
-      k_hq_keyhash<<<2 * p.nseg * kKeyParts, kHqThreads, kKeySmem, st>>>(p, b);
+      k_hq_items<<<1, kHqThreads, 0, st>>>(p, b.win, 1, b.items, b.counter);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      k_hq_keyhash<<<persistent_ctas(), kHqThreads, kKeySmem, st>>>(p, b, b.items, b.counter);
       break;
     default: {
       const uint32_t g = (p.nseg + 255) / 256;

@@ -47,9 +47,9 @@ def job_rate(units_all_ranks: float, elapsed_max_s: float) -> float:
 #
 # Each rank holds the time sum of its own windows.  The global sum is owned
 # in row (source) partitions: a row's owner is a hash of its source address
-# mod the number of ranks, so every rank sends each link to the owner of its
-# row (one all-to-all of (src << 32 | dst, count) pairs), and each owner adds
-# the sorted pieces it receives.  Rows never straddle owners, so the owners'
+# mod the number of ranks, so every rank sends each of its rows to the owner
+# (the library splits the partial sum by owner; one all-to-all of the DCSR
+# pieces), and each owner adds the pieces it receives.  Rows never straddle owners, so the owners'
 # matrices together are exactly the global sum, row-partitioned.
 
 import numpy as _np
@@ -64,66 +64,49 @@ def row_owner(row_ids, world: int):
     return ((h * world) >> 32).astype(_np.int64)
 
 
-def partition_links(row_ids, row_ptr, col_ids, vals, world: int):
-    """Split a DCSR matrix's links by the owner of their row: a list over
-    ranks of (keys, values) with keys src << 32 | dst, each in DCSR order."""
-    row_ids = _np.asarray(row_ids, dtype=_np.uint64)
-    row_ptr = _np.asarray(row_ptr, dtype=_np.int64)
-    counts = _np.diff(row_ptr)
-    src = _np.repeat(row_ids, counts)
-    keys = (src << _np.uint64(32)) | _np.asarray(col_ids, dtype=_np.uint64)
-    own = _np.repeat(row_owner(row_ids, world), counts)
-    vals = _np.asarray(vals, dtype=_np.uint64)
-    return [(keys[own == r], vals[own == r]) for r in range(world)]
-
-
-def exchange_links(parts, dist, device: str = "cpu"):
-    """All-to-all of the link pieces: parts[r] goes to rank r; returns the
-    pieces this rank received, one per sender, in rank order.  The buffers
-    live on `device` ("cpu" for gloo, the rank's GPU for NCCL)."""
+def exchange_pieces(pieces, dist, device: str = "cpu"):
+    """All-to-all of DCSR pieces: pieces[r] = (row_ids, row_ptr, col_ids,
+    vals) numpy arrays for rank r; returns the pieces this rank received, one
+    per sender, in rank order.  The buffers live on `device` ("cpu" for
+    gloo, the rank's GPU for NCCL)."""
     import torch
     world = dist.get_world_size()
-    send_n = torch.tensor([len(k) for k, _ in parts], dtype=torch.int64, device=device)
-    recv_n = torch.empty(world, dtype=torch.int64, device=device)
-    dist.all_to_all_single(recv_n, send_n)
-    send_k = torch.from_numpy(_np.concatenate([k for k, _ in parts]).view(_np.int64)).to(device)
-    send_v = torch.from_numpy(_np.concatenate([v for _, v in parts]).view(_np.int64)).to(device)
-    sizes_out, sizes_in = send_n.tolist(), recv_n.tolist()
-    total = int(sum(sizes_in))
-    recv_k = torch.empty(total, dtype=torch.int64, device=device)
-    recv_v = torch.empty(total, dtype=torch.int64, device=device)
-    dist.all_to_all_single(recv_k, send_k, output_split_sizes=sizes_in, input_split_sizes=sizes_out)
-    dist.all_to_all_single(recv_v, send_v, output_split_sizes=sizes_in, input_split_sizes=sizes_out)
-    keys = recv_k.cpu().numpy().view(_np.uint64)
-    vals = recv_v.cpu().numpy().view(_np.uint64)
-    out, o = [], 0
-    for n in sizes_in:
-        out.append((keys[o:o + n], vals[o:o + n]))
-        o += n
-    return out
-
-
-def keys_to_dcsr(keys, vals):
-    """DCSR arrays of sorted, distinct link keys with their counts."""
-    keys = _np.asarray(keys, dtype=_np.uint64)
-    src = (keys >> _np.uint64(32)).astype(_np.uint32)
-    col = (keys & _np.uint64(0xFFFFFFFF)).astype(_np.uint32)
-    if len(keys) == 0:
-        return _np.zeros(0, _np.uint32), _np.zeros(1, _np.uint64), col, _np.asarray(vals, _np.uint64)
-    starts = _np.concatenate([[0], _np.nonzero(src[1:] != src[:-1])[0] + 1])
-    row_ptr = _np.concatenate([starts, [len(keys)]]).astype(_np.uint64)
-    return src[starts], row_ptr, col, _np.asarray(vals, _np.uint64)
+    out = [[None] * 4 for _ in range(world)]
+    for a in range(4):
+        send = [_np.ascontiguousarray(p[a]) for p in pieces]
+        item = send[0].dtype
+        as_i = _np.int32 if item.itemsize == 4 else _np.int64
+        send_n = torch.tensor([len(x) for x in send], dtype=torch.int64, device=device)
+        recv_n = torch.empty(world, dtype=torch.int64, device=device)
+        dist.all_to_all_single(recv_n, send_n)
+        sizes_out, sizes_in = send_n.tolist(), recv_n.tolist()
+        buf = torch.from_numpy(_np.concatenate(send).view(as_i)).to(device)
+        recv = torch.empty(int(sum(sizes_in)), dtype=buf.dtype, device=device)
+        dist.all_to_all_single(recv, buf, output_split_sizes=sizes_in, input_split_sizes=sizes_out)
+        got = recv.cpu().numpy().view(item)
+        o = 0
+        for r, n in enumerate(sizes_in):
+            out[r][a] = got[o:o + n]
+            o += n
+    return [tuple(x) for x in out]
 
 
 def exchange_time_sum(ctx, partial, dist, device: str = "cpu"):
     """This rank's partition of the time sum over every rank's windows, from
-    its own partial sum `partial` (an ans.Matrix): the links go to their
-    rows' owners, and the pieces received are imported and added on this
-    rank's device.  Returns an ans.Matrix holding the rows this rank owns.
-    `device`: where the exchange buffers live (see exchange_links)."""
+    its own partial sum `partial` (an ans.Matrix): the library splits the
+    partial sum's rows by owner (ans_matrix_split_rows), each piece goes to
+    its owner (host-staged all-to-all of the DCSR arrays), and the pieces
+    received are imported and added on this rank's device.  Returns an
+    ans.Matrix holding exactly the rows this rank owns."""
     world = dist.get_world_size()
-    pieces = exchange_links(partition_links(*partial.to_numpy(), world), dist, device)
-    mats = [ctx.import_matrix(*keys_to_dcsr(k, v)) for k, v in pieces]
+    parts = ctx.split_rows(partial, world)
+    try:
+        pieces = [p.to_numpy() for p in parts]
+    finally:
+        for p in parts:
+            p.free()
+    received = exchange_pieces(pieces, dist, device)
+    mats = [ctx.import_matrix(*piece) for piece in received]
     try:
         return ctx.sum_windows(mats)
     finally:

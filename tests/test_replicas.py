@@ -64,6 +64,17 @@ def test_single_process_helpers():
     assert replicas.first_window(0, 64) == 0 and replicas.first_window(3, 64) == 192
 
 
+def _owned_rows(m, world, r):
+    """Rows of DCSR m whose owner is rank r (the test's own row split)."""
+    import oracle
+    from paper_2510_14050_gb300 import replicas
+    own = replicas.row_owner(m.row_ids, world) == r
+    counts = np.diff(m.row_ptr.astype(np.int64))
+    keep = np.repeat(own, counts)
+    rp = np.concatenate([[0], np.cumsum(counts[own])]).astype(np.uint64)
+    return oracle.DCSR(m.row_ids[own], rp, m.col_ids[keep], m.vals[keep])
+
+
 def _exchange_main(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -72,9 +83,9 @@ def _exchange_main(rank, world, port, out):
         from paper_2510_14050_gb300 import replicas, synth
         w = synth.generate(5, nwin=3, first_window=replicas.first_window(rank, 3))
         partial = oracle.sum_matrices([oracle.traffic_matrix(*w.window(i)) for i in range(w.nwin)])
-        parts = replicas.partition_links(*partial, world)
-        pieces = replicas.exchange_links(parts, dist)
-        owned = oracle.sum_matrices([oracle.DCSR(*replicas.keys_to_dcsr(k, v)) for k, v in pieces])
+        pieces = [tuple(_owned_rows(partial, world, r)) for r in range(world)]
+        received = replicas.exchange_pieces(pieces, dist)
+        owned = oracle.sum_matrices([oracle.DCSR(*p) for p in received])
         out[rank] = tuple(a.tolist() for a in owned)
     finally:
         dist.destroy_process_group()
@@ -82,9 +93,9 @@ def _exchange_main(rank, world, port, out):
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_gloo_ranks_exchange_their_time_sums(world):
-    """The one exchange step of a multi-rank time sum: links go to the owner
-    of their row; the owners' matrices are the row partition of the global
-    sum (checked against the oracle's sum of every rank's windows)."""
+    """The one exchange step of a multi-rank time sum: rows go to their
+    owners as DCSR pieces; the owners' matrices are the row partition of the
+    global sum (checked against the oracle's sum of every rank's windows)."""
     import oracle
     from paper_2510_14050_gb300 import replicas, synth
     port = _free_port()
@@ -97,15 +108,8 @@ def test_gloo_ranks_exchange_their_time_sums(world):
         w = synth.generate(5, nwin=3, first_window=replicas.first_window(r, 3))
         mats += [oracle.traffic_matrix(*w.window(i)) for i in range(w.nwin)]
     exp = oracle.sum_matrices(mats)
-    own = replicas.row_owner(exp.row_ids, world)
     for r in range(world):
-        rows, rp, cols, vals = res[r]
-        assert np.all(replicas.row_owner(rows, world) == r)
-        assert np.array_equal(rows, exp.row_ids[own == r])
-    # the union of the partitions is the global sum
-    keys = np.concatenate([replicas.partition_links(*[np.asarray(a) for a in res[r]], 1)[0][0] for r in range(world)])
-    vals = np.concatenate([res[r][3] for r in range(world)])
-    order = np.argsort(keys, kind="stable")
-    got = oracle.DCSR(*replicas.keys_to_dcsr(keys[order], vals[order]))
-    for x, y in zip(got, exp):
-        assert np.array_equal(np.asarray(x, dtype=np.uint64), np.asarray(y, dtype=np.uint64))
+        want = _owned_rows(exp, world, r)
+        for a, b in zip(res[r], want):
+            assert np.array_equal(np.asarray(a, dtype=np.uint64), np.asarray(b, dtype=np.uint64))
+    assert sum(len(res[r][0]) for r in range(world)) == exp.nrows
