@@ -655,14 +655,17 @@ def main(argv=None):
     if args.stream_batches > 0:
         from paper_2510_14050_gb300 import stream
         bp = int(-(-total // args.stream_batches))
-        stream.stream_windows(src_h, dst_h, w.offsets, batch_packets=bp).sum.free()  # warm-up
-        res = stream.stream_windows(src_h, dst_h, w.offsets, batch_packets=bp)
+        stream.stream_windows(src_h, dst_h, w.offsets, batch_packets=bp, tuning=tuning).sum.free()  # warm-up
+        res = stream.stream_windows(src_h, dst_h, w.offsets, batch_packets=bp, tuning=tuning)
         res.sum.free()
         s_max = max_over_ranks(res.seconds)
         out_of_core = {"value": replicas.job_rate(job_total, s_max), "unit": UNIT, "batches": res.batches,
                        "batch_packets": bp, "seconds": s_max,
+                       "over_in_core_e2e": (replicas.job_rate(job_total, s_max) / e2e["value"]) if e2e else None,
+                       "timeline_ms": res.timeline,
                        "what": "windows streamed from pinned host memory, two batches in flight "
-                               "(H2D of one overlapped with the analysis of the other); time sum folded on the device"}
+                               "(H2D of one overlapped with the analysis of the other); time sum folded on the "
+                               "device; timeline = per batch (slot, H2D start, H2D end, analysis end) in ms"}
 
     if rank == 0:
         line = {

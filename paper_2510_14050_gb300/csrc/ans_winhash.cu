@@ -305,8 +305,7 @@ __global__ void __launch_bounds__(kHqThreads, 2) k_hq_links(SegPlan p, const uin
       continue;    // (uniform: s_over is shared)
     }
     // distinct links of this partition: count, largest count, then append
-    // them in rounds of one slot per thread, so that a warp's lanes write
-    // consecutive places (the round's occupied slots compacted by ballot)
+    // (each thread its own slots' links, at its exclusive offset in the CTA)
     unsigned long long nl = 0, mx = 0;
     for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
       if (t_key[i] != kLinkEmpty) {
@@ -314,6 +313,14 @@ __global__ void __launch_bounds__(kHqThreads, 2) k_hq_links(SegPlan p, const uin
         mx = t_cnt[i] > mx ? t_cnt[i] : mx;
       }
     }
+    const uint32_t mine = (uint32_t)nl;
+    uint32_t x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wcnt[warp] = x;
     unsigned long long tot = nl, m2 = mx;
     block_sum_max(tot, m2, s_red);
     if (threadIdx.x == 0) {
@@ -326,28 +333,18 @@ __global__ void __launch_bounds__(kHqThreads, 2) k_hq_links(SegPlan p, const uin
       s_fill = (uint32_t)tot;  // (the table is done: reuse the word for the total)
     }
     __syncthreads();
+    uint32_t woff = 0;
+    for (int v = 0; v < warp; ++v) woff += s_wcnt[v];
+    uint32_t o = s_off + woff + x - mine;
     const uint64_t b = p.base[s];
-    uint32_t round_off = s_off;
-    for (uint32_t i0 = 0; i0 < kLinkSlots; i0 += kHqThreads) {
-      const uint64_t k = t_key[i0 + threadIdx.x];
-      const bool occ = k != kLinkEmpty;
-      const uint32_t bal = __ballot_sync(0xffffffffu, occ);
-      if (lane == 0) s_wcnt[warp] = __popc(bal);
-      __syncthreads();
-      uint32_t woff = 0, rtot = 0;
-      for (int v = 0; v < kHqThreads / 32; ++v) {
-        const uint32_t c = s_wcnt[v];
-        woff += v < warp ? c : 0u;
-        rtot += c;
-      }
-      if (occ) {
-        const uint32_t o = round_off + woff + __popc(bal & lanemask_lt());
+    for (uint32_t i = threadIdx.x; i < kLinkSlots; i += kHqThreads) {
+      const uint64_t k = t_key[i];
+      if (k != kLinkEmpty) {
         lsrc[b + o] = (uint32_t)(k >> 32);
         ldst[b + o] = (uint32_t)k;
-        lcnt[b + o] = t_cnt[i0 + threadIdx.x];
+        lcnt[b + o] = t_cnt[i];
+        ++o;
       }
-      round_off += rtot;
-      __syncthreads();  // s_wcnt is rewritten by the next round
     }
     if (threadIdx.x == 0 && s_spec) {  // the all-ones link, counted apart, goes last
       const uint32_t last = s_off + s_fill - 1;

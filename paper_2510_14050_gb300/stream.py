@@ -44,15 +44,21 @@ class StreamResult:
     sum: "ans.Matrix | None"  # the time sum of every window (device-resident), or None
     batches: int
     seconds: float
+    # per batch (slot, H2D start, H2D end, analysis end) in ms from the first
+    # batch's H2D start, from CUDA events on the slots' streams
+    timeline: list | None = None
 
 
 def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
-                   want_sum: bool = True, device: int = 0, budget_bytes: int = 0) -> StreamResult:
+                   want_sum: bool = True, device: int = 0, budget_bytes: int = 0,
+                   tuning: dict | None = None) -> StreamResult:
     """Analyse every window [offsets[w], offsets[w+1]) of the host arrays
     src/dst in batches of at most batch_packets packets, two batches in
     flight.  src/dst: uint32 numpy arrays (staged through pinned buffers) or
-    pinned int32 CPU tensors (copied to the device directly).  Returns the
-    quantities of every window and, with want_sum, their time sum."""
+    pinned int32 CPU tensors (copied to the device directly).  ``tuning``:
+    launch shapes and paths for both slots' contexts (ans_set_tuning fields).
+    Returns the quantities of every window and, with want_sum, their time
+    sum, with a per-batch timeline of the copies and the analysis."""
     import time
 
     import torch
@@ -80,6 +86,9 @@ def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
             "h_q": torch.empty((cap_w, 9), dtype=torch.int64).pin_memory(),
             "done": None, "pending": None,
         })
+        if tuning:
+            slots[-1]["ctx"].set_tuning(**tuning)
+    marks = []  # per batch: (slot, H2D start, H2D end, analysis end) events
     quant = np.zeros((nwin, 9), dtype=np.uint64)
     # Partial time sums as a binary counter: (level, matrix), levels strictly
     # decreasing; two partials of one level merge into the next level, so
@@ -119,16 +128,21 @@ def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
                 slot["h_src"][:n].numpy().view(np.uint32)[:] = src[p0:p1]
                 slot["h_dst"][:n].numpy().view(np.uint32)[:] = dst[p0:p1]
                 h_src, h_dst = slot["h_src"][:n], slot["h_dst"][:n]
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             with torch.cuda.stream(st):
+                e0.record(st)
                 slot["src"][:n].copy_(h_src, non_blocking=True)
                 slot["dst"][:n].copy_(h_dst, non_blocking=True)
+                e1.record(st)
             flags = ans.BATCH_SUM if want_sum else 0
             _, bsum, _ = slot["ctx"].batch_submit(slot["src"], slot["dst"], offsets[w0:w1 + 1] - offsets[w0], flags,
                                                   out=slot["q"], stream=st, want_ticket=False)
             with torch.cuda.stream(st):
                 slot["h_q"][: w1 - w0].copy_(slot["q"][: w1 - w0], non_blocking=True)
+                e2.record(st)
                 ev = torch.cuda.Event()
                 ev.record(st)
+            marks.append((i % 2, e0, e1, e2))
             slot["done"] = ev
             slot["pending"] = ((w0, w1), bsum)
         for i in range(len(plan), len(plan) + 2):
@@ -143,7 +157,12 @@ def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
         for m in retired:
             m.free()
         seconds = time.perf_counter() - t0
-        return StreamResult(quant, total_sum, len(plan), seconds)
+        timeline = None
+        if marks:
+            first = marks[0][1]
+            timeline = [(sl, round(first.elapsed_time(a), 3), round(first.elapsed_time(b), 3),
+                         round(first.elapsed_time(c), 3)) for sl, a, b, c in marks]
+        return StreamResult(quant, total_sum, len(plan), seconds, timeline)
     finally:
         for s in slots:
             s["ctx"].close()

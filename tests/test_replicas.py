@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, out):
 def test_two_gloo_ranks_take_disjoint_windows_and_agree_on_time():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork after CUDA is initialised
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -99,7 +99,7 @@ def test_gloo_ranks_exchange_their_time_sums(world):
     import oracle
     from paper_2510_14050_gb300 import replicas, synth
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork after CUDA is initialised
         out = mgr.dict()
         mp.spawn(_exchange_main, args=(world, port, out), nprocs=world, join=True)
         res = {r: tuple(np.asarray(a) for a in out[r]) for r in range(world)}
