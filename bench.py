@@ -250,6 +250,13 @@ def kernel_bytes_per_step(name, sizes, quants, sum_q, tuning, with_matrices):
         "merge": rounds * 32 * u,                      # each round: read both runs, write the merge
         "onesweep_sum": 8 * 32 * u,                    # 8 passes over (key, count)
         "scan_u64": 16 * us,
+        "pack_hist_sum": 16 * p_all,                   # the time sum's packets: read pairs, write keys
+        "onesweep_pk": 8 * 16 * p_all,                 # 8 passes over the batch's packets as one segment
+        "colhash_part": 24 * u,                        # regroup (read twice, write) + count (read) per link
+        "hq_split": 24 * p_all,                        # regroup packets: read twice, write once
+        "hq_links": 8 * p_all + 12 * u,                # read packets, append distinct links
+        "hq_keysplit": 2 * 3 * 8 * u,                  # two stages: read links twice, write once
+        "hq_keyhash": 2 * 8 * u,                       # two stages: read links
     }
     return rules.get(name)
 
@@ -505,11 +512,13 @@ def main(argv=None):
             if after is not None:
                 after()
             b.record(stream)
-            if prev is not None:
+            if prev is not None:  # the previous step: wait for its end (this step is queued behind it)
+                prev[2].synchronize()
                 release(prev[0])
                 ms.append(prev[1].elapsed_time(prev[2]))
             prev = (r, a, b)
         barrier()
+        prev[2].synchronize()
         release(prev[0])
         ms.append(prev[1].elapsed_time(prev[2]))
         prof = ctx.profile_read() if per_kernel else {}

@@ -308,8 +308,8 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * own time sum, windows stored back to back) every packet of the batch
  * sorted again as one segment by the key_* passes and reduced like a window
  * -- the sum of Table I's A_t is the matrix of the concatenated packets;
- * sums of given matrices, and batches of windows in their own arrays, then
- * take the kv_* passes.  agg_path: how
+ * batches of windows in their own arrays then take the kv_* passes, and sums
+ * of k given matrices merge them (k <= 256) or take the kv_* passes.  agg_path: how
  * a window's equal packets are grouped, 0 = sorting every packet's link key,
  * 1 = counting links in a per-window hash table (2^k >= 2 x packets slots of
  * 12 bytes, kept by the context between calls) and sorting only the distinct

@@ -819,7 +819,10 @@ int sum_order(ans_ctx* c, char* m, const PipeScratch& ps, const MatDesc* d_mats,
   // gather zeroes the tickets and, for the radix path, builds the sum
   // segment's histograms and zeroes the sort's first status words (the
   // gather plan has at least as many tiles as the sum plan)
-  const bool merge = c->sum_path == 0;
+  // sum_path 2 re-sorts a batch's packets; sums of given matrices then merge
+  // their sorted links when there are few of them (ceil(log2 k) <= 8 rounds,
+  // against the 8 kv passes) and take the kv passes otherwise
+  const bool merge = c->sum_path == 0 || (c->sum_path == 2 && k <= 256);
   const uint64_t* cat_off = at<uint64_t>(m, off_catoff);
   const bool in_place = merge && run_base;
   if (in_place) {
