@@ -90,10 +90,12 @@ def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
             slots[-1]["ctx"].set_tuning(**tuning)
     marks = []  # per batch: (slot, H2D start, H2D end, analysis end) events
     quant = np.zeros((nwin, 9), dtype=np.uint64)
-    # Partial time sums as a binary counter: (level, matrix), levels strictly
-    # decreasing; two partials of one level merge into the next level, so
-    # each link is re-merged O(log batches) times.
-    partials: list[tuple[int, "ans.Matrix"]] = []
+    # Batch sums wait in a list and are folded kFold at a time into one
+    # (one time-sum call: merge rounds over their sorted links and one column
+    # pass), and the rest at the end; a link is re-merged O(log_kFold batches)
+    # times and at most kFold + 1 partial sums are held.
+    kFold = 8
+    partials: list["ans.Matrix"] = []
     retired: list["ans.Matrix"] = []  # merged inputs, freed once later work has passed them
     t0 = time.perf_counter()
 
@@ -108,11 +110,11 @@ def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
         retired.clear()
         quant[w0:w1] = slot["h_q"][: w1 - w0].numpy().view(np.uint64)
         if bsum is not None:
-            partials.append((0, bsum))
-            while len(partials) >= 2 and partials[-1][0] == partials[-2][0]:
-                (lv, b), (_, a) = partials.pop(), partials.pop()
-                partials.append((lv + 1, slot["ctx"].sum_windows([a, b], stream=slot["stream"])))
-                retired.extend((a, b))
+            partials.append(bsum)
+            if len(partials) > kFold:
+                folded = slot["ctx"].sum_windows(partials, stream=slot["stream"])
+                retired.extend(partials)
+                partials[:] = [folded]
         slot["pending"] = None
 
     try:
@@ -149,7 +151,7 @@ def stream_windows(src, dst, offsets, batch_packets: int = 1 << 24,
             finish(slots[i % 2])
         total_sum = None
         if partials:
-            mats = [m for _, m in partials]
+            mats = list(partials)
             total_sum = mats[0] if len(mats) == 1 else slots[0]["ctx"].sum_windows(mats, stream=slots[0]["stream"])
             if len(mats) > 1:
                 retired.extend(mats)
