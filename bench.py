@@ -234,6 +234,8 @@ def kernel_bytes_per_step(name, sizes, quants, sum_q, tuning, with_matrices):
     us = sum_q["unique_links"] if sum_q else 0
     rs = sum_q["unique_sources"] if sum_q else 0
     rounds = max(1, (len(sizes) - 1).bit_length()) if len(sizes) > 1 else 0
+    # the windows' order from the packet sort: the packets carry 16-bit window ids
+    regroup = bool(tuning) and tuning.get("agg_path") == 3 and sum_q is not None and 2 <= len(sizes) <= 1 << 16
     rules = {
         "pack_hist": 16 * p_os,                        # read pairs, write keys
         "onesweep": 8 * 16 * p_os,                     # 8 passes: read + write a key
@@ -251,7 +253,9 @@ def kernel_bytes_per_step(name, sizes, quants, sum_q, tuning, with_matrices):
         "onesweep_sum": 8 * 32 * u,                    # 8 passes over (key, count)
         "scan_u64": 16 * us,
         "pack_hist_sum": 16 * p_all,                   # the time sum's packets: read pairs, write keys
-        "onesweep_pk": 8 * 16 * p_all,                 # 8 passes over the batch's packets as one segment
+        "onesweep_pk": 8 * (20 if regroup else 16) * p_all,  # 8 passes over the batch's packets (+ window ids)
+        "wid_fill": 2 * p_all,                         # a window id per packet
+        "regroup": 20 * p_all + 18 * p_all,            # (id, key) in and out; then (id, key) in, key out
         "colhash_part": 24 * u,                        # regroup (read twice, write) + count (read) per link
         "hq_split": 24 * p_all,                        # regroup packets: read twice, write once
         "hq_links": 8 * p_all + 12 * u,                # read packets, append distinct links

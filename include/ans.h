@@ -320,7 +320,15 @@ int ans_batch_bytes(ans_ctx* ctx, const uint64_t* h_offsets, size_t nwin, uint32
  * partitions of ~4096, one table of 8192 links per partition, then its
  * distinct links grouped by source and by destination, one table of 16384
  * keys per partition -- with no sort; a window whose table overflows, or of
- * more than 2^18 packets, is sorted instead (other batches sort as agg_path 0).  Setting agg_path 0 waits for the device and releases the tables.  graph: 1 = a batch's launch sequence is recorded into a CUDA
+ * more than 2^18 packets, is sorted instead (other batches sort as agg_path 0);
+ * 3 = for batches with a time sum, 2 to 2^16 windows and the packets in one
+ * stream: no window sort -- the time sum always comes from the batch's
+ * packets sorted as one segment (sum_path 2's sort), each packet carrying
+ * its 16-bit window id through the key_* passes, and a stable sort of the
+ * sorted packets by window id (two digit passes, the second writing each
+ * window at its padded base) leaves every window's packets in key order,
+ * as the window sort would (other batches sort as agg_path 0).  Setting
+ * agg_path 0 waits for the device and releases the tables.  graph: 1 = a batch's launch sequence is recorded into a CUDA
  * graph and replayed through a cached executable graph of the same shape
  * (updated in place with the call's pointers), 0 = launched directly; per-
  * kernel profiling always launches directly.  col_hash: 1 = each window's
@@ -361,7 +369,8 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
  * faster that way than by the best key passes plus their histogram sweep, and
  * finally picks sum_path, merge_tile (with merge rounds), then agg_path (2
  * only without ANS_BATCH_MATRICES in `flags`, together with sum_path 2 when
- * the batch has a time sum) by the batch's device time as submitted with
+ * the batch has a time sum; 3 only with ANS_BATCH_SUM and 2 to 2^16
+ * windows, together with sum_path 2) by the batch's device time as submitted with
  * `flags` (ANS_BATCH_* bits of the batches the context will run; one CUDA
  * graph with its concurrent branches, between CUDA events on `stream`, the
  * host's planning included).  An optional path whose trial cannot get its

@@ -917,14 +917,28 @@ int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s,
   return column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st, narrow);
 }
 
+// The windows of a batch whose sorted keys come from its packet sort
+// (agg_path 3): their plan, the packets' window ids (two buffers of one id
+// per packet: the second is the column keys' buffer, free until the sum's
+// column pass) and each window's offset from the batch sorted by window to
+// its padded base.
+struct Regroup {
+  SegPlan win;
+  uint16_t* wid = nullptr;
+  uint16_t* wid_b = nullptr;
+  uint64_t* shift = nullptr;
+};
+
 // Time sum of a batch from its packets (sum_path 2): every packet of the
 // batch, as the one segment of `pk`, is packed and sorted again, and the
 // sorted keys are reduced like a window (counts = run lengths) into `blk`,
 // with the sum's row and column statistics.  Runs after the window
-// statistics, whose key buffers, status words and tickets it reuses.  Only
-// queues work on `st`.
+// statistics, whose key buffers, status words and tickets it reuses -- or,
+// with `rg`, before them: the packets then carry their window ids through
+// the sort, which leaves the sorted keys in keys_a and their ids in
+// rg->wid for regroup_windows.  Only queues work on `st`.
 int sum_packets(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& pk, const uint32_t* d_src,
-                const uint32_t* d_dst, Block* blk, cudaStream_t st, bool narrow) {
+                const uint32_t* d_dst, Block* blk, cudaStream_t st, bool narrow, const Regroup* rg = nullptr) {
   uint64_t* ka = at<uint64_t>(m, ps.keys_a);
   uint64_t* kb = at<uint64_t>(m, ps.keys_b);
   uint32_t* seg_hist = at<uint32_t>(m, ps.seg_hist);
@@ -934,18 +948,36 @@ int sum_packets(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& pk, c
     return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
   int rc;
-  if ((rc = cu(launch_zero(seg_hist, kPasses * kRadix * 4, st), "memset")) ||
+  // with window ids, their two digit histograms follow the packets' eight
+  if ((rc = cu(launch_zero(seg_hist, (rg ? kPasses + 2 : kPasses) * kRadix * 4, st), "memset")) ||
       (rc = cu(launch_zero(m + ps.lb, (size_t)pk.ntiles * 8, st), "memset")) ||
       (rc = cu(launch_zero(m + ps.col_hist, kColPasses * kRadix * 4, st), "memset")) ||
       (rc = cu(launch_zero(blk->q, sizeof(ans_quantities), st), "memset")))
     return rc;
+  if (rg && (rc = cu(timed(c, "wid_fill", st, [&] {
+                       return launch_wid_fill(rg->win, pk.in_off, rg->wid, rg->shift, seg_hist + kPasses * kRadix, st);
+                     }), "window ids")))
+    return rc;
+  // (the kv passes with window ids run two sub-tiles per tile)
   if ((rc = cu(timed(c, "pack_hist_sum", st, [&] {
                  return launch_pack_hist(pk, d_src, d_dst, ka, seg_hist, at<uint64_t>(m, ps.st0), tickets, st,
-                                         key_subtiles(c->cfg_keys));
+                                         rg ? 2u : key_subtiles(c->cfg_keys));
                }), "pack")))
     return rc;
-  ANS_TRY(sort_segments(c, pk, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0), at<uint64_t>(m, ps.st1),
-                        tickets, st, "onesweep_pk"));
+  if (rg) {
+    uint64_t* st0 = at<uint64_t>(m, ps.st0);
+    uint64_t* st1 = at<uint64_t>(m, ps.st1);
+    for (int pass = 0; pass < kPasses; ++pass) {
+      const bool even = (pass % 2) == 0;
+      KTime kt(c, "onesweep_pk", st);
+      ANS_CUDA(launch_onesweep_wid(pk, pass, even ? ka : kb, even ? kb : ka, even ? rg->wid : rg->wid_b,
+                                   even ? rg->wid_b : rg->wid, seg_hist, even ? st0 : st1, even ? st1 : st0,
+                                   tickets + pass, c->d_err, c->cfg_keys, st));
+    }
+  } else {
+    ANS_TRY(sort_segments(c, pk, ka, kb, nullptr, nullptr, seg_hist, at<uint64_t>(m, ps.st0),
+                          at<uint64_t>(m, ps.st1), tickets, st, "onesweep_pk"));
+  }
   StatsArgs a;
   a.plan = pk;
   a.hdr = blk->hdr;
@@ -969,6 +1001,39 @@ int sum_packets(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& pk, c
   if ((rc = cu(timed(c, "rle", st, [&] { return launch_rle(a, st); }), "rle"))) return rc;
   if ((rc = cu(timed(c, "finish", st, [&] { return launch_finish(a, st); }), "finish"))) return rc;
   return column_pass(c, pk, a.ulen, blk->col_ids, blk->vals, ps, m, a.col_tickets, blk->q, st, narrow);
+}
+
+// The windows' sorted keys from the batch's packet sort (agg_path 3, after
+// sum_packets with `rg`): the sorted packets are sorted again by window id
+// in two stable digit passes (keys_a -> keys_b -> keys_a), the second of
+// which moves each window's packets to its padded base.  Within a window
+// the packets keep the key order of the packet sort, so keys_a ends as the
+// window sort would leave it.  The scratch words the sum's reduction used
+// (status words, tickets, look-back and column histograms) are cleared
+// again for the window statistics.  Only queues work on `st`.
+int regroup_windows(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& pk, const Regroup& rg,
+                    uint64_t win_tiles, cudaStream_t st) {
+  uint64_t* ka = at<uint64_t>(m, ps.keys_a);
+  uint64_t* kb = at<uint64_t>(m, ps.keys_b);
+  uint64_t* st0 = at<uint64_t>(m, ps.st0);
+  uint64_t* st1 = at<uint64_t>(m, ps.st1);
+  uint32_t* tickets = at<uint32_t>(m, ps.tickets);
+  const uint32_t* hist = at<uint32_t>(m, ps.seg_hist) + kPasses * kRadix;
+  ANS_CUDA(launch_zero(st0, (size_t)pk.ntiles * 2 * kRadix * 8, st));
+  ANS_CUDA(launch_zero(tickets, 32 * 4, st));  // these passes' and the window statistics
+  ANS_CUDA(launch_zero(m + ps.lb, (size_t)win_tiles * 8, st));
+  ANS_CUDA(launch_zero(m + ps.col_hist, (size_t)rg.win.nseg * kColPasses * kRadix * 4, st));
+  {
+    KTime kt(c, "regroup", st);
+    ANS_CUDA(launch_onesweep_regroup(pk, 0 | kPassStable, rg.wid, rg.wid_b, ka, kb, hist, st0, st1, tickets,
+                                     c->d_err, c->cfg_keys, nullptr, 0, st));
+  }
+  {
+    KTime kt(c, "regroup", st);
+    ANS_CUDA(launch_onesweep_regroup(pk, 1, rg.wid_b, nullptr, kb, ka, hist, st1, st0, tickets + 1, c->d_err,
+                                     c->cfg_keys, rg.shift, rg.win.nseg, st));
+  }
+  return ANS_OK;
 }
 
 // Snapshot the device error word into `dst` (device); reset_err clears it.
@@ -1075,6 +1140,14 @@ void plan_tables(const std::vector<uint64_t>& lens, std::vector<uint32_t>* lg, H
   tab->build(slots, nullptr);
 }
 
+// agg_path 3: the windows' sorted keys come from the batch's one packet sort
+// (which then also gives the time sum), for batches with a time sum, two or
+// more windows (at most 2^16: the ids travel as 16-bit values) and the
+// packets in one stream.
+bool regroup_windows_ok(const ans_ctx* c, uint32_t nseg, bool want_sum, bool addrs) {
+  return c->agg_path == 3 && want_sum && nseg >= 2 && nseg <= kMaxRegroupWindows && !addrs;
+}
+
 // Scratch layout of one batch (shared by run_windows and ans_batch_bytes).
 struct WinLayout {
   DevPlan dp, dp_big;  // every window; the windows sorted by onesweep passes
@@ -1085,12 +1158,14 @@ struct WinLayout {
   size_t off_hqwin = 0, off_lstart = 0, off_kstart = 0, off_sortlen = 0, off_items = 0;  // hashed window statistics
   DevPlan dp_tab;        // hash path: the windows' tables as segments
   DevPlan dp_pk;         // sum_path 2: all packets of the batch as one segment
+  size_t off_wid = 0, off_wshift = 0;  // agg_path 3: packets' window ids, windows' offsets to their bases
   size_t off_tlg = 0, off_special = 0, off_hulen = 0, off_nclaim = 0, off_claims = 0;
   PipeScratch ps;
   size_t s_col = 0, s_vals = 0, s_row = 0, s_rp = 0, s_hdr = 0, s_q = 0;
   size_t off_mats = 0, off_gplan = 0, off_splan = 0, off_catoff = 0, off_lens = 0, off_total = 0;
   size_t size = 0;
-  void reserve(const HostPlan& hp, uint32_t nseg, bool want_mats, bool want_sum, bool hash = false) {
+  void reserve(const HostPlan& hp, uint32_t nseg, bool want_mats, bool want_sum, bool hash = false,
+               bool regroup = false) {
     Layout L;
     const bool addrs = !hp.src_at.empty();
     dp.reserve(L, nseg, addrs);
@@ -1105,6 +1180,10 @@ struct WinLayout {
     off_sortlen = L.add((size_t)nseg * 8);
     off_items = L.add(((size_t)2 * nseg + 2) * 4);
     dp_pk.reserve(L, 1);
+    if (regroup) {
+      off_wid = L.add(hp.pad * 2);
+      off_wshift = L.add((size_t)nseg * 8);
+    }
     if (hash) {
       dp_tab.reserve(L, nseg);
       off_tlg = L.add((size_t)nseg * 4);
@@ -1190,7 +1269,9 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   const SortCfg cfg_win = c->cfg_win;
   // (hashed window statistics, agg_path 2, sort only the windows the hash
   // gives up on: those take the key passes)
-  const bool on_chip = !dev && win_path == 0 && !(c->agg_path == 2 && !want_mats) &&
+  // (the windows of the packet sort, agg_path 3, take no window sort at all)
+  const bool regroup = regroup_windows_ok(c, nseg, want_sum, h_srcs != nullptr);
+  const bool on_chip = !dev && win_path == 0 && !(c->agg_path == 2 && !want_mats) && !regroup &&
                        cluster_sort_clusters(c->device) > 0;
   for (uint32_t s = 0; s < nseg; ++s) {
     if (on_chip && lens[s] <= kClusterWindowMax) small_ids.push_back(s);
@@ -1212,7 +1293,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
 
   // ---- scratch layout
   WinLayout wl;
-  wl.reserve(hp, nseg, want_mats, want_sum, hash);
+  wl.reserve(hp, nseg, want_mats, want_sum, hash, regroup);
   const DevPlan& dp = wl.dp;
   const PipeScratch& ps = wl.ps;
   const size_t s_col = wl.s_col, s_vals = wl.s_vals, s_row = wl.s_row, s_rp = wl.s_rp, s_hdr = wl.s_hdr,
@@ -1267,7 +1348,7 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   // sum_path 2: all packets of the batch as one segment (device-planned
   // batches: its offset and length come from the planner, the tile count is
   // the capacity's)
-  const bool sum_pk = want_sum && nseg && c->sum_path == 2 && !h_srcs;
+  const bool sum_pk = want_sum && nseg && (c->sum_path == 2 || regroup) && !h_srcs;
   // agg_path 2: the windows' quantities by on-chip hashing, when no window
   // DCSR is returned and the time sum (if any) comes from the packets
   const bool hq = c->agg_path == 2 && nseg && !want_mats && (!want_sum || sum_pk);
@@ -1452,7 +1533,16 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
                      }), "cluster sort")))
           return rc;
       }
-      if (!hash && !big_ids.empty()) {
+      if (regroup) {  // the time sum first; its packet sort yields the windows' order
+        Regroup rg;
+        rg.win = p;
+        rg.wid = at<uint16_t>(m, wl.off_wid);
+        rg.wid_b = at<uint16_t>(m, ps.ck_a);
+        rg.shift = at<uint64_t>(m, wl.off_wshift);
+        const SegPlan pk = wl.dp_pk.bind(m, hp_pk);
+        if ((rc = sum_packets(c, m, ps, pk, d_src, d_dst, sump.blk, ls, total < (1ull << 32), &rg))) return rc;
+        if ((rc = regroup_windows(c, m, ps, pk, rg, hp.ntiles, ls))) return rc;
+      } else if (!hash && !big_ids.empty()) {
         const SegPlan pb = dev || big_ids.size() == nseg ? pwin : wl.dp_big.bind(m, hp_big);
         const size_t nb = big_ids.size();
         if ((rc = cu(launch_zero(seg_hist, nb * kPasses * kRadix * 4, ls), "memset hist"))) return rc;
@@ -1487,12 +1577,12 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
       // With merge rounds, the run reduction also writes each link's key
       // beside its stored value (keys_b at the window's padded base): the
       // windows' links are then the time sum's sorted input runs in place.
-      const bool in_place = want_sum && c->sum_path == 0;
+      const bool in_place = want_sum && c->sum_path == 0 && !regroup;
       if (in_place) a.sum_keys = kb;
       if ((rc = cu(timed(c, "empty_fixup", ls, [&] { return launch_empty_fixup(a, ls); }), "empty"))) return rc;
       if ((rc = cu(timed(c, "rle", ls, [&] { return launch_rle(a, ls); }), "rle"))) return rc;
       if ((rc = cu(timed(c, "finish", ls, [&] { return launch_finish(a, ls); }), "finish"))) return rc;
-      if (want_sum && c->sum_path == 0) {
+      if (in_place) {
         if ((rc = cu(cudaEventRecord(c->ev_fork, ls), "event")) ||
             (rc = cu(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "event")))
           return rc;
@@ -1535,6 +1625,8 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
         if ((rc = cu(launch_zero(sblk->q, sizeof(ans_quantities), ls), "memset"))) return rc;
       } else if (forked) {  // a sum of window counts stays below the batch's packets
         if ((rc = links_to_block(c, m, ps, sump.s, sfk, sfv, sump.blk, ls, total < (1ull << 32)))) return rc;
+      } else if (regroup) {
+        // (the sum came first, from the packet sort that ordered the windows)
       } else if (sum_pk) {
         if ((rc = sum_packets(c, m, ps, wl.dp_pk.bind(m, hp_pk), d_src, d_dst, sump.blk, ls, total < (1ull << 32))))
           return rc;
@@ -2349,7 +2441,8 @@ int ans_batch_bytes(ans_ctx* c, const uint64_t* h_offsets, size_t nwin, uint32_t
   std::lock_guard<std::mutex> g(c->mu);
   const bool hash = c->agg_path == 1 && nwin > 0;
   WinLayout wl;
-  wl.reserve(hp, (uint32_t)nwin, want_mats, want_sum, hash);
+  wl.reserve(hp, (uint32_t)nwin, want_mats, want_sum, hash,
+             nwin <= 0xFFFFFFF0ull && regroup_windows_ok(c, (uint32_t)nwin, want_sum, false));
   size_t need = 0;
   if (wl.size > c->scratch_size)  // the scratch is replaced by a larger one
     need += std::max(wl.size, c->scratch_size + c->scratch_size / 4) - c->scratch_size;
@@ -2403,7 +2496,7 @@ int ans_set_tuning(ans_ctx* c, const ans_tuning* t) {
   if (t->win_path > 1 || t->win_rank > 1 || !ok(t->win_threads, t->win_rank, 1))
     return fail(ANS_ERR_INVALID_ARG, "win_path must be 0 or 1, win_threads 512 or 1024, win_rank 0 or 1");
   if (t->sum_path > 2) return fail(ANS_ERR_INVALID_ARG, "sum_path must be 0, 1 or 2");
-  if (t->agg_path > 2) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0, 1 or 2");
+  if (t->agg_path > 3) return fail(ANS_ERR_INVALID_ARG, "agg_path must be 0, 1, 2 or 3");
   if (t->graph > 1) return fail(ANS_ERR_INVALID_ARG, "graph must be 0 or 1");
   if (t->col_hash > 1) return fail(ANS_ERR_INVALID_ARG, "col_hash must be 0 or 1");
   if (t->merge_tile != 2048 && t->merge_tile != 4096) return fail(ANS_ERR_INVALID_ARG, "merge_tile must be 2048 or 4096");
@@ -2631,11 +2724,16 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   }
   int agg_path = 0;
   {
-    // hashed statistics need no window DCSR, and a time sum from the packets
-    const bool hq_ok = !(flags & ANS_BATCH_MATRICES);
-    const int sum_for[3] = {sum_path, sum_path, (flags & ANS_BATCH_SUM) ? 2 : sum_path};
-    double wall[3] = {kNever, kNever, kNever};
-    for (int a = 0; a < (hq_ok ? 3 : 2); ++a) {
+    // hashed statistics need no window DCSR, and a time sum from the packets;
+    // the windows' order from the packet sort needs a time sum (and takes
+    // it from the packets)
+    const bool want_sum = (flags & ANS_BATCH_SUM) != 0;
+    const bool ok[4] = {true, true, !(flags & ANS_BATCH_MATRICES),
+                        want_sum && nwin >= 2 && nwin <= kMaxRegroupWindows};
+    const int sum_for[4] = {sum_path, sum_path, want_sum ? 2 : sum_path, 2};
+    double wall[4] = {kNever, kNever, kNever, kNever};
+    for (int a = 0; a < 4; ++a) {
+      if (!ok[a]) continue;
       Prof pr;
       bool ran = false;
       ANS_TRY(trial([&] {
@@ -2647,7 +2745,7 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       }, &pr, &ran));
       if (ran) wall[a] = pr[kWall];
     }
-    for (int a = 1; a < 3; ++a)
+    for (int a = 1; a < 4; ++a)
       if (wall[a] < wall[agg_path]) agg_path = a;
     sum_path = sum_for[agg_path];
   }

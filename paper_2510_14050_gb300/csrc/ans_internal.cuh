@@ -47,6 +47,9 @@ enum ErrBits : uint32_t {
   kErrPlan = 8u,       // device-resident batch offsets were invalid or above the capacity
 };
 constexpr uint64_t kMaxWindowItems = (1ull << 31) - 1;  // packets of one window, links of one time sum
+constexpr int kPassStable = 0x100;  // digit-pass flag: pass 0 keeps the input order of equal digits
+constexpr int kPassMask = 0xFF;
+constexpr uint32_t kMaxRegroupWindows = 1u << 16;  // window ids carried as 16-bit values
 
 // How a onesweep pass is launched (chosen per context by the autotuner):
 // threads per 8192-key tile (512 or 1024; for the 64-bit key passes and the
@@ -259,6 +262,25 @@ cudaError_t launch_onesweep(const SegPlan& p, int pass, const uint64_t* kin, uin
                             const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
                             uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
                             uint32_t* err, const SortCfg& cfg, cudaStream_t st);
+// The one packet sort of a batch that also yields its windows' order
+// (agg_path 3): a digit pass over the 64-bit keys carrying each packet's
+// 16-bit window id, and a stable digit pass over the window ids carrying the
+// keys (pass | kPassStable for its first pass; with `remap`, a key whose
+// window is w lands at its sorted place + remap[w]; a null kout drops the
+// ids).  Both in the 4096-key sub-tile shape with cfg's ranking mode.
+cudaError_t launch_onesweep_wid(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
+                                const uint16_t* vin, uint16_t* vout, const uint32_t* seg_hist, uint64_t* st_cur,
+                                uint64_t* st_next, uint32_t* ticket, uint32_t* err, const SortCfg& cfg,
+                                cudaStream_t st);
+cudaError_t launch_onesweep_regroup(const SegPlan& p, int pass, const uint16_t* kin, uint16_t* kout,
+                                    const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
+                                    uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
+                                    const SortCfg& cfg, const uint64_t* remap, uint32_t nremap, cudaStream_t st);
+// Window ids of the windows of `p` over their packets in the batch's
+// one-segment packet order, each window's offset from that order (sorted by
+// window) to its padded base, and the ids' two digit histograms.
+cudaError_t launch_wid_fill(const SegPlan& p, const uint64_t* pk_in_off, uint16_t* wid, uint64_t* shift,
+                            uint32_t* hist, cudaStream_t st);
 // One digit pass over 32-bit destination keys carrying uint64 counts.
 cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin, uint32_t* kout,
                                 const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,

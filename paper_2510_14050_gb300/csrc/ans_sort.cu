@@ -143,22 +143,39 @@ constexpr size_t onesweep_smem_bytes() {
 }
 
 // One stable digit pass over keys of type K (8 passes for 64-bit keys, 4 for
-// 32-bit keys; seg_hist holds sizeof(K) histograms per segment), optionally
-// carrying values of type V.  Each 8192-key tile of the plan is split into
-// kSub sub-tiles, one CTA each (look-back runs over sub-tiles: status word
-// u * kRadix + d belongs to sub-tile u = kSub * tile + half); kT threads
-// share a sub-tile (kTile / kSub / kT keys each); kRank selects how lanes
-// with equal digits find each other.
+// 32-bit keys, 2 for 16-bit keys; seg_hist holds sizeof(K) histograms per
+// segment), optionally carrying values of type V.  Each 8192-key tile of the
+// plan is split into kSub sub-tiles, one CTA each (look-back runs over
+// sub-tiles: status word u * kRadix + d belongs to sub-tile u = kSub * tile +
+// half); kT threads share a sub-tile (kTile / kSub / kT keys each); kRank
+// selects how lanes with equal digits find each other.
+//
+// `pass` is the digit index, plus kPassStable when the input order of equal
+// digits must survive pass 0 too (by default pass 0 ranks with plain
+// shared-memory atomics: the LSD passes after it only need a partition).
+// With `remap` (16-bit keys only), a key k is written to its sorted position
+// plus remap[min(k, nremap - 1)]; with a null `kout` only the values are
+// written.  A 16-bit key or value shares a 32-bit register with the key's
+// rank inside the tile (below 2^16), which keeps the kv forms at the
+// registers of the key-only form.
 template <typename K, typename V, int kT, int kRank, int kMinB, int kSub>
 __global__ void __launch_bounds__(kT, kMinB)
     k_onesweep(SegPlan p, int pass, const K* __restrict__ kin, K* __restrict__ kout,
                const V* __restrict__ vin, V* __restrict__ vout, const uint32_t* __restrict__ seg_hist,
-               uint64_t* st_cur, uint64_t* __restrict__ st_next, uint32_t* ticket, uint32_t* err) {
+               uint64_t* st_cur, uint64_t* __restrict__ st_next, uint32_t* ticket, uint32_t* err,
+               const uint64_t* __restrict__ remap, uint32_t nremap) {
   constexpr bool kVals = !std::is_same<V, NoVal>::value;
   constexpr int kNumPasses = (int)sizeof(K);
   constexpr uint32_t kTT = kTile / kSub;  // keys per CTA
   constexpr int kP = kTT / kT;            // keys per thread
   constexpr int kW = kT / 32;             // warps
+  // 16-bit keys live in the low half of the rank word (rank in the high
+  // half); 16-bit values in its high half (rank in the low half).
+  constexpr bool kPackK = sizeof(K) == 2;
+  constexpr bool kPackV = kVals && !kPackK && sizeof(V) == 2;
+  static_assert(kTT <= 0xFFFFu, "ranks must fit 16 bits");
+  const bool atomic_rank = pass == 0;  // pass 0 without kPassStable
+  pass &= kPassMask;
   extern __shared__ __align__(16) uint8_t smem[];
   K* s_keys = reinterpret_cast<K*>(smem);
   V* s_vals = reinterpret_cast<V*>(smem + (size_t)kTT * sizeof(K));
@@ -204,15 +221,40 @@ __global__ void __launch_bounds__(kT, kMinB)
 
   const uint64_t g0 = tl.base + tl.start;
   const uint32_t wbase = warp * (kP * 32);
-  K k[kP];
-  V v[kVals ? kP : 1];
+  K k[kPackK ? 1 : kP];
+  V v[(kVals && !kPackV) ? kP : 1];
   uint32_t r[kP];
+  // the key, value and rank of item i, wherever they are held
+  auto key_of = [&](int i) -> K {
+    if constexpr (kPackK) return (K)(r[i] & 0xFFFFu);
+    else return k[i];
+  };
+  auto val_of = [&](int i) -> V {
+    if constexpr (kPackV) return (V)(r[i] >> 16);
+    else return v[i];
+  };
+  auto rank_of = [&](int i) -> uint32_t {
+    if constexpr (kPackK) return r[i] >> 16;
+    else if constexpr (kPackV) return r[i] & 0xFFFFu;
+    else return r[i];
+  };
+  auto set_rank = [&](int i, uint32_t x) {
+    if constexpr (kPackK) r[i] = (r[i] & 0xFFFFu) | (x << 16);
+    else if constexpr (kPackV) r[i] = (r[i] & 0xFFFF0000u) | x;
+    else r[i] = x;
+  };
 #pragma unroll
   for (int i = 0; i < kP; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
     const bool valid = idx < tl.count;
-    k[i] = valid ? kin[g0 + idx] : K(0);
-    if constexpr (kVals) v[i] = valid ? vin[g0 + idx] : V(0);
+    if constexpr (kPackK) {
+      r[i] = valid ? (uint32_t)kin[g0 + idx] : 0u;
+    } else {
+      k[i] = valid ? kin[g0 + idx] : K(0);
+      r[i] = 0;
+    }
+    if constexpr (kPackV) r[i] = valid ? (uint32_t)vin[g0 + idx] << 16 : 0u;
+    else if constexpr (kVals) v[i] = valid ? vin[g0 + idx] : V(0);
   }
   // Stable rank inside (warp, digit): lanes with equal digits find each other
   // (digit_peers); the lowest lane updates the warp's counter.
@@ -224,7 +266,7 @@ __global__ void __launch_bounds__(kT, kMinB)
       // Each lane sets its bit in its digit's entry; every lane then reads
       // the entry (the lanes sharing its digit, and the digit's count so
       // far), and the lowest of them advances the count and clears the bits.
-      const uint32_t d = (uint32_t)(k[i] >> shift) & 0xffu;
+      const uint32_t d = (uint32_t)(key_of(i) >> shift) & 0xffu;
       if (valid) atomicOr(reinterpret_cast<unsigned int*>(tab + d), 1u << lane);
       __syncwarp();
       const uint64_t e = valid ? tab[d] : 0ull;
@@ -232,15 +274,15 @@ __global__ void __launch_bounds__(kT, kMinB)
       const uint32_t peers = (uint32_t)e, old = (uint32_t)(e >> 32);
       if (valid && lane == __ffs(peers) - 1) tab[d] = (uint64_t)(old + __popc(peers)) << 32;
       __syncwarp();
-      r[i] = old + __popc(peers & lanemask_lt());
-    } else if (pass == 0) {
+      set_rank(i, old + __popc(peers & lanemask_lt()));
+    } else if (atomic_rank) {
       // The first pass needs no stability (any order of equal digits is a
       // valid start for the stable passes after it): one shared-memory
       // atomic per key gives each its slot among the warp's equal digits.
-      const uint32_t d = (uint32_t)(k[i] >> shift) & 0xffu;
-      r[i] = valid ? atomicAdd(&wc[d], 1u) : 0u;
+      const uint32_t d = (uint32_t)(key_of(i) >> shift) & 0xffu;
+      set_rank(i, valid ? atomicAdd(&wc[d], 1u) : 0u);
     } else {
-      const uint32_t d = valid ? (uint32_t)(k[i] >> shift) & 0xffu : (uint32_t)kRadix;
+      const uint32_t d = valid ? (uint32_t)(key_of(i) >> shift) & 0xffu : (uint32_t)kRadix;
       const uint32_t peers = digit_peers<kRank>(d, valid);
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
@@ -250,7 +292,7 @@ __global__ void __launch_bounds__(kT, kMinB)
       }
       __syncwarp();
       old = __shfl_sync(0xffffffffu, old, valid ? leader : lane);
-      r[i] = old + __popc(peers & lanemask_lt());
+      set_rank(i, old + __popc(peers & lanemask_lt()));
     }
   }
   __syncthreads();
@@ -300,29 +342,31 @@ __global__ void __launch_bounds__(kT, kMinB)
   for (int i = 0; i < kP; ++i) {
     const uint32_t idx = wbase + i * 32 + lane;
     if (idx < tl.count) {
-      const uint32_t dg = (uint32_t)(k[i] >> shift) & 0xffu;
+      const K key = key_of(i);
+      const uint32_t dg = (uint32_t)(key >> shift) & 0xffu;
       const uint32_t woff = kRank == kRankTable ? (uint32_t)(tab[dg] >> 32) : wc[dg];
-      const uint32_t pos = s_dstart[dg] + woff + r[i];
-      s_keys[pos] = k[i];
-      if constexpr (kVals) s_vals[pos] = v[i];
+      const uint32_t pos = s_dstart[dg] + woff + rank_of(i);
+      s_keys[pos] = key;
+      if constexpr (kVals) s_vals[pos] = val_of(i);
     }
   }
   __syncthreads();
+  // write-out: sorted tile position i of a key with digit d goes to
+  // s_gofs[d] + i (plus the key's remap offset)
+  auto put = [&](uint32_t i) {
+    const K key = s_keys[i];
+    uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
+    if constexpr (kPackK) {
+      if (remap) o += remap[umin64((uint64_t)key, (uint64_t)nremap - 1)];
+    }
+    if (kout) kout[o] = key;
+    if constexpr (kVals) vout[o] = s_vals[i];
+  };
   if (tl.count == kTT) {  // a full tile: a fixed trip count the compiler unrolls
 #pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < kTT; i += kT) {
-      const K key = s_keys[i];
-      const uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
-      kout[o] = key;
-      if constexpr (kVals) vout[o] = s_vals[i];
-    }
+    for (uint32_t i = threadIdx.x; i < kTT; i += kT) put(i);
   } else {
-    for (uint32_t i = threadIdx.x; i < tl.count; i += kT) {
-      const K key = s_keys[i];
-      const uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
-      kout[o] = key;
-      if constexpr (kVals) vout[o] = s_vals[i];
-    }
+    for (uint32_t i = threadIdx.x; i < tl.count; i += kT) put(i);
   }
 }
 
@@ -475,12 +519,58 @@ cudaError_t configure_onesweep_variant() {
 template <typename K, typename V, int kT, int kRank, int kMinB, int kSub = 1>
 cudaError_t run_onesweep_variant(const SegPlan& p, int pass, const K* kin, K* kout, const V* vin, V* vout,
                                  const uint32_t* seg_hist, uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
-                                 uint32_t* err, cudaStream_t st) {
+                                 uint32_t* err, cudaStream_t st, const uint64_t* remap = nullptr,
+                                 uint32_t nremap = 0) {
   cudaError_t e = configure_onesweep_variant<K, V, kT, kRank, kMinB, kSub>();
   if (e != cudaSuccess) return e;
   k_onesweep<K, V, kT, kRank, kMinB, kSub><<<kSub * p.ntiles, kT, onesweep_smem_bytes<K, V, kT, kRank, kSub>(), st>>>(
-      p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err);
+      p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err, remap, nremap);
   return cudaGetLastError();
+}
+
+// The kv forms of the one packet sort of a batch (64-bit keys carrying
+// 16-bit window ids, and the regrouping by window id carrying the keys):
+// only the 4096-key sub-tile shape (256 threads, four CTAs per SM), with the
+// key passes' ranking mode.
+template <typename K, typename V>
+cudaError_t run_onesweep_sub(const SegPlan& p, int pass, const K* kin, K* kout, const V* vin, V* vout,
+                             const uint32_t* seg_hist, uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket,
+                             uint32_t* err, const SortCfg& cfg, cudaStream_t st, const uint64_t* remap,
+                             uint32_t nremap) {
+  if (p.ntiles == 0) return cudaSuccess;
+  if (cfg.rank == kRankBallot)
+    return run_onesweep_variant<K, V, 256, kRankBallot, 4, 2>(p, pass, kin, kout, vin, vout, seg_hist, st_cur,
+                                                              st_next, ticket, err, st, remap, nremap);
+  if (cfg.rank == kRankTable)
+    return run_onesweep_variant<K, V, 256, kRankTable, 4, 2>(p, pass, kin, kout, vin, vout, seg_hist, st_cur,
+                                                             st_next, ticket, err, st, remap, nremap);
+  return run_onesweep_variant<K, V, 256, kRankMatch, 4, 2>(p, pass, kin, kout, vin, vout, seg_hist, st_cur,
+                                                           st_next, ticket, err, st, remap, nremap);
+}
+
+// Window ids of a batch's packets in its one-segment packet plan `pk`: CTA w
+// writes id w over window w's packets (at in_off[w] - pk_in_off[0]), the
+// offset that takes window w's packets from their place in the batch sorted
+// by window to the window's padded base (shift[w] = base[w] - that place),
+// and adds the window's packets to the two digit histograms of the ids
+// (hist[0][w & 255], hist[1][w >> 8]; zeroed by the caller).
+__global__ void __launch_bounds__(256) k_wid_fill(SegPlan p, const uint64_t* __restrict__ pk_in_off,
+                                                  uint16_t* __restrict__ wid, uint64_t* __restrict__ shift,
+                                                  uint32_t* __restrict__ hist) {
+  const uint32_t w = blockIdx.x;
+  if (w >= p.nseg) return;
+  const uint64_t len = p.len[w];
+  const uint64_t at = p.in_off[w] - pk_in_off[0];
+  if (threadIdx.x == 0) {
+    shift[w] = p.base[w] - at;
+    if (len) {
+      atomicAdd(&hist[w & 0xffu], (uint32_t)len);
+      atomicAdd(&hist[kRadix + ((w >> 8) & 0xffu)], (uint32_t)len);
+    }
+  }
+  uint16_t* out = wid + at;
+  const uint16_t id = (uint16_t)w;
+  for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) out[i] = id;
 }
 
 template <typename K, typename V>
@@ -556,6 +646,31 @@ cudaError_t launch_onesweep_col(const SegPlan& p, int pass, const uint32_t* kin,
                                 const SortCfg& cfg, cudaStream_t st) {
   return run_onesweep<uint32_t, uint64_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err,
                                           cfg, st);
+}
+
+cudaError_t launch_onesweep_wid(const SegPlan& p, int pass, const uint64_t* kin, uint64_t* kout,
+                                const uint16_t* vin, uint16_t* vout, const uint32_t* seg_hist, uint64_t* st_cur,
+                                uint64_t* st_next, uint32_t* ticket, uint32_t* err, const SortCfg& cfg,
+                                cudaStream_t st) {
+  return run_onesweep_sub<uint64_t, uint16_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err,
+                                              cfg, st, nullptr, 0);
+}
+
+cudaError_t launch_onesweep_regroup(const SegPlan& p, int pass, const uint16_t* kin, uint16_t* kout,
+                                    const uint64_t* vin, uint64_t* vout, const uint32_t* seg_hist,
+                                    uint64_t* st_cur, uint64_t* st_next, uint32_t* ticket, uint32_t* err,
+                                    const SortCfg& cfg, const uint64_t* remap, uint32_t nremap, cudaStream_t st) {
+  if (remap && nremap == 0) return cudaErrorInvalidValue;
+  return run_onesweep_sub<uint16_t, uint64_t>(p, pass, kin, kout, vin, vout, seg_hist, st_cur, st_next, ticket, err,
+                                              cfg, st, remap, nremap);
+}
+
+cudaError_t launch_wid_fill(const SegPlan& p, const uint64_t* pk_in_off, uint16_t* wid, uint64_t* shift,
+                            uint32_t* hist, cudaStream_t st) {
+  if (p.nseg == 0) return cudaSuccess;
+  if (p.nseg > kMaxRegroupWindows) return cudaErrorInvalidValue;
+  k_wid_fill<<<p.nseg, 256, 0, st>>>(p, pk_in_off, wid, shift, hist);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const SegPlan& p, const MatDesc* mats, const uint64_t* cat_off, uint64_t* keys,

@@ -46,7 +46,8 @@ def _check(ans, mats, summ, q, w, src=None, dst=None):
 @pytest.mark.parametrize("cap", [0, 1 << 22])
 @pytest.mark.parametrize("paths", [dict(sum_path=0, agg_path=0), dict(sum_path=1, agg_path=0),
                                    dict(sum_path=2, agg_path=0), dict(sum_path=0, agg_path=1),
-                                   dict(sum_path=2, agg_path=1)])
+                                   dict(sum_path=2, agg_path=1), dict(sum_path=2, agg_path=3),
+                                   dict(sum_path=0, agg_path=3)])
 def test_device_offsets_match_the_oracle(mods, cap, paths):
     ans, synth = mods
     sizes = synth.window_sizes(5, 14)

@@ -432,6 +432,39 @@ def test_aggregation_paths_are_exact(ans, synth, agg_path):
         c.close()
 
 
+@pytest.mark.parametrize("sum_path", [0, 2])
+def test_windows_from_the_packet_sort(ans, synth, sum_path):
+    """agg_path 3: the windows' sorted keys come from the time sum's packet
+    sort (the packets carry their window ids; a stable two-pass sort by
+    window id puts every window back at its base).  Exact against the oracle
+    with and without per-window matrices, whatever sum_path says: mixed
+    sizes (empty, one packet, ragged tiles, larger than 2^17), more than 256
+    windows (both id digits), exactly 2^16 windows (the largest id), and the
+    batches the path leaves to the window sort (one window, 2^16 + 1 windows,
+    no time sum)."""
+    c = ans.Context(0)
+    try:
+        c.set_tuning(agg_path=3, sum_path=sum_path)
+        assert c.get_tuning()["agg_path"] == 3
+        w = synth.generate(5, sizes=[0, 1, 8191, 8193, 40000, 0, 131072, 150001], first_window=7)
+        for _ in range(2):  # the second call replays the cached graph
+            check_batch(ans, c, w)
+        check_batch(ans, c, w, check_mats=False)
+        rng = np.random.default_rng(5)
+        sizes = rng.integers(0, 3000, 700)
+        sizes[[0, 255, 256, 511, 699]] = [0, 1, 8192, 0, 5]
+        check_batch(ans, c, synth.generate(5, sizes=sizes, first_window=3))
+        check_batch(ans, c, synth.generate(3, nwin=6, first_window=40))
+        for nwin in (1 << 16, (1 << 16) + 1):
+            sizes = rng.integers(0, 4, nwin)
+            sizes[-1] = 2
+            check_batch(ans, c, synth.generate(5, sizes=sizes, first_window=1), check_mats=False)
+        check_batch(ans, c, synth.generate(5, sizes=[5000]))              # one window
+        check_batch(ans, c, synth.generate(5, nwin=4), check_sum=False)  # no time sum
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("graph", [0, 1])
 def test_graph_replay_follows_each_call(ans, synth, graph):
     """With graph replay, a cached executable graph is reused for batches of
