@@ -650,6 +650,11 @@ struct DevPlan {
 struct PipeScratch {
   size_t keys_a, keys_b, vals_a, vals_b, seg_hist, st0, st1, lb, lb2, tickets, run_start, row_pos, pre;
   size_t ck_a, ck_b, cv_a, cv_b, col_hist, ulen, bnd;
+  // hash-group column statistics of a time sum (buffers for up to
+  // hgroup_links links, when reserved)
+  size_t hbnd = 0, hitem = 0, hpart = 0, hheavy = 0, hmeta = 0, hcnt = 0, hbuf = 0, hacc = 0;
+  uint64_t hgroup_links = 0;
+  uint32_t hgroup_cap = 0;  // parts of cut groups the buffers hold
   void reserve(Layout& L, uint64_t pad, uint32_t nseg, uint32_t ntiles, bool with_vals) {
     ck_a = L.add(pad * 4);
     ck_b = L.add(pad * 4);
@@ -658,6 +663,18 @@ struct PipeScratch {
     col_hist = L.add((size_t)nseg * kColPasses * kRadix * 4);
     ulen = L.add((size_t)nseg * 8);
     bnd = L.add((size_t)ntiles * sizeof(ColBnd));
+    if (with_vals && pad >= kHGroupMinLinks) {
+      hgroup_links = pad;
+      hgroup_cap = (uint32_t)(2 * (pad / kHGroupPartLinks) + 1);
+      hbnd = L.add((size_t)kHGroupBounds * 4);
+      hitem = L.add((size_t)kHGroupBounds * 4);
+      hpart = L.add((size_t)kHGroupBounds * 4);
+      hheavy = L.add((size_t)kHGroups * 4);
+      hmeta = L.add(16);
+      hcnt = L.add((size_t)hgroup_cap * 4);
+      hbuf = L.add((size_t)hgroup_cap * kHGroupPartWords * 4);
+      hacc = L.add(3 * sizeof(ColPartAcc));
+    }
     keys_a = L.add(pad * 8);
     keys_b = L.add(pad * 8);
     vals_a = with_vals ? L.add(pad * 8) : 0;
@@ -699,10 +716,14 @@ int sort_segments(ans_ctx* c, const SegPlan& p, uint64_t* ka, uint64_t* kb, uint
 // passes (in -> A -> B -> A -> B) and the destination runs reduced.  Expects
 // k_finish to have filled col_hist and ulen and zeroed st0 and the tickets.
 // With vals32 (window matrices, whose counts fit 31 bits; k_finish wrote the
-// copy into the value buffer B) the passes carry uint32 counts.
-int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32_t* col_ids,
+// copy into the value buffer B) the passes carry uint32 counts.  With hkeys
+// (one segment, vals32: k_finish wrote the mixed destinations there and
+// counted their bytes), the passes sort the mixed destinations, and after
+// the first two the hash groups are counted (launch_hgroup_stats); if they
+// all fit, the segment's length drops to 0 and the rest finds no work.
+int column_pass(ans_ctx* c, const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids,
                 const uint64_t* vals, const PipeScratch& ps, char* m, uint32_t* tickets,
-                ans_quantities* q, cudaStream_t st, bool vals32 = false) {
+                ans_quantities* q, cudaStream_t st, bool vals32 = false, const uint32_t* hkeys = nullptr) {
   SegPlan cp = p;
   cp.len = ulen;
   uint32_t* ka = at<uint32_t>(m, ps.ck_a);
@@ -712,8 +733,24 @@ int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32
   uint64_t* st0 = at<uint64_t>(m, ps.st0);
   uint64_t* st1 = at<uint64_t>(m, ps.st1);
   uint32_t* hist = at<uint32_t>(m, ps.col_hist);
+  if (hkeys && (p.nseg != 1 || !vals32)) return fail(ANS_ERR_INTERNAL, "hash-group column statistics");
   for (int pass = 0; pass < kColPasses; ++pass) {
-    const uint32_t* kin = pass == 0 ? col_ids : (pass % 2 ? ka : kb);
+    if (hkeys && pass == 2) {  // the links grouped by the mix's low 16 bits (keys in B)
+      HGroupBufs hb;
+      hb.bnd = at<uint32_t>(m, ps.hbnd);
+      hb.item_start = at<uint32_t>(m, ps.hitem);
+      hb.hpart = at<uint32_t>(m, ps.hpart);
+      hb.heavy = at<uint32_t>(m, ps.hheavy);
+      hb.meta = at<uint32_t>(m, ps.hmeta);
+      hb.hcnt = at<uint32_t>(m, ps.hcnt);
+      hb.hbuf = at<uint32_t>(m, ps.hbuf);
+      hb.acc = at<ColPartAcc>(m, ps.hacc);
+      ANS_CUDA(launch_zero(hb.acc, 3 * sizeof(ColPartAcc), st));
+      ANS_CUDA(timed(c, "hgroup", st, [&] {
+        return launch_hgroup_stats(kb, (const uint32_t*)vb, ulen, hb, ps.hgroup_cap, q, st);
+      }));
+    }
+    const uint32_t* kin = pass == 0 ? (hkeys ? hkeys : col_ids) : (pass % 2 ? ka : kb);
     uint32_t* kout = pass % 2 ? kb : ka;
     ANS_CUDA(timed(c, "onesweep_col", st, [&] {
       if (vals32) {  // B (the copy, then pass 2's output) -> A -> B
@@ -733,6 +770,16 @@ int column_pass(ans_ctx* c, const SegPlan& p, const uint64_t* ulen, const uint32
     return launch_colstat(cp, kb, vb, at<ColBnd>(m, ps.bnd), q, st);
   }));
   return ANS_OK;
+}
+
+// A time sum (one segment at base 0) takes the hash-group column statistics
+// when its counts are 32-bit, the column hashes are on, it may hold 2^24
+// or more links (smaller sums sort their 2^16 groups' worth of work faster)
+// and the scratch holds the buffers for that many.
+bool hgroup_ok(const ans_ctx* c, const SegPlan& p, bool narrow, const PipeScratch& ps) {
+  const uint64_t links = (uint64_t)p.ntiles * kTile;
+  return narrow && c->col_hash && p.nseg == 1 && links >= kHGroupMinLinks && ps.hgroup_cap > 0 &&
+         links <= ps.hgroup_links;
 }
 
 struct SumPlan {
@@ -911,10 +958,11 @@ int links_to_block(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& s,
   a.err = c->d_err;
   a.mode = kModeSum;
   if (narrow) a.vals32 = (uint32_t*)at<uint64_t>(m, ps.cv_b);
+  if (hgroup_ok(c, s, narrow, ps)) a.col_hkeys = at<uint32_t>(m, ps.ck_b);
   if ((e = launch_zero(blk->q, sizeof(ans_quantities), st)) != cudaSuccess) return fail_blk(e, "memset");
   if ((e = timed(c, "rle", st, [&] { return launch_rle(a, st); })) != cudaSuccess) return fail_blk(e, "rle");
   if ((e = timed(c, "finish", st, [&] { return launch_finish(a, st); })) != cudaSuccess) return fail_blk(e, "finish");
-  return column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st, narrow);
+  return column_pass(c, s, a.ulen, blk->col_ids, blk->vals, ps, m, col_tickets, blk->q, st, narrow, a.col_hkeys);
 }
 
 // The windows of a batch whose sorted keys come from its packet sort
@@ -998,9 +1046,11 @@ int sum_packets(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& pk, c
   a.col_tickets = tickets + 3 * 32;
   a.err = c->d_err;
   a.mode = kModeWindow;
+  if (hgroup_ok(c, pk, narrow, ps)) a.col_hkeys = at<uint32_t>(m, ps.ck_b);
   if ((rc = cu(timed(c, "rle", st, [&] { return launch_rle(a, st); }), "rle"))) return rc;
   if ((rc = cu(timed(c, "finish", st, [&] { return launch_finish(a, st); }), "finish"))) return rc;
-  return column_pass(c, pk, a.ulen, blk->col_ids, blk->vals, ps, m, a.col_tickets, blk->q, st, narrow);
+  return column_pass(c, pk, a.ulen, blk->col_ids, blk->vals, ps, m, a.col_tickets, blk->q, st, narrow,
+                     a.col_hkeys);
 }
 
 // The windows' sorted keys from the batch's packet sort (agg_path 3, after
@@ -1154,6 +1204,7 @@ struct WinLayout {
   size_t off_small = 0;  // ids of the windows sorted on chip
   size_t off_colacc = 0; // per-window accumulators of the partitioned column hash
   size_t off_colpart = 0; // its partition starts per window
+  size_t off_colitems = 0; // its (window, partition) work items
   size_t off_tileseg = 0; // the window plan's segment of every tile
   size_t off_hqwin = 0, off_lstart = 0, off_kstart = 0, off_sortlen = 0, off_items = 0;  // hashed window statistics
   DevPlan dp_tab;        // hash path: the windows' tables as segments
@@ -1171,8 +1222,9 @@ struct WinLayout {
     dp.reserve(L, nseg, addrs);
     dp_big.reserve(L, nseg, addrs);
     off_small = L.add((size_t)nseg * 4);
-    off_colacc = L.add((size_t)nseg * sizeof(ColPartAcc));
+    off_colacc = L.add(((size_t)nseg + 1) * sizeof(ColPartAcc));
     off_colpart = L.add((size_t)nseg * 33 * 4);
+    off_colitems = L.add((size_t)nseg * 32 * 4);
     off_tileseg = L.add((size_t)hp.ntiles * 4);
     off_hqwin = L.add((size_t)nseg * sizeof(HqWin));
     off_lstart = L.add((size_t)nseg * 65 * 4);
@@ -1597,13 +1649,14 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
                 "colhash");
       if (rc == ANS_OK && c->col_hash) {  // windows with more destinations than one table holds
         ColPartAcc* acc = at<ColPartAcc>(m, wl.off_colacc);
-        rc = cu(launch_zero(acc, (size_t)nseg * sizeof(ColPartAcc), ls), "memset");
+        rc = cu(launch_zero(acc, ((size_t)nseg + 1) * sizeof(ColPartAcc), ls), "memset");
         if (rc == ANS_OK)
           rc = cu(timed(c, "colhash_part", ls,
                         [&] {  // links regrouped into the column sort's buffers, which it overwrites later
                           return launch_colhash_part(pw, a.ulen, sb.col_ids, a.vals32, at<uint32_t>(m, ps.ck_a),
                                                      (uint32_t*)at<uint64_t>(m, ps.cv_a),
-                                                     at<uint32_t>(m, wl.off_colpart), acc, sb.q, ls);
+                                                     at<uint32_t>(m, wl.off_colpart), acc,
+                                                     at<uint32_t>(m, wl.off_colitems), sb.q, ls);
                         }),
                   "colhash part");
       }

@@ -106,6 +106,10 @@ struct StatsArgs {
   // at base[s] + u, beside its column id -- with the link values this is the
   // time sum's input run of the window, read in place by the merge.
   uint64_t* sum_keys = nullptr;
+  // Optional: each link's mixed destination fmix32(dst) written at base[s] +
+  // u (the column sort's keys when a time sum's column statistics group
+  // destinations by hash); the column histograms then count its bytes.
+  uint32_t* col_hkeys = nullptr;
   int mode = 0;
 };
 
@@ -391,14 +395,43 @@ struct ColPartAcc {
   uint32_t fail, done;
 };
 // Window column statistics of the windows launch_colhash left (ulen[s] > 0)
-// with more than 8192 and at most 32 x 8192 links: their destinations split
-// by a hash into partitions (the links regrouped by partition into
-// pkeys/pvals at the window's base, partition starts in bstart[s][0..33)),
-// one CTA and shared-memory table per partition; windows whose partitions
-// all fit get their three column quantities and ulen[s] = 0.
+// with more than 8192 and at most 32 x 8192 links (window index below 2^27):
+// their destinations split by a hash into partitions (the links regrouped
+// by partition into pkeys/pvals at the window's base, partition starts in
+// bstart[s][0..33), the (window, partition) items listed in items[nseg *
+// 32]), one shared-memory table per partition, counted by one persistent
+// CTA per SM; windows whose partitions all fit get their three column
+// quantities and ulen[s] = 0.  acc: nseg + 1 zeroed accumulators (the last
+// one counts and hands out the items).
 cudaError_t launch_colhash_part(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
-                                uint32_t* pkeys, uint32_t* pvals, uint32_t* bstart, ColPartAcc* acc, ans_quantities* q,
-                                cudaStream_t st);
+                                uint32_t* pkeys, uint32_t* pvals, uint32_t* bstart, ColPartAcc* acc, uint32_t* items,
+                                ans_quantities* q, cudaStream_t st);
+// Column statistics of one segment of *len links (a time sum) whose mixed
+// destinations `keys` (fmix32 of each destination, with uint32 counts
+// `vals32`) have been sorted by their low 16 bits (two column passes): the
+// 2^16 groups counted in shared-memory tables by persistent CTAs (groups of
+// more than kHGroupPartLinks links in parts, merged afterwards).  If every
+// table fits, the segment's three column quantities go to *q and *len
+// becomes 0; otherwise nothing is published and the column sort goes on.
+// The buffers (HGroupBufs, acc zeroed) hold up to max_hparts parts of cut
+// groups; more fail the hash the same way.
+constexpr uint32_t kHGroups = 1u << 16;
+constexpr uint32_t kHGroupBounds = kHGroups + 1;
+constexpr uint32_t kHGroupPartLinks = 1u << 16;
+constexpr uint64_t kHGroupMinLinks = 1ull << 24;  // smaller sums take the column sort
+constexpr uint32_t kHGroupPartWords = 3 * ((1u << 13) / 4 * 3 + 1);  // a part's entries: its table's fill + 1
+struct HGroupBufs {
+  uint32_t* bnd = nullptr;         // [kHGroupBounds] group starts
+  uint32_t* item_start = nullptr;  // [kHGroupBounds] first work item of each group
+  uint32_t* hpart = nullptr;       // [kHGroupBounds] first part (of cut groups) of each group
+  uint32_t* heavy = nullptr;       // [kHGroups] the cut groups
+  uint32_t* meta = nullptr;        // [4] items, cut groups, their parts
+  uint32_t* hcnt = nullptr;        // [max_hparts] entries of each part
+  uint32_t* hbuf = nullptr;        // [max_hparts][kHGroupPartWords] (key, links, packets) entries
+  ColPartAcc* acc = nullptr;       // [3] zeroed: quantities + fail + CTAs done; item and group counters
+};
+cudaError_t launch_hgroup_stats(const uint32_t* keys, const uint32_t* vals32, uint64_t* len, const HGroupBufs& b,
+                                uint32_t max_hparts, ans_quantities* q, cudaStream_t st);
 // tile_seg[t] = the segment of tile t of `p` (its first_tile searched once
 // per tile), for SegPlan::tile_seg.
 cudaError_t launch_tile_seg(const SegPlan& p, uint32_t* tile_seg, cudaStream_t st);

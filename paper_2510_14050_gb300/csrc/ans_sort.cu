@@ -221,9 +221,9 @@ __global__ void __launch_bounds__(kT, kMinB)
 
   const uint64_t g0 = tl.base + tl.start;
   const uint32_t wbase = warp * (kP * 32);
-  K k[kPackK ? 1 : kP];
-  V v[(kVals && !kPackV) ? kP : 1];
-  uint32_t r[kP];
+  K k[kPackK ? 1 : kP] = {};  // (every element is written by the load loop below)
+  V v[(kVals && !kPackV) ? kP : 1] = {};
+  uint32_t r[kP] = {};
   // the key, value and rank of item i, wherever they are held
   auto key_of = [&](int i) -> K {
     if constexpr (kPackK) return (K)(r[i] & 0xFFFFu);

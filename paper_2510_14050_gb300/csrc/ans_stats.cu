@@ -218,7 +218,17 @@ __global__ void __launch_bounds__(kThreads) k_scan_u64(SegPlan p, const uint64_t
   }
 }
 
-template <int kMode>
+// Finalizer of MurmurHash3 (Appleby): a bijective 32-bit mix.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+template <int kMode, bool kHKeys>
 __global__ void __launch_bounds__(kThreads, 3) k_finish(StatsArgs a) {
   __shared__ Tile s_tile;
   __shared__ uint64_t s_red[3][kWarps];
@@ -281,9 +291,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_finish(StatsArgs a) {
         if (a.vals32) a.vals32[tl.base + u] = (uint32_t)v;
       }
       mlink = v > mlink ? v : mlink;
+      // the column sort's key: the destination, or its bijective mix when
+      // the sum's column statistics group destinations by hash
+      uint32_t ck = dst[j];
+      if constexpr (kHKeys) {
+        ck = fmix32(ck);
+        a.col_hkeys[tl.base + u] = ck;
+      }
 #pragma unroll
       for (int p = 0; p < kColPasses; ++p)
-        atomicAdd(&s_h[p * kRadix + ((dst[j] >> (p * kRadixBits)) & 0xffu)], 1u);
+        atomicAdd(&s_h[p * kRadix + ((ck >> (p * kRadixBits)) & 0xffu)], 1u);
     }
   }
   const uint64_t r_end = umin64(tl.start + kTile, nrows);
@@ -664,16 +681,6 @@ constexpr uint32_t kColHashMaxFill = kColHashSlots / 4 * 3;  // give up above th
 constexpr size_t kColHashSmem = (size_t)kColHashSlots * 12;  // key, links, packets (uint32 each)
 constexpr uint32_t kColEmpty = 0xFFFFFFFFu;                  // empty slot (that destination is counted apart)
 
-// Finalizer of MurmurHash3 (Appleby): a bijective 32-bit mix.
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
-}
-
 __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash(SegPlan p, uint64_t* __restrict__ ulen,
                                                                  const uint32_t* __restrict__ col_ids,
                                                                  const uint32_t* __restrict__ vals32,
@@ -921,27 +928,31 @@ __device__ __forceinline__ uint32_t col_part(uint32_t d, uint32_t parts) {
   return (uint32_t)(((uint64_t)(fmix32(d) >> 14) * parts) >> 18);
 }
 
-// Partitions of a window of n links, or 0 if the partitioned hash does not
-// take it (empty, finished, within one table, or too large).
-__device__ __forceinline__ uint32_t col_parts_of(uint64_t n) {
+// Partitions of window s of n links, or 0 if the partitioned hash does not
+// take it (empty, finished, within one table, too large, or an index past
+// the 2^27 windows whose (window, partition) items fit 32 bits).
+__device__ __forceinline__ uint32_t col_parts_of(uint64_t n, uint32_t s) {
   const uint64_t parts = (n + kColPartLinks - 1) / kColPartLinks;
-  return parts >= 2 && parts <= kColParts ? (uint32_t)parts : 0u;
+  return parts >= 2 && parts <= kColParts && s < (1u << 27) ? (uint32_t)parts : 0u;
 }
 
 // One CTA per window: the window's (destination, count) links regrouped by
 // partition into okeys/ovals at the window's base; the partition starts in
-// bstart[s][0..parts].
+// bstart[s][0..parts]; the window's (window, partition) items s * 32 + r
+// appended to `items` (their count in work->count).
 __global__ void __launch_bounds__(kSplitThreads, 2) k_colpart_split(SegPlan p, const uint64_t* __restrict__ ulen,
                                                                     const uint32_t* __restrict__ col_ids,
                                                                     const uint32_t* __restrict__ vals32,
                                                                     uint32_t* __restrict__ okeys,
                                                                     uint32_t* __restrict__ ovals,
-                                                                    uint32_t* __restrict__ bstart) {
+                                                                    uint32_t* __restrict__ bstart,
+                                                                    ColPartAcc* __restrict__ work,
+                                                                    uint32_t* __restrict__ items) {
   __shared__ uint32_t s_cnt[kColParts], s_cur[kColParts];
   const uint32_t s = blockIdx.x;
   if (s >= p.nseg) return;
   const uint64_t n = ulen[s];
-  const uint32_t parts = col_parts_of(n);
+  const uint32_t parts = col_parts_of(n, s);
   if (!parts) return;
   const uint64_t b = p.base[s];
   const uint32_t* ci = col_ids + b;
@@ -975,6 +986,8 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_colpart_split(SegPlan p, c
       run += s_cnt[r];
     }
     bstart[(uint64_t)s * (kColParts + 1) + parts] = run;
+    const uint32_t first = (uint32_t)atomicAdd(&work->count, (unsigned long long)parts);
+    for (uint32_t r = 0; r < parts; ++r) items[first + r] = s * kColParts + r;
   }
   __syncthreads();
   // pass 2: scatter each link to its partition (order within a partition is free)
@@ -1006,114 +1019,497 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_colpart_split(SegPlan p, c
   }
 }
 
-// CTA r of window s counts partition r's links (from k_colpart_split).
+// Partitions counted by persistent CTAs (one per SM: the table takes the
+// SM's shared memory), each taking the next (window s, partition r) item
+// that k_colpart_split listed and counting partition r's links.  The links
+// are read in chunks of kColPartChunk per thread, the first chunk's loads
+// issued before the table is cleared; the table's fill is counted once per
+// warp.
+constexpr int kColPartChunk = 8;
 __global__ void __launch_bounds__(kColHashThreads, 1) k_colhash_part(SegPlan p, uint64_t* __restrict__ ulen,
                                                                       const uint32_t* __restrict__ pkeys,
                                                                       const uint32_t* __restrict__ pvals,
                                                                       const uint32_t* __restrict__ bstart,
                                                                       ColPartAcc* __restrict__ acc,
+                                                                      const uint32_t* __restrict__ items,
                                                                       ans_quantities* __restrict__ q) {
   extern __shared__ __align__(16) uint32_t sm[];
   uint32_t* t_key = sm;
   uint32_t* t_cnt = sm + kColHashSlots;
   uint32_t* t_sum = sm + 2 * kColHashSlots;
-  __shared__ uint32_t s_fill, s_over, s_spec_cnt, s_spec_sum, s_last;
+  __shared__ uint32_t s_fill, s_over, s_spec_cnt, s_spec_sum, s_last, s_item;
   __shared__ unsigned long long s_red[3][kColHashThreads / 32];
-  const uint32_t s = blockIdx.x / kColParts, r = blockIdx.x % kColParts;
-  if (s >= p.nseg) return;
-  const uint32_t parts = col_parts_of(ulen[s]);
-  if (r >= parts) return;  // also: the window is not taken by the partitioned hash
-  const uint64_t b = p.base[s];
-  const uint32_t lo = bstart[(uint64_t)s * (kColParts + 1) + r], hi = bstart[(uint64_t)s * (kColParts + 1) + r + 1];
-  for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
-    t_key[i] = kColEmpty;
-    t_cnt[i] = 0;
-    t_sum[i] = 0;
-  }
-  if (threadIdx.x == 0) s_fill = s_over = s_spec_cnt = s_spec_sum = 0;
-  __syncthreads();
-  for (uint32_t u = lo + threadIdx.x; u < hi; u += kColHashThreads) {
-    if (*(volatile uint32_t*)&s_over) break;
-    const uint32_t d = pkeys[b + u];
-    const uint32_t v = pvals[b + u];
-    if (d == kColEmpty) {
-      atomicAdd(&s_spec_cnt, 1u);
-      atomicAdd(&s_spec_sum, v);
-      continue;
-    }
-    uint32_t h = fmix32(d) & (kColHashSlots - 1);
-    for (uint32_t probe = 0; probe < kColHashSlots; ++probe) {
-      uint32_t cur = *(volatile uint32_t*)&t_key[h];
-      if (cur == kColEmpty) {
-        cur = atomicCAS(&t_key[h], kColEmpty, d);
-        if (cur == kColEmpty) {
-          cur = d;
-          if (atomicAdd(&s_fill, 1u) + 1 > kColHashMaxFill) s_over = 1;
-        }
-      }
-      if (cur == d) {
-        atomicAdd(&t_cnt[h], 1u);
-        atomicAdd(&t_sum[h], v);
-        break;
-      }
-      h = (h + 1) & (kColHashSlots - 1);
-    }
-  }
-  __syncthreads();
-  ColPartAcc* a = acc + s;
-  if (!s_over) {
-    unsigned long long c = 0, mcnt = 0, msum = 0;
-    for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
-      if (t_key[i] != kColEmpty) {
-        ++c;
-        mcnt = t_cnt[i] > mcnt ? t_cnt[i] : mcnt;
-        msum = t_sum[i] > msum ? t_sum[i] : msum;
-      }
-    }
-    c = warp_sum(c);
-    mcnt = warp_max(mcnt);
-    msum = warp_max(msum);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-      s_red[0][warp] = c;
-      s_red[1][warp] = mcnt;
-      s_red[2][warp] = msum;
+  ColPartAcc* work = acc + p.nseg;
+  const uint32_t nitems = (uint32_t)work->count;  // written by k_colpart_split
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t i = atomicAdd(&work->done, 1u);
+      s_item = i < nitems ? items[i] : 0xFFFFFFFFu;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      c = 0;
-      mcnt = msum = 0;
-      for (int w = 0; w < kColHashThreads / 32; ++w) {
-        c += s_red[0][w];
-        mcnt = s_red[1][w] > mcnt ? s_red[1][w] : mcnt;
-        msum = s_red[2][w] > msum ? s_red[2][w] : msum;
+    const uint32_t item = s_item;
+    if (item == 0xFFFFFFFFu) break;
+    const uint32_t s = item / kColParts, r = item % kColParts;
+    const uint32_t parts = col_parts_of(ulen[s], s);
+    const uint64_t b = p.base[s];
+    const uint32_t lo = bstart[(uint64_t)s * (kColParts + 1) + r], hi = bstart[(uint64_t)s * (kColParts + 1) + r + 1];
+    const uint32_t* pk = pkeys + b;
+    const uint32_t* pv = pvals + b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t d[kColPartChunk], v[kColPartChunk];
+    auto load = [&](uint32_t u0) {
+#pragma unroll
+      for (int j = 0; j < kColPartChunk; ++j) {
+        const uint32_t u = u0 + (uint32_t)j * kColHashThreads + threadIdx.x;
+        d[j] = u < hi ? __ldg(pk + u) : 0u;
+        v[j] = u < hi ? __ldg(pv + u) : 0u;
       }
-      if (s_spec_cnt) {
-        ++c;
-        mcnt = s_spec_cnt > mcnt ? s_spec_cnt : mcnt;
-        msum = s_spec_sum > msum ? s_spec_sum : msum;
-      }
-      if (c) atomicAdd(&a->count, c);
-      if (mcnt) atomicMax(&a->max_fanin, mcnt);
-      if (msum) atomicMax(&a->max_packets, msum);
+    };
+    load(lo);
+    {
+      uint4* k4 = reinterpret_cast<uint4*>(t_key);
+      uint4* c4 = reinterpret_cast<uint4*>(t_cnt);  // t_cnt and t_sum, back to back
+      const uint4 empty = make_uint4(kColEmpty, kColEmpty, kColEmpty, kColEmpty), zero = make_uint4(0, 0, 0, 0);
+      for (uint32_t i = threadIdx.x; i < kColHashSlots / 4; i += kColHashThreads) k4[i] = empty;
+      for (uint32_t i = threadIdx.x; i < kColHashSlots / 2; i += kColHashThreads) c4[i] = zero;
     }
-  } else if (threadIdx.x == 0) {
-    atomicOr(&a->fail, 1u);
+    if (threadIdx.x == 0) s_fill = s_over = s_spec_cnt = s_spec_sum = 0;
+    __syncthreads();
+    constexpr uint32_t kStep = (uint32_t)kColPartChunk * kColHashThreads;
+    for (uint32_t u0 = lo; u0 < hi; u0 += kStep) {  // the same trip count for every thread
+      if (u0 != lo) load(u0);
+      if (__any_sync(0xffffffffu, *(volatile uint32_t*)&s_over != 0)) break;  // warp-uniform
+#pragma unroll
+      for (int j = 0; j < kColPartChunk; ++j) {
+        const uint32_t u = u0 + (uint32_t)j * kColHashThreads + threadIdx.x;
+        bool claimed = false;
+        if (u < hi) {
+          if (d[j] == kColEmpty) {
+            atomicAdd(&s_spec_cnt, 1u);
+            atomicAdd(&s_spec_sum, v[j]);
+          } else {
+            uint32_t h = fmix32(d[j]) & (kColHashSlots - 1);
+            for (uint32_t probe = 0; probe < kColHashSlots; ++probe) {
+              uint32_t cur = *(volatile uint32_t*)&t_key[h];
+              if (cur == kColEmpty) {
+                cur = atomicCAS(&t_key[h], kColEmpty, d[j]);
+                if (cur == kColEmpty) {
+                  cur = d[j];
+                  claimed = true;
+                }
+              }
+              if (cur == d[j]) {
+                atomicAdd(&t_cnt[h], 1u);
+                atomicAdd(&t_sum[h], v[j]);
+                break;
+              }
+              h = (h + 1) & (kColHashSlots - 1);
+            }
+          }
+        }
+        // new slots counted once per warp; past three quarters the table gives
+        // up (at most one slot per thread more can still be claimed meanwhile)
+        const uint32_t nc = __popc(__ballot_sync(0xffffffffu, claimed));
+        if (lane == 0 && nc && atomicAdd(&s_fill, nc) + nc > kColHashMaxFill) s_over = 1;
+      }
+    }
+    __syncthreads();
+    ColPartAcc* a = acc + s;
+    if (!s_over) {
+      unsigned long long c = 0, mcnt = 0, msum = 0;
+      for (uint32_t i = threadIdx.x; i < kColHashSlots; i += kColHashThreads) {
+        if (t_key[i] != kColEmpty) {
+          ++c;
+          mcnt = t_cnt[i] > mcnt ? t_cnt[i] : mcnt;
+          msum = t_sum[i] > msum ? t_sum[i] : msum;
+        }
+      }
+      c = warp_sum(c);
+      mcnt = warp_max(mcnt);
+      msum = warp_max(msum);
+      if (lane == 0) {
+        s_red[0][warp] = c;
+        s_red[1][warp] = mcnt;
+        s_red[2][warp] = msum;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        c = 0;
+        mcnt = msum = 0;
+        for (int w = 0; w < kColHashThreads / 32; ++w) {
+          c += s_red[0][w];
+          mcnt = s_red[1][w] > mcnt ? s_red[1][w] : mcnt;
+          msum = s_red[2][w] > msum ? s_red[2][w] : msum;
+        }
+        if (s_spec_cnt) {
+          ++c;
+          mcnt = s_spec_cnt > mcnt ? s_spec_cnt : mcnt;
+          msum = s_spec_sum > msum ? s_spec_sum : msum;
+        }
+        if (c) atomicAdd(&a->count, c);
+        if (mcnt) atomicMax(&a->max_fanin, mcnt);
+        if (msum) atomicMax(&a->max_packets, msum);
+      }
+    } else if (threadIdx.x == 0) {
+      atomicOr(&a->fail, 1u);
+    }
+    // The last partition of the window to arrive publishes the result.
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(&a->done, 1u) == parts - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_last) {
+      __threadfence();
+      const volatile ColPartAcc* va = a;
+      if (va->fail == 0) {
+        q[s].unique_destinations = va->count;
+        q[s].max_destination_fanin = va->max_fanin;
+        q[s].max_destination_packets = va->max_packets;
+        ulen[s] = 0;  // done: the column sort skips this window
+      }
+    }
+    __syncthreads();  // the table and the shared words are reused by the next item
   }
-  // The last partition of the window to arrive publishes the result.
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(&a->done, 1u) == parts - 1 ? 1u : 0u;
+}
+
+// ---- column statistics of one large segment (a time sum) by hash groups ---
+//
+// The column statistics only need equal destinations grouped, in any order,
+// and h = fmix32(dst) is a bijection: after the first two column passes over
+// h (its low 16 bits), the links form 2^16 groups of equal h & 0xffff, each
+// holding every link of its destinations.  Each group's distinct h (= its
+// destinations) are counted in a shared-memory table by persistent CTAs and
+// the three column quantities reduced into an accumulator.  A group of more
+// than kHGroupPartLinks links (a heavily linked destination lands all its
+// links in one group) is cut into parts counted by different CTAs, whose
+// tables are written out and merged per group afterwards.  If every table
+// fits, the last CTA publishes the quantities and sets the segment's length
+// to 0, so the two remaining column passes and the run reduction find
+// nothing to do; otherwise they complete the sort by h and count the runs.
+constexpr int kHGroupThreads = 512;
+constexpr uint32_t kHGroupSlots = 1u << 13;                   // 8192
+constexpr uint32_t kHGroupMaxFill = kHGroupSlots / 4 * 3;     // give up above this
+constexpr size_t kHGroupSmem = (size_t)kHGroupSlots * 12;     // key, links, packets
+constexpr int kHGroupChunk = 8;
+constexpr uint32_t kHNone = 0xFFFFFFFFu;
+static_assert(kHGroupPartWords == 3 * (kHGroupMaxFill + 1), "a part's entries: its table's fill and the key apart");
+
+// bnd[g] = first position of group g (g in [0, 2^16]; bnd[2^16] = n) in the
+// n = *len keys sorted by their low 16 bits.
+__global__ void __launch_bounds__(256) k_hgroup_bounds(const uint32_t* __restrict__ keys, const uint64_t* len,
+                                                       uint32_t* __restrict__ bnd) {
+  const uint64_t n = *len;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t prev = i == 0 ? -1 : (int64_t)(keys[i - 1] & 0xFFFFu);
+    const int64_t cur = i == n ? (int64_t)kHGroups : (int64_t)(keys[i] & 0xFFFFu);
+    for (int64_t g = prev + 1; g <= cur; ++g) bnd[g] = (uint32_t)i;
+  }
+}
+
+// One CTA: the work items (one per group, ceil(links / kHGroupPartLinks) per
+// group above that), their exclusive prefix item_start, the parts of the
+// groups cut in parts (prefix hpart, list heavy) and the counts in meta
+// {items, heavy groups, heavy parts}; too many heavy parts for the buffer
+// fail the hash (the column sort then finishes the job).
+__global__ void __launch_bounds__(1024) k_hgroup_plan(HGroupBufs b, uint32_t max_hparts) {
+  constexpr uint32_t kPer = kHGroups / 1024;
+  __shared__ uint32_t s_a[1024], s_b[1024], s_c[1024];
+  const uint32_t g0 = threadIdx.x * kPer;
+  uint32_t items = 0, hparts = 0, heavy = 0;
+  for (uint32_t k = 0; k < kPer; ++k) {
+    const uint32_t n = b.bnd[g0 + k + 1] - b.bnd[g0 + k];
+    const uint32_t parts = n > kHGroupPartLinks ? (n + kHGroupPartLinks - 1) / kHGroupPartLinks : 1u;
+    items += parts;
+    if (parts > 1) {
+      hparts += parts;
+      ++heavy;
+    }
+  }
+  s_a[threadIdx.x] = items;
+  s_b[threadIdx.x] = hparts;
+  s_c[threadIdx.x] = heavy;
+  __syncthreads();
+  for (uint32_t off = 1; off < 1024; off <<= 1) {  // inclusive scans (Hillis-Steele)
+    const uint32_t a = threadIdx.x >= off ? s_a[threadIdx.x - off] : 0u;
+    const uint32_t bb = threadIdx.x >= off ? s_b[threadIdx.x - off] : 0u;
+    const uint32_t c = threadIdx.x >= off ? s_c[threadIdx.x - off] : 0u;
+    __syncthreads();
+    s_a[threadIdx.x] += a;
+    s_b[threadIdx.x] += bb;
+    s_c[threadIdx.x] += c;
+    __syncthreads();
+  }
+  uint32_t ia = s_a[threadIdx.x] - items, ib = s_b[threadIdx.x] - hparts, ic = s_c[threadIdx.x] - heavy;
+  for (uint32_t k = 0; k < kPer; ++k) {
+    const uint32_t g = g0 + k;
+    const uint32_t n = b.bnd[g + 1] - b.bnd[g];
+    const uint32_t parts = n > kHGroupPartLinks ? (n + kHGroupPartLinks - 1) / kHGroupPartLinks : 1u;
+    b.item_start[g] = ia;
+    b.hpart[g] = ib;
+    ia += parts;
+    if (parts > 1) {
+      b.heavy[ic++] = g;
+      ib += parts;
+    }
+  }
+  if (threadIdx.x == 1023) {
+    b.item_start[kHGroups] = ia;
+    b.hpart[kHGroups] = ib;
+    b.meta[0] = ia;
+    b.meta[1] = ic;
+    b.meta[2] = ib;
+    if (ib > max_hparts) atomicOr(&b.acc[0].fail, 1u);
+  }
+}
+
+// Count (key, links, packets) into the group's table; true if this call took
+// a new slot.  The fill stays below the table size (the callers give up at
+// three quarters, and each thread takes at most one slot meanwhile), so a
+// slot is always found.
+__device__ __forceinline__ bool hg_insert(uint32_t* t_key, uint32_t* t_cnt, uint32_t* t_sum, uint32_t key,
+                                          uint32_t cnt, uint32_t sum) {
+  uint32_t h = (key >> 16) & (kHGroupSlots - 1);  // the group fixes the low 16 bits
+  for (uint32_t probe = 0; probe < kHGroupSlots; ++probe) {
+    uint32_t cur = *(volatile uint32_t*)&t_key[h];
+    bool claimed = false;
+    if (cur == kColEmpty) {
+      cur = atomicCAS(&t_key[h], kColEmpty, key);
+      if (cur == kColEmpty) {
+        cur = key;
+        claimed = true;
+      }
+    }
+    if (cur == key) {
+      atomicAdd(&t_cnt[h], cnt);
+      atomicAdd(&t_sum[h], sum);
+      return claimed;
+    }
+    h = (h + 1) & (kHGroupSlots - 1);
+  }
+  return false;
+}
+
+struct HGroupShared {
+  uint32_t fill, over, spec_cnt, spec_sum, item, nflush;
+  unsigned long long red[3][kHGroupThreads / 32];
+};
+
+__device__ __forceinline__ void hg_clear(uint32_t* t_key, HGroupShared& sh) {
+  uint4* k4 = reinterpret_cast<uint4*>(t_key);
+  uint4* c4 = reinterpret_cast<uint4*>(t_key + kHGroupSlots);  // t_cnt and t_sum, back to back
+  const uint4 empty = make_uint4(kColEmpty, kColEmpty, kColEmpty, kColEmpty), zero = make_uint4(0, 0, 0, 0);
+  for (uint32_t i = threadIdx.x; i < kHGroupSlots / 4; i += kHGroupThreads) k4[i] = empty;
+  for (uint32_t i = threadIdx.x; i < kHGroupSlots / 2; i += kHGroupThreads) c4[i] = zero;
+  if (threadIdx.x == 0) sh.fill = sh.over = sh.spec_cnt = sh.spec_sum = sh.nflush = 0;
+}
+
+// After an insert step of every thread of the warp: new slots counted once
+// per warp; past three quarters the table gives up.
+__device__ __forceinline__ void hg_count_fill(bool claimed, HGroupShared& sh) {
+  const uint32_t nc = __popc(__ballot_sync(0xffffffffu, claimed));
+  if ((threadIdx.x & 31) == 0 && nc && atomicAdd(&sh.fill, nc) + nc > kHGroupMaxFill) sh.over = 1;
+}
+
+// The table's (distinct keys, most links, most packets), the key counted
+// apart included, added into acc (call with the whole CTA).
+__device__ void hg_reduce(const uint32_t* t_key, const uint32_t* t_cnt, const uint32_t* t_sum, HGroupShared& sh,
+                          ColPartAcc* acc) {
+  unsigned long long c = 0, mcnt = 0, msum = 0;
+  for (uint32_t i = threadIdx.x; i < kHGroupSlots; i += kHGroupThreads) {
+    if (t_key[i] != kColEmpty) {
+      ++c;
+      mcnt = t_cnt[i] > mcnt ? t_cnt[i] : mcnt;
+      msum = t_sum[i] > msum ? t_sum[i] : msum;
+    }
+  }
+  c = warp_sum(c);
+  mcnt = warp_max(mcnt);
+  msum = warp_max(msum);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh.red[0][warp] = c;
+    sh.red[1][warp] = mcnt;
+    sh.red[2][warp] = msum;
   }
   __syncthreads();
-  if (threadIdx.x == 0 && s_last) {
+  if (threadIdx.x == 0) {
+    c = 0;
+    mcnt = msum = 0;
+    for (int w = 0; w < kHGroupThreads / 32; ++w) {
+      c += sh.red[0][w];
+      mcnt = sh.red[1][w] > mcnt ? sh.red[1][w] : mcnt;
+      msum = sh.red[2][w] > msum ? sh.red[2][w] : msum;
+    }
+    if (sh.spec_cnt) {
+      ++c;
+      mcnt = sh.spec_cnt > mcnt ? sh.spec_cnt : mcnt;
+      msum = sh.spec_sum > msum ? sh.spec_sum : msum;
+    }
+    if (c) atomicAdd(&acc->count, c);
+    if (mcnt) atomicMax(&acc->max_fanin, mcnt);
+    if (msum) atomicMax(&acc->max_packets, msum);
+  }
+}
+
+// Persistent CTAs over the work items: item i is part k of group g.  A
+// group in one part is reduced into acc[0] at once; a part of a cut group
+// writes its table's entries (key, links, packets; the key counted apart as
+// kColEmpty) to its region of hbuf and their number to hcnt.
+__global__ void __launch_bounds__(kHGroupThreads, 2) k_hgroup_hash(const uint32_t* __restrict__ keys,
+                                                                   const uint32_t* __restrict__ vals,
+                                                                   HGroupBufs b) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* t_key = sm;
+  uint32_t* t_cnt = sm + kHGroupSlots;
+  uint32_t* t_sum = sm + 2 * kHGroupSlots;
+  __shared__ HGroupShared sh;
+  const uint32_t nitems = b.meta[0];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t i = atomicAdd(&b.acc[1].done, 1u);
+      sh.item = i < nitems && *(volatile uint32_t*)&b.acc[0].fail == 0 ? i : kHNone;
+    }
+    __syncthreads();
+    const uint32_t i = sh.item;
+    if (i == kHNone) break;
+    uint32_t lo_g = 0, hi_g = kHGroups;  // the group: the last g with item_start[g] <= i
+    while (hi_g - lo_g > 1) {
+      const uint32_t mid = (lo_g + hi_g) >> 1;
+      if (b.item_start[mid] <= i) lo_g = mid; else hi_g = mid;
+    }
+    const uint32_t g = lo_g;
+    const uint32_t parts = b.item_start[g + 1] - b.item_start[g], k = i - b.item_start[g];
+    const uint32_t lo = b.bnd[g] + k * kHGroupPartLinks;
+    const uint32_t hi = min(lo + kHGroupPartLinks, b.bnd[g + 1]);
+    if (lo == hi) {  // an empty group (never cut in parts): nothing to count
+      __syncthreads();
+      continue;
+    }
+    uint32_t d[kHGroupChunk], v[kHGroupChunk];
+    auto load = [&](uint32_t u0) {
+#pragma unroll
+      for (int j = 0; j < kHGroupChunk; ++j) {
+        const uint32_t u = u0 + (uint32_t)j * kHGroupThreads + threadIdx.x;
+        d[j] = u < hi ? __ldg(keys + u) : 0u;
+        v[j] = u < hi ? __ldg(vals + u) : 0u;
+      }
+    };
+    load(lo);
+    hg_clear(t_key, sh);
+    __syncthreads();
+    constexpr uint32_t kStep = (uint32_t)kHGroupChunk * kHGroupThreads;
+    for (uint32_t u0 = lo; u0 < hi; u0 += kStep) {  // the same trip count for every thread
+      if (u0 != lo) load(u0);
+      if (__any_sync(0xffffffffu, *(volatile uint32_t*)&sh.over != 0)) break;  // warp-uniform
+#pragma unroll
+      for (int j = 0; j < kHGroupChunk; ++j) {
+        const uint32_t u = u0 + (uint32_t)j * kHGroupThreads + threadIdx.x;
+        bool claimed = false;
+        if (u < hi) {
+          if (d[j] == kColEmpty) {  // the one destination whose mix is the empty marker
+            atomicAdd(&sh.spec_cnt, 1u);
+            atomicAdd(&sh.spec_sum, v[j]);
+          } else {
+            claimed = hg_insert(t_key, t_cnt, t_sum, d[j], 1u, v[j]);
+          }
+        }
+        hg_count_fill(claimed, sh);
+      }
+    }
+    __syncthreads();
+    if (sh.over) {
+      if (threadIdx.x == 0) atomicOr(&b.acc[0].fail, 1u);
+    } else if (parts == 1) {
+      hg_reduce(t_key, t_cnt, t_sum, sh, &b.acc[0]);
+    } else {  // a part of a cut group: its entries out
+      const uint64_t pidx = (uint64_t)b.hpart[g] + k;
+      uint32_t* out = b.hbuf + pidx * kHGroupPartWords;
+      for (uint32_t e = threadIdx.x; e < kHGroupSlots; e += kHGroupThreads) {
+        if (t_key[e] != kColEmpty) {
+          const uint32_t at = atomicAdd(&sh.nflush, 1u);
+          out[3 * at] = t_key[e];
+          out[3 * at + 1] = t_cnt[e];
+          out[3 * at + 2] = t_sum[e];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t n = sh.nflush;
+        if (sh.spec_cnt) {
+          out[3 * n] = kColEmpty;
+          out[3 * n + 1] = sh.spec_cnt;
+          out[3 * n + 2] = sh.spec_sum;
+          ++n;
+        }
+        b.hcnt[pidx] = n;
+      }
+    }
+    __syncthreads();  // the table and the shared words are reused by the next item
+  }
+}
+
+// Persistent CTAs over the cut groups: each group's parts' entries merged in
+// one table and reduced into acc[0].  The last CTA to finish publishes the
+// segment's quantities unless a table overflowed.
+__global__ void __launch_bounds__(kHGroupThreads, 2) k_hgroup_merge(HGroupBufs b, uint64_t* len,
+                                                                    ans_quantities* __restrict__ q) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* t_key = sm;
+  uint32_t* t_cnt = sm + kHGroupSlots;
+  uint32_t* t_sum = sm + 2 * kHGroupSlots;
+  __shared__ HGroupShared sh;
+  const uint32_t nheavy = b.meta[1];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t j = atomicAdd(&b.acc[2].done, 1u);
+      sh.item = j < nheavy && *(volatile uint32_t*)&b.acc[0].fail == 0 ? b.heavy[j] : kHNone;
+    }
+    __syncthreads();
+    const uint32_t g = sh.item;
+    if (g == kHNone) break;
+    const uint32_t parts = b.item_start[g + 1] - b.item_start[g];
+    hg_clear(t_key, sh);
+    __syncthreads();
+    for (uint32_t k = 0; k < parts; ++k) {
+      const uint64_t pidx = (uint64_t)b.hpart[g] + k;
+      const uint32_t* in = b.hbuf + pidx * kHGroupPartWords;
+      const uint32_t n = b.hcnt[pidx];
+      for (uint32_t e0 = 0; e0 < n; e0 += kHGroupThreads) {  // the same trip count for every thread
+        if (__any_sync(0xffffffffu, *(volatile uint32_t*)&sh.over != 0)) break;
+        const uint32_t e = e0 + threadIdx.x;
+        bool claimed = false;
+        if (e < n) {
+          const uint32_t key = in[3 * e], cnt = in[3 * e + 1], sum = in[3 * e + 2];
+          if (key == kColEmpty) {
+            atomicAdd(&sh.spec_cnt, cnt);
+            atomicAdd(&sh.spec_sum, sum);
+          } else {
+            claimed = hg_insert(t_key, t_cnt, t_sum, key, cnt, sum);
+          }
+        }
+        hg_count_fill(claimed, sh);
+      }
+    }
+    __syncthreads();
+    if (sh.over) {
+      if (threadIdx.x == 0) atomicOr(&b.acc[0].fail, 1u);
+    } else {
+      hg_reduce(t_key, t_cnt, t_sum, sh, &b.acc[0]);
+    }
+    __syncthreads();  // the table and the shared words are reused by the next group
+  }
+  if (threadIdx.x == 0) {
     __threadfence();
-    const volatile ColPartAcc* va = a;
-    if (va->fail == 0) {
-      q[s].unique_destinations = va->count;
-      q[s].max_destination_fanin = va->max_fanin;
-      q[s].max_destination_packets = va->max_packets;
-      ulen[s] = 0;  // done: the column sort skips this window
+    if (atomicAdd(&b.acc[0].done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      const volatile ColPartAcc* va = b.acc;
+      if (va->fail == 0) {
+        q->unique_destinations = va->count;
+        q->max_destination_fanin = va->max_fanin;
+        q->max_destination_packets = va->max_packets;
+        *len = 0;  // done: the remaining column passes and their run reduction skip the segment
+      }
     }
   }
 }
@@ -1190,22 +1586,62 @@ cudaError_t launch_colhash(const SegPlan& p, uint64_t* ulen, const uint32_t* col
 }
 
 cudaError_t launch_colhash_part(const SegPlan& p, uint64_t* ulen, const uint32_t* col_ids, const uint32_t* vals32,
-                                uint32_t* pkeys, uint32_t* pvals, uint32_t* bstart, ColPartAcc* acc, ans_quantities* q,
-                                cudaStream_t st) {
+                                uint32_t* pkeys, uint32_t* pvals, uint32_t* bstart, ColPartAcc* acc, uint32_t* items,
+                                ans_quantities* q, cudaStream_t st) {
   if (p.nseg == 0) return cudaSuccess;
   static unsigned long long configured = 0;  // one bit per device ordinal
+  static int sms[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 64 || !((configured >> dev) & 1ull)) {
     e = cudaFuncSetAttribute(k_colhash_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColHashSmem);
     if (e != cudaSuccess) return e;
-    if (dev < 64) configured |= 1ull << dev;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) {
+      sms[dev] = n;
+      configured |= 1ull << dev;
+    }
   }
-  k_colpart_split<<<p.nseg, kSplitThreads, 0, st>>>(p, ulen, col_ids, vals32, pkeys, pvals, bstart);
+  const unsigned ctas = dev < 64 && sms[dev] > 0 ? (unsigned)sms[dev] : 1u;
+  k_colpart_split<<<p.nseg, kSplitThreads, 0, st>>>(p, ulen, col_ids, vals32, pkeys, pvals, bstart, acc + p.nseg,
+                                                    items);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_colhash_part<<<p.nseg * kColParts, kColHashThreads, kColHashSmem, st>>>(p, ulen, pkeys, pvals, bstart, acc, q);
+  k_colhash_part<<<ctas, kColHashThreads, kColHashSmem, st>>>(p, ulen, pkeys, pvals, bstart, acc, items, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hgroup_stats(const uint32_t* keys, const uint32_t* vals32, uint64_t* len, const HGroupBufs& b,
+                                uint32_t max_hparts, ans_quantities* q, cudaStream_t st) {
+  static unsigned long long configured = 0;  // one bit per device ordinal
+  static int sms[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !((configured >> dev) & 1ull)) {
+    e = cudaFuncSetAttribute(k_hgroup_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHGroupSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_hgroup_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHGroupSmem);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) {
+      sms[dev] = n;
+      configured |= 1ull << dev;
+    }
+  }
+  const unsigned ctas = 2u * (dev < 64 && sms[dev] > 0 ? (unsigned)sms[dev] : 1u);
+  k_hgroup_bounds<<<ctas * 4, 256, 0, st>>>(keys, len, b.bnd);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_hgroup_plan<<<1, 1024, 0, st>>>(b, max_hparts);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_hgroup_hash<<<ctas, kHGroupThreads, kHGroupSmem, st>>>(keys, vals32, b);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_hgroup_merge<<<ctas, kHGroupThreads, kHGroupSmem, st>>>(b, len, q);
   return cudaGetLastError();
 }
 
@@ -1268,10 +1704,17 @@ cudaError_t launch_scan_u64(const SegPlan& p, const uint64_t* in, uint64_t* out,
 
 cudaError_t launch_finish(const StatsArgs& a, cudaStream_t st) {
   if (a.plan.ntiles == 0) return cudaSuccess;
+  const bool h = a.col_hkeys != nullptr;
   switch (a.mode) {
-    case kModeWindow: k_finish<kModeWindow><<<a.plan.ntiles, kThreads, 0, st>>>(a); break;
-    case kModeSum: k_finish<kModeSum><<<a.plan.ntiles, kThreads, 0, st>>>(a); break;
-    default: k_finish<kModeMatrix><<<a.plan.ntiles, kThreads, 0, st>>>(a); break;
+    case kModeWindow:
+      if (h) k_finish<kModeWindow, true><<<a.plan.ntiles, kThreads, 0, st>>>(a);
+      else k_finish<kModeWindow, false><<<a.plan.ntiles, kThreads, 0, st>>>(a);
+      break;
+    case kModeSum:
+      if (h) k_finish<kModeSum, true><<<a.plan.ntiles, kThreads, 0, st>>>(a);
+      else k_finish<kModeSum, false><<<a.plan.ntiles, kThreads, 0, st>>>(a);
+      break;
+    default: k_finish<kModeMatrix, false><<<a.plan.ntiles, kThreads, 0, st>>>(a); break;
   }
   return cudaGetLastError();
 }

@@ -7,10 +7,13 @@ For each workload:
   the time sum): every window's nine quantities, and the whole time-summed
   DCSR -- checked row slice by row slice against the oracle's matrix of the
   packets whose sources fall in the slice -- with the sum's quantities;
-* the same batch with the other time-sum paths (every one on the
-  1024-window workload, one on the 2^30-packet workload), the last with
-  per-window matrices: their time sums again, and the DCSR of every window
-  (1024-window workload) or of 130 windows (2^30-packet workload).
+* the same batch on other (aggregation, time-sum) paths -- on the
+  1024-window workload every time-sum path with the window sort and the
+  windows from the packet sort, on the 2^30-packet workload the window sort
+  with merge rounds (and the windows from the packet sort, unless tuned) --
+  the last with per-window matrices: their time sums again, and the DCSR of
+  every window (1024-window workload) or of 130 windows (2^30-packet
+  workload).
 Tolerance 0: every output is an integer with one correct value.
 """
 import numpy as np
@@ -45,19 +48,19 @@ def test_full_size_batch_against_oracle(cfg):
     try:
         tuned = ctx.autotune(src, dst, w.offsets, flags=ans.BATCH_SUM)
         _, summ, q = _run(ans, ctx, src, dst, w, ans.BATCH_SUM)
-        results.append((f"bench paths (sum_path {tuned['sum_path']})", summ.to_numpy(), summ.quantities()))
+        mine = (tuned["agg_path"], 2 if tuned["agg_path"] == 3 else tuned["sum_path"])
+        results.append((f"bench paths (agg_path {mine[0]}, sum_path {mine[1]})", summ.to_numpy(), summ.quantities()))
         summ.free()
-        # the other time-sum paths (all of them on the 1024-window workload;
-        # the merge rounds, or else the packet re-sort, on the 2^30-packet one),
-        # the last with per-window matrices
-        others = [p for p in (0, 1, 2) if p != tuned["sum_path"]]
-        if cfg == 4:
-            others = others[:1]
-        for k, sp in enumerate(others):
-            ctx.set_tuning(sum_path=sp)
+        # other (aggregation, time-sum) paths, the last with per-window matrices
+        if cfg == 3:
+            others = [x for x in [(0, 0), (0, 1), (0, 2), (3, 2)] if x != mine]
+        else:
+            others = [x for x in [(3, 2), (0, 0)] if x != mine]
+        for k, (ap, sp) in enumerate(others):
+            ctx.set_tuning(agg_path=ap, sum_path=sp)
             last = k == len(others) - 1
             mats, summ2, q2 = _run(ans, ctx, src, dst, w, ans.BATCH_SUM | (ans.BATCH_MATRICES if last else 0))
-            results.append((f"sum_path {sp}", summ2.to_numpy(), summ2.quantities()))
+            results.append((f"agg_path {ap}, sum_path {sp}", summ2.to_numpy(), summ2.quantities()))
             summ2.free()
             assert q2 == q
         rng = np.random.default_rng(cfg)
