@@ -143,7 +143,13 @@ int ans_network_quantities(ans_ctx* ctx, const ans_matrix* m, ans_quantities* ou
 /* Batched analysis of nwin windows stored back to back (Sec. III-C batching,
  * taken to its limit: every window of the batch in one fixed launch sequence).
  *   d_src, d_dst : device arrays; window w is packets [d_offsets[w],
- *                  d_offsets[w+1]) of them.
+ *                  d_offsets[w+1]) of them.  They may also be page-locked
+ *                  host memory that the device addresses (cudaHostAlloc or
+ *                  cudaHostRegister): the kernels then read the pairs in
+ *                  place over the host link, so the host-to-device transfer
+ *                  happens inside the batch, without a staging copy.  With
+ *                  agg_path 3 the pairs are read exactly once (by the packet
+ *                  pack); the other paths read them once or twice.
  *   d_offsets    : DEVICE array of nwin + 1 nondecreasing uint64 offsets
  *                  (d_offsets[0] may be nonzero).  The batch is planned on the
  *                  device (window lengths, tile table, padded starts: one
@@ -373,7 +379,10 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
  * windows, together with sum_path 2) by the batch's device time as submitted with
  * `flags` (ANS_BATCH_* bits of the batches the context will run; one CUDA
  * graph with its concurrent branches, between CUDA events on `stream`, the
- * host's planning included).  An optional path whose trial cannot get its
+ * host's planning included).  With those paths fixed, it last retries the
+ * column passes' shape (when the chosen paths run column passes) and, with
+ * agg_path 3, the key passes' ranking mode, by the same device time.  An
+ * optional path whose trial cannot get its
  * device memory (ANS_ERR_OOM / ANS_ERR_BUDGET) is skipped; the call fails
  * with ANS_ERR_OOM only if the default paths do not fit.  The choice is
  * applied to the context and returned in *chosen (optional).  The call

@@ -163,6 +163,18 @@ def _dev_ptr(x) -> int:
     return x.data_ptr()
 
 
+def _pairs_ptr(x) -> int:
+    """Address of a packet array the kernels may read: a CUDA tensor, or a
+    page-locked host tensor (read in place over the host link)."""
+    if isinstance(x, int):
+        return x
+    if x.device.type == "cpu" and x.is_pinned():
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    return _dev_ptr(x)
+
+
 class _DevView:
     """Wrap a raw device pointer for torch.as_tensor (CUDA array interface)."""
 
@@ -397,7 +409,9 @@ class Context:
     def batch_submit(self, src, dst, offsets, flags: int = 0, out=None, stream=None, want_ticket: bool = True):
         """Analyse windows [offsets[w], offsets[w+1]) of (src, dst).
 
-        ``offsets``: nwin + 1 uint64 offsets -- a CUDA tensor (int64/uint64,
+        ``src``, ``dst``: int32 tensors on the device, or in page-locked host
+        memory (the kernels then read the pairs in place over the host link,
+        with no staging copy).  ``offsets``: nwin + 1 uint64 offsets -- a CUDA tensor (int64/uint64,
         read on the device: ans_batch_submit) or a host array-like
         (ans_batch_submit_host).  ``out``: optional tensor of nwin x 9 int64
         (device or pinned host) receiving the quantities.  Returns
@@ -417,10 +431,10 @@ class Context:
         tail = (nwin, int(flags), outp, per, C.byref(sm) if sm is not None else None,
                 C.byref(tk) if tk is not None else None, _vp(_stream(stream)))
         if on_device:
-            _check(self._lib.ans_batch_submit(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)),
+            _check(self._lib.ans_batch_submit(self._h, _vp(_pairs_ptr(src)), _vp(_pairs_ptr(dst)),
                                               _vp(offsets.data_ptr()), *tail), "batch_submit", self._h)
         else:
-            _check(self._lib.ans_batch_submit_host(self._h, _vp(_dev_ptr(src)), _vp(_dev_ptr(dst)),
+            _check(self._lib.ans_batch_submit_host(self._h, _vp(_pairs_ptr(src)), _vp(_pairs_ptr(dst)),
                                                    offs.ctypes.data_as(C.POINTER(_u64)), *tail),
                    "batch_submit_host", self._h)
         mats = [Matrix(per[i]) for i in range(nwin)] if per is not None else None

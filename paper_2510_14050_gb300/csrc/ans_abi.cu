@@ -387,8 +387,17 @@ struct UploadSet {
       s.size = want;
     }
     std::memcpy(s.h, img.data(), img.size());
-    for (const Item& it : items)
-      ANS_CUDA(cudaMemcpyAsync(it.dst, (char*)s.h + it.off, it.bytes, cudaMemcpyHostToDevice, st));
+    // copied by kernels reading the pinned slot in place: a copy-engine
+    // transfer would queue behind bulk copies of other streams
+    SmallCopyBatch b;
+    for (const Item& it : items) {
+      b.it[b.n++] = SmallCopyItem{it.dst, (const char*)s.h + it.off, it.bytes};
+      if (b.n == kSmallCopyItems) {
+        ANS_CUDA(launch_small_copy(b, st));
+        b.n = 0;
+      }
+    }
+    ANS_CUDA(launch_small_copy(b, st));
     ANS_CUDA(cudaEventRecord(s.ev, st));
     items.clear();
     img.clear();
@@ -1087,12 +1096,13 @@ int regroup_windows(ans_ctx* c, char* m, const PipeScratch& ps, const SegPlan& p
 }
 
 // Snapshot the device error word into `dst` (device); reset_err clears it.
+// (kernels: no copy engine, see UploadSet)
 int capture_err(ans_ctx* c, uint32_t* dst_dev, cudaStream_t st) {
-  ANS_CUDA(cudaMemcpyAsync(dst_dev, c->d_err, 4, cudaMemcpyDeviceToDevice, st));
+  ANS_CUDA(launch_copy_word(dst_dev, c->d_err, st));
   return ANS_OK;
 }
 int reset_err(ans_ctx* c, cudaStream_t st) {
-  ANS_CUDA(cudaMemsetAsync(c->d_err, 0, 4, st));
+  ANS_CUDA(launch_zero(c->d_err, 4, st));
   return ANS_OK;
 }
 
@@ -1110,8 +1120,23 @@ int new_ticket(ans_ctx* c, cudaStream_t st, ans_ticket* out) {
   return ANS_OK;
 }
 
+// The quantities to the caller's array: by a kernel when the device can
+// address it (its own memory, page-locked or managed host memory; see
+// UploadSet for why not the copy engines), else by cudaMemcpyAsync.
 int copy_quantities_out(ans_quantities* out, const ans_quantities* src, size_t n, cudaStream_t st) {
   if (!out || n == 0) return ANS_OK;
+  cudaPointerAttributes pa{};
+  int dev = -1;
+  const bool known = cudaPointerGetAttributes(&pa, out) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess;
+  if (!known) cudaGetLastError();
+  const bool addressable = known && (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeManaged ||
+                                     (pa.type == cudaMemoryTypeDevice && pa.device == dev));
+  if (addressable) {
+    SmallCopyBatch b;
+    b.it[b.n++] = SmallCopyItem{pa.devicePointer ? pa.devicePointer : out, src, n * sizeof(ans_quantities)};
+    ANS_CUDA(launch_small_copy(b, st));
+    return ANS_OK;
+  }
   ANS_CUDA(cudaMemcpyAsync(out, src, n * sizeof(ans_quantities), cudaMemcpyDefault, st));
   return ANS_OK;
 }
@@ -2803,8 +2828,53 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
     sum_path = sum_for[agg_path];
   }
 
+  // With the paths chosen, the column passes' shape (on the large time sums
+  // they order the summed links by destination hash) and, when the windows
+  // come from the packet sort, the ranking of its passes: each by the
+  // batch's device time as the production path runs it.
+  SortCfg bk = variants[bk_i], bc = variants[bc_i];
+  const SortCfg bv = variants[bv_i];
+  {
+    auto chosen_paths = [&] {
+      base();
+      c->cfg_keys = bk;
+      c->cfg_col = bc;
+      c->win_path = win_path;
+      c->cfg_win = win_cfg;
+      c->sum_path = sum_path;
+      c->agg_path = agg_path;
+      c->merge_tile = merge_tile;
+    };
+    Prof pr;
+    bool ran = false;
+    ANS_TRY(trial(chosen_paths, &pr, &ran));
+    double best_wall = ran ? pr[kWall] : kNever;
+    if (ran && get(pr, "onesweep_col") > 0) {
+      const SortCfg cv[6] = {{512, kRankMatch, 1}, {512, kRankBallot, 1}, {512, kRankMatch, 2},
+                             {512, kRankBallot, 2}, {256, kRankMatch, 4}, {256, kRankBallot, 4}};
+      for (const SortCfg& v : cv) {
+        if (v.threads == bc.threads && v.rank == bc.rank && v.blocks == bc.blocks) continue;
+        ANS_TRY(trial([&] { chosen_paths(); c->cfg_col = v; }, &pr, &ran));
+        if (ran && pr[kWall] < best_wall) {
+          best_wall = pr[kWall];
+          bc = v;
+        }
+      }
+    }
+    if (agg_path == 3) {
+      for (int r = kRankMatch; r <= kRankBallot; ++r) {
+        if (r == bk.rank) continue;
+        const SortCfg v{bk.threads, r, bk.blocks};
+        ANS_TRY(trial([&] { chosen_paths(); c->cfg_keys = v; }, &pr, &ran));
+        if (ran && pr[kWall] < best_wall) {
+          best_wall = pr[kWall];
+          bk = v;
+        }
+      }
+    }
+  }
+
   ans_tuning res{};
-  const SortCfg bk = variants[bk_i], bv = variants[bv_i], bc = variants[bc_i];
   res.key_threads = (uint32_t)bk.threads;
   res.key_rank = (uint32_t)bk.rank;
   res.key_blocks = (uint32_t)bk.blocks;

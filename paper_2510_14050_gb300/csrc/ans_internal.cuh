@@ -437,6 +437,23 @@ cudaError_t launch_hgroup_stats(const uint32_t* keys, const uint32_t* vals32, ui
 cudaError_t launch_tile_seg(const SegPlan& p, uint32_t* tile_seg, cudaStream_t st);
 // Zero `bytes` bytes at p (4-byte aligned pointer); a kernel, unlike a memset.
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+// Copies of small arrays by a kernel instead of the copy engines (so they
+// never queue behind other streams' bulk transfers): item i copies bytes from
+// src to dst, either of which may be page-locked host memory (read or written
+// in place) or device memory.  At most kSmallCopyItems items per launch.
+constexpr int kSmallCopyItems = 16;
+struct SmallCopyItem {
+  void* dst;
+  const void* src;
+  uint64_t bytes;
+};
+struct SmallCopyBatch {
+  uint32_t n = 0;
+  SmallCopyItem it[kSmallCopyItems];
+};
+cudaError_t launch_small_copy(const SmallCopyBatch& b, cudaStream_t st);
+// *dst = *src for one device word, by a kernel.
+cudaError_t launch_copy_word(uint32_t* dst, const uint32_t* src, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.
 cudaError_t launch_empty_fixup(const StatsArgs& a, cudaStream_t st);
 

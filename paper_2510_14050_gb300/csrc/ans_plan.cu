@@ -111,7 +111,60 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(const uint64_t* __restric
   }
 }
 
+// Small arrays copied by a kernel (host plans and descriptors to the device,
+// quantities out): CTA (x, i) copies bytes [x * kSmallCopyChunk, (x + 1) *
+// kSmallCopyChunk) of item i; either side may be page-locked host memory,
+// which the device reads and writes in place.  A kernel, not a copy-engine
+// transfer, so these copies never queue behind another stream's bulk copies
+// (e.g. the next batch's packets arriving meanwhile).
+constexpr uint64_t kSmallCopyChunk = 1u << 16;
+__global__ void __launch_bounds__(256) k_small_copy(SmallCopyBatch b) {
+  if (blockIdx.y >= b.n) return;
+  const SmallCopyItem it = b.it[blockIdx.y];
+  const uint64_t lo = (uint64_t)blockIdx.x * kSmallCopyChunk;
+  if (lo >= it.bytes) return;
+  const uint64_t hi = umin64(lo + kSmallCopyChunk, it.bytes);
+  uint8_t* dst = static_cast<uint8_t*>(it.dst);
+  const uint8_t* src = static_cast<const uint8_t*>(it.src);
+  uint64_t i = lo;
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15u) == 0) {
+    // 16-byte vectors, four loads in flight per thread
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    const uint64_t v_lo = lo / 16, v_hi = hi / 16;
+    uint64_t v = v_lo + threadIdx.x;
+    for (; v + 3 * blockDim.x < v_hi; v += 4 * blockDim.x) {
+      uint4 x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[k] = s4[v + k * blockDim.x];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d4[v + k * blockDim.x] = x[k];
+    }
+    for (; v < v_hi; v += blockDim.x) d4[v] = s4[v];
+    i = v_hi * 16;
+  }
+  for (i += threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
+}
+
+// One 32-bit word copied on the device (error-word snapshots).
+__global__ void k_copy_word(uint32_t* dst, const uint32_t* src) { *dst = *src; }
+
 }  // namespace
+
+cudaError_t launch_small_copy(const SmallCopyBatch& b, cudaStream_t st) {
+  if (b.n == 0) return cudaSuccess;
+  if (b.n > kSmallCopyItems) return cudaErrorInvalidValue;
+  uint64_t chunks = 1;
+  for (uint32_t i = 0; i < b.n; ++i) chunks = umax64(chunks, (b.it[i].bytes + kSmallCopyChunk - 1) / kSmallCopyChunk);
+  if (chunks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  k_small_copy<<<dim3((unsigned)chunks, b.n), 256, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_word(uint32_t* dst, const uint32_t* src, cudaStream_t st) {
+  k_copy_word<<<1, 1, 0, st>>>(dst, src);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_plan(const uint64_t* d_offsets, uint32_t nseg, uint64_t cap, const DevPlanOut& o, uint32_t* err,
                         cudaStream_t st) {

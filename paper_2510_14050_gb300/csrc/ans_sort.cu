@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kT, kMinB)
   uint8_t* s_cnt = smem + (size_t)kTT * sizeof(K) + (kVals ? (size_t)kTT * sizeof(V) : 0);
   uint32_t* s_wc = reinterpret_cast<uint32_t*>(s_cnt);   // [kW][kRadix+1] (match / ballot ranking)
   uint64_t* s_tab = reinterpret_cast<uint64_t*>(s_cnt);  // [kW][kRadix]   (table ranking)
-  __shared__ uint64_t s_gofs[kRadix];
+  __shared__ uint32_t s_grel[kRadix];
   __shared__ uint32_t s_dstart[kRadix];
   __shared__ uint32_t s_hv[kRadix];
   __shared__ uint64_t s_tmp[8];
@@ -209,7 +209,14 @@ __global__ void __launch_bounds__(kT, kMinB)
   }
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int shift = pass * kRadixBits;
+  // The pass's digit is one byte of the key: byte pass % 4 of its low or
+  // (64-bit keys, pass >= 4) high word, extracted by one byte permute.
+  const bool dig_hi = sizeof(K) == 8 && pass >= 4;
+  const uint32_t dig_sel = 0x4440u | (uint32_t)(pass & 3);
+  auto digit = [&](K key) -> uint32_t {
+    if constexpr (sizeof(K) == 8) return __byte_perm(dig_hi ? (uint32_t)(key >> 32) : (uint32_t)key, 0u, dig_sel);
+    else return __byte_perm((uint32_t)key, 0u, dig_sel);
+  };
   uint32_t* wc = s_wc + warp * (kRadix + 1);
   uint64_t* tab = s_tab + warp * kRadix;
   if constexpr (kRank == kRankTable) {
@@ -243,131 +250,150 @@ __global__ void __launch_bounds__(kT, kMinB)
     else if constexpr (kPackV) r[i] = (r[i] & 0xFFFF0000u) | x;
     else r[i] = x;
   };
-#pragma unroll
-  for (int i = 0; i < kP; ++i) {
-    const uint32_t idx = wbase + i * 32 + lane;
-    const bool valid = idx < tl.count;
-    if constexpr (kPackK) {
-      r[i] = valid ? (uint32_t)kin[g0 + idx] : 0u;
-    } else {
-      k[i] = valid ? kin[g0 + idx] : K(0);
-      r[i] = 0;
-    }
-    if constexpr (kPackV) r[i] = valid ? (uint32_t)vin[g0 + idx] << 16 : 0u;
-    else if constexpr (kVals) v[i] = valid ? vin[g0 + idx] : V(0);
-  }
-  // Stable rank inside (warp, digit): lanes with equal digits find each other
-  // (digit_peers); the lowest lane updates the warp's counter.
-#pragma unroll
-  for (int i = 0; i < kP; ++i) {
-    const uint32_t idx = wbase + i * 32 + lane;
-    const bool valid = idx < tl.count;
-    if constexpr (kRank == kRankTable) {
-      // Each lane sets its bit in its digit's entry; every lane then reads
-      // the entry (the lanes sharing its digit, and the digit's count so
-      // far), and the lowest of them advances the count and clears the bits.
-      const uint32_t d = (uint32_t)(key_of(i) >> shift) & 0xffu;
-      if (valid) atomicOr(reinterpret_cast<unsigned int*>(tab + d), 1u << lane);
-      __syncwarp();
-      const uint64_t e = valid ? tab[d] : 0ull;
-      __syncwarp();
-      const uint32_t peers = (uint32_t)e, old = (uint32_t)(e >> 32);
-      if (valid && lane == __ffs(peers) - 1) tab[d] = (uint64_t)(old + __popc(peers)) << 32;
-      __syncwarp();
-      set_rank(i, old + __popc(peers & lanemask_lt()));
-    } else if (atomic_rank) {
-      // The first pass needs no stability (any order of equal digits is a
-      // valid start for the stable passes after it): one shared-memory
-      // atomic per key gives each its slot among the warp's equal digits.
-      const uint32_t d = (uint32_t)(key_of(i) >> shift) & 0xffu;
-      set_rank(i, valid ? atomicAdd(&wc[d], 1u) : 0u);
-    } else {
-      const uint32_t d = valid ? (uint32_t)(key_of(i) >> shift) & 0xffu : (uint32_t)kRadix;
-      const uint32_t peers = digit_peers<kRank>(d, valid);
-      const int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-      if (valid && lane == leader) {
-        old = wc[d];
-        wc[d] = old + __popc(peers);
-      }
-      __syncwarp();
-      old = __shfl_sync(0xffffffffu, old, valid ? leader : lane);
-      set_rank(i, old + __popc(peers & lanemask_lt()));
-    }
-  }
-  __syncthreads();
 
-  // Per digit: exclusive offsets across warps and the tile's count.
-  const int d = threadIdx.x;
-  uint32_t cnt = 0;
-  uint64_t excl = 0;
-  if (d < kRadix) {
-#pragma unroll 4
-    for (int w = 0; w < kW; ++w) {
-      if constexpr (kRank == kRankTable) {
-        const uint32_t c = (uint32_t)(s_tab[w * kRadix + d] >> 32);
-        s_tab[w * kRadix + d] = (uint64_t)cnt << 32;
-        cnt += c;
+  // Everything from the loads to the write-out, compiled twice: for a full
+  // sub-tile (every item valid: no bounds tests, no inactive lanes) and for
+  // the last, partial one of a segment.
+  auto run = [&](auto full_tag) {
+    constexpr bool kFull = decltype(full_tag)::value;
+    auto valid_at = [&](uint32_t idx) -> bool {
+      if constexpr (kFull) return true;
+      else return idx < tl.count;
+    };
+#pragma unroll
+    for (int i = 0; i < kP; ++i) {
+      const uint32_t idx = wbase + i * 32 + lane;
+      const bool valid = valid_at(idx);
+      if constexpr (kPackK) {
+        r[i] = valid ? (uint32_t)kin[g0 + idx] : 0u;
       } else {
-        const uint32_t c = s_wc[w * (kRadix + 1) + d];
-        s_wc[w * (kRadix + 1) + d] = cnt;
-        cnt += c;
+        k[i] = valid ? kin[g0 + idx] : K(0);
+        r[i] = 0;
+      }
+      if constexpr (kPackV) r[i] = valid ? (uint32_t)vin[g0 + idx] << 16 : 0u;
+      else if constexpr (kVals) v[i] = valid ? vin[g0 + idx] : V(0);
+    }
+    // Stable rank inside (warp, digit): lanes with equal digits find each
+    // other (digit_peers); every lane reads its digit's count so far, the
+    // lowest lane of the digit advances it.
+#pragma unroll
+    for (int i = 0; i < kP; ++i) {
+      const uint32_t idx = wbase + i * 32 + lane;
+      const bool valid = valid_at(idx);
+      if constexpr (kRank == kRankTable) {
+        // Each lane sets its bit in its digit's entry; every lane then reads
+        // the entry (the lanes sharing its digit, and the digit's count so
+        // far), and the lowest of them advances the count and clears the bits.
+        const uint32_t d = digit(key_of(i));
+        if (valid) atomicOr(reinterpret_cast<unsigned int*>(tab + d), 1u << lane);
+        __syncwarp();
+        const uint64_t e = valid ? tab[d] : 0ull;
+        __syncwarp();
+        const uint32_t peers = (uint32_t)e, old = (uint32_t)(e >> 32);
+        if (valid && lane == __ffs(peers) - 1) tab[d] = (uint64_t)(old + __popc(peers)) << 32;
+        __syncwarp();
+        set_rank(i, old + __popc(peers & lanemask_lt()));
+      } else if (atomic_rank) {
+        // The first pass needs no stability (any order of equal digits is a
+        // valid start for the stable passes after it): one shared-memory
+        // atomic per key gives each its slot among the warp's equal digits.
+        const uint32_t d = digit(key_of(i));
+        set_rank(i, valid ? atomicAdd(&wc[d], 1u) : 0u);
+      } else {
+        // (inactive lanes of a partial tile share the spare digit kRadix)
+        const uint32_t d = valid ? digit(key_of(i)) : (uint32_t)kRadix;
+        const uint32_t peers = digit_peers<kRank>(d, valid);
+        const uint32_t old = wc[d];
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) wc[d] = old + __popc(peers);
+        __syncwarp();
+        set_rank(i, old + __popc(peers & lanemask_lt()));
       }
     }
-    uint64_t* my = st_cur + (uint64_t)u * kRadix + d;
-    if (tl.j == 0 && half == 0) {
-      st_relaxed(my, kFlagPre | cnt);
-    } else {
-      st_relaxed(my, kFlagAgg | cnt);
-      excl = lookback(st_cur + d, kRadix, kSub * (t - tl.j), u, err);
-      st_relaxed(my, kFlagPre | (excl + cnt));
+    __syncthreads();
+
+    // Per digit: exclusive offsets across warps and the tile's count.
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+    uint64_t excl = 0;
+    if (d < kRadix) {
+#pragma unroll 4
+      for (int w = 0; w < kW; ++w) {
+        if constexpr (kRank == kRankTable) {
+          const uint32_t c = (uint32_t)(s_tab[w * kRadix + d] >> 32);
+          s_tab[w * kRadix + d] = (uint64_t)cnt << 32;
+          cnt += c;
+        } else {
+          const uint32_t c = s_wc[w * (kRadix + 1) + d];
+          s_wc[w * (kRadix + 1) + d] = cnt;
+          cnt += c;
+        }
+      }
+      uint64_t* my = st_cur + (uint64_t)u * kRadix + d;
+      if (tl.j == 0 && half == 0) {
+        st_relaxed(my, kFlagPre | cnt);
+      } else {
+        st_relaxed(my, kFlagAgg | cnt);
+        excl = lookback(st_cur + d, kRadix, kSub * (t - tl.j), u, err);
+        st_relaxed(my, kFlagPre | (excl + cnt));
+      }
     }
-  }
-  // one scan for both: the digit's start in this tile (low half) and in the
-  // segment (high half; the segment holds fewer than 2^31 keys)
-  uint32_t hv = 0;
-  if (d < kRadix) {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    hv = s_hv[d];  // this thread's own copy
-  }
-  const uint64_t both = scan256_excl64(((uint64_t)hv << 32) | (d < kRadix ? cnt : 0u), s_tmp);
-  const uint32_t dstart = (uint32_t)both, bstart = (uint32_t)(both >> 32);
-  if (d < kRadix) {
-    s_dstart[d] = dstart;
-    s_gofs[d] = tl.base + bstart + excl - dstart;  // + position in the sorted tile
-  }
-  __syncthreads();
+    // one scan for both: the digit's start in this tile (low half) and in the
+    // segment (high half; the segment holds fewer than 2^31 keys)
+    uint32_t hv = 0;
+    if (d < kRadix) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      hv = s_hv[d];  // this thread's own copy
+    }
+    const uint64_t both = scan256_excl64(((uint64_t)hv << 32) | (d < kRadix ? cnt : 0u), s_tmp);
+    const uint32_t dstart = (uint32_t)both, bstart = (uint32_t)(both >> 32);
+    if (d < kRadix) {
+      s_dstart[d] = dstart;
+      // sorted tile position i of a key with digit d goes to segment
+      // position s_grel[d] + i (exact modulo 2^32: the sum lies below 2^31)
+      s_grel[d] = bstart + (uint32_t)excl - dstart;
+    }
+    __syncthreads();
 
 #pragma unroll
-  for (int i = 0; i < kP; ++i) {
-    const uint32_t idx = wbase + i * 32 + lane;
-    if (idx < tl.count) {
-      const K key = key_of(i);
-      const uint32_t dg = (uint32_t)(key >> shift) & 0xffu;
-      const uint32_t woff = kRank == kRankTable ? (uint32_t)(tab[dg] >> 32) : wc[dg];
-      const uint32_t pos = s_dstart[dg] + woff + rank_of(i);
-      s_keys[pos] = key;
-      if constexpr (kVals) s_vals[pos] = val_of(i);
+    for (int i = 0; i < kP; ++i) {
+      const uint32_t idx = wbase + i * 32 + lane;
+      if (valid_at(idx)) {
+        const K key = key_of(i);
+        const uint32_t dg = digit(key);
+        const uint32_t woff = kRank == kRankTable ? (uint32_t)(tab[dg] >> 32) : wc[dg];
+        const uint32_t pos = s_dstart[dg] + woff + rank_of(i);
+        s_keys[pos] = key;
+        if constexpr (kVals) s_vals[pos] = val_of(i);
+      }
     }
-  }
-  __syncthreads();
-  // write-out: sorted tile position i of a key with digit d goes to
-  // s_gofs[d] + i (plus the key's remap offset)
-  auto put = [&](uint32_t i) {
-    const K key = s_keys[i];
-    uint64_t o = s_gofs[(uint32_t)(key >> shift) & 0xffu] + i;
-    if constexpr (kPackK) {
-      if (remap) o += remap[umin64((uint64_t)key, (uint64_t)nremap - 1)];
-    }
-    if (kout) kout[o] = key;
-    if constexpr (kVals) vout[o] = s_vals[i];
-  };
-  if (tl.count == kTT) {  // a full tile: a fixed trip count the compiler unrolls
+    __syncthreads();
+    // write-out: runs of equal digits go to contiguous segment positions
+    K* ko = kout ? kout + tl.base : nullptr;
+    [[maybe_unused]] V* vo = kVals ? vout + tl.base : nullptr;
+    auto put = [&](uint32_t i) {
+      const K key = s_keys[i];
+      const uint32_t rel = s_grel[digit(key)] + i;
+      if constexpr (kPackK) {
+        if (remap) {
+          const uint64_t o = tl.base + rel + remap[umin64((uint64_t)key, (uint64_t)nremap - 1)];
+          if (kout) kout[o] = key;
+          if constexpr (kVals) vout[o] = s_vals[i];
+          return;
+        }
+      }
+      if (ko) ko[rel] = key;
+      if constexpr (kVals) vo[rel] = s_vals[i];
+    };
+    if constexpr (kFull) {  // a fixed trip count the compiler unrolls
 #pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < kTT; i += kT) put(i);
-  } else {
-    for (uint32_t i = threadIdx.x; i < tl.count; i += kT) put(i);
-  }
+      for (uint32_t i = threadIdx.x; i < kTT; i += kT) put(i);
+    } else {
+      for (uint32_t i = threadIdx.x; i < tl.count; i += kT) put(i);
+    }
+  };
+  if (tl.count == kTT) run(std::true_type{});
+  else run(std::false_type{});
 }
 
 // Last row r of matrix m with row_ptr[r] <= u.

@@ -465,6 +465,40 @@ def test_windows_from_the_packet_sort(ans, synth, sum_path):
         c.close()
 
 
+@pytest.mark.parametrize("agg_path", [0, 1, 2, 3])
+def test_pairs_read_in_place_from_pinned_host_memory(ans, synth, agg_path):
+    """The packet arrays given as page-locked host memory: the kernels read
+    them in place over the host link.  Exact against the oracle on every
+    aggregation path, with host and device offsets, with the arrays at an
+    offset that breaks 16-byte alignment, and equal to the same batch from
+    device copies of the arrays."""
+    c = ans.Context(0)
+    try:
+        c.set_tuning(agg_path=agg_path, sum_path=2 if agg_path >= 2 else 0)
+        w = synth.generate(5, sizes=[0, 1, 8191, 8193, 40000, 0, 131072], first_window=21)
+        one = np.ones(1, dtype=np.uint32)
+        src_h = torch.from_numpy(np.concatenate([7 * one, w.src]).view(np.int32))
+        dst_h = torch.from_numpy(np.concatenate([9 * one, w.dst]).view(np.int32))
+        assert src_h.numel() == w.total + 1 and dst_h.numel() == w.total + 1
+        src_h, dst_h = src_h.pin_memory(), dst_h.pin_memory()
+        offs = w.offsets + 1  # the first pair of each array is not part of the batch
+        exp_mats, exp_q, exp_sum = oracle.batch(w.src, w.dst, w.offsets)
+        for offsets in (offs, torch.from_numpy(offs.astype(np.int64)).cuda()):
+            for flags in (ans.BATCH_MATRICES | ans.BATCH_SUM, ans.BATCH_SUM):
+                out = torch.zeros((w.nwin, 9), dtype=torch.int64, device="cuda")
+                mats, summ, tk = c.batch_submit(src_h, dst_h, offsets, flags, out=out)
+                c.wait(tk)
+                assert ans.quantities_from_tensor(out) == exp_q
+                for i, m in enumerate(mats or []):
+                    assert_dcsr_equal(m.to_numpy(), exp_mats[i], f"window {i}")
+                    m.free()
+                assert_dcsr_equal(summ.to_numpy(), exp_sum, "sum")
+                assert summ.quantities() == oracle.network_quantities(exp_sum)
+                summ.free()
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("graph", [0, 1])
 def test_graph_replay_follows_each_call(ans, synth, graph):
     """With graph replay, a cached executable graph is reused for batches of
