@@ -387,7 +387,9 @@ int ans_set_tuning(ans_ctx* ctx, const ans_tuning* tuning);
  * with ANS_ERR_OOM only if the default paths do not fit.  The choice is
  * applied to the context and returned in *chosen (optional).  The call
  * blocks until the runs have finished; it leaves per-kernel profiling
- * disabled and its data cleared. */
+ * disabled and its data cleared.  With the environment variable
+ * ANS_AUTOTUNE_LOG set (and not "0"), every trial writes one line to stderr:
+ * its paths and shapes, the batch's device time and the per-kernel times. */
 int ans_autotune(ans_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, const uint64_t* h_offsets,
                  size_t nwin, uint32_t flags, ans_tuning* chosen, void* stream);
 

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -2636,6 +2638,8 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
   // (*out)[kWall].  A trial that cannot get its memory (a path the device
   // cannot hold for this batch) reports false instead of failing.
   const std::string kWall = "(batch)";
+  const char* log_env = std::getenv("ANS_AUTOTUNE_LOG");
+  const bool log_trials = log_env && *log_env && std::strcmp(log_env, "0") != 0;
   auto trial = [&](auto&& set, Prof* out, bool* ran) -> int {
     {
       std::lock_guard<std::mutex> g(c->mu);
@@ -2685,6 +2689,17 @@ int ans_autotune(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const
       cudaEventDestroy(e1);
     }
     (*out)[kWall] = wall;
+    if (log_trials) {
+      std::string line = "ans_autotune: agg_path " + std::to_string(c->agg_path) + " sum_path " +
+                         std::to_string(c->sum_path) + " win_path " + std::to_string(c->win_path) + " key " +
+                         std::to_string(c->cfg_keys.threads) + "," + std::to_string(c->cfg_keys.rank) + "," +
+                         std::to_string(c->cfg_keys.blocks) + " col " + std::to_string(c->cfg_col.threads) + "," +
+                         std::to_string(c->cfg_col.rank) + "," + std::to_string(c->cfg_col.blocks) + ": " +
+                         (rc == ANS_OK ? "batch " + std::to_string(wall) + " ms" : std::string("did not run"));
+      for (const auto& kv : *out)
+        if (kv.first != kWall) line += " " + kv.first + "=" + std::to_string(kv.second / 2);
+      std::fprintf(stderr, "%s\n", line.c_str());
+    }
     if (rc == ANS_ERR_OOM || rc == ANS_ERR_BUDGET) return ANS_OK;
     if (rc == ANS_OK) *ran = true;
     return rc;
