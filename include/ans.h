@@ -237,6 +237,20 @@ int ans_set_wait_limit(ans_ctx* ctx, uint32_t polls);
  * ANS_ERR_BUDGET, ANS_ERR_CUDA. */
 int ans_probe_wait_expiry(ans_ctx* ctx, ans_matrix** out, ans_ticket* ticket, void* stream);
 
+/* Scratch guards, a debug mode standing in for a memory checker (not in the
+ * paper): a context created while the environment variable
+ * ANS_SCRATCH_GUARDS is set (and not "0") places 256 bytes of a fixed pattern
+ * after every region of a batch's scratch layout and of every output block,
+ * writes them before the batch's kernels and compares them after; an
+ * overwritten guard is reported like a failed device check (ans_wait and the
+ * batch's matrices give ANS_ERR_INTERNAL).  ans_probe_guards checks that the
+ * mechanism reports: it fills one guard, overwrites its first word as a write
+ * one word past its region's end would, and checks it, so ans_wait(*ticket)
+ * must return ANS_ERR_INTERNAL; the context stays usable.  It works whether
+ * or not the context has the debug mode.  Errors: ANS_ERR_INVALID_ARG,
+ * ANS_ERR_OOM, ANS_ERR_BUDGET, ANS_ERR_CUDA. */
+int ans_probe_guards(ans_ctx* ctx, ans_ticket* ticket, void* stream);
+
 /* Host-side view of a matrix: counts and device pointers to its arrays
  * (row_ids[nrows], row_ptr[nrows + 1], col_ids[nnz], vals[nnz]).  Blocks
  * until the matrix has been computed.  Any output pointer may be NULL. */

@@ -47,7 +47,7 @@ EXPORTS = (
     "ans_window_quantities_noalloc", "ans_get_tuning", "ans_set_tuning", "ans_autotune", "ans_matrix_retain",
     "ans_ctx_memory", "ans_batch_bytes", "ans_matrix_import", "ans_batch_submit_windows", "ans_combine",
     "ans_set_wait_limit", "ans_probe_wait_expiry", "ans_batch_submit_host", "ans_set_batch_capacity",
-    "ans_matrix_split_rows",
+    "ans_matrix_split_rows", "ans_probe_guards",
 )
 
 # The allocator hook types of ans_ctx_create.
@@ -125,6 +125,7 @@ def load(path: str | os.PathLike | None = None):
                                       P(_u64), _vp], C.c_int),
         "ans_set_wait_limit": ([_vp, C.c_uint32], C.c_int),
         "ans_probe_wait_expiry": ([_vp, P(_vp), P(_u64), _vp], C.c_int),
+        "ans_probe_guards": ([_vp, P(_u64), _vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -538,6 +539,13 @@ class Context:
         _check(self._lib.ans_probe_wait_expiry(self._h, C.byref(m) if want_matrix else None, C.byref(tk),
                                                _vp(_stream(stream))), "probe_wait_expiry", self._h)
         return (Matrix(m.value) if want_matrix else None), int(tk.value)
+
+    def probe_guards(self, stream=None) -> int:
+        """Fill one scratch guard, overwrite it and check it; returns the
+        ticket, on which ans_wait then reports ERR_INTERNAL."""
+        tk = _u64()
+        _check(self._lib.ans_probe_guards(self._h, C.byref(tk), _vp(_stream(stream))), "probe_guards", self._h)
+        return int(tk.value)
 
     def wait_status(self, ticket: int, timeout_s: float = 60.0) -> int:
         """ans_wait's status code (no exception)."""

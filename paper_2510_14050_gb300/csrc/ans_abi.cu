@@ -74,15 +74,44 @@ struct DeviceGuard {
   }
 };
 
+// Scratch guards (debug mode, ANS_SCRATCH_GUARDS): while a GuardSink is in
+// scope on this thread, every Layout region is followed by kGuardBytes whose
+// offset the sink records.
+thread_local std::vector<size_t>* t_guard_sink = nullptr;
+struct GuardSink {
+  std::vector<size_t>* prev;
+  explicit GuardSink(std::vector<size_t>* sink) : prev(t_guard_sink) { t_guard_sink = sink; }
+  ~GuardSink() { t_guard_sink = prev; }
+};
+
 // Two-phase bump layout: add() records sizes, bind() turns offsets into pointers.
 struct Layout {
   size_t size = 0;
   size_t add(size_t bytes) {
     size_t off = size;
     size = align_up(size + std::max<size_t>(bytes, 1));
+    if (t_guard_sink) {
+      t_guard_sink->push_back(size);
+      size += kGuardBytes;
+    }
     return off;
   }
 };
+static_assert(kGuardBytes % kAlign == 0, "guards keep the regions aligned");
+
+// Fill (err == nullptr) or check the guards at these device addresses.
+cudaError_t run_guards(const std::vector<uint64_t>& addrs, uint32_t* err, cudaStream_t st) {
+  GuardList g;
+  for (size_t i = 0; i < addrs.size(); ++i) {
+    g.addr[g.n++] = addrs[i];
+    if (g.n == kGuardsPerLaunch || i + 1 == addrs.size()) {
+      const cudaError_t e = launch_guards(g, err, st);
+      if (e != cudaSuccess) return e;
+      g.n = 0;
+    }
+  }
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -108,6 +137,9 @@ struct ans_ctx {
   // The device error word (bounded waits that gave up set bits here).
   uint32_t* d_err = nullptr;
   void* small_mem = nullptr;
+  // Debug mode (ANS_SCRATCH_GUARDS at creation): guards after every region of
+  // a batch's scratch and of every output block, checked after each batch.
+  bool guards = false;
 
   // Pinned staging ring for plan uploads.
   struct Stage {
@@ -271,6 +303,7 @@ struct Block {
   std::vector<uint64_t> h_hdr;
   std::vector<ans_quantities> h_q;
   uint32_t h_status = 0;
+  std::vector<uint64_t> guards;  // device addresses of its guards (debug mode)
 };
 
 struct ans_matrix {
@@ -428,9 +461,22 @@ struct BlockLayout {
 // and cap stay empty until the block completes).
 int make_block(ans_ctx* c, uint64_t pad, uint32_t nseg, std::vector<uint64_t> base, std::vector<uint64_t> cap,
                cudaStream_t st, Block** out, bool dev_base = false) {
-  BlockLayout bl(pad, nseg, dev_base);
+  std::vector<size_t> goff;
+  const BlockLayout bl = [&] {
+    GuardSink gs(c->guards ? &goff : nullptr);
+    return BlockLayout(pad, nseg, dev_base);
+  }();
   void* mem = nullptr;
   ANS_TRY(dev_alloc(c, bl.total, st, &mem));
+  std::vector<uint64_t> gaddr;
+  for (size_t o : goff) gaddr.push_back((uint64_t)(uintptr_t)mem + o);
+  if (!gaddr.empty()) {
+    const cudaError_t ge = run_guards(gaddr, nullptr, st);
+    if (ge != cudaSuccess) {
+      dev_free(c, mem, bl.total, st);
+      return fail(ANS_ERR_CUDA, std::string("guards: ") + cudaGetErrorString(ge));
+    }
+  }
   Block* b = new Block();
   b->ctx = c;
   b->mem = mem;
@@ -438,6 +484,7 @@ int make_block(ans_ctx* c, uint64_t pad, uint32_t nseg, std::vector<uint64_t> ba
   b->nseg = nseg;
   b->base = std::move(base);
   b->cap = std::move(cap);
+  b->guards = std::move(gaddr);
   char* m = (char*)mem;
   b->col_ids = (uint32_t*)(m + bl.col_ids);
   b->vals = (uint64_t*)(m + bl.vals);
@@ -1370,9 +1417,13 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     plan_tables(lens, &tab_lg, &hp_tab);
   }
 
-  // ---- scratch layout
+  // ---- scratch layout (with guards after every region in debug mode)
   WinLayout wl;
-  wl.reserve(hp, nseg, want_mats, want_sum, hash, regroup);
+  std::vector<size_t> guard_off;
+  {
+    GuardSink gs(c->guards ? &guard_off : nullptr);
+    wl.reserve(hp, nseg, want_mats, want_sum, hash, regroup);
+  }
   const DevPlan& dp = wl.dp;
   const PipeScratch& ps = wl.ps;
   const size_t s_col = wl.s_col, s_vals = wl.s_vals, s_row = wl.s_row, s_rp = wl.s_rp, s_hdr = wl.s_hdr,
@@ -1483,6 +1534,9 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
     if (e == cudaSuccess) return ANS_OK;
     return fail(ANS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
+  std::vector<uint64_t> guard_addr;
+  for (size_t o : guard_off) guard_addr.push_back((uint64_t)(uintptr_t)(m + o));
+  if ((rc = cu(run_guards(guard_addr, nullptr, st), "guards"))) return bail(rc);
   // Empty batch with a time sum: an empty sum matrix.
   if (want_sum && nseg == 0) {
     if ((rc = make_block(c, 0, 1, {0}, {0}, st, &sblk))) return bail(rc);
@@ -1731,6 +1785,11 @@ int run_windows(ans_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, const 
   }
 
   // ---- completion
+  if (c->guards) {  // debug mode: every guard of the scratch and the outputs intact
+    for (const Block* b : {blk, sblk})
+      if (b) guard_addr.insert(guard_addr.end(), b->guards.begin(), b->guards.end());
+    if ((rc = cu(run_guards(guard_addr, c->d_err, st), "guards"))) return bail(rc);
+  }
   if (blk) {
     if ((rc = capture_err(c, blk->status, st))) return bail(rc);
   }
@@ -2012,6 +2071,10 @@ int ans_ctx_create(ans_ctx** out, int device, size_t mem_budget_bytes, ans_alloc
   c->alloc_fn = alloc;
   c->free_fn = free_fn;
   c->user = user;
+  {
+    const char* g = std::getenv("ANS_SCRATCH_GUARDS");
+    c->guards = g && *g && std::strcmp(g, "0") != 0;
+  }
   auto undo = [&](int rc) {
     for (auto& s : c->stage)
       if (s.ev) cudaEventDestroy(s.ev);
@@ -2309,6 +2372,22 @@ int ans_set_wait_limit(ans_ctx* c, uint32_t polls) {
   // the limit is read by kernels: change it only with nothing in flight
   ANS_CUDA(cudaDeviceSynchronize());
   ANS_CUDA(cudaMemcpy(c->d_err + 1, &polls, 4, cudaMemcpyHostToDevice));
+  return ANS_OK;
+}
+
+int ans_probe_guards(ans_ctx* c, ans_ticket* ticket, void* stream) {
+  if (!c || !ticket) return fail(ANS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(c->mu);
+  DeviceGuard dg(c->device);
+  // one 256-byte region of scratch and the guard after it
+  ANS_TRY(ensure_scratch(c, kAlign + kGuardBytes, st));
+  const std::vector<uint64_t> guard{(uint64_t)(uintptr_t)c->scratch + kAlign};
+  ANS_CUDA(run_guards(guard, nullptr, st));
+  ANS_CUDA(launch_guard_probe_write((uint64_t*)(uintptr_t)guard[0], st));
+  ANS_CUDA(run_guards(guard, c->d_err, st));
+  ANS_TRY(new_ticket(c, st, ticket));
+  ANS_TRY(reset_err(c, st));
   return ANS_OK;
 }
 

@@ -45,6 +45,7 @@ enum ErrBits : uint32_t {
   kErrHashFull = 2u,   // a hash probe sequence found no free slot
   kErrNegative = 4u,   // a signed combination left a negative count
   kErrPlan = 8u,       // device-resident batch offsets were invalid or above the capacity
+  kErrGuard = 16u,     // a scratch guard (debug mode) was overwritten
 };
 constexpr uint64_t kMaxWindowItems = (1ull << 31) - 1;  // packets of one window, links of one time sum
 constexpr int kPassStable = 0x100;  // digit-pass flag: pass 0 keeps the input order of equal digits
@@ -452,6 +453,20 @@ struct SmallCopyBatch {
   SmallCopyItem it[kSmallCopyItems];
 };
 cudaError_t launch_small_copy(const SmallCopyBatch& b, cudaStream_t st);
+// Scratch guards (debug mode): kGuardBytes after every region of a guarded
+// layout hold a fixed pattern, written before a batch's kernels and compared
+// after them; launch_guards fills (err == NULL) or checks the guards at the
+// given device addresses (a mismatch sets kErrGuard in err[0]).
+constexpr size_t kGuardBytes = 256;
+constexpr int kGuardsPerLaunch = 64;
+struct GuardList {
+  uint32_t n = 0;
+  uint64_t addr[kGuardsPerLaunch];
+};
+cudaError_t launch_guards(const GuardList& g, uint32_t* err, cudaStream_t st);
+// Overwrites the first word of the guard at `guard`, as a write one word past
+// the end of the region before it would: a later check must report it.
+cudaError_t launch_guard_probe_write(uint64_t* guard, cudaStream_t st);
 // *dst = *src for one device word, by a kernel.
 cudaError_t launch_copy_word(uint32_t* dst, const uint32_t* src, cudaStream_t st);
 // Zero-length segments: row_ptr[0] = 0 and hdr = {0, 0}.

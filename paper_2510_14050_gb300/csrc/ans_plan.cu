@@ -146,6 +146,23 @@ __global__ void __launch_bounds__(256) k_small_copy(SmallCopyBatch b) {
   for (i += threadIdx.x; i < hi; i += blockDim.x) dst[i] = src[i];
 }
 
+// Guard g of the list: one warp, one 64-bit word per lane (kGuardBytes = 32
+// words).  Fill without `err`; with it, compare and report a mismatch.
+__device__ __forceinline__ uint64_t guard_word(uint32_t i) { return 0xA5C3E1F00F1E3C5Aull ^ (0x9E3779B97F4A7C15ull * (i + 1)); }
+static_assert(kGuardBytes == 32 * 8, "a guard is one word per lane of a warp");
+__global__ void __launch_bounds__(32) k_guards(GuardList g, uint32_t* err) {
+  if (blockIdx.x >= g.n) return;
+  uint64_t* w = reinterpret_cast<uint64_t*>(g.addr[blockIdx.x]);
+  const uint32_t lane = threadIdx.x;
+  if (!err) {
+    w[lane] = guard_word(lane);
+  } else if (w[lane] != guard_word(lane)) {
+    atomicOr(err, (uint32_t)kErrGuard);
+  }
+}
+
+__global__ void k_guard_probe_write(uint64_t* guard) { guard[0] = ~guard[0]; }
+
 // One 32-bit word copied on the device (error-word snapshots).
 __global__ void k_copy_word(uint32_t* dst, const uint32_t* src) { *dst = *src; }
 
@@ -158,6 +175,18 @@ cudaError_t launch_small_copy(const SmallCopyBatch& b, cudaStream_t st) {
   for (uint32_t i = 0; i < b.n; ++i) chunks = umax64(chunks, (b.it[i].bytes + kSmallCopyChunk - 1) / kSmallCopyChunk);
   if (chunks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
   k_small_copy<<<dim3((unsigned)chunks, b.n), 256, 0, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guards(const GuardList& g, uint32_t* err, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  if (g.n > kGuardsPerLaunch) return cudaErrorInvalidValue;
+  k_guards<<<g.n, 32, 0, st>>>(g, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guard_probe_write(uint64_t* guard, cudaStream_t st) {
+  k_guard_probe_write<<<1, 1, 0, st>>>(guard);
   return cudaGetLastError();
 }
 
