@@ -673,9 +673,12 @@ def main(argv=None):
         in_place = {"value": replicas.job_rate(job_total * args.steps, ip_t / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 72 * nwin,
                     "how": "ans_batch_submit_host given the pinned host arrays: the kernels read the pairs in place"}
-        e2e = {"value": pipe["value"], "unit": UNIT, "h2d_bytes_per_step": 8 * total,
-               "d2h_bytes_per_step": 72 * nwin, "path": "pipelined", "pipelined": pipe,
-               "in_place": in_place, "staged": staged}
+        # the headline: the fastest of the three ways of feeding host-resident
+        # pairs (pipelining pays off on large batches, reading in place on small ones)
+        ways = {"pipelined": pipe, "in_place": in_place, "staged": staged}
+        best = max(ways, key=lambda k: ways[k]["value"])
+        e2e = {"value": ways[best]["value"], "unit": UNIT, "h2d_bytes_per_step": 8 * total,
+               "d2h_bytes_per_step": 72 * nwin, "path": best, **ways}
 
         # The same through ans_batch_submit_windows: the batch kernels read
         # every window's pairs in place from the pinned host arrays (the
