@@ -109,6 +109,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
     ap.add_argument("--serve-sweep", action="store_true",
                     help="only serving: every rate of 1e3..1e5 windows/s x budgets 32/64/128 GiB, one line each")
+    ap.add_argument("--library-sort", action="store_true",
+                    help="also time a library radix sort (torch.sort: CUB) of the step's packed 64-bit keys")
     return ap.parse_args(argv)
 
 
@@ -584,6 +586,34 @@ def main(argv=None):
                      "bytes_rule": "reads + writes each item needs once per launch of this kernel"}
     kernel_share = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4) for k, v in prof.items()}
 
+    # ---- optional comparator: a library radix sort of the same packed keys
+    # (torch.sort on int64, stable: CUB's radix sort of keys with int64
+    # indices), against the path's own packet sort (eight passes carrying
+    # 16-bit window ids)
+    lib_sort = None
+    if args.library_sort:
+        keys = (src_d.to(torch.int64) & 0xFFFFFFFF) << 32 | (dst_d.to(torch.int64) & 0xFFFFFFFF)
+        keys ^= -(1 << 63)  # unsigned order of src << 32 | dst as signed int64 order
+        for _ in range(2):
+            torch.sort(keys, stable=True)
+        torch.cuda.synchronize()
+        ls_ms = []
+        for i in range(max(1, min(args.steps, 5))):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            torch.sort(keys, stable=True)
+            b.record(stream)
+            b.synchronize()
+            ls_ms.append(a.elapsed_time(b))
+        del keys
+        torch.cuda.empty_cache()
+        own = prof.get("onesweep_pk") or prof.get("onesweep")
+        lib_sort = {"what": "torch.sort(stable=True) of the step's packets as int64 keys (CUB radix sort, "
+                            "keys + int64 indices)", "ms": round(min(ls_ms), 3),
+                    "own_sort_ms": round(own[1] / args.steps, 3) if own else None,
+                    "own_sort": "the path's eight digit passes per step (onesweep_pk or onesweep)"}
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -768,6 +798,7 @@ def main(argv=None):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "ms_per_step_min": round(min(step_ms), 4), "ms_per_step_median": round(statistics.median(step_ms), 4),
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS[cfg], "config": cfg, "windows": nwin, "packets_per_step": total,
                        "per_window_matrices": with_mats,
@@ -785,6 +816,7 @@ def main(argv=None):
                          "unique_destinations": sum_q["unique_destinations"],
                          "window_links": sum(q["unique_links"] for q in quants)},
             "tuning": tuning, "serving": serving, "out_of_core": out_of_core, "clocks": clk, "cpu_baseline": cpu,
+            "library_sort": lib_sort,
             "setup_s": {"generate": round(t_gen, 2), "autotune": round(t_tune, 2)},
         }
         print(json.dumps(line), flush=True)
