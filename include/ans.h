@@ -240,7 +240,7 @@ int ans_probe_wait_expiry(ans_ctx* ctx, ans_matrix** out, ans_ticket* ticket, vo
 /* Scratch guards, a debug mode standing in for a memory checker (not in the
  * paper): a context created while the environment variable
  * ANS_SCRATCH_GUARDS is set (and not "0") places 256 bytes of a fixed pattern
- * after every region of a batch's scratch layout and of every output block,
+ * after every region of a batch's scratch layout and of its output blocks,
  * writes them before the batch's kernels and compares them after; an
  * overwritten guard is reported like a failed device check (ans_wait and the
  * batch's matrices give ANS_ERR_INTERNAL).  ans_probe_guards checks that the

@@ -138,7 +138,7 @@ struct ans_ctx {
   uint32_t* d_err = nullptr;
   void* small_mem = nullptr;
   // Debug mode (ANS_SCRATCH_GUARDS at creation): guards after every region of
-  // a batch's scratch and of every output block, checked after each batch.
+  // a batch's scratch and of its output blocks, checked after each batch.
   bool guards = false;
 
   // Pinned staging ring for plan uploads.

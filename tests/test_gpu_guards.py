@@ -1,8 +1,8 @@
 """Scratch guards: a debug mode standing in for a memory checker.
 
 A context created with ANS_SCRATCH_GUARDS=1 puts 256 bytes of a fixed
-pattern after every region of a batch's scratch layout and of every output
-block, writes them before the batch's kernels and compares them after; an
+pattern after every region of a batch's scratch layout and of its output
+blocks, writes them before the batch's kernels and compares them after; an
 overwritten guard makes the batch report ERR_INTERNAL.
 
 * ans_probe_guards overwrites a guard's first word, as a write one word past
