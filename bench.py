@@ -107,6 +107,10 @@ def parse_args(argv=None):
     ap.add_argument("--serve-rate", type=float, default=1e4, help="serving arrivals, windows/s")
     ap.add_argument("--serve-windows", type=int, default=20000)
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
+    ap.add_argument("--serve-batch-windows", type=int, default=256, help="most windows in one serving batch")
+    ap.add_argument("--serve-batch-packets", type=int, default=1 << 24, help="most packets in one serving batch")
+    ap.add_argument("--serve-no-autotune", action="store_true",
+                    help="serve with the library's default launch shapes and paths")
     ap.add_argument("--serve-sweep", action="store_true",
                     help="only serving: every rate of 1e3..1e5 windows/s x budgets 32/64/128 GiB, one line each")
     ap.add_argument("--library-sort", action="store_true",
@@ -390,7 +394,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(local, rate, n, budget_gib, pool=None, seed=0):
+def serving_tuning(local, pool, nwin=256):
+    """Launch shapes and paths for the server's contexts: the autotuner's
+    choice on a batch of the first `nwin` pool windows with a time sum."""
+    import torch
+
+    from paper_2510_14050_gb300 import ans
+    n = int(pool.offsets[min(nwin, pool.offsets.size - 1)])
+    src = torch.from_numpy(pool.src[:n].view(np.int32)).cuda(local)
+    dst = torch.from_numpy(pool.dst[:n].view(np.int32)).cuda(local)
+    ctx = ans.Context(local)
+    try:
+        return ctx.autotune(src, dst, pool.offsets[: min(nwin, pool.offsets.size - 1) + 1], flags=ans.BATCH_SUM)
+    finally:
+        ctx.close()
+
+
+def run_serving(local, rate, n, budget_gib, pool=None, seed=0, tuning=None, batch_windows=256,
+                batch_packets=1 << 24):
     """Open-loop Poisson arrivals of serving-size windows (P uniform in
     [2^12, 2^17], traffic as the 64-window batch) through the
     continuous-batching server; latency from arrival to quantities on the host,
@@ -398,14 +419,17 @@ def run_serving(local, rate, n, budget_gib, pool=None, seed=0):
     from paper_2510_14050_gb300 import serve
     pool = pool or serve.pool_source(512, seed=seed)
     npool = pool.offsets.size - 1
-    srv = serve.Server(device=local, slots=4, budget_bytes=int(budget_gib * (1 << 30)), max_batch_windows=256,
-                       max_batch_packets=1 << 24, bucket_seconds=(60.0, 3600.0))
+    srv = serve.Server(device=local, slots=4, budget_bytes=int(budget_gib * (1 << 30)),
+                       max_batch_windows=batch_windows, max_batch_packets=batch_packets,
+                       bucket_seconds=(60.0, 3600.0), tuning=tuning)
     try:
         warm_t, warm_o = serve.poisson_schedule(rate, min(n, 200), npool, seed=seed + 1)
         srv.serve(pool, warm_t, warm_o)
         arr, order = serve.poisson_schedule(rate, n, npool, seed=seed)
         st = srv.serve(pool, arr, order)
-        out = {"lambda_windows_per_s": rate, "budget_gib": budget_gib, "slots": 4, **st.summary(),
+        out = {"lambda_windows_per_s": rate, "budget_gib": budget_gib, "slots": 4,
+               "max_batch_windows": batch_windows, "max_batch_packets": batch_packets,
+               "tuned": bool(tuning), **st.summary(),
                "offered_packets_per_s": float(np.diff(pool.offsets)[order].sum() / max(arr[-1], 1e-9))}
     finally:
         srv.close()
@@ -439,11 +463,15 @@ def main(argv=None):
     torch.cuda.set_device(local)
     if args.serve_sweep:
         if rank == 0:
-            pool = None
+            from paper_2510_14050_gb300 import serve
+            pool = serve.pool_source(512, seed=0)
+            tun = None if args.serve_no_autotune else serving_tuning(local, pool)
             for budget in (32.0, 64.0, 128.0):
                 for rate in (1e3, 3e3, 1e4, 3e4, 1e5):
                     n = max(args.serve_windows, int(min(rate * 10.0, 200000)))
-                    res, pool = run_serving(local, rate, n, budget, pool)
+                    res, pool = run_serving(local, rate, n, budget, pool, tuning=tun,
+                                            batch_windows=args.serve_batch_windows,
+                                            batch_packets=args.serve_batch_packets)
                     print(json.dumps({"metric": "serving window latency", "unit": "ms", **res}), flush=True)
         return
     dist = None
@@ -778,7 +806,12 @@ def main(argv=None):
 
     serving = None
     if rank == 0 and not args.no_serve:
-        serving, _ = run_serving(local, args.serve_rate, args.serve_windows, args.serve_budget_gib)
+        from paper_2510_14050_gb300 import serve
+        spool = serve.pool_source(512, seed=0)
+        stun = None if args.serve_no_autotune else serving_tuning(local, spool)
+        serving, _ = run_serving(local, args.serve_rate, args.serve_windows, args.serve_budget_gib, spool,
+                                 tuning=stun, batch_windows=args.serve_batch_windows,
+                                 batch_packets=args.serve_batch_packets)
 
     # ---- out of core: the step's windows streamed from pinned host memory
     out_of_core = None

@@ -203,9 +203,14 @@ int ans_set_batch_capacity(ans_ctx* ctx, uint64_t max_packets);
  * buffers), or in any host memory if the device reads pageable memory
  * (cudaDevAttrPageableMemoryAccess).  srcs, dsts and lens are host arrays of
  * nwin entries, read during the call; the windows' arrays must stay valid
- * until the batch completes.  Every other argument, result and error as
- * ans_batch_submit_host; ANS_ERR_INVALID_ARG also for a window the device cannot
- * read. */
+ * until the batch completes.  On the paths that sort a batch's packets as one
+ * segment (agg_path 2 or 3, sum_path 2) a kernel first gathers every window's
+ * pairs, read in place, into one context-owned device buffer (8 bytes per
+ * packet, kept for later calls and counted against the budget) and the batch
+ * is analysed from there; if that buffer cannot be allocated the windows are
+ * analysed in place on the other paths.  Every other argument, result and
+ * error as ans_batch_submit_host; ANS_ERR_INVALID_ARG also for a window the
+ * device cannot read. */
 int ans_batch_submit_windows(ans_ctx* ctx, const uint32_t* const* srcs, const uint32_t* const* dsts,
                              const uint64_t* lens, size_t nwin, uint32_t flags, ans_quantities* out,
                              ans_matrix** per_window, ans_matrix** sum, ans_ticket* ticket, void* stream);

@@ -200,6 +200,11 @@ struct ans_ctx {
   void* hash_mem = nullptr;
   size_t hash_slots = 0;
   bool hash_dirty = false;
+  // ans_batch_submit_windows on the paths that sort a batch's packets as one
+  // segment: the windows' pairs gathered into one buffer (src words, then
+  // dst words, then the windows' gather table), grown on demand.
+  void* gather_mem = nullptr;
+  size_t gather_bytes = 0;
 
   // Optional per-kernel timing: CUDA events recorded around each launch on
   // the launching stream, accumulated by name when read.
@@ -2131,6 +2136,9 @@ int ans_ctx_destroy(ans_ctx* c) {
     dev_free(c, c->hash_mem, c->hash_slots * 12, c->aux);
     c->hash_mem = nullptr;
     c->hash_slots = 0;
+    dev_free(c, c->gather_mem, c->gather_bytes, c->aux);
+    c->gather_mem = nullptr;
+    c->gather_bytes = 0;
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -2247,6 +2255,49 @@ int ans_batch_submit_windows(ans_ctx* c, const uint32_t* const* srcs, const uint
                                                ": packet arrays in pageable host memory this device cannot read");
         }
       }
+    }
+  }
+  // The paths that sort all of a batch's packets as one segment (the windows
+  // from the packet sort, the time sum by re-sorting the packets, the hashed
+  // statistics) read the packets as one stream: the windows' pairs are first
+  // gathered into one device buffer by a kernel (reading each window in
+  // place), then analysed like contiguous windows.  If that buffer cannot be
+  // had, the windows are analysed in place on the other paths.
+  const uint64_t total = offs[nwin];
+  const bool one_segment = c->agg_path == 2 || c->agg_path == 3 || c->sum_path == 2;
+  bool fits = nwin <= 0xFFFFFFF0ull && !((flags & ANS_BATCH_SUM) && total > kMaxWindow);
+  for (size_t w = 0; w < nwin && fits; ++w) fits = lens[w] <= kMaxWindow;
+  if (one_segment && fits && total > 0) {  // (otherwise run_windows reports what does not fit)
+    const size_t pairs = align_up((size_t)total * 4);
+    const size_t need = 2 * pairs + (size_t)nwin * sizeof(GatherWin);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (need > c->gather_bytes) {
+      const size_t want = std::max(need, c->gather_bytes + c->gather_bytes / 4);
+      dev_free(c, c->gather_mem, c->gather_bytes, st);
+      c->gather_mem = nullptr;
+      c->gather_bytes = 0;
+      void* p = nullptr;
+      int rc = dev_alloc(c, want, st, &p);
+      if (rc == ANS_OK) {
+        c->gather_mem = p;
+        c->gather_bytes = want;
+      } else if (rc != ANS_ERR_OOM && rc != ANS_ERR_BUDGET) {
+        return rc;
+      }
+    }
+    if (c->gather_mem) {
+      char* gm = (char*)c->gather_mem;
+      uint32_t* gsrc = (uint32_t*)gm;
+      uint32_t* gdst = (uint32_t*)(gm + pairs);
+      GatherWin* gw = (GatherWin*)(gm + 2 * pairs);
+      std::vector<GatherWin> table(nwin);
+      for (size_t w = 0; w < nwin; ++w)
+        table[w] = GatherWin{(uint64_t)(uintptr_t)srcs[w], (uint64_t)(uintptr_t)dsts[w], offs[w], lens[w]};
+      UploadSet us;
+      us.add(gw, table.data(), table.size() * sizeof(GatherWin));
+      ANS_TRY(us.flush(c, st));
+      ANS_CUDA(launch_gather_windows(gw, (uint32_t)nwin, gsrc, gdst, st));
+      return run_windows(c, gsrc, gdst, offs.data(), nwin, flags, out, per_window, sum, ticket, st);
     }
   }
   return run_windows(c, nullptr, nullptr, offs.data(), nwin, flags, out, per_window, sum, ticket,

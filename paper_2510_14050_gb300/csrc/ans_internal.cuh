@@ -453,6 +453,14 @@ struct SmallCopyBatch {
   SmallCopyItem it[kSmallCopyItems];
 };
 cudaError_t launch_small_copy(const SmallCopyBatch& b, cudaStream_t st);
+// Windows in their own arrays gathered into one contiguous pair of device
+// arrays: window w's len packets from (src, dst) -- device or page-locked
+// host memory, read in place -- to gsrc/gdst + off.
+struct GatherWin {
+  uint64_t src, dst, off, len;
+};
+cudaError_t launch_gather_windows(const GatherWin* wins, uint32_t nwin, uint32_t* gsrc, uint32_t* gdst,
+                                  cudaStream_t st);
 // Scratch guards (debug mode): kGuardBytes after every region of a guarded
 // layout hold a fixed pattern, written before a batch's kernels and compared
 // after them; launch_guards fills (err == NULL) or checks the guards at the

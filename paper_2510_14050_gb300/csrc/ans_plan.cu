@@ -11,6 +11,8 @@
 // leave at once.  Offsets that decrease, a window of 2^31 packets or more,
 // or a batch above the capacity make every window empty and set kErrPlan in
 // the context's error word; the batch then reports ANS_ERR_INVALID_ARG.
+#include <algorithm>
+
 #include "ans_internal.cuh"
 
 namespace ans {
@@ -163,6 +165,50 @@ __global__ void __launch_bounds__(32) k_guards(GuardList g, uint32_t* err) {
 
 __global__ void k_guard_probe_write(uint64_t* guard) { guard[0] = ~guard[0]; }
 
+// n 32-bit words from src to dst by one CTA: 16-byte vectors when both
+// addresses have the same alignment modulo 16 (after a short head), else
+// words; several loads in flight per thread either way (src may sit across
+// the host link).
+__device__ void copy_words(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint64_t n) {
+  const uint64_t t = threadIdx.x, nt = blockDim.x;
+  uint64_t done = 0;  // words below this are copied by the vector part
+  if (((reinterpret_cast<uintptr_t>(dst) ^ reinterpret_cast<uintptr_t>(src)) & 15u) == 0) {
+    const uint64_t head = umin64(n, ((16u - (reinterpret_cast<uintptr_t>(src) & 15u)) & 15u) / 4u);
+    if (t < head) dst[t] = src[t];
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
+    const uint64_t nv = (n - head) / 4;
+    uint64_t v = t;  // this thread's vectors: t, t + nt, t + 2 nt, ...
+    for (; v + 3 * nt < nv; v += 4 * nt) {
+      uint4 x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[k] = s4[v + k * nt];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d4[v + k * nt] = x[k];
+    }
+    for (; v < nv; v += nt) d4[v] = s4[v];
+    done = head + nv * 4;
+  }
+  uint64_t w = done + t;  // this thread's words: w, w + nt, ...
+  for (; w + 7 * nt < n; w += 8 * nt) {
+    uint32_t x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = src[w + k * nt];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[w + k * nt] = x[k];
+  }
+  for (; w < n; w += nt) dst[w] = src[w];
+}
+
+__global__ void __launch_bounds__(256) k_gather_windows(const GatherWin* __restrict__ wins, uint32_t nwin,
+                                                        uint32_t* __restrict__ gsrc, uint32_t* __restrict__ gdst) {
+  for (uint32_t w = blockIdx.x; w < nwin; w += gridDim.x) {
+    const GatherWin g = wins[w];
+    copy_words(gsrc + g.off, reinterpret_cast<const uint32_t*>(g.src), g.len);
+    copy_words(gdst + g.off, reinterpret_cast<const uint32_t*>(g.dst), g.len);
+  }
+}
+
 // One 32-bit word copied on the device (error-word snapshots).
 __global__ void k_copy_word(uint32_t* dst, const uint32_t* src) { *dst = *src; }
 
@@ -182,6 +228,18 @@ cudaError_t launch_guards(const GuardList& g, uint32_t* err, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
   if (g.n > kGuardsPerLaunch) return cudaErrorInvalidValue;
   k_guards<<<g.n, 32, 0, st>>>(g, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_windows(const GatherWin* wins, uint32_t nwin, uint32_t* gsrc, uint32_t* gdst,
+                                  cudaStream_t st) {
+  if (nwin == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const uint32_t grid = std::min<uint32_t>(nwin, (uint32_t)std::max(sms, 1) * 8u);
+  k_gather_windows<<<grid, 256, 0, st>>>(wins, nwin, gsrc, gdst);
   return cudaGetLastError();
 }
 

@@ -301,7 +301,7 @@ class Server:
     def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int = 64 << 30,
                  max_batch_windows: int = 256, max_batch_packets: int = 1 << 24,
                  bucket_seconds=(60.0, 3600.0), keep_sums: bool = True, zero_copy: bool = True,
-                 sliding=()):
+                 sliding=(), tuning: dict | None = None):
         import torch
         self.torch = torch
         self.device = device
@@ -318,6 +318,8 @@ class Server:
         self.slots = []
         for _ in range(slots):
             ctx = ans.Context(device, budget_bytes=budget_bytes)
+            if tuning:  # launch shapes and paths (ans_set_tuning fields), e.g. from Context.autotune
+                ctx.set_tuning(**tuning)
             st = torch.cuda.Stream(device=device)
             self.slots.append({
                 "ctx": ctx, "stream": st,
@@ -332,6 +334,8 @@ class Server:
         nb = len(self.bucket_seconds)
         slide = {nb + i: max(1, int(round(h / g))) for i, (h, g) in enumerate(self.sliding)}
         self.sums = SumKeeper(device, budget_bytes, slide) if keep_sums else None
+        if self.sums is not None and tuning:
+            self.sums.ctx.set_tuning(**tuning)
 
     def live_bytes(self) -> int:
         """Device bytes held by all of the server's contexts."""

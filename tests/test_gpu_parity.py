@@ -499,6 +499,56 @@ def test_pairs_read_in_place_from_pinned_host_memory(ans, synth, agg_path):
         c.close()
 
 
+@pytest.mark.parametrize("agg_path,sum_path", [(0, 0), (3, 2), (2, 2), (0, 2)])
+def test_windows_in_their_own_arrays(ans, synth, agg_path, sum_path):
+    """ans_batch_submit_windows with every window in its own arrays -- in
+    page-locked host memory at word offsets of every alignment modulo 16, or
+    in device memory -- exact against the oracle on each path; on the paths
+    that sort the batch's packets as one segment a kernel first gathers the
+    windows into one device buffer (the copy's vector and word forms, window
+    lengths around the 1024-word vector chunk and the tile)."""
+    c = ans.Context(0)
+    try:
+        c.set_tuning(agg_path=agg_path, sum_path=sum_path)
+        w = synth.generate(5, sizes=[0, 1, 3, 1023, 1025, 8191, 8193, 40000, 0, 131072], first_window=31)
+        pool_src = torch.from_numpy(np.concatenate([np.arange(64, dtype=np.uint32), w.src]).view(np.int32))
+        pool_dst = torch.from_numpy(np.concatenate([np.arange(64, dtype=np.uint32), w.dst]).view(np.int32))
+        pin_src, pin_dst = pool_src.pin_memory(), pool_dst.pin_memory()
+        dev_src, dev_dst = pool_src.cuda(), pool_dst.cuda()
+        exp_mats, exp_q, exp_sum = oracle.batch(w.src, w.dst, w.offsets)
+        for where in ("pinned", "device"):
+            s_all, d_all = (pin_src, pin_dst) if where == "pinned" else (dev_src, dev_dst)
+            wins = []
+            for i in range(w.nwin):
+                a, b = int(w.offsets[i]), int(w.offsets[i + 1])
+                # window i's copy starts `shift` words further into a shifted copy of the pool
+                shift = i % 4
+                base_s = s_all.data_ptr() + 4 * (64 + a)
+                base_d = d_all.data_ptr() + 4 * (64 + a)
+                if shift:  # the same pairs, read from a copy placed `shift` words later
+                    cs = torch.empty(b - a + shift, dtype=torch.int32)
+                    cd = torch.empty(b - a + shift, dtype=torch.int32)
+                    cs[shift:] = torch.from_numpy(w.src[a:b].view(np.int32))
+                    cd[shift:] = torch.from_numpy(w.dst[a:b].view(np.int32))
+                    cs, cd = (cs.pin_memory(), cd.pin_memory()) if where == "pinned" else (cs.cuda(), cd.cuda())
+                    wins.append((cs, cd))  # keep the copies alive
+                    base_s, base_d = cs.data_ptr() + 4 * shift, cd.data_ptr() + 4 * shift
+                wins.append((base_s, base_d, b - a))
+            triples = [x for x in wins if len(x) == 3]
+            for flags in (ans.BATCH_MATRICES | ans.BATCH_SUM, ans.BATCH_SUM):
+                out = torch.zeros((w.nwin, 9), dtype=torch.int64, device="cuda")
+                mats, summ, tk = c.batch_submit_windows(triples, flags, out=out)
+                c.wait(tk)
+                assert ans.quantities_from_tensor(out) == exp_q, where
+                for i, m in enumerate(mats or []):
+                    assert_dcsr_equal(m.to_numpy(), exp_mats[i], f"{where} window {i}")
+                    m.free()
+                assert_dcsr_equal(summ.to_numpy(), exp_sum, f"{where} sum")
+                summ.free()
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("graph", [0, 1])
 def test_graph_replay_follows_each_call(ans, synth, graph):
     """With graph replay, a cached executable graph is reused for batches of
