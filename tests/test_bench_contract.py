@@ -38,3 +38,23 @@ def test_reference_arm_other_ranks_exit_quietly():
                   env={"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_traffic_record_follows_the_kernels_code(tmp_path, monkeypatch):
+    """The DRAM-traffic figures bench.py reports apply to one build of the
+    kernels: its fingerprint ignores comments and blank lines but changes
+    with any code change."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    csrc = tmp_path / "paper_2510_14050_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "ans_x.cu").write_text("// header\n__global__ void k(int* p) { p[0] = 1; }  // store\n")
+    (csrc / "ans_x.cuh").write_text("#pragma once\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    a = bench.library_fingerprint()
+    (csrc / "ans_x.cu").write_text("/* reworded\n   header */\n\n__global__ void k(int* p) { p[0] = 1; }\n")
+    assert bench.library_fingerprint() == a
+    (csrc / "ans_x.cu").write_text("__global__ void k(int* p) { p[0] = 2; }\n")
+    assert bench.library_fingerprint() != a
+    rec = bench.NCU_TRAFFIC[bench.DEFAULT_CONFIG]
+    assert rec["step"] > 0 and all(v > 0 for v in rec["kernels"].values())
