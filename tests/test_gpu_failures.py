@@ -115,3 +115,64 @@ def test_zero_timeout_wait_on_a_queued_batch(mods):
         assert ctx.wait_status(tk, 1.0) == ans.ERR_INVALID_ARG  # a finished ticket is gone
     finally:
         ctx.close()
+
+
+class _FailOnce:
+    """Allocator hooks over torch's caching allocator whose allocation
+    number `fail_at` (and only that one) returns NULL."""
+
+    def __init__(self, ans, device=0):
+        self.calls = 0
+        self.fail_at = None
+        self.sizes = []
+        self.live = {}
+
+        def _alloc(nbytes, stream, user):
+            self.calls += 1
+            self.sizes.append(int(nbytes))
+            if self.fail_at is not None and self.calls == self.fail_at:
+                return None
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+            self.live[ptr] = int(nbytes)
+            return ptr
+
+        def _free(ptr, stream, user):
+            if ptr:
+                self.live.pop(ptr, None)
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = ans.ALLOC_FN(_alloc)
+        self.free_fn = ans.FREE_FN(_free)
+
+
+def test_windows_gather_falls_back_when_its_buffer_is_refused(mods):
+    """ans_batch_submit_windows on the packet-sort paths gathers the windows
+    into one buffer first; when that buffer's allocation fails, the windows
+    are analysed in place on the other paths -- still exact -- and the next
+    call, allocating again, gathers."""
+    ans, synth = mods
+    alloc = _FailOnce(ans)
+    ctx = ans.Context(0, allocator=alloc)
+    try:
+        ctx.set_tuning(agg_path=3, sum_path=2)
+        w = synth.generate(5, sizes=[3000, 0, 8193, 40000, 1, 20000], first_window=17)
+        pin = (torch.from_numpy(w.src.view(np.int32)).pin_memory(), torch.from_numpy(w.dst.view(np.int32)).pin_memory())
+        wins = [(pin[0][int(a):int(b)], pin[1][int(a):int(b)]) for a, b in zip(w.offsets[:-1], w.offsets[1:])]
+        exp_m, exp_q, exp_s = oracle.batch(w.src, w.dst, w.offsets)
+        gather_bytes = 8 * w.total  # at least: the windows' pairs
+        for attempt in range(2):
+            first = alloc.calls + 1
+            alloc.fail_at = first if attempt == 0 else None  # the call's first allocation: the gather buffer
+            out = torch.zeros((w.nwin, 9), dtype=torch.int64, device="cuda")
+            mats, summ, tk = ctx.batch_submit_windows(wins, ans.BATCH_MATRICES | ans.BATCH_SUM, out=out)
+            ctx.wait(tk)
+            assert alloc.sizes[first - 1] >= gather_bytes  # that first allocation was the gather buffer
+            assert ans.quantities_from_tensor(out) == exp_q
+            for m, e in zip(mats, exp_m):
+                assert all(np.array_equal(a, b) for a, b in zip(m.to_numpy(), e))
+                m.free()
+            assert all(np.array_equal(a, b) for a, b in zip(summ.to_numpy(), exp_s))
+            summ.free()
+    finally:
+        ctx.close()
+    assert not alloc.live

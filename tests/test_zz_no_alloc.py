@@ -14,6 +14,7 @@ pytest collects last so that a run stopping at the first failure has already
 run every other test.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -74,6 +75,9 @@ def test_noalloc_allocates_nothing():
     # the first call looks up the scratch array and loads the kernels
     rc, _, _ = _noalloc(lib, *wins[0], MAX_PACKETS, out=outs[0], status=False)
     assert rc == ans.OK
+    # memory that earlier tests' objects still hold is released first, so that
+    # only this call's behaviour is measured
+    gc.collect()
     torch.cuda.synchronize()
     torch_bytes = torch.cuda.memory_allocated()
     free_before = torch.cuda.mem_get_info()[0]
